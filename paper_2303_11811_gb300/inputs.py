@@ -1,0 +1,188 @@
+"""Seeded synthetic inputs shared by the tests, the bench and both of their legs.
+
+This module holds no arithmetic of the method: it only draws particle
+placements, random perturbations and initial network weights from seeded
+NumPy generators, and names the workloads with their sizes.  Both the CUDA
+path and the oracle receive what it returns as plain arrays.
+
+Workloads (stand-ins for the paper's fluidized bed, Sec. 4.1, whose initial
+particle bed is not public):
+
+* ``sphere32``   32^3 periodic box, one fixed sphere r = 4 at the centre,
+  SRT tau = 0.6, body force 1e-6 in x, 4^3 sub-division sampling, FP64.
+* ``settle128``  128^3 periodic box, 400 spheres r = 6 placed by random
+  sequential addition (surface gap >= 1), density ratio 2.5, gravity 2e-5 in
+  -z, TRT (Lambda = 3/16) tau = 0.55, spring-dashpot DEM (k_n = 1e3, e = 0.9).
+* ``channel``    256x256x512 channel, walls at the x faces, periodic y/z,
+  12,816 fixed spheres r = 5 at solid fraction 0.20, TRT tau = 0.55, body
+  force 1e-5 along z.
+* ``settle512``  512x512x1024 periodic box, polydisperse spheres r in [3, 6]
+  at solid fraction 0.15, settling under gravity 2e-5, density ratio 2.5.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+DEFAULT_SEED = 20230321
+
+
+@dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    tau: float
+    relax: str                     # "srt" | "trt"
+    walls: tuple = (0, 0, 0, 0, 0, 0)
+    fbody: tuple = (0.0, 0.0, 0.0)
+    gravity: tuple = (0.0, 0.0, 0.0)
+    weighting: str = "nt"          # "eps" | "nt"
+    eps_mode: str = "supersample"  # "supersample" | "linear" | "mlp"
+    eps_n: int = 4
+    kn: float = 1e3
+    restitution: float = 0.9
+    subcycles: int = 10
+    dem: bool = False
+    density: float = 2.5
+    steps: int = 1000
+    particles: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def rsa_spheres(dims, walls, radii, gap, seed, max_tries=200):
+    """Random sequential addition of non-overlapping spheres.
+
+    ``radii`` is the list of radii in placement order; each sphere is drawn
+    uniformly in the box (kept r away from wall faces) and accepted when its
+    surface is at least ``gap`` from every sphere already placed (nearest image
+    along periodic axes).  Returns centres (n x 3).
+    """
+    rng = np.random.default_rng(seed)
+    dims = np.asarray(dims, dtype=np.float64)
+    per = np.array([not walls[0], not walls[2], not walls[4]])
+    radii = np.asarray(radii, dtype=np.float64)
+    rmax = float(radii.max()) if radii.size else 1.0
+    h = 2.0 * rmax + gap
+    ncell = np.maximum(1, np.floor(dims / h).astype(int))
+    csize = dims / ncell
+    grid: dict = {}
+    out = np.zeros((radii.size, 3))
+    for i, r in enumerate(radii):
+        lo = np.where(per, 0.0, r)
+        hi = np.where(per, dims, dims - r)
+        for _ in range(max_tries):
+            p = lo + (hi - lo) * rng.random(3)
+            c = np.minimum((p // csize).astype(int), ncell - 1)
+            ok = True
+            for dz in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        k = c + (dx, dy, dz)
+                        if np.any((~per) & ((k < 0) | (k >= ncell))):
+                            continue
+                        k = tuple(np.mod(k, ncell))
+                        for j in grid.get(k, ()):
+                            d = p - out[j]
+                            d = np.where(per & (d > 0.5 * dims), d - dims, d)
+                            d = np.where(per & (d < -0.5 * dims), d + dims, d)
+                            if d @ d < (r + radii[j] + gap) ** 2:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                out[i] = p
+                grid.setdefault(tuple(c), []).append(i)
+                break
+        else:
+            raise RuntimeError(f"random sequential addition stalled at sphere {i}")
+    return out
+
+
+def sphere32() -> Workload:
+    w = Workload("sphere32", 32, 32, 32, tau=0.6, relax="srt", fbody=(1e-6, 0.0, 0.0),
+                 weighting="nt", eps_mode="supersample", eps_n=4, steps=1000)
+    w.particles = dict(x=np.array([[16.0, 16.0, 16.0]]), r=np.array([4.0]),
+                       density=np.array([1.0]), fixed=np.array([1], np.uint8))
+    return w
+
+
+def settle128(n=128, count=400, radius=6.0, seed=DEFAULT_SEED) -> Workload:
+    w = Workload("settle128", n, n, n, tau=0.55, relax="trt", gravity=(0.0, 0.0, -2e-5),
+                 weighting="nt", eps_mode="supersample", eps_n=4, dem=True,
+                 density=2.5, steps=2000)
+    r = np.full(count, radius)
+    x = rsa_spheres((n, n, n), w.walls, r, 1.0, seed)
+    w.particles = dict(x=x, r=r, density=np.full(count, 2.5),
+                       fixed=np.zeros(count, np.uint8))
+    return w
+
+
+def channel(nx=256, ny=256, nz=512, phi=0.20, radius=5.0, seed=DEFAULT_SEED,
+            eps_mode="supersample", eps_n=4) -> Workload:
+    w = Workload("channel", nx, ny, nz, tau=0.55, relax="trt", walls=(1, 1, 0, 0, 0, 0),
+                 fbody=(0.0, 0.0, 1e-5), weighting="nt", eps_mode=eps_mode, eps_n=eps_n,
+                 dem=False, steps=5000)
+    count = int(round(phi * nx * ny * nz / (4.0 / 3.0 * math.pi * radius ** 3)))
+    r = np.full(count, radius)
+    x = rsa_spheres((nx, ny, nz), w.walls, r, 1.0, seed)
+    w.particles = dict(x=x, r=r, density=np.full(count, 2.5),
+                       fixed=np.ones(count, np.uint8))
+    return w
+
+
+def settle512(nx=512, ny=512, nz=1024, phi=0.15, rmin=3.0, rmax=6.0,
+              seed=DEFAULT_SEED) -> Workload:
+    w = Workload("settle512", nx, ny, nz, tau=0.55, relax="trt", gravity=(0.0, 0.0, -2e-5),
+                 weighting="nt", eps_mode="supersample", eps_n=4, dem=True, steps=1000)
+    rng = np.random.default_rng(seed + 1)
+    target = phi * nx * ny * nz
+    radii = []
+    vol = 0.0
+    while vol < target:
+        r = rmin + (rmax - rmin) * rng.random()
+        radii.append(r)
+        vol += 4.0 / 3.0 * math.pi * r ** 3
+    r = np.array(radii)
+    x = rsa_spheres((nx, ny, nz), w.walls, r, 1.0, seed)
+    w.particles = dict(x=x, r=r, density=np.full(r.size, 2.5),
+                       fixed=np.zeros(r.size, np.uint8))
+    return w
+
+
+def noise(shape, scale, seed):
+    """Uniform noise in [-scale, scale) of the given shape."""
+    rng = np.random.default_rng(seed)
+    return scale * (2.0 * rng.random(shape) - 1.0)
+
+
+def random_velocities(n, scale, seed):
+    rng = np.random.default_rng(seed)
+    return scale * (2.0 * rng.random((n, 3)) - 1.0)
+
+
+def mlp_init(seed):
+    """He-uniform initial weights for the 4-32-32-1 network (FP64 arrays)."""
+    rng = np.random.default_rng(seed)
+
+    def lin(fan_out, fan_in):
+        b = math.sqrt(6.0 / fan_in)
+        return rng.uniform(-b, b, (fan_out, fan_in)), np.zeros(fan_out)
+
+    W1, b1 = lin(32, 4)
+    W2, b2 = lin(32, 32)
+    W3, b3 = lin(1, 32)
+    b1 += 0.01
+    b2 += 0.01
+    return [W1, b1, W2, b2, W3, b3]
