@@ -1,0 +1,215 @@
+/*
+ * psm.h -- C ABI of the GB300 LBM-PSM engine (fully resolved fluid-particle
+ * coupling with the Partially Saturated Cells Method).
+ *
+ * The engine computes, per time step, the hot path of Kemmler et al.,
+ * "Efficiency and scalability of fully-resolved fluid-particle simulations on
+ * heterogeneous CPU-GPU architectures":
+ *   (a) particle mapping: per-cell solid fraction B_i of spherical particles
+ *       (Sec. 2.3.2: linear approximation, Eqs. 25-27; sub-division sampling;
+ *       or a learned surrogate with a sampling fallback),
+ *   (b) the PSM collision (Sec. 2.3, Eqs. 17-19) blending the SRT (Eq. 3) or
+ *       TRT fluid relaxation with the solid operator, driven by the particle
+ *       surface velocity of Eq. 20, fused with D3Q19 streaming (Eq. 2) and the
+ *       forcing operator (Eq. 8),
+ *   (c) the per-particle reduction of hydrodynamic force and torque
+ *       (Eqs. 21-22),
+ * followed by the DEM sub-cycles of Sec. 2.2 (linear spring-dashpot, Eq. 12;
+ * velocity Verlet, Eqs. 15-16) on the device, so particle state stays in GPU
+ * memory between steps.
+ *
+ * Conventions
+ *  - Units are lattice units (dx = dt = 1, rho_0 = 1).  Cell (x,y,z) has its
+ *    centre at (x+1/2, y+1/2, z+1/2); the domain is [0,nx)x[0,ny)x[0,nz).
+ *  - D3Q19 ordering: q = 0 rest; q = 1..18 in opposite pairs (q, q+1) for odd
+ *    q, with c_1 = (1,0,0), c_3 = (0,1,0), c_5 = (0,0,1), c_7 = (1,1,0),
+ *    c_9 = (1,-1,0), c_11 = (1,0,1), c_13 = (1,0,-1), c_15 = (0,1,1),
+ *    c_17 = (0,1,-1) and c_{q+1} = -c_q.
+ *  - Host arrays of PDFs are f[q][z][y][x] (x fastest, nx*ny*nz cells per q);
+ *    vector fields are component-major u[a][z][y][x]; particle vectors are
+ *    n x 3 row-major.
+ *  - Every pointer argument of the functions below is a HOST pointer owned by
+ *    the caller; every call copies.  The context owns all device memory,
+ *    allocated through psm_options.alloc (cudaMalloc when NULL).
+ *  - All device work is queued on psm_options.stream (a cudaStream_t; NULL is
+ *    the legacy default stream).  Functions that return data synchronise that
+ *    stream only.
+ *  - Every function returns a status and never aborts.  Errors detected on
+ *    the device (slot overflow, non-finite force) are returned by the next
+ *    psm_step / psm_get_* call; the context then refuses further steps with
+ *    PSM_ERR_STATE until psm_set_pdfs or psm_set_particles is called.
+ *  - A context must not be used from two host threads at once.
+ */
+#ifndef PSM_H
+#define PSM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct psm_ctx psm_ctx;
+
+typedef enum {
+  PSM_OK = 0,
+  PSM_ERR_ARG = 1,           /* invalid argument; nothing was changed */
+  PSM_ERR_CUDA = 2,          /* a CUDA call failed; see psm_last_error */
+  PSM_ERR_OOM = 3,           /* the allocator returned NULL */
+  PSM_ERR_SLOT_OVERFLOW = 4, /* a cell lies within reach of > 2 particles */
+  PSM_ERR_NONFINITE = 5,     /* a hydrodynamic force or a check sum is NaN/Inf */
+  PSM_ERR_TIMEOUT = 6,       /* reserved: a bounded device wait gave up */
+  PSM_ERR_STATE = 7          /* call not allowed in the current state */
+} psm_status;
+
+/* Domain: nx, ny, nz cells.  wall[f] = 1 puts a stationary halfway
+ * bounce-back wall on face f (order -x,+x,-y,+y,-z,+z; the walls sit on the
+ * domain faces, all cells are fluid cells); 0 makes that axis periodic.  Both
+ * faces of an axis must agree. */
+typedef struct {
+  int nx, ny, nz;
+  int wall[6];
+} psm_grid;
+
+typedef enum { PSM_SRT = 0, PSM_TRT = 1 } psm_relax;
+
+enum { PSM_FP64 = 0,       /* PDFs stored and collided in FP64 */
+       PSM_FP32_DEV = 1 }; /* PDFs stored as FP32 deviations f_q - w_q,
+                              collided in FP32; forces and checks in FP64 */
+enum { PSM_PULL = 0,       /* two buffers, pull streaming */
+       PSM_AA = 1 };       /* one buffer, AA-pattern in-place streaming */
+enum { PSM_EPS_SUPERSAMPLE = 0, /* eps from eps_n^3 sub-cell sample points */
+       PSM_EPS_LINEAR = 1,      /* linear approximation, Eqs. 25-27 */
+       PSM_EPS_MLP = 2 };       /* learned surrogate; 8^3 sampling for cells
+                                   within reach of two particles or next to a
+                                   wall face */
+enum { PSM_W_EPS = 0,      /* B = eps (Sec. 2.3) */
+       PSM_W_NT = 1 };     /* B = eps (tau-1/2) / ((1-eps) + (tau-1/2)),
+                              Noble and Torczynski (cited in Sec. 2.3) */
+
+typedef struct {
+  double magic;          /* TRT magic parameter Lambda (default 3/16) */
+  int precision;         /* PSM_FP64 | PSM_FP32_DEV */
+  int streaming;         /* PSM_PULL | PSM_AA */
+  int eps_mode;          /* PSM_EPS_* */
+  int eps_n;             /* samples per axis for PSM_EPS_SUPERSAMPLE (1..16) */
+  int weighting;         /* PSM_W_EPS | PSM_W_NT */
+  double body_force[3];  /* fluid body-force density f_ext */
+  double gravity[3];     /* acceleration of free particles; a free particle
+                            feels (m - V) g and the fluid a uniform counter
+                            force so that a periodic box gains no momentum */
+  double k_n;            /* normal contact stiffness (Eq. 12) */
+  double restitution;    /* normal restitution coefficient, (0, 1] */
+  int dem_subcycles;     /* DEM sub-steps per LBM step (default 10) */
+  int dem;               /* 1: integrate free particles on the device */
+  int deterministic;     /* 1: fixed-order force/torque reduction (bitwise
+                            reproducible); 0: fused atomic reduction */
+  int use_graphs;        /* 1: replay captured CUDA graphs for steps */
+  void* stream;          /* cudaStream_t to queue all work on */
+  void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL */
+  void (*free)(void* ptr, void* user);      /* matching release or NULL */
+  void* alloc_user;                         /* passed to alloc/free */
+} psm_options;
+
+/* Fills *o with the defaults: Lambda = 3/16, FP64, pull, 4^3 sampling, NT
+ * weighting, no forces, k_n = 1e3, e = 0.9, 10 sub-cycles, DEM on,
+ * deterministic reduction, graphs on, default stream, cudaMalloc. */
+void psm_default_options(psm_options* o);
+
+/* Creates a context for the grid, relaxation time tau (> 1/2; tau_plus for
+ * TRT) and relaxation model.  The fluid starts at rest, f_q = w_q.  On success
+ * *out receives the context; on failure *out is NULL. */
+psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax,
+                      const psm_options* opt, psm_ctx** out);
+
+/* Replaces the particle set: n spheres with centres x (n*3), radii r,
+ * velocities u (n*3), angular velocities omega (n*3), density ratios
+ * density (particle/fluid), and fixed[i] != 0 for particles that never move
+ * (fixed may be NULL: all free).  Positions along periodic axes are wrapped
+ * into the box.  A particle must fit twice across a periodic box
+ * (2 r + 3 <= n along that axis).  The next step re-maps the particles. */
+psm_status psm_set_particles(psm_ctx* ctx, int n, const double* x, const double* r,
+                             const double* u, const double* omega,
+                             const double* density, const unsigned char* fixed);
+
+/* Advances nsteps time steps: mapping (when particles moved or were set),
+ * PSM stream-collide, force/torque reduction, DEM sub-cycles. */
+psm_status psm_step(psm_ctx* ctx, int nsteps);
+
+/* Hydrodynamic force and torque of Eqs. 21-22 from the last step (n*3 each). */
+psm_status psm_get_force_torque(psm_ctx* ctx, double* F, double* T);
+
+/* rho (N) and U (3*N, component-major) of the streamed PDFs: Eqs. 6-7 with
+ * the fluid force density of the last step. */
+psm_status psm_get_macroscopic(psm_ctx* ctx, double* rho, double* u);
+
+/* Current particle centres, velocities and angular velocities (n*3 each). */
+psm_status psm_get_particles(psm_ctx* ctx, double* x, double* u, double* omega);
+
+/* The post-collision PDFs f~ of the last step (before streaming), 19*N FP64,
+ * in the canonical layout above, whatever the storage precision/pattern. */
+psm_status psm_get_pdfs(psm_ctx* ctx, double* f);
+
+/* Replaces the PDF field (canonical layout, 19*N FP64) and clears a device
+ * error state. */
+psm_status psm_set_pdfs(psm_ctx* ctx, const double* f);
+
+/* Mapping of the current particles as dense per-cell slots (N each): slot 0
+ * holds the lower particle index; pid = -1 marks an empty slot; B is the
+ * weight after the B > 1 normalisation of Sec. 2.3.  Maps first if needed. */
+psm_status psm_get_slots(psm_ctx* ctx, int* pid0, double* B0, int* pid1, double* B1);
+
+/* FP64 sums over the stored PDFs: mass sum_x sum_q f_q and momentum
+ * sum_x sum_q f_q c_q (3 values); fixed summation order. */
+psm_status psm_check(psm_ctx* ctx, double* mass, double* momentum);
+
+/* Surrogate network for PSM_EPS_MLP: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1 with
+ * inputs (d/r, r), d the offset of the cell centre from the sphere centre.
+ * params is the packed FP32 vector [W1 (32x4), b1 (32), W2 (32x32), b2 (32),
+ * W3 (32), b3 (1)], row-major, PSM_MLP_PARAMS floats.  Inference uses BF16
+ * copies of the weights on the tensor cores with FP32 accumulation. */
+#define PSM_MLP_PARAMS 1249
+psm_status psm_set_mlp(psm_ctx* ctx, const float* params);
+psm_status psm_get_mlp(psm_ctx* ctx, float* params);
+
+/* Trains the surrogate on the device with the engine's own forward/backward
+ * and Adam kernels: nsamples samples of the SplitMix64 training recipe
+ * (stream seed), labelled by 8^3 sub-division sampling, minibatches of batch
+ * samples, epochs passes, learning rate lr.  Starts from the current
+ * parameters.  loss_out (may be NULL) receives the mean squared error of the
+ * last epoch. */
+psm_status psm_train_surrogate(psm_ctx* ctx, long nsamples, unsigned long long seed,
+                               int epochs, int batch, float lr, float* loss_out);
+
+/* Kernel-level entry points of the surrogate (used to check them):
+ * training samples i = first .. first+count-1 of stream seed: inputs X
+ * (count*4) and labels eps (count); loss and gradient (PSM_MLP_PARAMS floats)
+ * of the mean squared error of params on (X, t); eps of the BF16 inference
+ * kernel for inputs X, clamped to [0, 1]. */
+psm_status psm_mlp_samples(psm_ctx* ctx, unsigned long long seed, long first, long count,
+                           float* X, float* eps);
+psm_status psm_mlp_loss_grad(psm_ctx* ctx, const float* params, long m, const float* X,
+                             const float* t, float* loss, float* grad);
+psm_status psm_mlp_infer(psm_ctx* ctx, const float* params, long m, const float* X,
+                         float* eps);
+
+/* Event timings (ms) of the kernel classes over the last psm_step call:
+ * out[0] mapping, out[1] PSM stream-collide, out[2] force/torque reduction,
+ * out[3] DEM; requires timing = 1. */
+psm_status psm_set_timing(psm_ctx* ctx, int enable);
+psm_status psm_get_timings(psm_ctx* ctx, double* out4);
+
+/* Kernel launches queued by the last psm_step call (all of this library's
+ * kernels, graph nodes included). */
+long psm_last_launch_count(const psm_ctx* ctx);
+
+/* Human-readable description of the last error of ctx (never NULL). */
+const char* psm_last_error(const psm_ctx* ctx);
+
+/* Releases every device buffer of ctx through the free callback. */
+void psm_destroy(psm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

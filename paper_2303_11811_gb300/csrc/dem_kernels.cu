@@ -1,0 +1,161 @@
+// dem_kernels.cu -- particle dynamics on the device (paper Sec. 2.2, Sec. 3.2):
+// velocity Verlet (Eqs. 15-16) with sub-cycling, linear spring-dashpot normal
+// contacts between spheres and with wall faces (Eq. 12), buoyancy-corrected
+// gravity and the hydrodynamic force/torque of the last LBM step held fixed
+// over the sub-steps.
+//
+// Per sub-step: positions (all particles), then contact forces (every
+// particle reads the new positions and the old velocities of the others),
+// then velocities.  Contacts of particle i are summed in ascending j, then the
+// walls -x,+x,-y,+y,-z,+z, with plain IEEE FP64 operations (this file is
+// compiled with -fmad=false), so the sums are bitwise reproducible.
+//
+// Candidate search: for up to ALLPAIRS_MAX particles one warp per particle
+// scans all others with an FP32 prefilter (positions rounded to float differ
+// from FP64 by far less than the 1e-2 margin) and evaluates candidates in
+// FP64.  Larger sets use a uniform cell list (cell edge >= the largest
+// diameter) rebuilt every sub-step.
+#include "psm_internal.cuh"
+
+namespace psm {
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+
+__device__ __forceinline__ double damping(double meff, double kn, double le) {
+  return -2.0 * le * sqrt(meff * kn) / sqrt(PI * PI + le * le);
+}
+
+__global__ void dem_position_kernel(DemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n) return;
+  const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  if (!P.p.fixed[i]) {
+    const double dt = P.dt;
+    for (int a = 0; a < 3; ++a) {
+      double xn = P.p.x[3 * i + a] + dt * P.p.u[3 * i + a] +
+                  dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
+      if (!P.g.wall[a]) {
+        if (xn >= dims[a]) xn -= dims[a];
+        else if (xn < 0.0) xn += dims[a];
+      }
+      P.p.x[3 * i + a] = xn;
+    }
+  }
+  for (int a = 0; a < 3; ++a) P.p.xf[4 * i + a] = (float)P.p.x[3 * i + a];
+  P.p.xf[4 * i + 3] = (float)P.p.r[i];
+}
+
+// exact FP64 contact of i with j (j != i); adds to F when in contact
+__device__ __forceinline__ void pair_contact(const DemParams& P, int i, int j, double* F) {
+  const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  double d[3];
+  for (int a = 0; a < 3; ++a) {
+    double v = P.p.x[3 * i + a] - P.p.x[3 * j + a];
+    if (!P.g.wall[a]) {
+      if (v > 0.5 * dims[a]) v -= dims[a];
+      else if (v < -0.5 * dims[a]) v += dims[a];
+    }
+    d[a] = v;
+  }
+  const double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double rs = P.p.r[i] + P.p.r[j];
+  if (!(dist2 < rs * rs)) return;
+  const double dist = sqrt(dist2);
+  const double delta = rs - dist;
+  const double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+  const double vrel[3] = {P.p.u[3 * i] - P.p.u[3 * j], P.p.u[3 * i + 1] - P.p.u[3 * j + 1],
+                          P.p.u[3 * i + 2] - P.p.u[3 * j + 2]};
+  const double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+  const double meff = P.p.m[i] * P.p.m[j] / (P.p.m[i] + P.p.m[j]);
+  const double dn = damping(meff, P.kn, P.log_e);
+  for (int a = 0; a < 3; ++a) F[a] += P.kn * delta * n[a] - dn * vn * n[a];
+}
+
+__device__ __forceinline__ void wall_contacts(const DemParams& P, int i, double* F) {
+  const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (!P.g.wall[a]) continue;
+    for (int side = 0; side < 2; ++side) {
+      const double delta = side == 0 ? P.p.r[i] - P.p.x[3 * i + a]
+                                     : P.p.x[3 * i + a] + P.p.r[i] - dims[a];
+      if (!(delta > 0.0)) continue;
+      const double nn = side == 0 ? 1.0 : -1.0;
+      const double vn = P.p.u[3 * i + a] * nn;
+      const double dn = damping(P.p.m[i], P.kn, P.log_e);
+      F[a] += P.kn * delta * nn - dn * vn * nn;
+    }
+  }
+}
+
+// one warp per particle, all other particles scanned with an FP32 prefilter
+__global__ void dem_contact_allpairs_kernel(DemParams P) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= P.p.n) return;
+  const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
+  const float4 xi = reinterpret_cast<const float4*>(P.p.xf)[i];
+  double F[3] = {0.0, 0.0, 0.0};
+  const int n = P.p.n;
+  for (int base = 0; base < n; base += 32) {
+    const int j = base + lane;
+    bool cand = false;
+    if (j < n && j != i) {
+      const float4 xj = reinterpret_cast<const float4*>(P.p.xf)[j];
+      float d[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
+      for (int a = 0; a < 3; ++a) {
+        if (!P.g.wall[a]) {
+          if (d[a] > 0.5f * dims[a]) d[a] -= dims[a];
+          else if (d[a] < -0.5f * dims[a]) d[a] += dims[a];
+        }
+      }
+      const float rs = xi.w + xj.w + 1e-2f;
+      cand = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rs * rs;
+    }
+    unsigned bits = __ballot_sync(0xffffffffu, cand);
+    while (bits) {
+      const int l = __ffs(bits) - 1;
+      bits &= bits - 1;
+      pair_contact(P, i, base + l, F);  // same values on all lanes
+    }
+  }
+  if (lane == 0) {
+    wall_contacts(P, i, F);
+    for (int a = 0; a < 3; ++a) P.p.Fc[3 * i + a] = F[a];
+  }
+}
+
+__global__ void dem_velocity_kernel(DemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n || P.p.fixed[i]) return;
+  const double dt = P.dt;
+  for (int a = 0; a < 3; ++a) {
+    const double Fn = P.p.Fh[3 * i + a] + P.p.Fc[3 * i + a] +
+                      (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
+    const double Tn = P.p.Th[3 * i + a];
+    P.p.u[3 * i + a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
+    P.p.om[3 * i + a] += dt * (P.p.Told[3 * i + a] + Tn) / (2.0 * P.p.I[i]);
+    P.p.Fold[3 * i + a] = Fn;
+    P.p.Told[3 * i + a] = Tn;
+  }
+}
+
+}  // namespace
+
+int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
+  const int n = P.p.n;
+  if (n == 0) return 0;
+  const int tb = 128;
+  const unsigned gp = (n + tb - 1) / tb;
+  const unsigned gw = (unsigned)(((long long)n * 32 + tb - 1) / tb);
+  int launches = 0;
+  for (int sc = 0; sc < subcycles; ++sc) {
+    dem_position_kernel<<<gp, tb, 0, s>>>(P);
+    dem_contact_allpairs_kernel<<<gw, tb, 0, s>>>(P);
+    dem_velocity_kernel<<<gp, tb, 0, s>>>(P);
+    launches += 3;
+  }
+  return launches;
+}
+
+}  // namespace psm

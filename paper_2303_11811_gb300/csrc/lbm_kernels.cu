@@ -1,0 +1,582 @@
+// lbm_kernels.cu -- D3Q19 stream + PSM collide (paper Sec. 2.1 and 2.3), one
+// thread per cell, one warp per 32 cells of an x-row and per coverage word.
+//
+// The collision is written in deviation form, delta_q = f_q - w_q, and in
+// opposite pairs (q, qbar) = (2k+1, 2k+2) with velocity +-c_k:
+//   s_k = delta_q + delta_qbar, a_k = delta_q - delta_qbar,
+//   rho - 1 = delta_0 + sum_k s_k,  j = sum_k a_k c_k,  U = j + f_ext/2 (Eq. 7)
+// The equilibrium of Eq. 5 splits into a symmetric part
+//   E_s,k = w_k (rho - 1 - 3/2 U.U + 9/2 (c_k.U)^2)  and antisymmetric part
+//   E_a,k = 3 w_k c_k.U.
+// TRT relaxes (s_k/2 - E_s,k) with omega+ and (a_k/2 - E_a,k) with omega-;
+// SRT (Eq. 3) is the case omega- = omega+.  The forcing term of Eq. 8 carries
+// the Guo prefactor (1 - omega/2) per part.  PSM (Eq. 17): the fluid change is
+// weighted by (1 - B) and each particle i adds B_i C^s_i (Eq. 19), whose
+// symmetric part per pair is E_s(U_p) - E_s(U_f) and antisymmetric part
+// E_a(U_f) + E_a(U_p) - a_k; its momentum gives the force of Eq. 21.
+#include "psm_internal.cuh"
+
+namespace psm {
+namespace {
+
+__host__ __device__ constexpr int ckx(int k) {
+  return (k == 0 || k == 3 || k == 4 || k == 5 || k == 6) ? 1 : 0;
+}
+__host__ __device__ constexpr int cky(int k) {
+  return (k == 1 || k == 3 || k == 7 || k == 8) ? 1 : (k == 4 ? -1 : 0);
+}
+__host__ __device__ constexpr int ckz(int k) {
+  return (k == 2 || k == 5 || k == 7) ? 1 : ((k == 6 || k == 8) ? -1 : 0);
+}
+template <typename T>
+__host__ __device__ constexpr T wk(int k) {
+  return k < 3 ? T(1.0 / 18.0) : T(1.0 / 36.0);
+}
+template <typename T>
+__host__ __device__ constexpr T w0() {
+  return T(1.0 / 3.0);
+}
+
+// lattice weight of direction q in the canonical ordering
+__host__ __device__ inline double wq(int q) {
+  return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// neighbours of one cell with periodic wrap and wall validity
+struct Nbr {
+  int X[3], Y[3], Z[3];
+  bool VX[3], VY[3], VZ[3];
+  __device__ void init(int x, int y, int z, int nx, int ny, int nz, int pitch_x,
+                       const int* wall) {
+    X[1] = x;
+    X[0] = x == 0 ? nx - 1 : x - 1;
+    X[2] = x == nx - 1 ? 0 : x + 1;
+    VX[1] = true;
+    VX[0] = !(wall[0] && x == 0);
+    VX[2] = !(wall[0] && x == nx - 1);
+    int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    Y[0] = ym * pitch_x;
+    Y[1] = y * pitch_x;
+    Y[2] = yp * pitch_x;
+    VY[1] = true;
+    VY[0] = !(wall[1] && y == 0);
+    VY[2] = !(wall[1] && y == ny - 1);
+    int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    int plane = pitch_x * ny;
+    Z[0] = zm * plane;
+    Z[1] = z * plane;
+    Z[2] = zp * plane;
+    VZ[1] = true;
+    VZ[0] = !(wall[2] && z == 0);
+    VZ[2] = !(wall[2] && z == nz - 1);
+  }
+  __device__ __forceinline__ int idx(int ox, int oy, int oz) const {
+    return X[ox + 1] + Y[oy + 1] + Z[oz + 1];
+  }
+  __device__ __forceinline__ bool ok(int ox, int oy, int oz) const {
+    return VX[ox + 1] && VY[oy + 1] && VZ[oz + 1];
+  }
+};
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld(const T* p) {
+  return __ldg(p);
+}
+
+template <typename T>
+struct Coef {
+  T ffx, ffy, ffz, Gs[9], Fa[9], H0, H1, H2;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_coef(const StepConst* sc, Coef<T>& c);
+template <>
+__device__ __forceinline__ void load_coef<double>(const StepConst* sc, Coef<double>& c) {
+  c.ffx = __ldg(&sc->fext[0]);
+  c.ffy = __ldg(&sc->fext[1]);
+  c.ffz = __ldg(&sc->fext[2]);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    c.Gs[k] = __ldg(&sc->Gs[k]);
+    c.Fa[k] = __ldg(&sc->Fa[k]);
+  }
+  c.H0 = __ldg(&sc->H[0]);
+  c.H1 = __ldg(&sc->H[1]);
+  c.H2 = __ldg(&sc->H[2]);
+}
+template <>
+__device__ __forceinline__ void load_coef<float>(const StepConst* sc, Coef<float>& c) {
+  c.ffx = __ldg(&sc->ffext[0]);
+  c.ffy = __ldg(&sc->ffext[1]);
+  c.ffz = __ldg(&sc->ffext[2]);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    c.Gs[k] = __ldg(&sc->fGs[k]);
+    c.Fa[k] = __ldg(&sc->fFa[k]);
+  }
+  c.H0 = __ldg(&sc->fH[0]);
+  c.H1 = __ldg(&sc->fH[1]);
+  c.H2 = __ldg(&sc->fH[2]);
+}
+
+// particle data for the solid operator
+template <typename T>
+__device__ __forceinline__ void load_particle(const LbmParams& P, int p, T* xp, T* up, T* op);
+template <>
+__device__ __forceinline__ void load_particle<double>(const LbmParams& P, int p, double* xp,
+                                                      double* up, double* op) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    xp[a] = __ldg(&P.px[3 * p + a]);
+    up[a] = __ldg(&P.pu[3 * p + a]);
+    op[a] = __ldg(&P.pom[3 * p + a]);
+  }
+}
+template <>
+__device__ __forceinline__ void load_particle<float>(const LbmParams& P, int p, float* xp,
+                                                     float* up, float* op) {
+  float4 a = __ldg(reinterpret_cast<const float4*>(P.pxf) + p);
+  float4 b = __ldg(reinterpret_cast<const float4*>(P.puf) + p);
+  float4 c = __ldg(reinterpret_cast<const float4*>(P.pomf) + p);
+  xp[0] = a.x; xp[1] = a.y; xp[2] = a.z;
+  up[0] = b.x; up[1] = b.y; up[2] = b.z;
+  op[0] = c.x; op[1] = c.y; op[2] = c.z;
+}
+
+// nearest-image offset of the cell centre from the particle centre
+template <typename T>
+__device__ __forceinline__ T image_offset(int i, T xp, int n, bool periodic) {
+  T d = (T(i) + T(0.5)) - xp;
+  if (periodic) {
+    if (d > T(0.5) * T(n)) d = (T(i - n) + T(0.5)) - xp;
+    else if (d < -T(0.5) * T(n)) d = (T(i + n) + T(0.5)) - xp;
+  }
+  return d;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) lbm_kernel(LbmParams P) {
+  using T2 = typename Vec2<T>::type;
+  const Grid& g = P.g;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= g.nwords) return;
+  const int row = (int)(warp / g.wpr);
+  const int x = (int)(warp - (long long)row * g.wpr) * 32 + lane;
+  const int y = row % g.ny;
+  const int z = row / g.ny;
+  const uint32_t m = P.mask ? __ldg(&P.mask[warp]) : 0u;
+  if (x >= g.nx) return;
+
+  Nbr nb;
+  nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
+  const int cell = nb.idx(0, 0, 0);
+  const long long NC = g.ncell;
+  // src == dst for the AA pattern: every thread reads its whole set of
+  // locations before it writes the same set, so no restrict on dst
+  const T* src = static_cast<const T*>(P.src);
+  T* dst = static_cast<T*>(P.dst);
+
+  // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls)
+  T d[Q];
+  d[0] = ld(src + cell);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+    const int qa = 2 * k + 1, qb = 2 * k + 2;
+    long long ia, ib;
+    if (MODE == 0) {         // pull from the other buffer
+      ia = nb.ok(-cx, -cy, -cz) ? qa * NC + nb.idx(-cx, -cy, -cz) : qb * NC + cell;
+      ib = nb.ok(cx, cy, cz) ? qb * NC + nb.idx(cx, cy, cz) : qa * NC + cell;
+    } else if (MODE == 1) {  // AA even: own cell
+      ia = qa * NC + cell;
+      ib = qb * NC + cell;
+    } else {                 // AA odd: swapped slots of the neighbours
+      ia = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
+      ib = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
+    }
+    d[qa] = ld(src + ia);
+    d[qb] = ld(src + ib);
+  }
+
+  // ---- coverage of this cell
+  const bool cov = (m >> lane) & 1u;
+  int e = 0;
+  int2 pid = make_int2(-1, -1);
+  T2 Bs;
+  Bs.x = T(0);
+  Bs.y = T(0);
+  if (cov) {
+    e = __ldg(&P.base[warp]) + __popc(m & ((1u << lane) - 1u));
+    if (e < P.slot_cap) {
+      pid = __ldg(&P.slot_pid[e]);
+      Bs = __ldg(static_cast<const T2*>(P.slot_B) + e);
+    }
+  }
+  T B = Bs.x + Bs.y;
+  if (B > T(1)) B = T(1);
+  const T omB = T(1) - B;
+
+  // ---- moments (Eqs. 6-7)
+  Coef<T> cf;
+  load_coef<T>(P.sc, cf);
+  T a[9];
+  T drho = d[0];
+  T jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const T s = d[2 * k + 1] + d[2 * k + 2];
+    a[k] = d[2 * k + 1] - d[2 * k + 2];
+    drho += s;
+    if (ckx(k) > 0) jx += a[k];
+    if (cky(k) > 0) jy += a[k];
+    if (cky(k) < 0) jy -= a[k];
+    if (ckz(k) > 0) jz += a[k];
+    if (ckz(k) < 0) jz -= a[k];
+  }
+  const T Ux = jx + T(0.5) * cf.ffx;
+  const T Uy = jy + T(0.5) * cf.ffy;
+  const T Uz = jz + T(0.5) * cf.ffz;
+  const T uu = Ux * Ux + Uy * Uy + Uz * Uz;
+  const T Uf = Ux * cf.ffx + Uy * cf.ffy + Uz * cf.ffz;
+  const T base0 = drho - T(1.5) * uu;
+  const T wp = T(P.omega_p), wm = T(P.omega_m);
+
+  // ---- fluid relaxation + forcing, weighted by (1 - B)
+  {
+    const T E0 = w0<T>() * base0;
+    T dl = -wp * (d[0] - E0) + cf.H0 * Uf;
+    d[0] += omB * dl;
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const T w = wk<T>(k);
+    const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
+    const T Es = (T(4.5) * w * cu) * cu + w * base0;
+    const T Fs = cf.Gs[k] * cu + (k < 3 ? cf.H1 : cf.H2) * Uf;
+    const T s = d[2 * k + 1] + d[2 * k + 2];
+    T ds = (T(-0.5) * wp) * s + (wp * Es + Fs);
+    T da = (T(-0.5) * wm) * a[k] + ((T(3) * w * wm) * cu + cf.Fa[k]);
+    ds *= omB;
+    da *= omB;
+    d[2 * k + 1] += ds + da;
+    d[2 * k + 2] += ds - da;
+  }
+
+  // ---- solid operator of each overlapping particle (Eqs. 19-21)
+  if (cov && e < P.slot_cap) {
+#pragma unroll 1
+    for (int sl = 0; sl < 2; ++sl) {
+      const int p = sl ? pid.y : pid.x;
+      const T Bi = sl ? Bs.y : Bs.x;
+      T Fx = T(0), Fy = T(0), Fz = T(0);
+      if (p >= 0) {
+        T xp[3], up[3], op[3];
+        load_particle<T>(P, p, xp, up, op);
+        const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
+        const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
+        const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
+        // Eq. 20: surface velocity at the cell centre
+        const T Vx = up[0] + (op[1] * dz - op[2] * dy);
+        const T Vy = up[1] + (op[2] * dx - op[0] * dz);
+        const T Vz = up[2] + (op[0] * dy - op[1] * dx);
+        const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+        d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
+        T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const T w = wk<T>(k);
+          const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
+          const T cv = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
+          const T dS = w * (T(4.5) * (cv - cu) * (cv + cu) - T(1.5) * dU2);
+          const T A = (T(3) * w) * (cu + cv) - a[k];
+          d[2 * k + 1] += Bi * (dS + A);
+          d[2 * k + 2] += Bi * (dS - A);
+          if (ckx(k) > 0) ax += A;
+          if (cky(k) > 0) ay += A;
+          if (cky(k) < 0) ay -= A;
+          if (ckz(k) > 0) az += A;
+          if (ckz(k) < 0) az -= A;
+        }
+        // Eq. 21: B_i sum_q C^s_q c_qbar = -2 B_i sum_k A_k c_k
+        Fx = T(-2) * Bi * ax;
+        Fy = T(-2) * Bi * ay;
+        Fz = T(-2) * Bi * az;
+      }
+      T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
+      o[0] = Fx;
+      o[1] = Fy;
+      o[2] = Fz;
+    }
+  }
+
+  // ---- store
+  dst[cell] = d[0];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+    const int qa = 2 * k + 1, qb = 2 * k + 2;
+    long long oa, ob;
+    if (MODE == 0) {
+      oa = qa * NC + cell;
+      ob = qb * NC + cell;
+    } else if (MODE == 1) {
+      oa = qb * NC + cell;
+      ob = qa * NC + cell;
+    } else {
+      oa = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
+      ob = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
+    }
+    dst[oa] = d[qa];
+    dst[ob] = d[qb];
+  }
+}
+
+// canonical FP64 f~ (unpadded, full f = w + delta) from the storage layout
+template <typename T>
+__global__ void to_canonical_kernel(Grid g, const T* __restrict__ buf, int aa, int parity,
+                                    double* __restrict__ out) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx);
+    const int y = (int)((c / g.nx) % g.ny);
+    const int z = (int)(c / ((long long)g.nx * g.ny));
+    Nbr nb;
+    nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
+    const int cell = nb.idx(0, 0, 0);
+    const long long NC = g.ncell;
+    out[c] = wq(0) + (double)buf[cell];
+    for (int k = 0; k < 9; ++k) {
+      const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+      const int qa = 2 * k + 1, qb = 2 * k + 2;
+      long long ia, ib;
+      if (!aa) {
+        ia = qa * NC + cell;
+        ib = qb * NC + cell;
+      } else if (parity == 1) {
+        ia = qb * NC + cell;
+        ib = qa * NC + cell;
+      } else {
+        ia = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
+        ib = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
+      }
+      out[qa * N + c] = wq(qa) + (double)buf[ia];
+      out[qb * N + c] = wq(qb) + (double)buf[ib];
+    }
+  }
+}
+
+// storage layout from canonical f~; the AA buffer is written in the state
+// "next step is even" (each cell holds its streamed PDFs)
+template <typename T>
+__global__ void from_canonical_kernel(Grid g, const double* __restrict__ in, int aa,
+                                      T* __restrict__ buf) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx);
+    const int y = (int)((c / g.nx) % g.ny);
+    const int z = (int)(c / ((long long)g.nx * g.ny));
+    Nbr nc;  // neighbours in the unpadded canonical array
+    nc.init(x, y, z, g.nx, g.ny, g.nz, g.nx, g.wall);
+    const long long cell = (long long)x + (long long)g.nxp * (y + (long long)g.ny * z);
+    const long long NC = g.ncell;
+    buf[cell] = (T)(in[c] - wq(0));
+    for (int k = 0; k < 9; ++k) {
+      const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+      const int qa = 2 * k + 1, qb = 2 * k + 2;
+      double va, vb;
+      if (!aa) {
+        va = in[qa * N + c];
+        vb = in[qb * N + c];
+      } else {
+        va = nc.ok(-cx, -cy, -cz) ? in[qa * N + nc.idx(-cx, -cy, -cz)] : in[qb * N + c];
+        vb = nc.ok(cx, cy, cz) ? in[qb * N + nc.idx(cx, cy, cz)] : in[qa * N + c];
+      }
+      buf[qa * NC + cell] = (T)(va - wq(qa));
+      buf[qb * NC + cell] = (T)(vb - wq(qb));
+    }
+  }
+}
+
+// rho and U of the streamed canonical field (Eqs. 6-7)
+__global__ void macroscopic_kernel(Grid g, const double* __restrict__ f, const StepConst* sc,
+                                   double* __restrict__ rho, double* __restrict__ u) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+       c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % g.nx);
+    const int y = (int)((c / g.nx) % g.ny);
+    const int z = (int)(c / ((long long)g.nx * g.ny));
+    Nbr nc;
+    nc.init(x, y, z, g.nx, g.ny, g.nz, g.nx, g.wall);
+    double r = f[c], jx = 0.0, jy = 0.0, jz = 0.0;
+    for (int k = 0; k < 9; ++k) {
+      const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+      const int qa = 2 * k + 1, qb = 2 * k + 2;
+      const double va = nc.ok(-cx, -cy, -cz) ? f[qa * N + nc.idx(-cx, -cy, -cz)] : f[qb * N + c];
+      const double vb = nc.ok(cx, cy, cz) ? f[qb * N + nc.idx(cx, cy, cz)] : f[qa * N + c];
+      r += va + vb;
+      jx += (va - vb) * cx;
+      jy += (va - vb) * cy;
+      jz += (va - vb) * cz;
+    }
+    rho[c] = r;
+    u[c] = jx + 0.5 * sc->fext[0];
+    u[N + c] = jy + 0.5 * sc->fext[1];
+    u[2 * N + c] = jz + 0.5 * sc->fext[2];
+  }
+}
+
+// fixed-order sums of mass and momentum over the canonical field
+constexpr int SUM_THREADS = 256;
+__global__ void sums_partial_kernel(long long N, const double* __restrict__ f,
+                                    double* __restrict__ partials) {
+  __shared__ double sh[4][SUM_THREADS];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long per = (N + gridDim.x - 1) / gridDim.x;
+  const long long lo = per * blockIdx.x;
+  const long long hi = lo + per < N ? lo + per : N;
+  for (long long c = lo + threadIdx.x; c < hi; c += SUM_THREADS) {
+    double r = f[c], jx = 0.0, jy = 0.0, jz = 0.0;
+    for (int k = 0; k < 9; ++k) {
+      const double va = f[(2 * k + 1) * N + c], vb = f[(2 * k + 2) * N + c];
+      r += va + vb;
+      jx += (va - vb) * ckx(k);
+      jy += (va - vb) * cky(k);
+      jz += (va - vb) * ckz(k);
+    }
+    acc[0] += r;
+    acc[1] += jx;
+    acc[2] += jy;
+    acc[3] += jz;
+  }
+  for (int i = 0; i < 4; ++i) sh[i][threadIdx.x] = acc[i];
+  __syncthreads();
+  for (int s = SUM_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int i = 0; i < 4; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i) partials[4 * blockIdx.x + i] = sh[i][0];
+}
+
+__global__ void sums_final_kernel(int nparts, const double* __restrict__ partials,
+                                  double* __restrict__ out) {
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partials[4 * b + threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+}  // namespace
+
+int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s) {
+  const long long threads = P.g.nwords * 32;
+  const int block = 256;
+  const unsigned grid = (unsigned)((threads + block - 1) / block);
+  if (fp32) {
+    if (mode == 0) lbm_kernel<float, 0><<<grid, block, 0, s>>>(P);
+    else if (mode == 1) lbm_kernel<float, 1><<<grid, block, 0, s>>>(P);
+    else lbm_kernel<float, 2><<<grid, block, 0, s>>>(P);
+  } else {
+    if (mode == 0) lbm_kernel<double, 0><<<grid, block, 0, s>>>(P);
+    else if (mode == 1) lbm_kernel<double, 1><<<grid, block, 0, s>>>(P);
+    else lbm_kernel<double, 2><<<grid, block, 0, s>>>(P);
+  }
+  return 1;
+}
+
+static unsigned grid_for(long long n, int block) {
+  long long b = (n + block - 1) / block;
+  if (b > 152LL * 64) b = 152LL * 64;
+  return (unsigned)(b > 0 ? b : 1);
+}
+
+int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
+                        double* out, cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  if (fp32)
+    to_canonical_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
+        g, static_cast<const float*>(buf), aa, aa_parity, out);
+  else
+    to_canonical_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
+        g, static_cast<const double*>(buf), aa, aa_parity, out);
+  return 1;
+}
+
+int launch_from_canonical(const Grid& g, const double* in, void* buf, int fp32, int aa,
+                             cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  if (fp32)
+    from_canonical_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(g, in, aa,
+                                                                  static_cast<float*>(buf));
+  else
+    from_canonical_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(g, in, aa,
+                                                                   static_cast<double*>(buf));
+  return 1;
+}
+
+int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,
+                       double* u, cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  macroscopic_kernel<<<grid_for(N, 256), 256, 0, s>>>(g, f, sc, rho, u);
+  return 1;
+}
+
+int launch_sums(const Grid& g, const double* f, double* partials, int nparts, double* out4,
+                cudaStream_t s) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  sums_partial_kernel<<<nparts, SUM_THREADS, 0, s>>>(N, f, partials);
+  sums_final_kernel<<<1, 32, 0, s>>>(nparts, partials, out4);
+  return 2;
+}
+
+// per-step constants: fluid force density (body force and the counter force
+// of the buoyancy-corrected gravity) and the forcing coefficients
+__global__ void step_const_kernel(MapParams P) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  StepConst* sc = P.sc;
+  const double vf = sc->vfluid;
+  double f[3];
+  for (int a = 0; a < 3; ++a)
+    f[a] = P.fbody[a] - ((P.G[a] != 0.0 && vf > 0.0) ? P.G[a] / vf : 0.0);
+  const double gp = 1.0 - 0.5 * P.omega_p, gm = 1.0 - 0.5 * P.omega_m;
+  for (int a = 0; a < 3; ++a) {
+    sc->fext[a] = f[a];
+    sc->ffext[a] = (float)f[a];
+  }
+  for (int k = 0; k < 9; ++k) {
+    const double cfk = ckx(k) * f[0] + cky(k) * f[1] + ckz(k) * f[2];
+    const double w = wk<double>(k);
+    sc->Gs[k] = gp * 9.0 * w * cfk;
+    sc->Fa[k] = gm * 3.0 * w * cfk;
+    sc->fGs[k] = (float)sc->Gs[k];
+    sc->fFa[k] = (float)sc->Fa[k];
+  }
+  sc->H[0] = -3.0 * (1.0 / 3.0) * gp;
+  sc->H[1] = -3.0 * (1.0 / 18.0) * gp;
+  sc->H[2] = -3.0 * (1.0 / 36.0) * gp;
+  for (int i = 0; i < 3; ++i) sc->fH[i] = (float)sc->H[i];
+}
+
+int launch_step_const(MapParams P, cudaStream_t s) {
+  step_const_kernel<<<1, 32, 0, s>>>(P);
+  return 1;
+}
+
+}  // namespace psm

@@ -1,0 +1,840 @@
+// psm_capi.cu -- the engine behind include/psm.h: device buffers, the order of
+// the kernels within one time step, CUDA-graph replay, error and status
+// handling.  Host arithmetic that feeds the device (particle volume, mass,
+// inertia, f(r) of Eq. 26) is compiled with -ffp-contract=off.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/psm.h"
+#include "psm_internal.cuh"
+
+namespace psm {
+int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
+                         const float* X, float* eps, cudaStream_t s);
+int launch_map_mlp(MapParams P, cudaStream_t s);
+}
+
+using namespace psm;
+
+struct Alloc {
+  void* ptr;
+};
+
+struct psm_ctx {
+  psm_options opt{};
+  Grid g{};
+  double tau = 0.6, omega_p = 0, omega_m = 0;
+  int relax = 0, fp32 = 0, aa = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  std::vector<void*> allocs;
+  void* buf[2] = {nullptr, nullptr};
+  int cur = 0;        // pull: buffer holding f~ of the last step
+  int parity = 0;     // AA: 0 = buffer holds streamed PDFs (next step even)
+  Coverage cov{};
+  Slots slots{};
+  StepConst* sc = nullptr;
+  unsigned* status = nullptr;
+  double* partials = nullptr;
+  Particles p{};
+  std::vector<void*> palloc;  // particle-sized allocations
+  bool any_free = false;
+  bool need_map = false;
+  bool need_pack = false;
+  double G[3] = {0, 0, 0};
+  double log_e = 0;
+  float* mlp = nullptr;   // FP32 parameters on the device
+  bool have_mlp = false;
+  float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
+  float* mlp_eps = nullptr;
+  int* mlp_work = nullptr;   // entry index per worklist item
+  int* mlp_count = nullptr;
+  long long mlp_cap = 0;
+  bool error_state = false;
+  std::string err;
+  // graphs: [buffer or parity][with mapping]
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  long graph_launches[2][2] = {{0, 0}, {0, 0}};
+  long launches = 0;
+  bool timing = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double t_ms[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+psm_status fail(psm_ctx* c, psm_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(c, PSM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+  } while (0)
+
+void* dalloc(psm_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->opt.alloc) {
+    p = c->opt.alloc(bytes, c->opt.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dfree(psm_ctx* c, void* p) {
+  if (!p) return;
+  if (c->opt.free) c->opt.free(p, c->opt.alloc_user);
+  else if (!c->opt.alloc) cudaFree(p);
+}
+
+template <typename T>
+T* alloc_n(psm_ctx* c, size_t n, std::vector<void*>& owner) {
+  void* p = dalloc(c, sizeof(T) * n);
+  if (p) owner.push_back(p);
+  return static_cast<T*>(p);
+}
+
+void free_graphs(psm_ctx* c) {
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (c->graph[i][j]) {
+        cudaGraphExecDestroy(c->graph[i][j]);
+        c->graph[i][j] = nullptr;
+      }
+}
+
+void free_particles(psm_ctx* c) {
+  for (void* q : c->palloc) dfree(c, q);
+  c->palloc.clear();
+  c->p = Particles{};
+  c->slots = Slots{};
+  c->mlp_X = nullptr;
+  c->mlp_eps = nullptr;
+  c->mlp_work = nullptr;
+  c->mlp_cap = 0;
+}
+
+MapParams map_params(psm_ctx* c) {
+  MapParams P{};
+  P.g = c->g;
+  P.p = c->p;
+  P.cov = c->cov;
+  P.s = c->slots;
+  P.fp32 = c->fp32;
+  P.eps_mode = c->opt.eps_mode;
+  P.eps_n = c->opt.eps_n;
+  P.weighting = c->opt.weighting;
+  P.tau = c->tau;
+  P.status = c->status;
+  P.sc = c->sc;
+  for (int a = 0; a < 3; ++a) {
+    P.G[a] = c->G[a];
+    P.fbody[a] = c->opt.body_force[a];
+  }
+  P.omega_p = c->omega_p;
+  P.omega_m = c->omega_m;
+  P.mlp = c->have_mlp ? c->mlp : nullptr;
+  P.partials = c->partials;
+  P.mlp_X = c->mlp_X;
+  P.mlp_eps = c->mlp_eps;
+  P.mlp_work = c->mlp_work;
+  P.mlp_count = c->mlp_count;
+  return P;
+}
+
+// Eq. 27 and Eq. 26: f(r) = V_a(r) - r + 1/2 (same closed form as printed)
+double jones_fr(double r) {
+  double r2 = r * r;
+  double s = std::sqrt(r2 - 0.5);
+  double Va = (1.0 / 12.0 - r2) * std::atan((0.5 * s) / (0.5 - r2)) + s / 3.0 +
+              (r2 - 1.0 / 12.0) * std::atan(0.5 / s) -
+              4.0 / 3.0 * r2 * r * std::atan(0.25 / (r * s));
+  return Va - r + 0.5;
+}
+
+// Kernels of one time step, in the order of the paper's Fig. "implementation":
+// mapping (when needed), stream + PSM collide, force/torque reduction, DEM.
+int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
+  int n = 0;
+  MapParams MP = map_params(c);
+  if (c->timing) cudaEventRecord(c->ev[0], s);
+  if (with_map) {
+    if (c->opt.eps_mode == PSM_EPS_MLP) n += launch_map_mlp(MP, s);
+    else n += launch_map(MP, s);
+    n += launch_step_const(MP, s);
+  }
+  if (c->fp32 && c->p.n > 0 && (with_map || c->any_free)) n += launch_pack_particles(c->p, s);
+  if (c->timing) cudaEventRecord(c->ev[1], s);
+  LbmParams L{};
+  L.g = c->g;
+  int mode = 0;
+  if (c->aa) {
+    L.src = c->buf[0];
+    L.dst = c->buf[0];
+    mode = c->parity == 0 ? 1 : 2;
+  } else {
+    L.src = c->buf[c->cur];
+    L.dst = c->buf[1 - c->cur];
+  }
+  if (c->p.n > 0) {
+    L.mask = c->cov.mask;
+    L.base = c->cov.base;
+    L.slot_pid = c->slots.pid;
+    L.slot_B = c->slots.B;
+    L.slot_Fc = c->slots.Fc;
+    L.slot_cap = c->slots.cap;
+  }
+  L.px = c->p.x;
+  L.pu = c->p.u;
+  L.pom = c->p.om;
+  L.pxf = c->p.xf;
+  L.puf = c->p.uf;
+  L.pomf = c->p.omf;
+  L.sc = c->sc;
+  L.omega_p = c->omega_p;
+  L.omega_m = c->omega_m;
+  n += launch_lbm(L, c->fp32, mode, s);
+  if (c->timing) cudaEventRecord(c->ev[2], s);
+  if (c->p.n > 0) n += launch_force_reduce(MP, s);
+  if (c->timing) cudaEventRecord(c->ev[3], s);
+  if (c->any_free) {
+    DemParams D{};
+    D.g = c->g;
+    D.p = c->p;
+    D.kn = c->opt.k_n;
+    D.log_e = c->log_e;
+    D.dt = 1.0 / c->opt.dem_subcycles;
+    for (int a = 0; a < 3; ++a) D.gravity[a] = c->opt.gravity[a];
+    D.status = c->status;
+    n += launch_dem_step(D, c->opt.dem_subcycles, s);
+  }
+  if (c->timing) cudaEventRecord(c->ev[4], s);
+  return n;
+}
+
+void advance_state(psm_ctx* c) {
+  if (c->aa) c->parity ^= 1;
+  else c->cur ^= 1;
+}
+
+int state_index(const psm_ctx* c) { return c->aa ? c->parity : c->cur; }
+
+psm_status ensure_mapped(psm_ctx* c) {
+  if (!c->need_map) return PSM_OK;
+  MapParams MP = map_params(c);
+  if (c->opt.eps_mode == PSM_EPS_MLP) launch_map_mlp(MP, c->stream);
+  else launch_map(MP, c->stream);
+  launch_step_const(MP, c->stream);
+  if (c->fp32 && c->p.n > 0) launch_pack_particles(c->p, c->stream);
+  CK(cudaGetLastError());
+  c->need_map = c->any_free;
+  return PSM_OK;
+}
+
+psm_status read_status(psm_ctx* c) {
+  unsigned st = 0;
+  CK(cudaMemcpyAsync(&st, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    c->error_state = true;
+    if (st & ST_SLOT_OVERFLOW)
+      return fail(c, PSM_ERR_SLOT_OVERFLOW, "a cell lies within reach of more than two particles");
+    if (st & ST_NONFINITE) return fail(c, PSM_ERR_NONFINITE, "non-finite hydrodynamic force");
+    return fail(c, PSM_ERR_STATE, "device status " + std::to_string(st));
+  }
+  return PSM_OK;
+}
+
+psm_status canonical(psm_ctx* c, double** out) {
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  double* f = static_cast<double*>(dalloc(c, sizeof(double) * Q * N));
+  if (!f) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  launch_to_canonical(c->g, c->aa ? c->buf[0] : c->buf[c->cur], c->fp32, c->parity, c->aa, f,
+                      c->stream);
+  *out = f;
+  CK(cudaGetLastError());
+  return PSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void psm_default_options(psm_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->magic = 3.0 / 16.0;
+  o->precision = PSM_FP64;
+  o->streaming = PSM_PULL;
+  o->eps_mode = PSM_EPS_SUPERSAMPLE;
+  o->eps_n = 4;
+  o->weighting = PSM_W_NT;
+  o->k_n = 1e3;
+  o->restitution = 0.9;
+  o->dem_subcycles = 10;
+  o->dem = 1;
+  o->deterministic = 1;
+  o->use_graphs = 1;
+}
+
+psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const psm_options* opt,
+                      psm_ctx** out) {
+  if (!out) return PSM_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !opt) return PSM_ERR_ARG;
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return PSM_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (grid->wall[2 * a] != grid->wall[2 * a + 1]) return PSM_ERR_ARG;
+  if (!(tau > 0.5) || !std::isfinite(tau)) return PSM_ERR_ARG;
+  if (relax != PSM_SRT && relax != PSM_TRT) return PSM_ERR_ARG;
+  if (opt->precision != PSM_FP64 && opt->precision != PSM_FP32_DEV) return PSM_ERR_ARG;
+  if (opt->streaming != PSM_PULL && opt->streaming != PSM_AA) return PSM_ERR_ARG;
+  if (opt->eps_mode < 0 || opt->eps_mode > 2) return PSM_ERR_ARG;
+  if (opt->eps_n < 1 || opt->eps_n > 16) return PSM_ERR_ARG;
+  if (opt->weighting != PSM_W_EPS && opt->weighting != PSM_W_NT) return PSM_ERR_ARG;
+  if (relax == PSM_TRT && !(opt->magic > 0.0)) return PSM_ERR_ARG;
+  if (opt->dem && (opt->dem_subcycles < 1 || !(opt->k_n > 0) || !(opt->restitution > 0) ||
+                   opt->restitution > 1.0))
+    return PSM_ERR_ARG;
+  const long long nxp = ((grid->nx + 31) / 32) * 32LL;
+  const long long ncell = nxp * grid->ny * grid->nz;
+  if (ncell >= (1LL << 31)) return PSM_ERR_ARG;
+
+  psm_ctx* c = new psm_ctx();
+  c->opt = *opt;
+  c->tau = tau;
+  c->relax = relax;
+  c->fp32 = opt->precision == PSM_FP32_DEV;
+  c->aa = opt->streaming == PSM_AA;
+  c->stream = static_cast<cudaStream_t>(opt->stream);
+  c->omega_p = 1.0 / tau;
+  c->omega_m = relax == PSM_TRT ? 1.0 / (0.5 + opt->magic / (tau - 0.5)) : c->omega_p;
+  c->log_e = opt->restitution > 0 ? std::log(opt->restitution) : 0.0;
+  Grid& g = c->g;
+  g.nx = grid->nx;
+  g.ny = grid->ny;
+  g.nz = grid->nz;
+  g.nxp = (int)nxp;
+  for (int a = 0; a < 3; ++a) g.wall[a] = grid->wall[2 * a] ? 1 : 0;
+  g.wpr = (int)(nxp / 32);
+  g.ncell = ncell;
+  g.nwords = ncell / 32;
+
+  auto bail = [&](psm_status st, const char* msg) {
+    psm_status r = st;
+    c->err = msg;
+    psm_destroy(c);
+    return r;
+  };
+  const size_t esz = c->fp32 ? sizeof(float) : sizeof(double);
+  const int nbuf = c->aa ? 1 : 2;
+  for (int b = 0; b < nbuf; ++b) {
+    c->buf[b] = alloc_n<unsigned char>(c, esz * Q * (size_t)ncell, c->allocs);
+    if (!c->buf[b]) return bail(PSM_ERR_OOM, "allocator returned NULL for the PDF field");
+  }
+  c->cov.mask = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
+  c->cov.base = alloc_n<int>(c, (size_t)g.nwords, c->allocs);
+  c->cov.nblocks = (g.nwords + 1023) / 1024;
+  c->cov.blocksum = alloc_n<int>(c, (size_t)c->cov.nblocks, c->allocs);
+  c->cov.ncov = alloc_n<int>(c, 1, c->allocs);
+  c->sc = alloc_n<StepConst>(c, 1, c->allocs);
+  c->status = alloc_n<unsigned>(c, 1, c->allocs);
+  c->partials = alloc_n<double>(c, MAP_PARTIALS * 4, c->allocs);
+  c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
+  c->mlp_count = alloc_n<int>(c, 1, c->allocs);
+  if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
+      !c->status || !c->partials || !c->mlp || !c->mlp_count)
+    return bail(PSM_ERR_OOM, "allocator returned NULL");
+  cudaStream_t s = c->stream;
+  bool ok = true;
+  for (int b = 0; b < nbuf; ++b)
+    ok = ok && cudaMemsetAsync(c->buf[b], 0, esz * Q * (size_t)ncell, s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->cov.mask, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->cov.ncov, 0, sizeof(int), s) == cudaSuccess;
+  StepConst h{};
+  h.ncells = (double)g.nx * g.ny * g.nz;
+  h.vfluid = h.ncells;
+  ok = ok && cudaMemcpyAsync(c->sc, &h, sizeof(h), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "initialisation of device buffers failed");
+  }
+  launch_step_const(map_params(c), s);
+  if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "cudaStreamCreate failed");
+  }
+  for (int i = 0; i < 5; ++i) cudaEventCreate(&c->ev[i]);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "initialisation kernel failed");
+  }
+  *out = c;
+  return PSM_OK;
+}
+
+psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r,
+                             const double* u, const double* omega, const double* density,
+                             const unsigned char* fixed) {
+  if (!c) return PSM_ERR_ARG;
+  if (n < 0) return fail(c, PSM_ERR_ARG, "negative particle count");
+  if (n > 0 && (!x || !r || !u || !omega || !density))
+    return fail(c, PSM_ERR_ARG, "NULL particle array");
+  const int dims[3] = {c->g.nx, c->g.ny, c->g.nz};
+  std::vector<double> hx(3 * (size_t)n), vol(n), m(n), I(n), fr(n), Fold(3 * (size_t)n, 0.0);
+  std::vector<unsigned char> fx(n, 0);
+  double G[3] = {0, 0, 0};
+  bool any_free = false;
+  const double PI = 3.14159265358979323846;
+  long long cap = 0;
+  for (int i = 0; i < n; ++i) {
+    if (!(r[i] > 0.0) || !std::isfinite(r[i]) || !(density[i] > 0.0))
+      return fail(c, PSM_ERR_ARG, "radius and density must be positive");
+    for (int a = 0; a < 3; ++a) {
+      double v = x[3 * i + a];
+      if (!std::isfinite(v) || !std::isfinite(u[3 * i + a]) || !std::isfinite(omega[3 * i + a]))
+        return fail(c, PSM_ERR_ARG, "non-finite particle state");
+      if (!c->g.wall[a]) {
+        if (2.0 * r[i] + 4.0 > dims[a])
+          return fail(c, PSM_ERR_ARG, "particle too large for the periodic box");
+        v = std::fmod(v, (double)dims[a]);
+        if (v < 0) v += dims[a];
+      }
+      hx[3 * i + a] = v;
+    }
+    vol[i] = 4.0 / 3.0 * PI * r[i] * r[i] * r[i];
+    m[i] = density[i] * vol[i];
+    I[i] = 0.4 * m[i] * r[i] * r[i];
+    fr[i] = r[i] * r[i] > 0.5 ? jones_fr(r[i]) : 0.5;
+    fx[i] = fixed ? (fixed[i] ? 1 : 0) : 0;
+    if (!fx[i] && c->opt.dem) {
+      any_free = true;
+      for (int a = 0; a < 3; ++a) {
+        Fold[3 * i + a] = (m[i] - vol[i]) * c->opt.gravity[a];
+        G[a] += (m[i] - vol[i]) * c->opt.gravity[a];
+      }
+    }
+    const double R = r[i] + std::sqrt(3.0);
+    cap += (long long)(4.0 / 3.0 * PI * R * R * R) + 1;
+  }
+  if (cap > c->g.ncell) cap = c->g.ncell;
+  free_graphs(c);
+  free_particles(c);
+  Particles& P = c->p;
+  const size_t n1 = n > 0 ? n : 1, n3 = 3 * n1, n4 = 4 * n1;
+  P.n = n;
+  P.x = alloc_n<double>(c, n3, c->palloc);
+  P.u = alloc_n<double>(c, n3, c->palloc);
+  P.om = alloc_n<double>(c, n3, c->palloc);
+  P.r = alloc_n<double>(c, n1, c->palloc);
+  P.m = alloc_n<double>(c, n1, c->palloc);
+  P.I = alloc_n<double>(c, n1, c->palloc);
+  P.vol = alloc_n<double>(c, n1, c->palloc);
+  P.fr = alloc_n<double>(c, n1, c->palloc);
+  P.fixed = alloc_n<unsigned char>(c, n1, c->palloc);
+  P.Fh = alloc_n<double>(c, n3, c->palloc);
+  P.Th = alloc_n<double>(c, n3, c->palloc);
+  P.Fold = alloc_n<double>(c, n3, c->palloc);
+  P.Told = alloc_n<double>(c, n3, c->palloc);
+  P.Fc = alloc_n<double>(c, n3, c->palloc);
+  P.xf = alloc_n<float>(c, n4, c->palloc);
+  P.uf = alloc_n<float>(c, n4, c->palloc);
+  P.omf = alloc_n<float>(c, n4, c->palloc);
+  Slots& S = c->slots;
+  const size_t cp = cap > 0 ? (size_t)cap : 1;
+  S.cap = (long long)cp;
+  S.cell = alloc_n<int>(c, cp, c->palloc);
+  S.pid = alloc_n<int2>(c, cp, c->palloc);
+  S.B = alloc_n<unsigned char>(c, cp * 2 * (c->fp32 ? 4 : 8), c->palloc);
+  S.cnt = alloc_n<int>(c, cp, c->palloc);
+  S.Fc = alloc_n<unsigned char>(c, cp * 6 * (c->fp32 ? 4 : 8), c->palloc);
+  if (c->opt.eps_mode == PSM_EPS_MLP) {
+    c->mlp_cap = (long long)cp;
+    c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
+    c->mlp_eps = alloc_n<float>(c, cp, c->palloc);
+    c->mlp_work = alloc_n<int>(c, cp, c->palloc);
+  }
+  for (void* q : c->palloc)
+    if (!q) {
+      free_particles(c);
+      return fail(c, PSM_ERR_OOM, "allocator returned NULL for particle buffers");
+    }
+  cudaStream_t s = c->stream;
+  const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
+  if (n > 0) {
+    CK(cudaMemcpyAsync(P.x, hx.data(), b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.u, u, b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.om, omega, b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.r, r, b1, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.m, m.data(), b1, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.I, I.data(), b1, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.vol, vol.data(), b1, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.fr, fr.data(), b1, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.fixed, fx.data(), n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(P.Fold, Fold.data(), b3, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(P.Told, 0, b3, s));
+    CK(cudaMemsetAsync(P.Fh, 0, b3, s));
+    CK(cudaMemsetAsync(P.Th, 0, b3, s));
+    CK(cudaMemsetAsync(P.Fc, 0, b3, s));
+  }
+  for (int a = 0; a < 3; ++a) c->G[a] = G[a];
+  c->any_free = any_free;
+  c->need_map = true;
+  c->error_state = false;
+  CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), s));
+  CK(cudaStreamSynchronize(s));
+  return PSM_OK;
+}
+
+psm_status psm_step(psm_ctx* c, int nsteps) {
+  if (!c) return PSM_ERR_ARG;
+  if (nsteps < 0) return fail(c, PSM_ERR_ARG, "negative step count");
+  if (c->error_state) return fail(c, PSM_ERR_STATE, "context is in an error state");
+  c->launches = 0;
+  const bool graphs = c->opt.use_graphs && !c->timing;
+  for (int k = 0; k < nsteps; ++k) {
+    const bool with_map = c->need_map;
+    const int si = state_index(c);
+    if (graphs) {
+      cudaGraphExec_t& ge = c->graph[si][with_map ? 1 : 0];
+      if (!ge) {
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+        const int nl = enqueue_step(c, with_map, c->capture);
+        cudaError_t e1 = cudaStreamEndCapture(c->capture, &gr);
+        if (e1 != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e1));
+        cudaError_t e2 = cudaGraphInstantiate(&ge, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e2 != cudaSuccess) {
+          ge = nullptr;
+          return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e2));
+        }
+        c->graph_launches[si][with_map ? 1 : 0] = nl;
+      }
+      CK(cudaGraphLaunch(ge, c->stream));
+      c->launches += c->graph_launches[si][with_map ? 1 : 0];
+    } else {
+      c->launches += enqueue_step(c, with_map, c->stream);
+      if (c->timing) {
+        CK(cudaEventSynchronize(c->ev[4]));
+        for (int i = 0; i < 4; ++i) {
+          float ms = 0;
+          cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
+          c->t_ms[i] += ms;
+        }
+      }
+    }
+    CK(cudaGetLastError());
+    if (with_map) c->need_map = c->any_free;
+    advance_state(c);
+  }
+  return read_status(c);
+}
+
+psm_status psm_get_force_torque(psm_ctx* c, double* F, double* T) {
+  if (!c || (c->p.n > 0 && (!F || !T))) return PSM_ERR_ARG;
+  if (c->p.n == 0) return PSM_OK;
+  const size_t b3 = sizeof(double) * 3 * c->p.n;
+  CK(cudaMemcpyAsync(F, c->p.Fh, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(T, c->p.Th, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PSM_OK;
+}
+
+psm_status psm_get_particles(psm_ctx* c, double* x, double* u, double* om) {
+  if (!c || (c->p.n > 0 && (!x || !u || !om))) return PSM_ERR_ARG;
+  if (c->p.n == 0) return PSM_OK;
+  const size_t b3 = sizeof(double) * 3 * c->p.n;
+  CK(cudaMemcpyAsync(x, c->p.x, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(u, c->p.u, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(om, c->p.om, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PSM_OK;
+}
+
+psm_status psm_get_pdfs(psm_ctx* c, double* f) {
+  if (!c || !f) return PSM_ERR_ARG;
+  double* d = nullptr;
+  psm_status st = canonical(c, &d);
+  if (st != PSM_OK) return st;
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  cudaError_t e = cudaMemcpyAsync(f, d, sizeof(double) * Q * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_set_pdfs(psm_ctx* c, const double* f) {
+  if (!c || !f) return PSM_ERR_ARG;
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  double* d = static_cast<double*>(dalloc(c, sizeof(double) * Q * N));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * Q * N, cudaMemcpyHostToDevice, c->stream);
+  void* target = c->aa ? c->buf[0] : c->buf[c->cur];
+  if (e == cudaSuccess) {
+    launch_from_canonical(c->g, d, target, c->fp32, c->aa, c->stream);
+    e = cudaStreamSynchronize(c->stream);
+  }
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  c->parity = 0;
+  c->error_state = false;
+  return PSM_OK;
+}
+
+psm_status psm_get_macroscopic(psm_ctx* c, double* rho, double* u) {
+  if (!c || !rho || !u) return PSM_ERR_ARG;
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  double* f = nullptr;
+  psm_status st = canonical(c, &f);
+  if (st != PSM_OK) return st;
+  double* ru = static_cast<double*>(dalloc(c, sizeof(double) * 4 * N));
+  if (!ru) {
+    dfree(c, f);
+    return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  }
+  launch_macroscopic(c->g, f, c->sc, ru, ru + N, c->stream);
+  cudaError_t e = cudaMemcpyAsync(rho, ru, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(u, ru + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, f);
+  dfree(c, ru);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_get_slots(psm_ctx* c, int* pid0, double* B0, int* pid1, double* B1) {
+  if (!c || !pid0 || !B0 || !pid1 || !B1) return PSM_ERR_ARG;
+  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+  if (c->p.n == 0) {
+    for (size_t i = 0; i < N; ++i) {
+      pid0[i] = pid1[i] = -1;
+      B0[i] = B1[i] = 0.0;
+    }
+    return PSM_OK;
+  }
+  psm_status st = ensure_mapped(c);
+  if (st != PSM_OK) return st;
+  st = read_status(c);
+  if (st != PSM_OK) return st;
+  unsigned char* d = static_cast<unsigned char*>(dalloc(c, N * 24));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  int* dp0 = reinterpret_cast<int*>(d);
+  int* dp1 = dp0 + N;
+  double* db0 = reinterpret_cast<double*>(d + 8 * N);
+  double* db1 = db0 + N;
+  launch_slots_to_dense(map_params(c), dp0, db0, dp1, db1, c->stream);
+  cudaError_t e = cudaMemcpyAsync(pid0, dp0, 4 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pid1, dp1, 4 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B0, db0, 8 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(B1, db1, 8 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_check(psm_ctx* c, double* mass, double* momentum) {
+  if (!c || !mass || !momentum) return PSM_ERR_ARG;
+  double* f = nullptr;
+  psm_status st = canonical(c, &f);
+  if (st != PSM_OK) return st;
+  double out[4];
+  launch_sums(c->g, f, c->partials, 1024, c->partials + 4 * 1024, c->stream);
+  cudaError_t e = cudaMemcpyAsync(out, c->partials + 4 * 1024, sizeof(out),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, f);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  *mass = out[0];
+  for (int a = 0; a < 3; ++a) momentum[a] = out[1 + a];
+  if (!std::isfinite(out[0])) return fail(c, PSM_ERR_NONFINITE, "non-finite mass");
+  return PSM_OK;
+}
+
+psm_status psm_set_mlp(psm_ctx* c, const float* params) {
+  if (!c || !params) return PSM_ERR_ARG;
+  CK(cudaMemcpyAsync(c->mlp, params, sizeof(float) * PSM_MLP_PARAMS, cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->have_mlp = true;
+  c->need_map = c->need_map || c->p.n > 0;
+  free_graphs(c);
+  return PSM_OK;
+}
+
+psm_status psm_get_mlp(psm_ctx* c, float* params) {
+  if (!c || !params) return PSM_ERR_ARG;
+  if (!c->have_mlp) return fail(c, PSM_ERR_STATE, "no surrogate parameters set");
+  CK(cudaMemcpyAsync(params, c->mlp, sizeof(float) * PSM_MLP_PARAMS, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PSM_OK;
+}
+
+psm_status psm_mlp_samples(psm_ctx* c, unsigned long long seed, long first, long count,
+                           float* X, float* eps) {
+  if (!c || !X || !eps || first < 0 || count < 0) return PSM_ERR_ARG;
+  if (count == 0) return PSM_OK;
+  float* d = static_cast<float*>(dalloc(c, sizeof(float) * 5 * count));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  launch_mlp_samples(seed, first, count, d, d + 4 * count, c->stream);
+  cudaError_t e = cudaMemcpyAsync(X, d, sizeof(float) * 4 * count, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(eps, d + 4 * count, sizeof(float) * count, cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_mlp_loss_grad(psm_ctx* c, const float* params, long m, const float* X,
+                             const float* t, float* loss, float* grad) {
+  if (!c || !params || !X || !t || !loss || !grad || m <= 0) return PSM_ERR_ARG;
+  const int nb = mlp_grad_blocks(m);
+  const size_t floats = PSM_MLP_PARAMS * 2 + 1 + 5 * (size_t)m + (size_t)nb * (PSM_MLP_PARAMS + 1);
+  float* d = static_cast<float*>(dalloc(c, sizeof(float) * floats));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  float* dp = d;
+  float* dg = dp + PSM_MLP_PARAMS;
+  float* dl = dg + PSM_MLP_PARAMS;
+  float* dX = dl + 1;
+  float* dt = dX + 4 * m;
+  float* part = dt + m;
+  cudaError_t e = cudaMemcpyAsync(dp, params, sizeof(float) * PSM_MLP_PARAMS,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dX, X, sizeof(float) * 4 * m, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dt, t, sizeof(float) * m, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    launch_mlp_loss_grad(dp, m, dX, dt, part, nb, dg, dl, c->stream);
+    e = cudaMemcpyAsync(grad, dg, sizeof(float) * PSM_MLP_PARAMS, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(loss, dl, sizeof(float), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_mlp_infer(psm_ctx* c, const float* params, long m, const float* X, float* eps) {
+  if (!c || !params || !X || !eps || m < 0) return PSM_ERR_ARG;
+  if (m == 0) return PSM_OK;
+  float* d = static_cast<float*>(dalloc(c, sizeof(float) * (PSM_MLP_PARAMS + 5 * (size_t)m + 4)));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  float* dp = d;
+  float* dX = d + ((PSM_MLP_PARAMS + 3) / 4) * 4;  // float4-aligned
+  float* de = dX + 4 * m;
+  cudaError_t e = cudaMemcpyAsync(dp, params, sizeof(float) * PSM_MLP_PARAMS,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dX, X, sizeof(float) * 4 * m, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    launch_mlp_infer(dp, m, dX, de, c->stream);
+    e = cudaMemcpyAsync(eps, de, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_train_surrogate(psm_ctx* c, long nsamples, unsigned long long seed, int epochs,
+                               int batch, float lr, float* loss_out) {
+  if (!c || nsamples <= 0 || epochs < 1 || batch < 1 || !(lr > 0)) return PSM_ERR_ARG;
+  if (!c->have_mlp) return fail(c, PSM_ERR_STATE, "set initial surrogate parameters first");
+  const int nb = mlp_grad_blocks(batch);
+  const size_t floats = 5 * (size_t)nsamples + 3 * PSM_MLP_PARAMS + 1 +
+                        (size_t)nb * (PSM_MLP_PARAMS + 1);
+  float* d = static_cast<float*>(dalloc(c, sizeof(float) * floats));
+  if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
+  float* X = d;
+  float* T = X + 4 * nsamples;
+  float* g = T + nsamples;
+  float* ms = g + PSM_MLP_PARAMS;
+  float* vs = ms + PSM_MLP_PARAMS;
+  float* dl = vs + PSM_MLP_PARAMS;
+  float* part = dl + 1;
+  cudaStream_t s = c->stream;
+  launch_mlp_samples(seed, 0, nsamples, X, T, s);
+  cudaMemsetAsync(ms, 0, sizeof(float) * 2 * PSM_MLP_PARAMS, s);
+  int step = 0;
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (long b0 = 0; b0 < nsamples; b0 += batch) {
+      const long mb = nsamples - b0 < batch ? nsamples - b0 : batch;
+      launch_mlp_loss_grad(c->mlp, mb, X + 4 * b0, T + b0, part, mlp_grad_blocks(mb), g, dl, s);
+      launch_adam(c->mlp, g, ms, vs, ++step, lr, s);
+    }
+  }
+  // loss of the final parameters over the whole sample set, in minibatches
+  double acc = 0.0;
+  for (long b0 = 0; b0 < nsamples; b0 += batch) {
+    const long mb = nsamples - b0 < batch ? nsamples - b0 : batch;
+    launch_mlp_loss_grad(c->mlp, mb, X + 4 * b0, T + b0, part, mlp_grad_blocks(mb), g, dl, s);
+    float hl = 0;
+    cudaMemcpyAsync(&hl, dl, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) break;
+    acc += (double)hl * mb;
+  }
+  last = acc / nsamples;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  if (loss_out) *loss_out = (float)last;
+  c->need_map = c->need_map || c->p.n > 0;
+  free_graphs(c);
+  return PSM_OK;
+}
+
+psm_status psm_set_timing(psm_ctx* c, int enable) {
+  if (!c) return PSM_ERR_ARG;
+  c->timing = enable != 0;
+  for (int i = 0; i < 4; ++i) c->t_ms[i] = 0;
+  return PSM_OK;
+}
+
+psm_status psm_get_timings(psm_ctx* c, double* out4) {
+  if (!c || !out4) return PSM_ERR_ARG;
+  for (int i = 0; i < 4; ++i) out4[i] = c->t_ms[i];
+  return PSM_OK;
+}
+
+long psm_last_launch_count(const psm_ctx* c) { return c ? c->launches : 0; }
+
+const char* psm_last_error(const psm_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void psm_destroy(psm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  free_graphs(c);
+  free_particles(c);
+  for (void* q : c->allocs) dfree(c, q);
+  c->allocs.clear();
+  for (int i = 0; i < 5; ++i)
+    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  if (c->capture) cudaStreamDestroy(c->capture);
+  delete c;
+}
+
+}  // extern "C"

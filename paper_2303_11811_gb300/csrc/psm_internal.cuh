@@ -1,0 +1,175 @@
+// psm_internal.cuh -- device data layout and kernel launchers of the engine.
+//
+// Layout in HBM (one GPU):
+//   PDFs      T* buf[q * ncell + cell], cell = x + nxp*(y + ny*z), x padded to
+//             nxp = a multiple of 32 so that one warp covers 32 cells of one
+//             x-row and one 32-bit coverage word.  Values are deviations
+//             delta_q = f_q - w_q (FP64 or FP32).  Pull streaming keeps two
+//             buffers; the AA pattern keeps one.
+//   Coverage  mask[word] (bit = cell within reach of some particle), base[word]
+//             = exclusive prefix count of set bits: the covered cells, in cell
+//             order, index the slot table.
+//   Slots     per covered cell: int2 pid (slot 0 < slot 1, -1 = empty), B as
+//             T2 (after the B > 1 normalisation), cnt (particles in reach),
+//             and the per-slot hydrodynamic contribution Fc[6] (T) written by
+//             the collision kernel for the fixed-order force reduction.
+//   Particles FP64 SoA on the device (x, u, omega, r, m, I, F_hyd, T_hyd,
+//             F_old, T_old, fixed); the FP32 path reads float copies.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace psm {
+
+constexpr int Q = 19;
+
+// Status bits raised on the device
+enum : unsigned {
+  ST_SLOT_OVERFLOW = 1u,
+  ST_NONFINITE = 2u,
+  ST_CONTACT_OVERFLOW = 4u,
+};
+
+struct Grid {
+  int nx, ny, nz, nxp;
+  int wall[3];          // 1 = walls on both faces of that axis
+  int wpr;              // warps (coverage words) per x-row = nxp / 32
+  long long ncell;      // nxp * ny * nz
+  long long nwords;     // ncell / 32
+};
+
+// Constants of one time step, computed on the device after the mapping
+struct StepConst {
+  double fext[3];       // fluid force density (body force + counter force)
+  double vfluid;        // sum over cells of (1 - B)
+  double sumB;          // sum over cells of min(B, 1), accumulated by the mapping
+  double ncells;        // nx * ny * nz
+  // forcing coefficients (Eq. 8 with the Guo prefactors), per pair k:
+  //   symmetric part  = Gs[k] * (c_k . U) + H[class] * (U . f)
+  //   antisymmetric   = Fa[k]
+  double Gs[9], Fa[9], H[3];   // H[0] rest, H[1] faces, H[2] edges
+  float fGs[9], fFa[9], fH[3], ffext[3];
+};
+
+struct Particles {
+  int n;
+  double* x;      // n*3
+  double* u;      // n*3
+  double* om;     // n*3
+  double* r;      // n
+  double* m;      // n
+  double* I;      // n
+  double* vol;    // n
+  double* fr;     // n, f(r) of Eq. 26 for the linear approximation
+  unsigned char* fixed;  // n
+  double* Fh;     // n*3 hydrodynamic force of the last step
+  double* Th;     // n*3
+  double* Fold;   // n*3 total force of the last DEM sub-step
+  double* Told;   // n*3
+  double* Fc;     // n*3 contact force scratch
+  float* xf;      // n*4 float copies for the FP32 collision
+  float* uf;      // n*4
+  float* omf;     // n*4
+};
+
+struct Slots {
+  int* cell;      // padded cell index of each entry
+  int2* pid;
+  void* B;        // T2
+  int* cnt;
+  void* Fc;       // T[6] per entry
+  long long cap;
+};
+
+struct Coverage {
+  uint32_t* mask;
+  int* base;
+  int* blocksum;
+  int* ncov;      // device scalar
+  long long nblocks;
+};
+
+struct MapParams {
+  Grid g;
+  Particles p;
+  Coverage cov;
+  Slots s;
+  int fp32;             // slot B stored as float2 (1) or double2 (0)
+  int eps_mode, eps_n, weighting;
+  double tau;
+  unsigned* status;
+  StepConst* sc;
+  double G[3];          // sum over free particles of (m - V) g
+  double fbody[3];
+  double omega_p, omega_m;
+  const float* mlp;     // FP32 parameters (PSM_MLP_PARAMS)
+  double* partials;     // >= MAP_PARTIALS doubles of scratch
+  // surrogate worklist (eps mode 2): inputs, outputs, slot entry, count
+  float* mlp_X;
+  float* mlp_eps;
+  int* mlp_work;
+  int* mlp_count;
+};
+constexpr int MAP_PARTIALS = 152 * 32;
+
+struct LbmParams {
+  Grid g;
+  const void* src;      // T*
+  void* dst;            // T*
+  const uint32_t* mask; // nullptr when there are no particles
+  const int* base;
+  const int2* slot_pid;
+  const void* slot_B;   // T2
+  void* slot_Fc;        // T[6] per entry
+  long long slot_cap;   // entries allocated
+  const double* px;     // FP64 path
+  const double* pu;
+  const double* pom;
+  const float* pxf;     // FP32 path (n*4)
+  const float* puf;
+  const float* pomf;
+  const StepConst* sc;
+  double omega_p, omega_m;
+};
+
+// ---- launchers (stream-ordered; return the number of kernel launches) ----
+int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s);
+int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
+                        double* out, cudaStream_t s);
+int launch_from_canonical(const Grid& g, const double* in, void* buf, int fp32, int aa,
+                          cudaStream_t s);
+int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,
+                       double* u, cudaStream_t s);
+int launch_sums(const Grid& g, const double* f, double* partials, int nparts, double* out4,
+                cudaStream_t s);
+int launch_step_const(MapParams P, cudaStream_t s);
+
+int launch_map(MapParams P, cudaStream_t s);                   // full mapping
+int launch_force_reduce(MapParams P, cudaStream_t s);          // fixed-order F/T
+int launch_force_reduce_atomic_finish(MapParams P, cudaStream_t s);
+int launch_pack_particles(Particles p, cudaStream_t s);
+int launch_slots_to_dense(MapParams P, int* pid0, double* B0, int* pid1, double* B1,
+                          cudaStream_t s);
+
+struct DemParams {
+  Grid g;
+  Particles p;
+  double kn, log_e, dt;
+  double gravity[3];
+  unsigned* status;
+};
+int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
+
+// MLP
+int launch_mlp_samples(unsigned long long seed, long long first, long long count, float* X,
+                       float* eps, cudaStream_t s);
+int launch_mlp_loss_grad(const float* params, long long m, const float* X, const float* t,
+                         float* grad_partials, int nblocks, float* grad, float* loss,
+                         cudaStream_t s);
+int launch_adam(float* params, const float* grad, float* mstate, float* vstate, int step,
+                float lr, cudaStream_t s);
+int launch_mlp_infer(const float* params, long long m, const float* X, float* eps,
+                     cudaStream_t s);
+int mlp_grad_blocks(long long m);
+
+}  // namespace psm

@@ -1,0 +1,191 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 path: PDFs within 1e-12 relative, max over cells and directions of
+|f_gpu - f_oracle| / |f_oracle| (the bound stated for this path); forces and
+torques within 1e-10 relative to the largest component (they are sums of
+thousands of cell contributions accumulated in a different order).
+Mapping: particle indices exact, B within 1e-15 (same FP64 decisions).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2303_11811_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PDF_TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def capi():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2303_11811_gb300 import build, capi as c
+    build.build()
+    return c
+
+
+def pair(capi, shape, **kw):
+    nx, ny, nz = shape
+    gpu_kw = {k: kw.pop(k) for k in ("precision", "streaming", "deterministic", "use_graphs")
+              if k in kw}
+    return capi.Engine(nx, ny, nz, **kw, **gpu_kw), Oracle(nx, ny, nz, **kw)
+
+
+def rel_pdf_err(fg, fo):
+    return float(np.max(np.abs(fg - fo) / np.abs(fo)))
+
+
+def force_err(a, b):
+    scale = max(float(np.max(np.abs(b))), 1e-300)
+    return float(np.max(np.abs(a - b))) / scale
+
+
+def test_sphere32_fp64_1000_steps(capi):
+    """32^3 periodic box, one fixed sphere r = 4 at the centre, SRT tau = 0.6,
+    body force 1e-6 in x, 4^3 sampling, FP64: 1000 steps."""
+    w = inputs.sphere32()
+    e, o = pair(capi, (32, 32, 32), tau=w.tau, relax=w.relax, fbody=w.fbody,
+                weighting=w.weighting, eps_mode=w.eps_mode, eps_n=w.eps_n)
+    for s in (e, o):
+        s.set_particles(w.particles["x"], w.particles["r"], density=w.particles["density"],
+                        fixed=w.particles["fixed"])
+    e.step(1000)
+    o.step(1000)
+    assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
+    Fg, Tg = e.force_torque()
+    Fo, To = o.force_torque()
+    assert force_err(Fg, Fo) < 1e-10
+    assert np.max(np.abs(Tg - To)) < 1e-10 * np.max(np.abs(Fo))
+
+
+@pytest.mark.parametrize("streaming", ["pull", "aa"])
+@pytest.mark.parametrize("relax,eps_mode,weighting", [("trt", "linear", "nt"),
+                                                      ("srt", "supersample", "eps"),
+                                                      ("trt", "supersample", "nt")])
+def test_moving_particles_walls_ragged_grid(capi, streaming, relax, eps_mode, weighting):
+    """37x24x20 cells (x not a multiple of 32: padded lanes), walls on the x
+    faces, noisy initial field, three moving spheres with DEM (contacts with
+    each other and a wall), gravity and body force: 25 steps."""
+    shape = (37, 24, 20)
+    kw = dict(tau=0.57, relax=relax, walls=(1, 1, 0, 0, 0, 0), fbody=(0.0, 1e-5, 2e-5),
+              weighting=weighting, eps_mode=eps_mode, eps_n=4, gravity=(0.0, 0.0, -3e-5),
+              dem=True, kn=100.0, restitution=0.8)
+    e, o = pair(capi, shape, streaming=streaming, **kw)
+    x = np.array([[6.0, 7.5, 9.2], [14.1, 8.3, 10.1], [30.2, 16.7, 3.3]])
+    r = np.array([4.3, 3.6, 3.1])
+    u = np.array([[-2e-3, 1e-3, 0.0], [-1e-3, 0.0, 1e-3], [5e-4, -1e-3, -2e-3]])
+    om = inputs.random_velocities(3, 1e-3, 4)
+    f0 = o.pdfs()
+    f0 = f0 * (1.0 + inputs.noise(f0.shape, 1e-3, 3))
+    for s in (e, o):
+        s.set_pdfs(f0.ravel())
+        s.set_particles(x, r, u=u, omega=om, density=np.array([2.5, 2.0, 3.0]))
+    e.step(25)
+    o.step(25)
+    assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
+    Fg, Tg = e.force_torque()
+    Fo, To = o.force_torque()
+    assert force_err(Fg, Fo) < 1e-10 and force_err(Tg, To) < 1e-10
+    xg, ug, wg = e.particles()
+    xo, uo, wo = o.particles()
+    assert np.max(np.abs(xg - xo)) < 1e-12
+    assert np.max(np.abs(ug - uo)) < 1e-13 and np.max(np.abs(wg - wo)) < 1e-13
+
+
+@pytest.mark.parametrize("eps_mode,eps_n", [("supersample", 4), ("supersample", 8),
+                                            ("supersample", 3), ("linear", 4)])
+def test_mapping_slots(capi, eps_mode, eps_n):
+    """Slots and weights of the mapping, spheres wrapping around the periodic
+    faces, two spheres sharing cells."""
+    shape = (48, 40, 36)
+    e, o = pair(capi, shape, tau=0.6, relax="srt", weighting="nt", eps_mode=eps_mode,
+                eps_n=eps_n)
+    x = np.array([[1.2, 39.4, 17.9], [24.25, 20.0, 18.0], [24.25 + 9.4, 20.3, 18.5],
+                  [46.9, 3.3, 35.2]])
+    r = np.array([5.5, 4.0, 5.0, 3.3])
+    for s in (e, o):
+        s.set_particles(x, r)
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = e.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    assert np.max(np.abs(bg0 - bo0)) < 1e-15 and np.max(np.abs(bg1 - bo1)) < 1e-15
+    assert (pg1 >= 0).sum() > 0
+
+
+def test_aa_equals_pull_bitwise_fp64(capi):
+    """The AA pattern changes where PDFs live, not what is computed: FP64 AA
+    and pull give identical bits after an odd and an even number of steps."""
+    shape = (33, 20, 18)
+    kw = dict(tau=0.62, relax="trt", walls=(1, 1, 0, 0, 0, 0), fbody=(1e-5, 0, 0),
+              weighting="nt", eps_mode="supersample", eps_n=4)
+    a = capi.Engine(*shape, streaming="aa", **kw)
+    b = capi.Engine(*shape, streaming="pull", **kw)
+    x = np.array([[10.2, 9.1, 8.7], [22.4, 11.3, 9.2]])
+    for s in (a, b):
+        s.set_particles(x, np.array([4.0, 3.5]), u=inputs.random_velocities(2, 1e-3, 8),
+                        fixed=np.ones(2, np.uint8))
+    for n in (7, 6):
+        a.step(n)
+        b.step(n)
+        assert np.array_equal(a.pdfs(), b.pdfs())
+        assert np.array_equal(a.force_torque()[0], b.force_torque()[0])
+
+
+def test_no_particles_and_tiny_grid(capi):
+    """Degenerate cases: no particles; a 5x6x7 grid with walls on all faces."""
+    for walls in ((0, 0, 0, 0, 0, 0), (1, 1, 1, 1, 1, 1)):
+        e, o = pair(capi, (5, 6, 7), tau=0.8, relax="trt", walls=walls, fbody=(1e-4, -2e-4, 3e-4))
+        f0 = o.pdfs() * (1.0 + inputs.noise((19, 7, 6, 5), 1e-2, 5))
+        for s in (e, o):
+            s.set_pdfs(f0.ravel())
+        e.step(40)
+        o.step(40)
+        assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
+        rg, ug = e.macroscopic()
+        ro, uo = o.macroscopic()
+        assert np.max(np.abs(rg - ro)) < 1e-13 and np.max(np.abs(ug - uo)) < 1e-13
+
+
+def test_zero_steps_and_mass_check(capi):
+    e = capi.Engine(32, 8, 8, 0.7)
+    e.step(0)
+    m, P = e.check()
+    assert abs(m - 32 * 8 * 8) < 1e-10 and np.max(np.abs(P)) < 1e-13
+
+
+def test_slot_overflow_is_reported(capi):
+    """Three spheres within reach of one cell: the step returns
+    PSM_ERR_SLOT_OVERFLOW and the context refuses further steps."""
+    e = capi.Engine(24, 24, 24, 0.6)
+    c = np.array([12.0, 12.0, 12.0])
+    x = np.array([c + 2.8 * np.array(v) for v in ((1, 0, 0), (-0.5, 0.866, 0), (-0.5, -0.866, 0))])
+    e.set_particles(x, np.array([3.0, 3.0, 3.0]))
+    assert e.step_status(1) == capi.PSM_ERR_SLOT_OVERFLOW
+    assert e.step_status(1) == capi.PSM_ERR_STATE
+    e.set_particles(x[:2], np.array([3.0, 3.0]))
+    assert e.step_status(1) == capi.PSM_OK
+
+
+def test_settle128_full_size_three_steps(capi):
+    """The 128^3 settling workload (400 spheres r = 6, TRT tau = 0.55, DEM,
+    gravity): the launch configuration of the bench, 3 full steps, every
+    PDF compared."""
+    w = inputs.settle128()
+    kw = dict(tau=w.tau, relax=w.relax, gravity=w.gravity, weighting=w.weighting,
+              eps_mode=w.eps_mode, eps_n=w.eps_n, dem=True, kn=w.kn, restitution=w.restitution)
+    e, o = pair(capi, (128, 128, 128), **kw)
+    p = w.particles
+    for s in (e, o):
+        s.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])
+    e.step(3)
+    o.step(3)
+    assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
+    Fg, _ = e.force_torque()
+    Fo, _ = o.force_torque()
+    assert force_err(Fg, Fo) < 1e-10
+    xg, _, _ = e.particles()
+    xo, _, _ = o.particles()
+    assert np.max(np.abs(xg - xo)) < 1e-12
