@@ -1,0 +1,351 @@
+"""Throughput of the LBM-PSM hot path on GB300.
+
+One step = one pass of the whole hot path over the 128^3 settling workload
+(400 spheres r = 6, density ratio 2.5, gravity, TRT tau = 0.55, 4^3 sampling,
+Noble-Torczynski weighting, FP64, pull streaming): particle mapping, fused
+stream + PSM collide, fixed-order force/torque reduction, 10 DEM sub-cycles.
+Inputs are synthetic and seeded (random sequential addition of the spheres).
+
+Prints one JSON line (rank 0): MLUPS of the device-resident loop (``value``),
+the same through the C ABI with host buffers (``e2e``: the particle state goes
+host -> device and the forces and particle state device -> host every step),
+the roofline of the dominant kernel, the FP64 oracle on the host cores
+(``cpu_baseline``), and the FP32 form measured against FP64 on the same GPU.
+
+``--impl reference`` times the FP64 oracle (the plain CPU implementation) on
+the same workload and prints the same line with ``"impl": "reference"``.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LBM-PSM MLUPS and % of HBM roofline; FP32+MLP-eps vs FP64 at drag err<=0.5%"
+WORKLOAD = ("settle128: 128^3 periodic box, 400 spheres r=6 (random sequential addition, "
+            "gap>=1, seed 20230321), density ratio 2.5, gravity 2e-5 in -z, D3Q19 TRT "
+            "(Lambda=3/16) tau=0.55, 4^3 sub-division sampling, Noble-Torczynski B, "
+            "spring-dashpot DEM k_n=1e3 e=0.9 x10 sub-cycles, FP64 PDFs, pull streaming")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(kernel_src, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", f"lbm_kernel_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    want = source_hash(kernel_src)
+    traffic, h = None, None
+    for line in open(path):
+        if line.startswith("source_sha256_16:"):
+            h = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    return traffic if (h == want and traffic) else None
+
+
+def make_engine(w, capi, precision="fp64", streaming="pull", eps_mode=None):
+    e = capi.Engine(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=w.walls, fbody=w.fbody,
+                    weighting=w.weighting, eps_mode=eps_mode or w.eps_mode, eps_n=w.eps_n,
+                    gravity=w.gravity, kn=w.kn, restitution=w.restitution,
+                    subcycles=w.subcycles, dem=w.dem, precision=precision,
+                    streaming=streaming)
+    p = w.particles
+    e.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])
+    return e
+
+
+def timed_steps(e, torch, K):
+    s = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(s)
+    e.step(K)
+    b.record(s)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def oracle_rate(w, seconds, max_steps):
+    """MLUPS of the FP64 oracle on the workload: steps until `seconds`."""
+    from oracle import Oracle
+    o = Oracle(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=w.walls, fbody=w.fbody,
+               weighting=w.weighting, eps_mode=w.eps_mode, eps_n=w.eps_n, gravity=w.gravity,
+               kn=w.kn, restitution=w.restitution, subcycles=w.subcycles, dem=w.dem)
+    p = w.particles
+    o.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])
+    n = 0
+    t0 = time.perf_counter()
+    while n < max_steps:
+        o.step(1)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return w.cells * n / dt / 1e6, n, dt
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return
+    budget = float(os.environ.get("PSM_REFERENCE_SECONDS", "120"))
+    value, n, dt = oracle_rate(w, budget, args.steps + args.warmup)
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / n * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} full steps of settle128 (of {args.steps} requested; "
+                                   f"capped at {budget:.0f} s of host time)"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def forms_comparison(capi, torch, steps):
+    """FP32 deviation storage (AA single buffer) against FP64 on the same GPU:
+    channel workload with fixed spheres, MLUPS of both and the drag and
+    velocity differences after the same number of steps."""
+    from paper_2303_11811_gb300 import inputs
+    w = inputs.channel(nx=128, ny=128, nz=256)
+    out = {"workload": "channel 128x128x256, walls at the x faces, %d fixed spheres r=5 "
+           "(solid fraction 0.20), TRT tau=0.55, body force 1e-5 along z, 4^3 sampling"
+           % w.particles["r"].size}
+    res = {}
+    for name, prec, stream in (("fp64_pull", "fp64", "pull"), ("fp32_aa", "fp32", "aa")):
+        e = make_engine(w, capi, precision=prec, streaming=stream)
+        e.step(3)
+        ms = timed_steps(e, torch, steps)
+        F, _ = e.force_torque()
+        _, u = e.macroscopic()
+        res[name] = (w.cells * steps / (ms * 1e-3) / 1e6, F, u)
+        e.close()
+    F64, F32 = res["fp64_pull"][1], res["fp32_aa"][1]
+    u64, u32 = res["fp64_pull"][2], res["fp32_aa"][2]
+    out["fp64_mlups"] = res["fp64_pull"][0]
+    out["fp32_mlups"] = res["fp32_aa"][0]
+    out["speedup_fp32_vs_fp64"] = res["fp32_aa"][0] / res["fp64_pull"][0]
+    out["steps"] = steps
+    out["drag_rel_err"] = float(np.linalg.norm(F32 - F64) / np.linalg.norm(F64))
+    out["velocity_rel_err"] = float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2303_11811_gb300 import inputs
+    w = inputs.settle128()
+
+    if args.impl == "reference":
+        import oracle
+        oracle.build()
+        run_reference(args, w, world, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2303_11811_gb300 import build, capi
+    if rank == 0 or world == 1:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    e = make_engine(w, capi)
+    e.step(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    ms = timed_steps(e, torch, args.steps)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = e.last_launch_count()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    cells = w.cells
+    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+
+    # dominant kernel: per-class CUDA-event timings over a second pass of the
+    # same loop (steps launched without graphs, events on the same stream)
+    kr = min(args.steps, 100)
+    e.set_timing(True)
+    e.step(kr)
+    t = e.timings()
+    e.set_timing(False)
+    lbm_ms = t[1] / t[4]
+    p0, _, _, _ = e.slots()
+    ncov = int((p0 >= 0).sum())
+    bytes_lbm = cells * 19 * 2 * 8
+    bytes_psm = bytes_lbm + ncov * 24
+    hbm, peak_kind = peaks()
+    achieved = bytes_psm / (lbm_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_2303_11811_gb300", "csrc",
+                                            "lbm_kernels.cu"), "settle128")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "kernel": "lbm_kernel<double,pull>", "peak_source": peak_kind,
+                "bytes_per_launch": bytes_psm, "lbm_only_bytes_per_launch": bytes_lbm,
+                "covered_cells": ncov, "avg_launch_ms": lbm_ms,
+                "class_ms_per_step": {"mapping": t[0] / t[4], "stream_collide": lbm_ms,
+                                      "force_reduce": t[2] / t[4], "dem": t[3] / t[4]}}
+
+    # end to end through the C ABI with host buffers in pinned memory
+    n = w.particles["r"].size
+    xs, us, oms = e.particles()
+    hx = torch.from_numpy(xs.copy()).pin_memory()
+    hu = torch.from_numpy(us.copy()).pin_memory()
+    ho = torch.from_numpy(oms.copy()).pin_memory()
+    hF = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    hT = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
+    ke = max(10, min(args.steps, 100))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        e.update_particles(hx.data_ptr(), hu.data_ptr(), ho.data_ptr())
+        e.step(1)
+        e.force_torque_into(hF.data_ptr(), hT.data_ptr())
+        e.particles_into(hx.data_ptr(), hu.data_ptr(), ho.data_ptr())
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    e2e = {"value": cells * ke * world / te / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 3 * 3 * n * 8, "d2h_bytes_per_step": (6 + 9) * n * 8,
+           "steps": ke}
+    e.close()
+
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = forms_comparison(capi, torch, min(args.steps, 100))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, nst, dt = oracle_rate(w, args.cpu_seconds, 1000)
+        cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{nst} full steps of settle128 on one host core ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": cells,
+                       "l2": "working set 638 MB (two FP64 PDF buffers) > 126 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
+            "cpu_baseline": cpu, "forms": forms,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -132,6 +132,13 @@ psm_status psm_set_particles(psm_ctx* ctx, int n, const double* x, const double*
                              const double* u, const double* omega,
                              const double* density, const unsigned char* fixed);
 
+/* Overwrites the centres, velocities and angular velocities (n*3 each, n as
+ * set) of the current particles from host arrays, keeping radii, densities
+ * and forces; the next step re-maps.  This is the per-step host->device
+ * particle transfer of a hybrid CPU-GPU loop (Sec. 3.1.1). */
+psm_status psm_update_particles(psm_ctx* ctx, const double* x, const double* u,
+                                const double* omega);
+
 /* Advances nsteps time steps: mapping (when particles moved or were set),
  * PSM stream-collide, force/torque reduction, DEM sub-cycles. */
 psm_status psm_step(psm_ctx* ctx, int nsteps);
@@ -193,11 +200,13 @@ psm_status psm_mlp_loss_grad(psm_ctx* ctx, const float* params, long m, const fl
 psm_status psm_mlp_infer(psm_ctx* ctx, const float* params, long m, const float* X,
                          float* eps);
 
-/* Event timings (ms) of the kernel classes over the last psm_step call:
- * out[0] mapping, out[1] PSM stream-collide, out[2] force/torque reduction,
- * out[3] DEM; requires timing = 1. */
+/* Event timings (ms) of the kernel classes, summed over the psm_step calls
+ * since timing was enabled: out[0] mapping, out[1] PSM stream-collide,
+ * out[2] force/torque reduction, out[3] DEM, out[4] steps timed.  With timing
+ * on, steps are launched without graphs and bracketed by CUDA events on the
+ * context's stream (no host synchronisation inside psm_step). */
 psm_status psm_set_timing(psm_ctx* ctx, int enable);
-psm_status psm_get_timings(psm_ctx* ctx, double* out4);
+psm_status psm_get_timings(psm_ctx* ctx, double* out5);
 
 /* Kernel launches queued by the last psm_step call (all of this library's
  * kernels, graph nodes included). */

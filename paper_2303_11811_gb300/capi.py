@@ -29,7 +29,8 @@ PSM_MLP_PARAMS = 1249
 Q = 19
 
 EXPORTS = [
-    "psm_default_options", "psm_create", "psm_set_particles", "psm_step",
+    "psm_default_options", "psm_create", "psm_set_particles", "psm_update_particles",
+    "psm_step",
     "psm_get_force_torque", "psm_get_macroscopic", "psm_get_particles", "psm_get_pdfs",
     "psm_set_pdfs", "psm_get_slots", "psm_check", "psm_set_mlp", "psm_get_mlp",
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
@@ -79,6 +80,8 @@ def lib():
     L.psm_create.restype = st
     L.psm_set_particles.argtypes = [P, C.c_int, dp, dp, dp, dp, dp, C.c_void_p]
     L.psm_set_particles.restype = st
+    L.psm_update_particles.argtypes = [P, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.psm_update_particles.restype = st
     L.psm_step.argtypes = [P, C.c_int]
     L.psm_step.restype = st
     for name in ("psm_get_force_torque",):
@@ -260,6 +263,30 @@ class Engine:
             fx.ctypes.data_as(C.c_void_p) if fx is not None else None))
         self.np = n
 
+    def update_particles(self, x, u, omega):
+        """x, u, omega: float64 numpy arrays (n x 3), or integer host addresses
+        (e.g. the data_ptr() of pinned torch tensors)."""
+        args = []
+        for a in (x, u, omega):
+            if isinstance(a, int):
+                args.append(C.c_void_p(a))
+            else:
+                a = _f64(a, 3 * self.np)
+                args.append(a.ctypes.data_as(C.c_void_p))
+                self._keep_upd = getattr(self, "_keep_upd", []) + [a]
+        self._check(self._L.psm_update_particles(self.h, *args))
+        self._keep_upd = []
+
+    def force_torque_into(self, F_addr, T_addr):
+        """psm_get_force_torque into caller-owned host buffers (addresses)."""
+        dp = C.POINTER(C.c_double)
+        self._check(self._L.psm_get_force_torque(self.h, C.cast(F_addr, dp), C.cast(T_addr, dp)))
+
+    def particles_into(self, x_addr, u_addr, om_addr):
+        dp = C.POINTER(C.c_double)
+        self._check(self._L.psm_get_particles(self.h, C.cast(x_addr, dp), C.cast(u_addr, dp),
+                                              C.cast(om_addr, dp)))
+
     def step(self, n=1):
         return self._check(self._L.psm_step(self.h, int(n)))
 
@@ -358,7 +385,8 @@ class Engine:
         self._check(self._L.psm_set_timing(self.h, int(bool(on))))
 
     def timings(self):
-        t = np.zeros(4)
+        """[mapping, stream-collide, force reduction, DEM] ms summed, steps."""
+        t = np.zeros(5)
         self._check(self._L.psm_get_timings(self.h, _dp(t)))
         return t
 

@@ -402,6 +402,19 @@ __global__ void pack_particles_kernel(Particles p) {
   p.omf[4 * i + 3] = 0.f;
 }
 
+// positions along periodic axes wrapped into the box (host-supplied states)
+__global__ void wrap_particles_kernel(Grid g, Particles p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  const int dims[3] = {g.nx, g.ny, g.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (g.wall[a]) continue;
+    double v = fmod(p.x[3 * i + a], (double)dims[a]);
+    if (v < 0.0) v += dims[a];
+    p.x[3 * i + a] = v;
+  }
+}
+
 __global__ void dense_clear_kernel(long long N, int* pid0, double* B0, int* pid1, double* B1) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
@@ -507,6 +520,12 @@ int launch_force_reduce(MapParams P, cudaStream_t s) {
 int launch_pack_particles(Particles p, cudaStream_t s) {
   if (p.n == 0) return 0;
   pack_particles_kernel<<<(p.n + 127) / 128, 128, 0, s>>>(p);
+  return 1;
+}
+
+int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s) {
+  if (p.n == 0) return 0;
+  wrap_particles_kernel<<<(p.n + 127) / 128, 128, 0, s>>>(g, p);
   return 1;
 }
 

@@ -60,8 +60,11 @@ struct psm_ctx {
   long graph_launches[2][2] = {{0, 0}, {0, 0}};
   long launches = 0;
   bool timing = false;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  double t_ms[4] = {0, 0, 0, 0};
+  static constexpr int kTimedRing = 64;   // steps whose events are in flight
+  std::vector<cudaEvent_t> tev;           // 5 events per ring slot
+  int tpending = 0;                       // recorded, not yet accumulated
+  cudaEvent_t* ev = nullptr;              // events of the step being enqueued
+  double t_ms[5] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -222,6 +225,23 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   return n;
 }
 
+// adds the event intervals of the pending timed steps to t_ms
+cudaError_t flush_timing(psm_ctx* c) {
+  for (int k = 0; k < c->tpending; ++k) {
+    cudaEvent_t* e = &c->tev[5 * k];
+    cudaError_t err = cudaEventSynchronize(e[4]);
+    if (err != cudaSuccess) return err;
+    for (int i = 0; i < 4; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e[i], e[i + 1]);
+      c->t_ms[i] += ms;
+    }
+    c->t_ms[4] += 1;
+  }
+  c->tpending = 0;
+  return cudaSuccess;
+}
+
 void advance_state(psm_ctx* c) {
   if (c->aa) c->parity ^= 1;
   else c->cur ^= 1;
@@ -376,7 +396,6 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "cudaStreamCreate failed");
   }
-  for (int i = 0; i < 5; ++i) cudaEventCreate(&c->ev[i]);
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "initialisation kernel failed");
@@ -526,15 +545,12 @@ psm_status psm_step(psm_ctx* c, int nsteps) {
       CK(cudaGraphLaunch(ge, c->stream));
       c->launches += c->graph_launches[si][with_map ? 1 : 0];
     } else {
-      c->launches += enqueue_step(c, with_map, c->stream);
       if (c->timing) {
-        CK(cudaEventSynchronize(c->ev[4]));
-        for (int i = 0; i < 4; ++i) {
-          float ms = 0;
-          cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]);
-          c->t_ms[i] += ms;
-        }
+        if (c->tpending == psm_ctx::kTimedRing) CK(flush_timing(c));
+        c->ev = &c->tev[5 * c->tpending];
+        ++c->tpending;
       }
+      c->launches += enqueue_step(c, with_map, c->stream);
     }
     CK(cudaGetLastError());
     if (with_map) c->need_map = c->any_free;
@@ -806,14 +822,35 @@ psm_status psm_train_surrogate(psm_ctx* c, long nsamples, unsigned long long see
 
 psm_status psm_set_timing(psm_ctx* c, int enable) {
   if (!c) return PSM_ERR_ARG;
+  if (enable && c->tev.empty()) {
+    c->tev.resize(5 * psm_ctx::kTimedRing);
+    for (auto& e : c->tev) CK(cudaEventCreate(&e));
+  }
+  CK(flush_timing(c));
   c->timing = enable != 0;
-  for (int i = 0; i < 4; ++i) c->t_ms[i] = 0;
+  for (int i = 0; i < 5; ++i) c->t_ms[i] = 0;
   return PSM_OK;
 }
 
-psm_status psm_get_timings(psm_ctx* c, double* out4) {
-  if (!c || !out4) return PSM_ERR_ARG;
-  for (int i = 0; i < 4; ++i) out4[i] = c->t_ms[i];
+psm_status psm_get_timings(psm_ctx* c, double* out5) {
+  if (!c || !out5) return PSM_ERR_ARG;
+  CK(flush_timing(c));
+  for (int i = 0; i < 5; ++i) out5[i] = c->t_ms[i];
+  return PSM_OK;
+}
+
+psm_status psm_update_particles(psm_ctx* c, const double* x, const double* u, const double* om) {
+  if (!c) return PSM_ERR_ARG;
+  const int n = c->p.n;
+  if (n == 0) return PSM_OK;
+  if (!x || !u || !om) return fail(c, PSM_ERR_ARG, "NULL particle array");
+  const size_t b3 = sizeof(double) * 3 * n;
+  CK(cudaMemcpyAsync(c->p.x, x, b3, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->p.u, u, b3, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->p.om, om, b3, cudaMemcpyHostToDevice, c->stream));
+  launch_wrap_particles(c->g, c->p, c->stream);
+  CK(cudaGetLastError());
+  c->need_map = true;
   return PSM_OK;
 }
 
@@ -831,8 +868,8 @@ void psm_destroy(psm_ctx* c) {
   free_particles(c);
   for (void* q : c->allocs) dfree(c, q);
   c->allocs.clear();
-  for (int i = 0; i < 5; ++i)
-    if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+  for (auto& e : c->tev)
+    if (e) cudaEventDestroy(e);
   if (c->capture) cudaStreamDestroy(c->capture);
   delete c;
 }

@@ -148,6 +148,7 @@ int launch_map(MapParams P, cudaStream_t s);                   // full mapping
 int launch_force_reduce(MapParams P, cudaStream_t s);          // fixed-order F/T
 int launch_force_reduce_atomic_finish(MapParams P, cudaStream_t s);
 int launch_pack_particles(Particles p, cudaStream_t s);
+int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s);
 int launch_slots_to_dense(MapParams P, int* pid0, double* B0, int* pid1, double* B1,
                           cudaStream_t s);
 

@@ -56,7 +56,7 @@ class Workload:
         return self.nx * self.ny * self.nz
 
 
-def rsa_spheres(dims, walls, radii, gap, seed, max_tries=200):
+def rsa_spheres(dims, walls, radii, gap, seed, max_tries=100000):
     """Random sequential addition of non-overlapping spheres.
 
     ``radii`` is the list of radii in placement order; each sphere is drawn
