@@ -1,32 +1,73 @@
 // geom.cuh -- sub-division sampling of a cell against a sphere (paper
 // Sec. 2.3.2), shared by the mapping and the surrogate's training sampler.
-// Plain IEEE FP64 operations; files including it are compiled with -fmad=false.
+//
+// The definition is an FP64 computation: sample offsets
+//   s_a = (a + 1/2)/n - 1/2,  p = d + s,  inside <=> ((p_x^2 + p_y^2) + p_z^2) <= r^2
+// with every operation rounded in FP64 (files including this are compiled with
+// -fmad=false).  FP64 runs at 1/58 of the FP32 rate on this GPU, so the count
+// is evaluated in FP32 and a sample goes to the FP64 definition only when its
+// FP32 value lies within a certified bound E of r^2:
+//   |S_fp32 - S_fp64| <= 2^-19 (r + 2.5)^2 for |d| <= r + 2 (each of the three
+//   squared terms is off by at most 2^-21 (r + 2.5)^2, the two sums by
+//   2^-24 S each), |fl32(r^2) - r^2| <= 2^-24 r^2, so E = 2^-18 (r + 2.5)^2.
+// Outside that band the FP32 decision equals the FP64 one, so the count is
+// exactly the FP64 definition's.
 #pragma once
 
 namespace psm {
 
 constexpr double kHalfSqrt3 = 0.86602540378443864676;
 
-// number of the n^3 sub-cell centres d + s, s_a = (a + 1/2)/n - 1/2, that lie
-// inside the sphere of radius r centred at the origin (|p|^2 <= r^2)
-__device__ inline int supersample_count(double dx, double dy, double dz, double r, int n) {
+__device__ __forceinline__ double sample_offset(int a, int n) { return (a + 0.5) / n - 0.5; }
+
+// FP64 definition for one sample point
+__device__ __forceinline__ bool sample_inside_fp64(double dx, double dy, double dz, double sx,
+                                                   double sy, double sz, double r2) {
+  const double px = dx + sx, py = dy + sy, pz = dz + sz;
+  return px * px + py * py + pz * pz <= r2;
+}
+
+__device__ __forceinline__ float certified_band(double r) {
+  const float q = (float)r + 2.5f;
+  return 3.8147e-6f * q * q;  // 2^-18 (r + 2.5)^2, rounded up
+}
+
+// count of the n^3 sample points inside; s64/s32 hold the n offsets
+__device__ inline int supersample_count_fast(double dx, double dy, double dz, double r, int n,
+                                             const double* s64, const float* s32) {
   const double r2 = r * r;
+  const float r2f = (float)r2;
+  const float E = certified_band(r);
+  const float lo = r2f - E, hi = r2f + E;
+  const float dxf = (float)dx, dyf = (float)dy, dzf = (float)dz;
   int count = 0;
   for (int a = 0; a < n; ++a) {
-    const double sx = (a + 0.5) / n - 0.5;
-    const double px = dx + sx;
-    const double X = px * px;
+    const float px = dxf + s32[a];
+    const float X = px * px;
     for (int b = 0; b < n; ++b) {
-      const double sy = (b + 0.5) / n - 0.5;
-      const double py = dy + sy;
-      const double XY = X + py * py;
+      const float py = dyf + s32[b];
+      const float XY = X + py * py;
       for (int c = 0; c < n; ++c) {
-        const double sz = (c + 0.5) / n - 0.5;
-        const double pz = dz + sz;
-        if (XY + pz * pz <= r2) ++count;
+        const float pz = dzf + s32[c];
+        const float S = XY + pz * pz;
+        if (S < lo) ++count;
+        else if (S <= hi && sample_inside_fp64(dx, dy, dz, s64[a], s64[b], s64[c], r2)) ++count;
       }
     }
   }
+  return count;
+}
+
+// FP64 definition, all samples (reference for small counts and tests)
+__device__ inline int supersample_count(double dx, double dy, double dz, double r, int n) {
+  const double r2 = r * r;
+  int count = 0;
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b)
+      for (int c = 0; c < n; ++c)
+        if (sample_inside_fp64(dx, dy, dz, sample_offset(a, n), sample_offset(b, n),
+                               sample_offset(c, n), r2))
+          ++count;
   return count;
 }
 

@@ -8,47 +8,65 @@
 //   2. scan   exclusive prefix count of the mask words gives each covered
 //             cell its slot-table index, in cell order;
 //   3. fill   each (particle, covered cell) pair claims one of the cell's two
-//             slots and stores B_i = W(eps_i);
-//   4. finish slots are ordered by particle index, MLP-mode cells get their
-//             eps, and B > 1 is normalised (every B_i divided by the sum).
-// Distances, sample points and reach tests use plain IEEE FP64 operations
-// (no fused multiply-add: this file is compiled with -fmad=false) so the
-// decisions they take are the ones the FP64 definition takes.
-#include "psm_internal.cuh"
+//             slots, stores B_i = W(eps_i) and appends the entry to the
+//             particle's list (box order, deterministic);
+//   4. finish slots are ordered by particle index, MLP-mode and fallback cells
+//             get their eps, and B > 1 is normalised (every B_i divided by
+//             the sum).
+// Reach tests and sub-cell sampling take the FP64 definition's decisions: FP32
+// with a certified band and FP64 inside the band (geom.cuh); this file is
+// compiled with -fmad=false.
 #include "geom.cuh"
+#include "psm_internal.cuh"
 
 namespace psm {
 namespace {
 
 constexpr double HALF_SQRT3 = kHalfSqrt3;
 constexpr int MAP_THREADS = 128;
+constexpr int RED_THREADS = 128;
+constexpr int SCAN_THREADS = 1024;
 
 struct Box {
   int lo[3], n[3];
-  long long count;
+  int count;
+  int ip[3];          // floor of the centre
+  float fpf[3];       // centre minus its floor, rounded to FP32
+  double xp[3];
+  double r;
+  double reach2;      // (r + sqrt(3)/2)^2 in FP64
+  float reach2f, E;   // its FP32 value and the certified band of geom.cuh
 };
 
-__device__ __forceinline__ Box particle_box(const Grid& g, double x0, double x1, double x2,
-                                            double r) {
+__device__ __forceinline__ Box particle_box(const Grid& g, const double* x, double r) {
   Box b;
-  const double xp[3] = {x0, x1, x2};
   const int dims[3] = {g.nx, g.ny, g.nz};
   for (int a = 0; a < 3; ++a) {
-    int lo = (int)floor(xp[a] - r - 1.0);
-    int hi = (int)floor(xp[a] + r + 1.0);
+    const double xp = x[a];
+    int lo = (int)floor(xp - r - 1.0);
+    int hi = (int)floor(xp + r + 1.0);
     if (g.wall[a]) {
       if (lo < 0) lo = 0;
       if (hi > dims[a] - 1) hi = dims[a] - 1;
     }
     b.lo[a] = lo;
     b.n[a] = hi >= lo ? hi - lo + 1 : 0;
+    b.xp[a] = xp;
+    const double fl = floor(xp);
+    b.ip[a] = (int)fl;
+    b.fpf[a] = (float)(xp - fl);
   }
-  b.count = (long long)b.n[0] * b.n[1] * b.n[2];
+  b.count = b.n[0] * b.n[1] * b.n[2];
+  b.r = r;
+  const double reach = r + HALF_SQRT3;
+  b.reach2 = reach * reach;
+  b.reach2f = (float)b.reach2;
+  b.E = certified_band(r);
   return b;
 }
 
 __device__ __forceinline__ int wrap(int k, int n) {
-  int i = k % n;
+  const int i = k % n;
   return i < 0 ? i + n : i;
 }
 
@@ -62,32 +80,52 @@ __device__ __forceinline__ double image_d(int i, double xp, int n, int periodic)
   return d;
 }
 
+// One cell of a particle's bounding box.  Box coordinates k are unwrapped
+// around the centre and the box is narrower than half a periodic box, so
+// ((double)k + 1/2) - x_p is the nearest-image offset.
 struct CellHit {
   int ix, iy, iz;
+  int kx, ky, kz;
   double dx, dy, dz, d2;
 };
 
-__device__ __forceinline__ void box_cell(const Grid& g, const Box& b, long long t, double x0,
-                                         double x1, double x2, CellHit& h) {
-  const int kx = b.lo[0] + (int)(t % b.n[0]);
-  const int ky = b.lo[1] + (int)((t / b.n[0]) % b.n[1]);
-  const int kz = b.lo[2] + (int)(t / ((long long)b.n[0] * b.n[1]));
-  h.ix = wrap(kx, g.nx);
-  h.iy = wrap(ky, g.ny);
-  h.iz = wrap(kz, g.nz);
-  h.dx = image_d(h.ix, x0, g.nx, !g.wall[0]);
-  h.dy = image_d(h.iy, x1, g.ny, !g.wall[1]);
-  h.dz = image_d(h.iz, x2, g.nz, !g.wall[2]);
-  h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
+__device__ __forceinline__ void box_coords(const Grid& g, const Box& b, int t, CellHit& h) {
+  const int nxy = b.n[0] * b.n[1];
+  const int kz = t / nxy;
+  const int rem = t - kz * nxy;
+  const int ky = rem / b.n[0];
+  h.kx = b.lo[0] + (rem - ky * b.n[0]);
+  h.ky = b.lo[1] + ky;
+  h.kz = b.lo[2] + kz;
+  h.ix = wrap(h.kx, g.nx);
+  h.iy = wrap(h.ky, g.ny);
+  h.iz = wrap(h.kz, g.nz);
 }
 
-__device__ __forceinline__ bool in_reach(double d2, double r) {
-  const double reach = r + HALF_SQRT3;
-  return d2 < reach * reach;
+// reach test of the FP64 definition, evaluated in FP32 outside the certified
+// band; fills the FP64 offsets and squared distance of a cell in reach
+__device__ __forceinline__ bool reach_test(const Box& b, CellHit& h) {
+  const float dxf = (float)(h.kx - b.ip[0]) + (0.5f - b.fpf[0]);
+  const float dyf = (float)(h.ky - b.ip[1]) + (0.5f - b.fpf[1]);
+  const float dzf = (float)(h.kz - b.ip[2]) + (0.5f - b.fpf[2]);
+  const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+  if (d2f > b.reach2f + b.E) return false;
+  h.dx = ((double)h.kx + 0.5) - b.xp[0];
+  h.dy = ((double)h.ky + 0.5) - b.xp[1];
+  h.dz = ((double)h.kz + 0.5) - b.xp[2];
+  h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
+  if (d2f < b.reach2f - b.E) return true;
+  return h.d2 < b.reach2;
 }
 
 __device__ __forceinline__ long long padded_cell(const Grid& g, int x, int y, int z) {
   return (long long)x + (long long)g.nxp * ((long long)y + (long long)g.ny * z);
+}
+
+__device__ __forceinline__ void cell_xyz(const Grid& g, int cell, int& x, int& y, int& z) {
+  x = cell % g.nxp;
+  y = (cell / g.nxp) % g.ny;
+  z = cell / (g.nxp * g.ny);
 }
 
 __device__ __forceinline__ double weight(double eps, double tau, int nt) {
@@ -95,23 +133,47 @@ __device__ __forceinline__ double weight(double eps, double tau, int nt) {
   return eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5));
 }
 
-__global__ void mark_kernel(MapParams P) {
+__device__ __forceinline__ void store_B(const MapParams& P, long long e, int s, double B) {
+  if (P.fp32) reinterpret_cast<float*>(static_cast<float2*>(P.s.B) + e)[s] = (float)B;
+  else reinterpret_cast<double*>(static_cast<double2*>(P.s.B) + e)[s] = B;
+}
+__device__ __forceinline__ double load_B(const MapParams& P, long long e, int s) {
+  if (P.fp32) return (double)reinterpret_cast<const float*>(static_cast<float2*>(P.s.B) + e)[s];
+  return reinterpret_cast<const double*>(static_cast<double2*>(P.s.B) + e)[s];
+}
+
+__device__ __forceinline__ long long slot_index(const Coverage& cov, long long cell) {
+  const long long w = cell >> 5;
+  const uint32_t below = (1u << (cell & 31)) - 1u;
+  return (long long)cov.base[w] + __popc(cov.mask[w] & below);
+}
+
+__device__ __forceinline__ int slot_count(const MapParams& P) {
+  const long long n = *P.cov.ncov;
+  return (int)(n < P.s.cap ? n : P.s.cap);
+}
+
+__device__ __forceinline__ void load_offsets(int n, double* s64, float* s32) {
+  if (threadIdx.x < n) {
+    s64[threadIdx.x] = sample_offset(threadIdx.x, n);
+    s32[threadIdx.x] = (float)s64[threadIdx.x];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   const int p = blockIdx.x;
-  const double x0 = P.p.x[3 * p], x1 = P.p.x[3 * p + 1], x2 = P.p.x[3 * p + 2];
-  const double r = P.p.r[p];
-  const Box b = particle_box(P.g, x0, x1, x2, r);
-  for (long long t = threadIdx.x; t < b.count; t += blockDim.x) {
+  const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
+  for (int t = threadIdx.x; t < b.count; t += MAP_THREADS) {
     CellHit h;
-    box_cell(P.g, b, t, x0, x1, x2, h);
-    if (!in_reach(h.d2, r)) continue;
+    box_coords(P.g, b, t, h);
+    if (!reach_test(b, h)) continue;
     const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
     atomicOr(&P.cov.mask[cell >> 5], 1u << (cell & 31));
   }
 }
 
 // ---- exclusive scan of the popcounts of the mask words
-constexpr int SCAN_THREADS = 1024;
-
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   __shared__ int warp_sums[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -169,11 +231,6 @@ __global__ void scan_add_kernel(Coverage cov, long long nwords) {
   if (w < nwords) cov.base[w] += cov.blocksum[blockIdx.x];
 }
 
-__device__ __forceinline__ int slot_count(const MapParams& P) {
-  const long long n = *P.cov.ncov;
-  return (int)(n < P.s.cap ? n : P.s.cap);
-}
-
 __global__ void clear_slots_kernel(MapParams P) {
   const int n = slot_count(P);
   if (blockIdx.x == 0 && threadIdx.x == 0 && *P.cov.ncov > P.s.cap)
@@ -186,26 +243,12 @@ __global__ void clear_slots_kernel(MapParams P) {
   }
 }
 
-__device__ __forceinline__ void store_B(const MapParams& P, long long e, int s, double B) {
-  if (P.fp32) reinterpret_cast<float*>(static_cast<float2*>(P.s.B) + e)[s] = (float)B;
-  else reinterpret_cast<double*>(static_cast<double2*>(P.s.B) + e)[s] = B;
-}
-__device__ __forceinline__ double load_B(const MapParams& P, long long e, int s) {
-  if (P.fp32) return (double)reinterpret_cast<const float*>(static_cast<float2*>(P.s.B) + e)[s];
-  return reinterpret_cast<const double*>(static_cast<double2*>(P.s.B) + e)[s];
-}
-
-__device__ __forceinline__ long long slot_index(const Coverage& cov, long long cell) {
-  const long long w = cell >> 5;
-  const uint32_t below = (1u << (cell & 31)) - 1u;
-  return (long long)cov.base[w] + __popc(cov.mask[w] & below);
-}
-
-// eps of a cell for one particle; returns -1 for "resolve in the finish pass"
-__device__ double cell_eps(const MapParams& P, const CellHit& h, double r, double fr) {
+// eps of a cell for one particle; -1 means "resolved in a later pass"
+__device__ double cell_eps(const MapParams& P, const CellHit& h, double r, double fr,
+                           const double* s64, const float* s32) {
   const double rin = r - HALF_SQRT3;
   if (rin > 0.0 && h.d2 <= rin * rin) return 1.0;
-  if (P.eps_mode == 1) {
+  if (P.eps_mode == 1) {  // Eqs. 25-26
     const double dist = sqrt(h.d2);
     const double D = dist - r;
     double e = -D + fr;
@@ -214,32 +257,65 @@ __device__ double cell_eps(const MapParams& P, const CellHit& h, double r, doubl
     return e;
   }
   if (P.eps_mode == 2) return -1.0;
-  return (double)supersample_count(h.dx, h.dy, h.dz, r, P.eps_n) /
-         ((double)P.eps_n * P.eps_n * P.eps_n);
+  const int n = P.eps_n;
+  return (double)supersample_count_fast(h.dx, h.dy, h.dz, r, n, s64, s32) /
+         ((double)n * n * n);
 }
 
-__global__ void fill_kernel(MapParams P) {
+// claims the slots of one particle's cells and lists them in box order
+__global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
+  __shared__ double s64[16];
+  __shared__ float s32[16];
+  __shared__ int warp_tot[MAP_THREADS / 32];
+  __shared__ int running;
   const int p = blockIdx.x;
-  const double x0 = P.p.x[3 * p], x1 = P.p.x[3 * p + 1], x2 = P.p.x[3 * p + 2];
-  const double r = P.p.r[p];
+  const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const double fr = P.p.fr[p];
-  const Box b = particle_box(P.g, x0, x1, x2, r);
-  for (long long t = threadIdx.x; t < b.count; t += blockDim.x) {
+  if (threadIdx.x == 0) running = 0;
+  load_offsets(P.eps_n, s64, s32);
+  const long long loff = P.list_off[p];
+  const int lcap = (int)(P.list_off[p + 1] - loff);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
+    const int t = t0 + threadIdx.x;
     CellHit h;
-    box_cell(P.g, b, t, x0, x1, x2, h);
-    if (!in_reach(h.d2, r)) continue;
-    const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-    const long long e = slot_index(P.cov, cell);
-    if (e >= P.s.cap) continue;
-    const int s = atomicAdd(&P.s.cnt[e], 1);
-    if (s >= 2) {
-      atomicOr(P.status, ST_SLOT_OVERFLOW);
-      continue;
+    bool in = false;
+    if (t < b.count) {
+      box_coords(P.g, b, t, h);
+      in = reach_test(b, h);
     }
-    P.s.cell[e] = (int)cell;
-    reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
-    const double eps = cell_eps(P, h, r, fr);
-    store_B(P, e, s, eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting));
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    __syncthreads();
+    int before = running, chunk = 0;
+    for (int w = 0; w < MAP_THREADS / 32; ++w) {
+      if (w < wid) before += warp_tot[w];
+      chunk += warp_tot[w];
+    }
+    const int pos = before + __popc(bal & ((1u << lane) - 1u));
+    if (in) {
+      const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
+      const long long e = slot_index(P.cov, cell);
+      if (e < P.s.cap) {
+        if (pos < lcap) P.list[loff + pos] = (int)e;
+        const int s = atomicAdd(&P.s.cnt[e], 1);
+        if (s >= 2) {
+          atomicOr(P.status, ST_SLOT_OVERFLOW);
+        } else {
+          P.s.cell[e] = (int)cell;
+          reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
+          const double eps = cell_eps(P, h, b.r, fr, s64, s32);
+          store_B(P, e, s, eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting));
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) running += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.list_cnt[p] = running < lcap ? running : lcap;
+    if (running > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
   }
 }
 
@@ -252,10 +328,8 @@ __global__ void classify_kernel(MapParams P) {
     if (P.s.cnt[e] != 1) continue;
     const int2 pid = P.s.pid[e];
     if (pid.x < 0 || load_B(P, e, 0) >= 0.0) continue;
-    const int cell = P.s.cell[e];
-    const int x = cell % P.g.nxp;
-    const int y = (cell / P.g.nxp) % P.g.ny;
-    const int z = cell / (P.g.nxp * P.g.ny);
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
     const bool wall = (P.g.wall[0] && (x == 0 || x == P.g.nx - 1)) ||
                       (P.g.wall[1] && (y == 0 || y == P.g.ny - 1)) ||
                       (P.g.wall[2] && (z == 0 || z == P.g.nz - 1));
@@ -282,21 +356,26 @@ __global__ void apply_mlp_kernel(MapParams P) {
 
 __global__ void finish_kernel(MapParams P) {
   __shared__ double red[256];
+  __shared__ double s64[16];
+  __shared__ float s32[16];
+  load_offsets(8, s64, s32);
   const int n = slot_count(P);
   double accB = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int2 pid = P.s.pid[e];
     double B0 = load_B(P, e, 0), B1 = load_B(P, e, 1);
     if (pid.y >= 0 && pid.y < pid.x) {
-      const int t = pid.x; pid.x = pid.y; pid.y = t;
-      const double tb = B0; B0 = B1; B1 = tb;
+      const int t = pid.x;
+      pid.x = pid.y;
+      pid.y = t;
+      const double tb = B0;
+      B0 = B1;
+      B1 = tb;
     }
     if (B0 < 0.0 || B1 < 0.0) {
       // cells left for the surrogate and not taken by it: 8^3 sampling
-      const int cell = P.s.cell[e];
-      const int x = cell % P.g.nxp;
-      const int y = (cell / P.g.nxp) % P.g.ny;
-      const int z = cell / (P.g.nxp * P.g.ny);
+      int x, y, z;
+      cell_xyz(P.g, P.s.cell[e], x, y, z);
       for (int s = 0; s < 2; ++s) {
         const int p = s ? pid.y : pid.x;
         double& Bs = s ? B1 : B0;
@@ -305,7 +384,7 @@ __global__ void finish_kernel(MapParams P) {
         const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
         const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
         const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-        const double eps = (double)supersample_count(dx, dy, dz, r, 8) / 512.0;
+        const double eps = (double)supersample_count_fast(dx, dy, dz, r, 8, s64, s32) / 512.0;
         Bs = weight(eps, P.tau, P.weighting);
       }
     }
@@ -339,37 +418,35 @@ __global__ void vfluid_kernel(MapParams P, int nparts) {
   }
 }
 
-// ---- fixed-order force and torque reduction, one block per particle
-constexpr int RED_THREADS = 128;
-
+// ---- fixed-order force and torque reduction over each particle's list
 template <typename T>
-__global__ void force_reduce_kernel(MapParams P) {
+__global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) {
   __shared__ double sh[6][RED_THREADS];
   const int p = blockIdx.x;
-  const double x0 = P.p.x[3 * p], x1 = P.p.x[3 * p + 1], x2 = P.p.x[3 * p + 2];
-  const double r = P.p.r[p];
-  const Box b = particle_box(P.g, x0, x1, x2, r);
+  const double xp0 = P.p.x[3 * p], xp1 = P.p.x[3 * p + 1], xp2 = P.p.x[3 * p + 2];
   const T* Fc = static_cast<const T*>(P.s.Fc);
+  const long long loff = P.list_off[p];
+  const int cnt = P.list_cnt[p];
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (long long t = threadIdx.x; t < b.count; t += RED_THREADS) {
-    CellHit h;
-    box_cell(P.g, b, t, x0, x1, x2, h);
-    if (!in_reach(h.d2, r)) continue;
-    const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-    const long long e = slot_index(P.cov, cell);
-    if (e >= P.s.cap) continue;
+  for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
+    const int e = P.list[loff + k];
     const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
-    const double f0 = (double)Fc[6 * e + 3 * s];
-    const double f1 = (double)Fc[6 * e + 3 * s + 1];
-    const double f2 = (double)Fc[6 * e + 3 * s + 2];
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
+    const double dx = image_d(x, xp0, P.g.nx, !P.g.wall[0]);
+    const double dy = image_d(y, xp1, P.g.ny, !P.g.wall[1]);
+    const double dz = image_d(z, xp2, P.g.nz, !P.g.wall[2]);
+    const double f0 = (double)Fc[6LL * e + 3 * s];
+    const double f1 = (double)Fc[6LL * e + 3 * s + 1];
+    const double f2 = (double)Fc[6LL * e + 3 * s + 2];
     acc[0] += f0;
     acc[1] += f1;
     acc[2] += f2;
-    acc[3] += h.dy * f2 - h.dz * f1;
-    acc[4] += h.dz * f0 - h.dx * f2;
-    acc[5] += h.dx * f1 - h.dy * f0;
+    acc[3] += dy * f2 - dz * f1;
+    acc[4] += dz * f0 - dx * f2;
+    acc[5] += dx * f1 - dy * f0;
   }
   for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] = acc[i];
   __syncthreads();
@@ -428,10 +505,8 @@ __global__ void dense_clear_kernel(long long N, int* pid0, double* B0, int* pid1
 __global__ void dense_scatter_kernel(MapParams P, int* pid0, double* B0, int* pid1, double* B1) {
   const int n = slot_count(P);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const int cell = P.s.cell[e];
-    const int x = cell % P.g.nxp;
-    const int y = (cell / P.g.nxp) % P.g.ny;
-    const int z = cell / (P.g.nxp * P.g.ny);
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
     const long long c = (long long)x + (long long)P.g.nx * ((long long)y + (long long)P.g.ny * z);
     const int2 pid = P.s.pid[e];
     pid0[c] = pid.x;
@@ -443,46 +518,14 @@ __global__ void dense_scatter_kernel(MapParams P, int* pid0, double* B0, int* pi
 
 unsigned grid_cap(long long n, int block) {
   long long b = (n + block - 1) / block;
-  if (b > 152LL * 32) b = 152LL * 32;
+  if (b > MAP_PARTIALS) b = MAP_PARTIALS;
   return (unsigned)(b > 0 ? b : 1);
 }
 
-}  // namespace
-
-int launch_map(MapParams P, cudaStream_t s) {
+int map_common(MapParams P, cudaStream_t s, bool mlp) {
   int launches = 0;
   cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
-  if (P.p.n > 0) {
-    mark_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    ++launches;
-  }
-  const unsigned nb = (unsigned)P.cov.nblocks;
-  scan_words_kernel<<<nb, SCAN_THREADS, 0, s>>>(P.cov, P.g.nwords);
-  scan_blocks_kernel<<<1, SCAN_THREADS, 0, s>>>(P.cov, P.cov.nblocks);
-  scan_add_kernel<<<nb, SCAN_THREADS, 0, s>>>(P.cov, P.g.nwords);
-  launches += 3;
-  clear_slots_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
-  ++launches;
-  if (P.p.n > 0) {
-    fill_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    ++launches;
-  }
-  const unsigned nfin = grid_cap(P.s.cap, 256);
-  finish_kernel<<<nfin, 256, 0, s>>>(P);
-  vfluid_kernel<<<1, 32, 0, s>>>(P, (int)nfin);
-  launches += 2;
-  return launches;
-}
-
-int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
-                         const float* X, float* eps, cudaStream_t s);
-
-// mapping with the surrogate: as launch_map, with the network evaluated on the
-// tensor cores for the worklist between the fill and finish passes
-int launch_map_mlp(MapParams P, cudaStream_t s) {
-  int launches = 0;
-  cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
-  cudaMemsetAsync(P.mlp_count, 0, sizeof(int), s);
+  if (mlp) cudaMemsetAsync(P.mlp_count, 0, sizeof(int), s);
   if (P.p.n > 0) {
     mark_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
     ++launches;
@@ -497,17 +540,36 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
     fill_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
     ++launches;
   }
+  return launches;
+}
+
+int map_finish(MapParams P, cudaStream_t s) {
+  const unsigned nfin = grid_cap(P.s.cap, 256);
+  finish_kernel<<<nfin, 256, 0, s>>>(P);
+  vfluid_kernel<<<1, 32, 0, s>>>(P, (int)nfin);
+  return 2;
+}
+
+}  // namespace
+
+int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
+                         const float* X, float* eps, cudaStream_t s);
+
+int launch_map(MapParams P, cudaStream_t s) {
+  return map_common(P, s, false) + map_finish(P, s);
+}
+
+// mapping with the surrogate: the network runs on the tensor cores for the
+// worklist between the fill and finish passes
+int launch_map_mlp(MapParams P, cudaStream_t s) {
+  int launches = map_common(P, s, true);
   if (P.mlp) {
     classify_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
     launches += launch_mlp_infer_dev(P.mlp, P.mlp_count, P.s.cap, P.mlp_X, P.mlp_eps, s);
     apply_mlp_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
     launches += 2;
   }
-  const unsigned nfin = grid_cap(P.s.cap, 256);
-  finish_kernel<<<nfin, 256, 0, s>>>(P);
-  vfluid_kernel<<<1, 32, 0, s>>>(P, (int)nfin);
-  launches += 2;
-  return launches;
+  return launches + map_finish(P, s);
 }
 
 int launch_force_reduce(MapParams P, cudaStream_t s) {

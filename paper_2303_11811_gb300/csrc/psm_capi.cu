@@ -53,6 +53,9 @@ struct psm_ctx {
   int* mlp_work = nullptr;   // entry index per worklist item
   int* mlp_count = nullptr;
   long long mlp_cap = 0;
+  long long* list_off = nullptr;  // per-particle entry lists (force reduction)
+  int* list = nullptr;
+  int* list_cnt = nullptr;
   bool error_state = false;
   std::string err;
   // graphs: [buffer or parity][with mapping]
@@ -125,6 +128,9 @@ void free_particles(psm_ctx* c) {
   c->mlp_eps = nullptr;
   c->mlp_work = nullptr;
   c->mlp_cap = 0;
+  c->list_off = nullptr;
+  c->list = nullptr;
+  c->list_cnt = nullptr;
 }
 
 MapParams map_params(psm_ctx* c) {
@@ -152,6 +158,9 @@ MapParams map_params(psm_ctx* c) {
   P.mlp_eps = c->mlp_eps;
   P.mlp_work = c->mlp_work;
   P.mlp_count = c->mlp_count;
+  P.list_off = c->list_off;
+  P.list = c->list;
+  P.list_cnt = c->list_cnt;
   return P;
 }
 
@@ -418,6 +427,9 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   bool any_free = false;
   const double PI = 3.14159265358979323846;
   long long cap = 0;
+  // cells within reach of a sphere: their unit cubes lie in the ball of
+  // radius r + sqrt(3), so at most 4/3 pi (r + sqrt(3))^3 of them
+  std::vector<long long> loff(n + 1, 0);
   for (int i = 0; i < n; ++i) {
     if (!(r[i] > 0.0) || !std::isfinite(r[i]) || !(density[i] > 0.0))
       return fail(c, PSM_ERR_ARG, "radius and density must be positive");
@@ -446,8 +458,11 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
       }
     }
     const double R = r[i] + std::sqrt(3.0);
-    cap += (long long)(4.0 / 3.0 * PI * R * R * R) + 1;
+    const long long ci = (long long)(4.0 / 3.0 * PI * R * R * R) + 1;
+    cap += ci;
+    loff[i + 1] = loff[i] + ci;
   }
+  const long long list_total = cap > 0 ? cap : 1;
   if (cap > c->g.ncell) cap = c->g.ncell;
   free_graphs(c);
   free_particles(c);
@@ -479,6 +494,9 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   S.B = alloc_n<unsigned char>(c, cp * 2 * (c->fp32 ? 4 : 8), c->palloc);
   S.cnt = alloc_n<int>(c, cp, c->palloc);
   S.Fc = alloc_n<unsigned char>(c, cp * 6 * (c->fp32 ? 4 : 8), c->palloc);
+  c->list_off = alloc_n<long long>(c, (size_t)n + 1, c->palloc);
+  c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
+  c->list_cnt = alloc_n<int>(c, n1, c->palloc);
   if (c->opt.eps_mode == PSM_EPS_MLP) {
     c->mlp_cap = (long long)cp;
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
@@ -508,6 +526,8 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
     CK(cudaMemsetAsync(P.Th, 0, b3, s));
     CK(cudaMemsetAsync(P.Fc, 0, b3, s));
   }
+  CK(cudaMemcpyAsync(c->list_off, loff.data(), sizeof(long long) * (n + 1),
+                     cudaMemcpyHostToDevice, s));
   for (int a = 0; a < 3; ++a) c->G[a] = G[a];
   c->any_free = any_free;
   c->need_map = true;

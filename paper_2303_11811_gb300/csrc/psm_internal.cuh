@@ -109,6 +109,11 @@ struct MapParams {
   float* mlp_eps;
   int* mlp_work;
   int* mlp_count;
+  // per-particle lists of covered slot entries (box order) for the
+  // fixed-order force/torque reduction
+  const long long* list_off;   // n+1 offsets
+  int* list;
+  int* list_cnt;
 };
 constexpr int MAP_PARTIALS = 152 * 32;
 
