@@ -10,11 +10,12 @@
 // walls -x,+x,-y,+y,-z,+z, with plain IEEE FP64 operations (this file is
 // compiled with -fmad=false), so the sums are bitwise reproducible.
 //
-// Candidate search: for up to ALLPAIRS_MAX particles one warp per particle
-// scans all others with an FP32 prefilter (positions rounded to float differ
-// from FP64 by far less than the 1e-2 margin) and evaluates candidates in
-// FP64.  Larger sets use a uniform cell list (cell edge >= the largest
-// diameter) rebuilt every sub-step.
+// Per sub-step two launches: contacts (one warp per particle scanning all
+// others with an FP32 prefilter -- float positions differ from FP64 by far
+// less than the 1e-2 margin -- and evaluating candidates in FP64, ascending
+// j), then the velocity update fused with the next sub-step's positions.
+// FP64 runs at 1/58 of the FP32 rate here, so the per-particle FP64 work is
+// spread over many SMs rather than run in one block.
 #include "psm_internal.cuh"
 
 namespace psm {
@@ -125,19 +126,37 @@ __global__ void dem_contact_allpairs_kernel(DemParams P) {
   }
 }
 
-__global__ void dem_velocity_kernel(DemParams P) {
+// velocity update of one sub-step (Eq. 16) fused with the position update
+// of the next (Eq. 15): both only touch particle i
+__global__ void dem_velocity_position_kernel(DemParams P, int next_position) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n || P.p.fixed[i]) return;
+  if (i >= P.p.n) return;
   const double dt = P.dt;
-  for (int a = 0; a < 3; ++a) {
-    const double Fn = P.p.Fh[3 * i + a] + P.p.Fc[3 * i + a] +
-                      (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
-    const double Tn = P.p.Th[3 * i + a];
-    P.p.u[3 * i + a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
-    P.p.om[3 * i + a] += dt * (P.p.Told[3 * i + a] + Tn) / (2.0 * P.p.I[i]);
-    P.p.Fold[3 * i + a] = Fn;
-    P.p.Told[3 * i + a] = Tn;
+  const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  if (!P.p.fixed[i]) {
+    for (int a = 0; a < 3; ++a) {
+      const double Fn = P.p.Fh[3 * i + a] + P.p.Fc[3 * i + a] +
+                        (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
+      const double Tn = P.p.Th[3 * i + a];
+      P.p.u[3 * i + a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
+      P.p.om[3 * i + a] += dt * (P.p.Told[3 * i + a] + Tn) / (2.0 * P.p.I[i]);
+      P.p.Fold[3 * i + a] = Fn;
+      P.p.Told[3 * i + a] = Tn;
+    }
+    if (next_position) {
+      for (int a = 0; a < 3; ++a) {
+        double xn = P.p.x[3 * i + a] + dt * P.p.u[3 * i + a] +
+                    dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
+        if (!P.g.wall[a]) {
+          if (xn >= dims[a]) xn -= dims[a];
+          else if (xn < 0.0) xn += dims[a];
+        }
+        P.p.x[3 * i + a] = xn;
+      }
+    }
   }
+  if (next_position)
+    for (int a = 0; a < 3; ++a) P.p.xf[4 * i + a] = (float)P.p.x[3 * i + a];
 }
 
 }  // namespace
@@ -149,11 +168,12 @@ int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
   const unsigned gp = (n + tb - 1) / tb;
   const unsigned gw = (unsigned)(((long long)n * 32 + tb - 1) / tb);
   int launches = 0;
+  dem_position_kernel<<<gp, tb, 0, s>>>(P);
+  ++launches;
   for (int sc = 0; sc < subcycles; ++sc) {
-    dem_position_kernel<<<gp, tb, 0, s>>>(P);
     dem_contact_allpairs_kernel<<<gw, tb, 0, s>>>(P);
-    dem_velocity_kernel<<<gp, tb, 0, s>>>(P);
-    launches += 3;
+    dem_velocity_position_kernel<<<gp, tb, 0, s>>>(P, sc + 1 < subcycles);
+    launches += 2;
   }
   return launches;
 }

@@ -28,6 +28,8 @@ constexpr int RED_THREADS = 128;
 constexpr int SCAN_THREADS = 1024;
 
 struct Box {
+  double rin2;        // (r - sqrt(3)/2)^2 when r > sqrt(3)/2, else -1
+  float rin2f;
   int lo[3], n[3];
   int count;
   int ip[3];          // floor of the centre
@@ -62,6 +64,9 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
   b.reach2 = reach * reach;
   b.reach2f = (float)b.reach2;
   b.E = certified_band(r);
+  const double rin = r - HALF_SQRT3;
+  b.rin2 = rin > 0.0 ? rin * rin : -1.0;
+  b.rin2f = (float)b.rin2;
   return b;
 }
 
@@ -87,6 +92,7 @@ struct CellHit {
   int ix, iy, iz;
   int kx, ky, kz;
   double dx, dy, dz, d2;
+  float d2f;
 };
 
 __device__ __forceinline__ void box_coords(const Grid& g, const Box& b, int t, CellHit& h) {
@@ -109,6 +115,7 @@ __device__ __forceinline__ bool reach_test(const Box& b, CellHit& h) {
   const float dyf = (float)(h.ky - b.ip[1]) + (0.5f - b.fpf[1]);
   const float dzf = (float)(h.kz - b.ip[2]) + (0.5f - b.fpf[2]);
   const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+  h.d2f = d2f;
   if (d2f > b.reach2f + b.E) return false;
   h.dx = ((double)h.kx + 0.5) - b.xp[0];
   h.dy = ((double)h.ky + 0.5) - b.xp[1];
@@ -128,8 +135,9 @@ __device__ __forceinline__ void cell_xyz(const Grid& g, int cell, int& x, int& y
   z = cell / (g.nxp * g.ny);
 }
 
+// B(eps); for eps = 0 and eps = 1 the FP64 formula gives exactly 0 and 1
 __device__ __forceinline__ double weight(double eps, double tau, int nt) {
-  if (!nt) return eps;
+  if (!nt || eps == 0.0 || eps == 1.0) return eps;
   return eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5));
 }
 
@@ -243,11 +251,15 @@ __global__ void clear_slots_kernel(MapParams P) {
   }
 }
 
-// eps of a cell for one particle; -1 means "resolved in a later pass"
-__device__ double cell_eps(const MapParams& P, const CellHit& h, double r, double fr,
+// eps of a cell for one particle; -1 means "resolved in a later pass".  The
+// inside test d2 <= (r - sqrt(3)/2)^2 is taken in FP32 outside the band.
+__device__ double cell_eps(const MapParams& P, const Box& b, const CellHit& h, double fr,
                            const double* s64, const float* s32) {
-  const double rin = r - HALF_SQRT3;
-  if (rin > 0.0 && h.d2 <= rin * rin) return 1.0;
+  const double r = b.r;
+  if (b.rin2 >= 0.0) {
+    if (h.d2f < b.rin2f - b.E) return 1.0;
+    if (h.d2f <= b.rin2f + b.E && h.d2 <= b.rin2) return 1.0;
+  }
   if (P.eps_mode == 1) {  // Eqs. 25-26
     const double dist = sqrt(h.d2);
     const double D = dist - r;
@@ -258,8 +270,12 @@ __device__ double cell_eps(const MapParams& P, const CellHit& h, double r, doubl
   }
   if (P.eps_mode == 2) return -1.0;
   const int n = P.eps_n;
-  return (double)supersample_count_fast(h.dx, h.dy, h.dz, r, n, s64, s32) /
-         ((double)n * n * n);
+  const int cnt = supersample_count_fast(h.dx, h.dy, h.dz, r, n, s64, s32);
+  const int n3 = n * n * n;
+  // count / n^3; for n^3 a power of two the product with the reciprocal is
+  // the same IEEE result as the quotient
+  if ((n3 & (n3 - 1)) == 0) return (double)cnt * (1.0 / (double)n3);
+  return (double)cnt / (double)n3;
 }
 
 // claims the slots of one particle's cells and lists them in box order
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
         } else {
           P.s.cell[e] = (int)cell;
           reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
-          const double eps = cell_eps(P, h, b.r, fr, s64, s32);
+          const double eps = cell_eps(P, b, h, fr, s64, s32);
           store_B(P, e, s, eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting));
         }
       }
@@ -384,7 +400,7 @@ __global__ void finish_kernel(MapParams P) {
         const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
         const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
         const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-        const double eps = (double)supersample_count_fast(dx, dy, dz, r, 8, s64, s32) / 512.0;
+        const double eps = (double)supersample_count_fast(dx, dy, dz, r, 8, s64, s32) * (1.0 / 512.0);
         Bs = weight(eps, P.tau, P.weighting);
       }
     }
@@ -408,13 +424,21 @@ __global__ void finish_kernel(MapParams P) {
   if (threadIdx.x == 0) P.partials[blockIdx.x] = red[0];
 }
 
-// fluid volume sum_x (1 - B) from the finish-pass partial sums, fixed order
+// fluid volume sum_x (1 - B) from the finish-pass partial sums, fixed order:
+// each thread sums a strided subset, then a tree (one block of 256)
 __global__ void vfluid_kernel(MapParams P, int nparts) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += P.partials[b];
-    P.sc->sumB = s;
-    P.sc->vfluid = P.sc->ncells - s;
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += 256) s += P.partials[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.sc->sumB = red[0];
+    P.sc->vfluid = P.sc->ncells - red[0];
   }
 }
 
@@ -546,7 +570,7 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
 int map_finish(MapParams P, cudaStream_t s) {
   const unsigned nfin = grid_cap(P.s.cap, 256);
   finish_kernel<<<nfin, 256, 0, s>>>(P);
-  vfluid_kernel<<<1, 32, 0, s>>>(P, (int)nfin);
+  vfluid_kernel<<<1, 256, 0, s>>>(P, (int)nfin);
   return 2;
 }
 

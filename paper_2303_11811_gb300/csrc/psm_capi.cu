@@ -46,6 +46,8 @@ struct psm_ctx {
   bool need_pack = false;
   double G[3] = {0, 0, 0};
   double log_e = 0;
+  int dem_nc[3] = {1, 1, 1};   // DEM cell list
+  float dem_h[3] = {1, 1, 1};
   float* mlp = nullptr;   // FP32 parameters on the device
   bool have_mlp = false;
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
@@ -226,7 +228,11 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
     D.kn = c->opt.k_n;
     D.log_e = c->log_e;
     D.dt = 1.0 / c->opt.dem_subcycles;
-    for (int a = 0; a < 3; ++a) D.gravity[a] = c->opt.gravity[a];
+    for (int a = 0; a < 3; ++a) {
+      D.gravity[a] = c->opt.gravity[a];
+      D.nc[a] = c->dem_nc[a];
+      D.h[a] = c->dem_h[a];
+    }
     D.status = c->status;
     n += launch_dem_step(D, c->opt.dem_subcycles, s);
   }
@@ -529,6 +535,17 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   CK(cudaMemcpyAsync(c->list_off, loff.data(), sizeof(long long) * (n + 1),
                      cudaMemcpyHostToDevice, s));
   for (int a = 0; a < 3; ++a) c->G[a] = G[a];
+  // DEM cell list: edge >= the largest diameter (plus the prefilter margin),
+  // at least three cells along an axis or a single one
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
+  for (int a = 0; a < 3; ++a) {
+    int nc = (int)std::floor(dims[a] / (2.0 * rmax + 0.05));
+    if (nc < 3) nc = 1;
+    if (nc > 1024) nc = 1024;
+    c->dem_nc[a] = nc;
+    c->dem_h[a] = (float)((double)dims[a] / nc);
+  }
   c->any_free = any_free;
   c->need_map = true;
   c->error_state = false;

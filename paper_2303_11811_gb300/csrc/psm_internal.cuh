@@ -163,6 +163,8 @@ struct DemParams {
   double kn, log_e, dt;
   double gravity[3];
   unsigned* status;
+  int nc[3];          // cell-list cells per axis (edge >= largest diameter)
+  float h[3];         // cell edges
 };
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
 
