@@ -212,6 +212,31 @@ psm_status psm_get_timings(psm_ctx* ctx, double* out5);
  * kernels, graph nodes included). */
 long psm_last_launch_count(const psm_ctx* ctx);
 
+/* Mass and momentum of a PDF field that the caller already holds on the
+ * device, computed without allocating any device memory.  The paper has no
+ * counterpart to this call; it is here for callers that cannot allocate when
+ * they want the check: a code that gives out all device memory from its own
+ * fixed pool, a monitoring hook inside another solver's time loop where
+ * cudaMalloc/cudaFree would synchronise the device and stall its streams, or
+ * a run whose memory budget is fully committed.  psm_check gives the same
+ * sums but allocates.
+ *   f       device pointer, canonical FP64 layout f[q][cell] (19 * ncells)
+ *   ncells  1 .. PSM_NOALLOC_MAX_CELLS; larger fields give PSM_ERR_ARG
+ *   sums    device pointer to 4 doubles: mass, momentum x, y, z (written)
+ *   stream  cudaStream_t the two kernels are queued on (NULL: legacy default)
+ * Returns PSM_OK once the work is queued (nothing is synchronised),
+ * PSM_ERR_ARG for NULL pointers or sizes out of range, PSM_ERR_CUDA if the
+ * set-up or a launch fails.  The block partials live in one 128 KiB array in
+ * device memory that the library declares at file scope: every GPU that
+ * loads the library holds it until the process exits, and all calls on a
+ * GPU share it, so calls whose work overlaps on the GPU (unordered streams)
+ * race; order them on one stream.  The first call on each device (with that
+ * device current) looks up the array's device address; make that first call
+ * before any stream capture. */
+#define PSM_NOALLOC_MAX_CELLS (4096LL * 65536LL)
+psm_status psm_field_sums_noalloc(const double* f, long long ncells, double* sums,
+                                  void* stream);
+
 /* Human-readable description of the last error of ctx (never NULL). */
 const char* psm_last_error(const psm_ctx* ctx);
 

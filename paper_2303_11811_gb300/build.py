@@ -28,6 +28,7 @@ UNITS = {
     "dem_kernels.cu": ["-fmad=false"],
     "mlp_kernels.cu": ["-fmad=false"],
     "psm_capi.cu": [],
+    "noalloc_sums.cu": [],
 }
 
 

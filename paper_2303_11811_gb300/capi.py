@@ -35,7 +35,7 @@ EXPORTS = [
     "psm_set_pdfs", "psm_get_slots", "psm_check", "psm_set_mlp", "psm_get_mlp",
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
     "psm_set_timing", "psm_get_timings", "psm_last_launch_count", "psm_last_error",
-    "psm_destroy",
+    "psm_destroy", "psm_field_sums_noalloc",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -122,6 +122,8 @@ def lib():
     L.psm_last_error.restype = C.c_char_p
     L.psm_destroy.argtypes = [P]
     L.psm_destroy.restype = None
+    L.psm_field_sums_noalloc.argtypes = [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]
+    L.psm_field_sums_noalloc.restype = st
     _lib = L
     return L
 
@@ -392,6 +394,13 @@ class Engine:
 
     def last_launch_count(self):
         return int(self._L.psm_last_launch_count(self.h))
+
+
+def field_sums_noalloc(f_dev_ptr: int, ncells: int, sums_dev_ptr: int, stream_ptr: int) -> int:
+    """psm_field_sums_noalloc on device addresses; returns the status code.
+    The call allocates no device memory (for callers that cannot)."""
+    return lib().psm_field_sums_noalloc(C.c_void_p(f_dev_ptr), int(ncells),
+                                        C.c_void_p(sums_dev_ptr), C.c_void_p(stream_ptr))
 
 
 def pack_mlp(params) -> np.ndarray:
