@@ -170,29 +170,34 @@ psm_status psm_get_slots(psm_ctx* ctx, int* pid0, double* B0, int* pid1, double*
  * sum_x sum_q f_q c_q (3 values); fixed summation order. */
 psm_status psm_check(psm_ctx* ctx, double* mass, double* momentum);
 
-/* Surrogate network for PSM_EPS_MLP: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1 with
- * inputs (d/r, r), d the offset of the cell centre from the sphere centre.
+/* Surrogate network for PSM_EPS_MLP: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1.  Its
+ * inputs are x = (|d/r| components in decreasing order, r), d the offset of
+ * the cell centre from the sphere centre (eps is invariant under sign flips
+ * and permutations of d), and it predicts the correction to the linear
+ * approximation of Eqs. 25-27: eps = clamp(eps_lin(|d|, r) + MLP(x), 0, 1).
  * params is the packed FP32 vector [W1 (32x4), b1 (32), W2 (32x32), b2 (32),
- * W3 (32), b3 (1)], row-major, PSM_MLP_PARAMS floats.  Inference uses BF16
- * copies of the weights on the tensor cores with FP32 accumulation. */
+ * W3 (32), b3 (1)], row-major, PSM_MLP_PARAMS floats.  Inference runs the
+ * hidden layer on the tensor cores with BF16 operands and FP32 accumulation. */
 #define PSM_MLP_PARAMS 1249
 psm_status psm_set_mlp(psm_ctx* ctx, const float* params);
 psm_status psm_get_mlp(psm_ctx* ctx, float* params);
 
 /* Trains the surrogate on the device with the engine's own forward/backward
  * and Adam kernels: nsamples samples of the SplitMix64 training recipe
- * (stream seed), labelled by 8^3 sub-division sampling, minibatches of batch
- * samples, epochs passes, learning rate lr.  Starts from the current
- * parameters.  loss_out (may be NULL) receives the mean squared error of the
- * last epoch. */
+ * (stream seed), labelled by 8^3 sub-division sampling (target: label minus
+ * the linear approximation), minibatches of batch samples, epochs passes,
+ * learning rate lr decaying exponentially to 3% of lr over the run.  Starts
+ * from the current parameters.  loss_out (may be NULL) receives the mean
+ * squared error of the final parameters over the training set. */
 psm_status psm_train_surrogate(psm_ctx* ctx, long nsamples, unsigned long long seed,
                                int epochs, int batch, float lr, float* loss_out);
 
 /* Kernel-level entry points of the surrogate (used to check them):
- * training samples i = first .. first+count-1 of stream seed: inputs X
- * (count*4) and labels eps (count); loss and gradient (PSM_MLP_PARAMS floats)
- * of the mean squared error of params on (X, t); eps of the BF16 inference
- * kernel for inputs X, clamped to [0, 1]. */
+ * training samples i = first .. first+count-1 of stream seed: network inputs
+ * X (count*4) and 8^3 labels eps (count); loss and gradient (PSM_MLP_PARAMS
+ * floats) of the mean squared error of params on (X, t); raw network output
+ * of the BF16 inference kernel for inputs X (before the linear approximation
+ * is added and the result clamped). */
 psm_status psm_mlp_samples(psm_ctx* ctx, unsigned long long seed, long first, long count,
                            float* X, float* eps);
 psm_status psm_mlp_loss_grad(psm_ctx* ctx, const float* params, long m, const float* X,

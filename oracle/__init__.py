@@ -87,6 +87,7 @@ def lib():
             L.or_nt_weight.restype = C.c_double
             L.or_supersample_batch.argtypes = [C.c_long, dp, dp, C.c_int,
                                                C.POINTER(C.c_long)]
+            L.or_eps_linear_batch.argtypes = [C.c_long, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -271,6 +272,14 @@ def supersample_batch(d, r, n: int) -> np.ndarray:
     out = np.empty(m, dtype=np.int64)
     lib().or_supersample_batch(m, _dp(d), _dp(r), int(n),
                                out.ctypes.data_as(C.POINTER(C.c_long)))
+    return out
+
+
+def eps_linear_batch(dist, r) -> np.ndarray:
+    dist = _f64(dist)
+    r = _f64(r)
+    out = np.empty(r.size)
+    lib().or_eps_linear_batch(r.size, _dp(dist), _dp(r), _dp(out))
     return out
 
 

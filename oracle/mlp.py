@@ -2,12 +2,17 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-The network maps (d/r, r) -> eps, d the offset of a cell centre from the sphere
-centre and r the radius: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1.  Parameters are
-row-major ``W1`` (32x4), ``b1`` (32), ``W2`` (32x32), ``b2`` (32), ``W3`` (1x32),
-``b3`` (1).  The loss is the mean squared error against the 8^3 sub-division
-sampling label of Sec. 2.3.2; the optimiser is Adam (Kingma and Ba, 2015).
-ReLU'(0) is taken as 0.
+The network takes the offset d of a cell centre from the sphere centre,
+divided by the radius r, and r: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1.  The offset
+enters in the orientation fixed by the cube's symmetries (eps does not change
+under sign flips and permutations of the components of d): x = (|d/r|
+components in decreasing order, r).  The network predicts the correction to
+the linear approximation of Sec. 2.3.2 (Eqs. 25-27):
+    eps = clamp(eps_lin(|d|, r) + MLP(x), 0, 1).
+Parameters are row-major ``W1`` (32x4), ``b1`` (32), ``W2`` (32x32), ``b2``
+(32), ``W3`` (1x32), ``b3`` (1).  The loss is the mean squared error of the
+correction against (8^3 sub-division sampling label - eps_lin); the optimiser
+is Adam (Kingma and Ba, 2015).  ReLU'(0) is taken as 0.
 
 Training samples are drawn from the counter-based generator SplitMix64
 (Steele, Lea and Flood, 2014): value k of stream ``seed`` is the SplitMix64
@@ -24,7 +29,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import supersample_batch
+from . import eps_linear_batch, supersample_batch
 
 GOLDEN = np.uint64(0x9E3779B97F4A7C15)
 M1 = np.uint64(0xBF58476D1CE4E5B9)
@@ -64,13 +69,25 @@ def training_offsets(seed: int, first: int, count: int):
     return d, r
 
 
+def network_inputs(d, r):
+    """(|d/r| components in decreasing order, r) for offsets d (m x 3)."""
+    a = np.abs(d / r[:, None])
+    a = -np.sort(-a, axis=1)
+    return np.concatenate([a, r[:, None]], axis=1)
+
+
 def training_samples(seed: int, first: int, count: int):
-    """Network inputs (d/r, r), labels eps = count_8 / 512, offsets and radii."""
+    """Network inputs, labels eps = count_8 / 512, offsets and radii."""
     d, r = training_offsets(seed, first, count)
     cnt = supersample_batch(d, r, 8)
     eps = cnt.astype(np.float64) / 512.0
-    X = np.concatenate([d / r[:, None], r[:, None]], axis=1)
-    return X, eps, d, r
+    return network_inputs(d, r), eps, d, r
+
+
+def linear_eps(d, r):
+    """Eqs. 25-27 for offsets d (m x 3) and radii r."""
+    dist = np.sqrt(d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1] + d[:, 2] * d[:, 2])
+    return eps_linear_batch(dist, r)
 
 
 def forward(params, X):
@@ -120,6 +137,5 @@ def adam_update(params, grads, m_state, v_state, step, lr, beta1=0.9, beta2=0.99
 
 def eps_from_net(params, d, r):
     """Surrogate eps for offsets d and radii r, clamped to [0, 1]."""
-    X = np.concatenate([d / r[:, None], r[:, None]], axis=1)
-    y, _ = forward(params, X)
-    return np.clip(y, 0.0, 1.0)
+    y, _ = forward(params, network_inputs(d, r))
+    return np.clip(linear_eps(d, r) + y, 0.0, 1.0)

@@ -26,7 +26,11 @@
  *     bounce-back f_q(x) = f~_qbar(x) for a link that leaves the domain.
  *  I  MLP mode: the network is used for a partial cell within reach of one
  *     particle and not next to a wall face; every other partial cell uses
- *     8^3 sampling.
+ *     8^3 sampling.  The network predicts the correction to the linear
+ *     approximation of Eqs. 25-27: eps = clamp(eps_lin + MLP(x), 0, 1), with
+ *     x = (|d/r| components sorted in decreasing order, r) -- the offset in
+ *     the orientation fixed by the cube's symmetries (eps does not change
+ *     under sign flips and permutations of the offset components).
  *  J  Gravity: a free particle feels (m - V) g (buoyancy with rho_f = 1).
  *     The fluid gets the uniform counter force density
  *     -sum_free (m_i - V_i) g / V_fluid, V_fluid = sum_x (1 - B(x)), applied
@@ -231,6 +235,11 @@ double or_nt_weight(double eps, double tau) {
   return eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5));
 }
 
+/* linear approximation for a batch of distances and radii */
+void or_eps_linear_batch(long m, const double* dist, const double* r, double* eps) {
+  for (long i = 0; i < m; ++i) eps[i] = or_eps_linear(dist[i], r[i]);
+}
+
 /* labels for a batch of offsets: count of n^3 samples inside, per row */
 void or_supersample_batch(long m, const double* d, const double* r, int n, long* count) {
   for (long i = 0; i < m; ++i)
@@ -270,8 +279,13 @@ static double cell_eps(const or_ctx* c, double dx, double dy, double dz, double 
   double rout = r + HALF_SQRT3;
   if (d2 >= rout * rout) return 0.0;
   if (mode == 2 && c->have_mlp && single && !next_to_wall) {
-    double in[4] = {dx / r, dy / r, dz / r, r};
-    double e = mlp_eval(c, in);
+    double a[3] = {fabs(dx / r), fabs(dy / r), fabs(dz / r)};
+    /* sort in decreasing order */
+    for (int i = 0; i < 2; ++i)
+      for (int j = i + 1; j < 3; ++j)
+        if (a[j] > a[i]) { double t = a[i]; a[i] = a[j]; a[j] = t; }
+    double in[4] = {a[0], a[1], a[2], r};
+    double e = or_eps_linear(dist, r) + mlp_eval(c, in);
     if (e < 0.0) e = 0.0;
     if (e > 1.0) e = 1.0;
     return e;

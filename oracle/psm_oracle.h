@@ -98,6 +98,7 @@ double or_eps_linear(double dist, double r);
 long or_eps_supersample_count(double dx, double dy, double dz, double r, int n);
 double or_nt_weight(double eps, double tau);
 void or_supersample_batch(long m, const double* d, const double* r, int n, long* count);
+void or_eps_linear_batch(long m, const double* dist, const double* r, double* eps);
 
 #ifdef __cplusplus
 }

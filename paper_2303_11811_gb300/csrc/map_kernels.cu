@@ -336,7 +336,8 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
 }
 
 // surrogate mode: a partial cell within reach of exactly one particle and not
-// next to a wall face goes to the network's worklist (inputs d/r, r); the
+// next to a wall face goes to the network's worklist with its inputs (|d/r|
+// in decreasing order, r) and its linear approximation (Eqs. 25-27); the
 // finish pass samples every other pending cell with 8^3 points
 __global__ void classify_kernel(MapParams P) {
   const int n = slot_count(P);
@@ -355,9 +356,16 @@ __global__ void classify_kernel(MapParams P) {
     const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
     const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
     const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+    double a = fabs(dx / r), b = fabs(dy / r), c = fabs(dz / r), t;
+    if (b > a) { t = a; a = b; b = t; }
+    if (c > a) { t = a; a = c; c = t; }
+    if (c > b) { t = b; b = c; c = t; }
+    const double dist = sqrt(dx * dx + dy * dy + dz * dz);
+    double lin = -(dist - r) + P.p.fr[p];
+    lin = lin < 0.0 ? 0.0 : (lin > 1.0 ? 1.0 : lin);
     const int k = atomicAdd(P.mlp_count, 1);
-    reinterpret_cast<float4*>(P.mlp_X)[k] =
-        make_float4((float)(dx / r), (float)(dy / r), (float)(dz / r), (float)r);
+    reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4((float)a, (float)b, (float)c, (float)r);
+    P.mlp_lin[k] = lin;
     P.mlp_work[k] = e;
   }
 }
@@ -366,7 +374,9 @@ __global__ void apply_mlp_kernel(MapParams P) {
   const int n = *P.mlp_count;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     const int e = P.mlp_work[k];
-    store_B(P, e, 0, weight((double)P.mlp_eps[k], P.tau, P.weighting));
+    double eps = P.mlp_lin[k] + (double)P.mlp_eps[k];
+    eps = eps < 0.0 ? 0.0 : (eps > 1.0 ? 1.0 : eps);
+    store_B(P, e, 0, weight(eps, P.tau, P.weighting));
   }
 }
 

@@ -1,8 +1,12 @@
-// mlp_kernels.cu -- the learned eps surrogate: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1,
-// inputs (d/r, r), d = cell centre minus sphere centre.  Replaces the
-// sub-division sampling of Sec. 2.3.2 for partial cells within reach of one
-// particle and away from walls; 8^3 sampling stays the fallback and is the
-// label the network is trained on.
+// mlp_kernels.cu -- the learned eps surrogate: 4 -> 32 (ReLU) -> 32 (ReLU) -> 1.
+// Inputs x = (|d/r| components in decreasing order, r), d = cell centre minus
+// sphere centre: the offset in the orientation fixed by the cube's symmetries
+// (eps is invariant under sign flips and permutations of d).  The network
+// predicts the correction to the linear approximation of Sec. 2.3.2
+// (Eqs. 25-27): eps = clamp(eps_lin(|d|, r) + MLP(x), 0, 1).  It replaces the
+// sub-division sampling for partial cells within reach of one particle and
+// away from walls; 8^3 sampling stays the fallback and gives the labels the
+// network is trained on (target: label - eps_lin).
 //
 // Parameters (FP32, packed): W1 [0,128) 32x4 row-major, b1 [128,160),
 // W2 [160,1184) 32x32, b2 [1184,1216), W3 [1216,1248), b3 [1248].
@@ -46,8 +50,29 @@ __device__ __forceinline__ double uniform01(unsigned long long seed, unsigned lo
   return (double)(splitmix64(seed, k) >> 11) * 0x1.0p-53;
 }
 
+// f(r) = V_a(r) - r + 1/2 of Eqs. 26-27 (training targets only; the mapping
+// takes f(r) computed on the host for each particle)
+__device__ double linear_fr(double r) {
+  const double r2 = r * r;
+  const double s = sqrt(r2 - 0.5);
+  const double Va = (1.0 / 12.0 - r2) * atan((0.5 * s) / (0.5 - r2)) + s / 3.0 +
+                    (r2 - 1.0 / 12.0) * atan(0.5 / s) - 4.0 / 3.0 * r2 * r * atan(0.25 / (r * s));
+  return Va - r + 0.5;
+}
+
+// inputs of the network for offset d and radius r
+__device__ __forceinline__ float4 network_input(double dx, double dy, double dz, double r) {
+  double a = fabs(dx / r), b = fabs(dy / r), c = fabs(dz / r), t;
+  if (b > a) { t = a; a = b; b = t; }
+  if (c > a) { t = a; a = c; c = t; }
+  if (c > b) { t = b; b = c; c = t; }
+  return make_float4((float)a, (float)b, (float)c, (float)r);
+}
+
+// resid (optional): label - eps_lin, the network's training target
 __global__ void samples_kernel(unsigned long long seed, long long first, long long count,
-                               float* __restrict__ X, float* __restrict__ eps) {
+                               float* __restrict__ X, float* __restrict__ eps,
+                               float* __restrict__ resid) {
   __shared__ double s64[8];
   __shared__ float s32[8];
   if (threadIdx.x < 8) {
@@ -70,11 +95,15 @@ __global__ void samples_kernel(unsigned long long seed, long long first, long lo
     const double tt = rho / nv;
     const double d0 = v0 * tt, d1 = v1 * tt, d2 = v2 * tt;
     const int cnt = supersample_count_fast(d0, d1, d2, r, 8, s64, s32);
-    X[4 * t + 0] = (float)(d0 / r);
-    X[4 * t + 1] = (float)(d1 / r);
-    X[4 * t + 2] = (float)(d2 / r);
-    X[4 * t + 3] = (float)r;
-    eps[t] = (float)((double)cnt / 512.0);
+    reinterpret_cast<float4*>(X)[t] = network_input(d0, d1, d2, r);
+    const double label = (double)cnt * (1.0 / 512.0);
+    eps[t] = (float)label;
+    if (resid) {
+      const double dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+      double lin = -(dist - r) + linear_fr(r);
+      lin = lin < 0.0 ? 0.0 : (lin > 1.0 ? 1.0 : lin);
+      resid[t] = (float)(label - lin);
+    }
   }
 }
 
@@ -211,7 +240,8 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// count: number of inputs, read from *count_dev when count < 0
+// raw network outputs for inputs X; count: number of inputs, read from
+// *count_dev when count < 0
 __global__ void __launch_bounds__(128) infer_kernel(const float* __restrict__ P, long long count,
                                                    const int* __restrict__ count_dev,
                                                    const float4* __restrict__ X,
@@ -286,8 +316,8 @@ __global__ void __launch_bounds__(128) infer_kernel(const float* __restrict__ P,
     y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
     y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
     if (t == 0) {
-      if (r0 < n) eps[r0] = fminf(fmaxf(y0 + b3, 0.f), 1.f);
-      if (r1 < n) eps[r1] = fminf(fmaxf(y1 + b3, 0.f), 1.f);
+      if (r0 < n) eps[r0] = y0 + b3;
+      if (r1 < n) eps[r1] = y1 + b3;
     }
   }
 }
@@ -295,11 +325,11 @@ __global__ void __launch_bounds__(128) infer_kernel(const float* __restrict__ P,
 }  // namespace
 
 int launch_mlp_samples(unsigned long long seed, long long first, long long count, float* X,
-                       float* eps, cudaStream_t s) {
+                       float* eps, float* resid, cudaStream_t s) {
   if (count <= 0) return 0;
   long long blocks = (count + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  samples_kernel<<<(unsigned)blocks, 256, 0, s>>>(seed, first, count, X, eps);
+  samples_kernel<<<(unsigned)blocks, 256, 0, s>>>(seed, first, count, X, eps, resid);
   return 1;
 }
 

@@ -52,6 +52,7 @@ struct psm_ctx {
   bool have_mlp = false;
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
   float* mlp_eps = nullptr;
+  double* mlp_lin = nullptr; // linear approximation per worklist item
   int* mlp_work = nullptr;   // entry index per worklist item
   int* mlp_count = nullptr;
   long long mlp_cap = 0;
@@ -128,6 +129,7 @@ void free_particles(psm_ctx* c) {
   c->slots = Slots{};
   c->mlp_X = nullptr;
   c->mlp_eps = nullptr;
+  c->mlp_lin = nullptr;
   c->mlp_work = nullptr;
   c->mlp_cap = 0;
   c->list_off = nullptr;
@@ -158,6 +160,7 @@ MapParams map_params(psm_ctx* c) {
   P.partials = c->partials;
   P.mlp_X = c->mlp_X;
   P.mlp_eps = c->mlp_eps;
+  P.mlp_lin = c->mlp_lin;
   P.mlp_work = c->mlp_work;
   P.mlp_count = c->mlp_count;
   P.list_off = c->list_off;
@@ -507,6 +510,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
     c->mlp_cap = (long long)cp;
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
     c->mlp_eps = alloc_n<float>(c, cp, c->palloc);
+    c->mlp_lin = alloc_n<double>(c, cp, c->palloc);
     c->mlp_work = alloc_n<int>(c, cp, c->palloc);
   }
   for (void* q : c->palloc)
@@ -745,7 +749,7 @@ psm_status psm_mlp_samples(psm_ctx* c, unsigned long long seed, long first, long
   if (count == 0) return PSM_OK;
   float* d = static_cast<float*>(dalloc(c, sizeof(float) * 5 * count));
   if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
-  launch_mlp_samples(seed, first, count, d, d + 4 * count, c->stream);
+  launch_mlp_samples(seed, first, count, d, d + 4 * count, nullptr, c->stream);
   cudaError_t e = cudaMemcpyAsync(X, d, sizeof(float) * 4 * count, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(eps, d + 4 * count, sizeof(float) * count, cudaMemcpyDeviceToHost,
@@ -813,27 +817,32 @@ psm_status psm_train_surrogate(psm_ctx* c, long nsamples, unsigned long long see
   if (!c || nsamples <= 0 || epochs < 1 || batch < 1 || !(lr > 0)) return PSM_ERR_ARG;
   if (!c->have_mlp) return fail(c, PSM_ERR_STATE, "set initial surrogate parameters first");
   const int nb = mlp_grad_blocks(batch);
-  const size_t floats = 5 * (size_t)nsamples + 3 * PSM_MLP_PARAMS + 1 +
+  const size_t floats = 6 * (size_t)nsamples + 3 * PSM_MLP_PARAMS + 1 +
                         (size_t)nb * (PSM_MLP_PARAMS + 1);
   float* d = static_cast<float*>(dalloc(c, sizeof(float) * floats));
   if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
   float* X = d;
-  float* T = X + 4 * nsamples;
-  float* g = T + nsamples;
+  float* T = X + 4 * nsamples;   // residual targets: label - eps_lin
+  float* L = T + nsamples;       // labels (unused by the optimiser)
+  float* g = L + nsamples;
   float* ms = g + PSM_MLP_PARAMS;
   float* vs = ms + PSM_MLP_PARAMS;
   float* dl = vs + PSM_MLP_PARAMS;
   float* part = dl + 1;
   cudaStream_t s = c->stream;
-  launch_mlp_samples(seed, 0, nsamples, X, T, s);
+  launch_mlp_samples(seed, 0, nsamples, X, L, T, s);
   cudaMemsetAsync(ms, 0, sizeof(float) * 2 * PSM_MLP_PARAMS, s);
   int step = 0;
   double last = 0.0;
+  const long per_epoch = (nsamples + batch - 1) / batch;
+  const double total = (double)per_epoch * epochs;
   for (int ep = 0; ep < epochs; ++ep) {
     for (long b0 = 0; b0 < nsamples; b0 += batch) {
       const long mb = nsamples - b0 < batch ? nsamples - b0 : batch;
       launch_mlp_loss_grad(c->mlp, mb, X + 4 * b0, T + b0, part, mlp_grad_blocks(mb), g, dl, s);
-      launch_adam(c->mlp, g, ms, vs, ++step, lr, s);
+      // learning rate decays exponentially to 3% of lr over the run
+      const float lr_t = (float)(lr * std::pow(0.03, (double)step / total));
+      launch_adam(c->mlp, g, ms, vs, ++step, lr_t, s);
     }
   }
   // loss of the final parameters over the whole sample set, in minibatches

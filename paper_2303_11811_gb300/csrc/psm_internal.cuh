@@ -107,6 +107,7 @@ struct MapParams {
   // surrogate worklist (eps mode 2): inputs, outputs, slot entry, count
   float* mlp_X;
   float* mlp_eps;
+  double* mlp_lin;      // linear approximation of each worklist cell
   int* mlp_work;
   int* mlp_count;
   // per-particle lists of covered slot entries (box order) for the
@@ -170,7 +171,7 @@ int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
 
 // MLP
 int launch_mlp_samples(unsigned long long seed, long long first, long long count, float* X,
-                       float* eps, cudaStream_t s);
+                       float* eps, float* resid, cudaStream_t s);
 int launch_mlp_loss_grad(const float* params, long long m, const float* X, const float* t,
                          float* grad_partials, int nblocks, float* grad, float* loss,
                          cudaStream_t s);

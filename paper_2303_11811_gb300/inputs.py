@@ -173,7 +173,11 @@ def random_velocities(n, scale, seed):
 
 
 def mlp_init(seed):
-    """He-uniform initial weights for the 4-32-32-1 network (FP64 arrays)."""
+    """He-uniform initial weights for the 4-32-32-1 network (FP64 arrays).
+
+    The radius input (range 2..12) enters the first layer as (r - 7)/5; that
+    fixed affine map is folded into W1 and b1.  The output layer starts small
+    (the network predicts a correction)."""
     rng = np.random.default_rng(seed)
 
     def lin(fan_out, fan_in):
@@ -183,6 +187,8 @@ def mlp_init(seed):
     W1, b1 = lin(32, 4)
     W2, b2 = lin(32, 32)
     W3, b3 = lin(1, 32)
-    b1 += 0.01
+    b1 += 0.01 - W1[:, 3] * 7.0 / 5.0
+    W1[:, 3] /= 5.0
     b2 += 0.01
+    W3 *= 0.01
     return [W1, b1, W2, b2, W3, b3]

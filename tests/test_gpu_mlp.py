@@ -1,0 +1,157 @@
+"""The eps surrogate's CUDA kernels against the FP64 reference (oracle/mlp.py).
+
+- training sampler: inputs and 8^3 labels bit-identical (the recipe is a
+  sequence of IEEE operations on SplitMix64 outputs);
+- loss and gradient of the FP32 forward/backward kernels: within 1e-5 relative
+  (FP32 sums over the batch; the FP64 reference has no rounding to speak of);
+- BF16 tensor-core inference: within a bound derived per sample from the BF16
+  rounding of the layer-2 operands (relative 2^-8 each, FP32 accumulation);
+- training on the device: the surrogate (linear approximation of Eqs. 25-27
+  plus the network's correction) against the 8^3 labels on held-out cells,
+  compared with 4^3 sampling and the linear approximation alone.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Oracle, mlp
+from paper_2303_11811_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2303_11811_gb300 import build, capi
+    build.build()
+    e = capi.Engine(32, 8, 8, 0.6)
+    yield e, capi
+    e.close()
+
+
+def test_sampler_bit_identical(eng):
+    e, capi = eng
+    for seed, first, count in ((123, 0, 20000), (7, 10 ** 6, 5000)):
+        Xg, eg = e.mlp_samples(seed, first, count)
+        X, eps, _, _ = mlp.training_samples(seed, first, count)
+        assert np.array_equal(Xg, X.astype(np.float32))
+        assert np.array_equal(eg, eps.astype(np.float32))
+
+
+def test_loss_and_gradient_match_fp64_backprop(eng):
+    e, capi = eng
+    params = inputs.mlp_init(11)
+    p32 = capi.pack_mlp(params)
+    X, t, _, _ = mlp.training_samples(5, 0, 3000)
+    X32, t32 = X.astype(np.float32), t.astype(np.float32)
+    loss_g, grad_g = e.mlp_loss_grad(p32, X32, t32)
+    ref = capi.unpack_mlp(p32)
+    loss_o, grads_o = mlp.loss_and_grads(ref, X32.astype(np.float64), t32.astype(np.float64))
+    go = np.concatenate([g.ravel() for g in grads_o])
+    assert abs(loss_g - loss_o) <= 1e-5 * loss_o
+    assert np.linalg.norm(grad_g - go) <= 1e-5 * np.linalg.norm(go)
+    big = np.abs(go) > 1e-3 * np.max(np.abs(go))
+    assert np.max(np.abs(grad_g[big] - go[big]) / np.abs(go[big])) < 1e-4
+
+
+def _bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even)."""
+    a = np.asarray(a, np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32)
+
+
+def test_bf16_inference_within_derived_bound(eng):
+    e, capi = eng
+    params = inputs.mlp_init(2)
+    p32 = capi.pack_mlp(params)
+    ref = capi.unpack_mlp(p32)
+    X, _, _, _ = mlp.training_samples(9, 0, 4000)
+    X32 = X.astype(np.float32)
+    got = e.mlp_infer(p32, X32)
+    want, (_, a1, h1, a2, h2) = mlp.forward(ref, X32.astype(np.float64))
+    # layer 2 multiplies BF16(h1) by BF16(W2): each operand is within 2^-8 of
+    # its FP32 value, so each pre-activation moves by at most
+    # 2^-7 * sum_k |W2_jk| |h1_k| (plus FP32 accumulation, far smaller); the
+    # output moves by at most sum_j |W3_j| times that (ReLU is 1-Lipschitz)
+    W2, W3 = np.abs(ref[2]), np.abs(ref[4]).ravel()
+    bound = (2.0 ** -7) * (np.abs(h1) @ W2.T) @ W3 + 1e-5
+    assert np.all(np.abs(got - want) <= bound)
+    assert np.mean(np.abs(got - want)) < 0.1 * np.mean(bound)
+
+
+def test_training_on_device_and_gain(eng):
+    """Train on 2^20 samples; the surrogate's eps error against the 8^3
+    labels on held-out cells (another SplitMix64 stream) is compared with the
+    method without the network: the linear approximation of Eqs. 25-27 alone,
+    and 4^3 sub-division sampling."""
+    e, capi = eng
+    e.set_mlp(capi.pack_mlp(inputs.mlp_init(1)))
+    Xh, th, dh, rh = mlp.training_samples(99, 0, 20000)
+    lin = mlp.linear_eps(dh, rh)
+    loss = e.train_surrogate(1 << 21, 4, epochs=10, batch=1024, lr=3e-3)
+    y = e.mlp_infer(e.get_mlp(), Xh.astype(np.float32))
+    eps = np.clip(lin + y, 0.0, 1.0)
+    rms_mlp = float(np.sqrt(np.mean((eps - th) ** 2)))
+    rms_lin = float(np.sqrt(np.mean((lin - th) ** 2)))
+    c4 = oracle.supersample_batch(dh, rh, 4) / 64.0
+    rms_4 = float(np.sqrt(np.mean((c4 - th) ** 2)))
+    print(f"eps RMS vs 8^3 labels: surrogate {rms_mlp:.4f}, linear {rms_lin:.4f}, "
+          f"4^3 sampling {rms_4:.4f}; training loss {loss:.2e}")
+    assert rms_mlp < 0.7 * rms_lin
+    assert rms_mlp < rms_4
+
+
+def test_mlp_mode_mapping_matches_oracle(eng):
+    """Mapping in surrogate mode: the same cells are partial, single-particle
+    and wall-free on both sides; the network's cells agree within the BF16
+    bound, every other cell (8^3 fallback, inside cells) exactly."""
+    _, capi = eng
+    net = inputs.mlp_init(4)
+    net[4] = net[4] * 0.02   # keep the outputs inside (0, 1), away from the clamp
+    net[5] = np.array([0.5])
+    params = capi.pack_mlp(net)
+    ref = capi.unpack_mlp(params)
+    shape = (40, 32, 36)
+    kw = dict(tau=0.6, relax="trt", walls=(1, 1, 0, 0, 0, 0), weighting="eps",
+              eps_mode="mlp")
+    g = capi.Engine(*shape, **kw)
+    o = Oracle(*shape, **kw)
+    x = np.array([[6.5, 10.2, 12.3], [14.0, 10.6, 12.0], [30.3, 20.2, 30.9]])
+    r = np.array([4.1, 3.5, 5.2])
+    g.set_mlp(params)
+    o.set_mlp(*ref)
+    for s in (g, o):
+        s.set_particles(x, r, fixed=np.ones(3, np.uint8))
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = g.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    # the engine reports the weights after the B > 1 normalisation of Sec. 2.3
+    Bsum = bo0 + bo1
+    over = Bsum > 1.0
+    bo0 = np.where(over, bo0 / np.where(over, Bsum, 1.0), bo0)
+    bo1 = np.where(over, bo1 / np.where(over, Bsum, 1.0), bo1)
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    diff = np.abs(bg0 - bo0)
+    assert np.max(diff) < 0.02
+    wall = np.zeros(pg0.shape, bool)
+    wall[:, :, 0] = wall[:, :, -1] = True
+    # cells fully inside their particle (eps = 1 before any network)
+    z, yy, xx = np.meshgrid(np.arange(shape[2]) + 0.5, np.arange(shape[1]) + 0.5,
+                            np.arange(shape[0]) + 0.5, indexing="ij")
+    inside = np.zeros(pg0.shape, bool)
+    for k in range(len(r)):
+        dy = (yy - x[k, 1] + shape[1] / 2) % shape[1] - shape[1] / 2
+        dz = (z - x[k, 2] + shape[2] / 2) % shape[2] - shape[2] / 2
+        dd = np.sqrt((xx - x[k, 0]) ** 2 + dy ** 2 + dz ** 2)
+        inside |= (pg0 == k) & (dd < r[k] - np.sqrt(3) / 2 - 1e-9)
+    exact = (pg1 >= 0) | inside | wall
+    assert np.max(diff[exact & (pg0 >= 0)]) < 1e-15
+    assert np.sum((~exact) & (pg0 >= 0)) > 100  # the network did map cells
+    assert np.max(np.abs(bg1 - bo1)) < 1e-15
+    g.close()

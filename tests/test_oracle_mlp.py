@@ -59,7 +59,9 @@ def test_training_samples_lie_in_the_partial_band():
     X, eps, _, _ = mlp.training_samples(77, 0, 5000)
     assert np.all((eps >= 0) & (eps <= 1))
     assert np.all(eps * 512 == np.round(eps * 512))
-    assert np.allclose(X[:, :3] * r[:, None], d) and np.all(X[:, 3] == r)
+    a = -np.sort(-np.abs(d / r[:, None]), axis=1)
+    assert np.array_equal(X[:, :3], a) and np.all(X[:, 3] == r)
+    assert np.all(X[:, 0] >= X[:, 1]) and np.all(X[:, 1] >= X[:, 2])
 
 
 def test_labels_agree_with_the_linear_approximation():
@@ -70,6 +72,25 @@ def test_labels_agree_with_the_linear_approximation():
     lin = np.array([oracle.eps_linear(a, b) for a, b in zip(dist, r)])
     assert np.mean(np.abs(lin - eps)) < 0.03
     assert np.corrcoef(lin, eps)[0, 1] > 0.98
+
+
+def test_surrogate_with_zero_network_is_the_linear_approximation():
+    """With the network's output fixed at 0 the surrogate is Eqs. 25-27."""
+    net = inputs.mlp_init(3)
+    net[4] = np.zeros_like(net[4])
+    net[5] = np.zeros(1)
+    d, r = mlp.training_offsets(3, 0, 500)
+    dist = np.sqrt((d * d).sum(axis=1))
+    lin = np.array([oracle.eps_linear(a, b) for a, b in zip(dist, r)])
+    assert np.array_equal(mlp.eps_from_net(net, d, r), lin)
+
+
+def test_network_inputs_are_symmetry_invariant():
+    """Sign flips and permutations of the offset give the same inputs."""
+    d, r = mlp.training_offsets(8, 0, 200)
+    X = mlp.network_inputs(d, r)
+    Y = mlp.network_inputs(-d[:, [2, 0, 1]], r)
+    assert np.array_equal(X, Y)
 
 
 def test_counter_streams_are_reproducible_and_disjoint():
