@@ -42,8 +42,11 @@ __host__ __device__ inline double wq(int q) {
   return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
 }
 
-// neighbours of one cell with periodic wrap and wall validity
-struct Nbr {
+// neighbours of one cell with periodic wrap and wall validity.  WALLS is a
+// compile-time bitmask of the axes that may have walls (bit a for axis a);
+// for the other axes every link is valid and no test is compiled.
+template <int WALLS>
+struct NbrT {
   int X[3], Y[3], Z[3];
   bool VX[3], VY[3], VZ[3];
   __device__ void init(int x, int y, int z, int nx, int ny, int nz, int pitch_x,
@@ -74,9 +77,13 @@ struct Nbr {
     return X[ox + 1] + Y[oy + 1] + Z[oz + 1];
   }
   __device__ __forceinline__ bool ok(int ox, int oy, int oz) const {
-    return VX[ox + 1] && VY[oy + 1] && VZ[oz + 1];
+    const bool okx = (ox == 0 || !(WALLS & 1)) ? true : VX[ox + 1];
+    const bool oky = (oy == 0 || !(WALLS & 2)) ? true : VY[oy + 1];
+    const bool okz = (oz == 0 || !(WALLS & 4)) ? true : VZ[oz + 1];
+    return okx && oky && okz;
   }
 };
+using Nbr = NbrT<7>;
 
 template <typename T>
 struct Vec2;
@@ -165,53 +172,79 @@ __device__ __forceinline__ T image_offset(int i, T xp, int n, bool periodic) {
   return d;
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) lbm_kernel(LbmParams P) {
+// Shared memory of one warp for the solid operator.  Work is split in
+// "jobs" (one per covered cell and occupied slot, at most 32 per round) and
+// "items" (job x direction pair, 9 per job) spread over all 32 lanes, so that
+// the FP64 work of a warp with a few covered cells is not repeated by its
+// idle lanes.  The owner lane of a job folds the item results into its PDFs
+// and its force in a fixed order.
+template <typename T>
+struct SolidSmem {
+  T cu[32][9];     // per lane: c_k . U_f of its cell
+  T am[32][9];     // per lane: antisymmetric moments a_k of its cell
+  T cv[32][9];     // per job: c_k . U_p
+  T con[32][7];    // per job: alpha, beta, gamma for faces and edges, B_i
+  T oq[32][9];     // per job and pair: change of f_q
+  T ob[32][9];     // per job and pair: change of f_qbar
+  T ba[32][9];     // per job and pair: B_i A_k (momentum exchange)
+  int owner[32];
+};
+constexpr int LBM_THREADS = 256;
+
+template <typename T>
+size_t lbm_smem_bytes() {
+  return sizeof(SolidSmem<T>) * (LBM_THREADS / 32);
+}
+
+// FP32 kernels are bandwidth bound and want resident warps (3 blocks per
+// SM); FP64 kernels are FP64-pipe bound and keep their registers
+template <typename T, int MODE, int WALLS>
+__global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 3 : 1) lbm_kernel(LbmParams P) {
   using T2 = typename Vec2<T>::type;
+  extern __shared__ __align__(16) unsigned char lbm_smem[];
   const Grid& g = P.g;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= g.nwords) return;
+  if (warp >= g.nwords) return;  // whole warps only
   const int row = (int)(warp / g.wpr);
-  const int x = (int)(warp - (long long)row * g.wpr) * 32 + lane;
+  const int xr = (int)(warp - (long long)row * g.wpr) * 32 + lane;
+  const bool live = xr < g.nx;   // padding lanes compute on a copy of a real cell
+  const int x = live ? xr : g.nx - 1;
   const int y = row % g.ny;
   const int z = row / g.ny;
   const uint32_t m = P.mask ? __ldg(&P.mask[warp]) : 0u;
-  if (x >= g.nx) return;
 
-  Nbr nb;
+  NbrT<WALLS> nb;
   nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
   const int cell = nb.idx(0, 0, 0);
-  const long long NC = g.ncell;
-  // src == dst for the AA pattern: every thread reads its whole set of
-  // locations before it writes the same set, so no restrict on dst
-  const T* src = static_cast<const T*>(P.src);
-  T* dst = static_cast<T*>(P.dst);
+  // per-direction base pointers live in the kernel parameters: one address
+  // computation per access.  For the AA pattern source and destination are
+  // the same array: every thread reads its whole set of locations before it
+  // writes the same set.
+#define SRC(q) static_cast<const T*>(P.srcq[q])
+#define DST(q) static_cast<T*>(P.dstq[q])
 
   // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls)
   T d[Q];
-  d[0] = ld(src + cell);
+  d[0] = ld(SRC(0) + cell);
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int cx = ckx(k), cy = cky(k), cz = ckz(k);
     const int qa = 2 * k + 1, qb = 2 * k + 2;
-    long long ia, ib;
     if (MODE == 0) {         // pull from the other buffer
-      ia = nb.ok(-cx, -cy, -cz) ? qa * NC + nb.idx(-cx, -cy, -cz) : qb * NC + cell;
-      ib = nb.ok(cx, cy, cz) ? qb * NC + nb.idx(cx, cy, cz) : qa * NC + cell;
+      d[qa] = nb.ok(-cx, -cy, -cz) ? ld(SRC(qa) + nb.idx(-cx, -cy, -cz)) : ld(SRC(qb) + cell);
+      d[qb] = nb.ok(cx, cy, cz) ? ld(SRC(qb) + nb.idx(cx, cy, cz)) : ld(SRC(qa) + cell);
     } else if (MODE == 1) {  // AA even: own cell
-      ia = qa * NC + cell;
-      ib = qb * NC + cell;
+      d[qa] = ld(SRC(qa) + cell);
+      d[qb] = ld(SRC(qb) + cell);
     } else {                 // AA odd: swapped slots of the neighbours
-      ia = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
-      ib = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
+      d[qa] = nb.ok(-cx, -cy, -cz) ? ld(SRC(qb) + nb.idx(-cx, -cy, -cz)) : ld(SRC(qa) + cell);
+      d[qb] = nb.ok(cx, cy, cz) ? ld(SRC(qa) + nb.idx(cx, cy, cz)) : ld(SRC(qb) + cell);
     }
-    d[qa] = ld(src + ia);
-    d[qb] = ld(src + ib);
   }
 
   // ---- coverage of this cell
-  const bool cov = (m >> lane) & 1u;
+  bool cov = live && ((m >> lane) & 1u);
   int e = 0;
   int2 pid = make_int2(-1, -1);
   T2 Bs;
@@ -222,6 +255,8 @@ __global__ void __launch_bounds__(256) lbm_kernel(LbmParams P) {
     if (e < P.slot_cap) {
       pid = __ldg(&P.slot_pid[e]);
       Bs = __ldg(static_cast<const T2*>(P.slot_B) + e);
+    } else {
+      cov = false;
     }
   }
   T B = Bs.x + Bs.y;
@@ -274,73 +309,167 @@ __global__ void __launch_bounds__(256) lbm_kernel(LbmParams P) {
     d[2 * k + 2] += ds - da;
   }
 
-  // ---- solid operator of each overlapping particle (Eqs. 19-21)
-  if (cov && e < P.slot_cap) {
+  // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
+  // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
+  // warp; in FP32 each covered lane does its own cell.
+  if (sizeof(T) == 4 && cov) {
 #pragma unroll 1
     for (int sl = 0; sl < 2; ++sl) {
       const int p = sl ? pid.y : pid.x;
+      if (p < 0) continue;
       const T Bi = sl ? Bs.y : Bs.x;
-      T Fx = T(0), Fy = T(0), Fz = T(0);
-      if (p >= 0) {
-        T xp[3], up[3], op[3];
-        load_particle<T>(P, p, xp, up, op);
-        const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
-        const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
-        const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
-        // Eq. 20: surface velocity at the cell centre
-        const T Vx = up[0] + (op[1] * dz - op[2] * dy);
-        const T Vy = up[1] + (op[2] * dx - op[0] * dz);
-        const T Vz = up[2] + (op[0] * dy - op[1] * dx);
-        const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
-        d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
-        T ax = T(0), ay = T(0), az = T(0);
+      T xp[3], up[3], op[3];
+      load_particle<T>(P, p, xp, up, op);
+      const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
+      const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
+      const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
+      // Eq. 20: surface velocity at the cell centre
+      const T Vx = up[0] + (op[1] * dz - op[2] * dy);
+      const T Vy = up[1] + (op[2] * dx - op[0] * dz);
+      const T Vz = up[2] + (op[0] * dy - op[1] * dx);
+      const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+      d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
+      T ax = T(0), ay = T(0), az = T(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const T w = wk<T>(k);
-          const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
-          const T cv = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
-          const T dS = w * (T(4.5) * (cv - cu) * (cv + cu) - T(1.5) * dU2);
-          const T A = (T(3) * w) * (cu + cv) - a[k];
-          d[2 * k + 1] += Bi * (dS + A);
-          d[2 * k + 2] += Bi * (dS - A);
-          if (ckx(k) > 0) ax += A;
-          if (cky(k) > 0) ay += A;
-          if (cky(k) < 0) ay -= A;
-          if (ckz(k) > 0) az += A;
-          if (ckz(k) < 0) az -= A;
-        }
-        // Eq. 21: B_i sum_q C^s_q c_qbar = -2 B_i sum_k A_k c_k
-        Fx = T(-2) * Bi * ax;
-        Fy = T(-2) * Bi * ay;
-        Fz = T(-2) * Bi * az;
+      for (int k = 0; k < 9; ++k) {
+        const T w = wk<T>(k);
+        const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
+        const T cv = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
+        const T Sv = cv + cu;
+        const T BdS = (T(4.5) * w * Bi) * ((cv - cu) * Sv) + (T(-1.5) * w) * (Bi * dU2);
+        const T BA = (T(3) * w * Bi) * Sv - Bi * a[k];
+        d[2 * k + 1] += BdS + BA;
+        d[2 * k + 2] += BdS - BA;
+        if (ckx(k) > 0) ax += BA;
+        if (cky(k) > 0) ay += BA;
+        if (cky(k) < 0) ay -= BA;
+        if (ckz(k) > 0) az += BA;
+        if (ckz(k) < 0) az -= BA;
       }
+      // Eq. 21: B_i sum_q C^s_q c_qbar = -2 sum_k B_i A_k c_k
       T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
-      o[0] = Fx;
-      o[1] = Fy;
-      o[2] = Fz;
+      o[0] = T(-2) * ax;
+      o[1] = T(-2) * ay;
+      o[2] = T(-2) * az;
     }
   }
+  if (sizeof(T) == 8 && m != 0u) {
+    SolidSmem<T>& S = reinterpret_cast<SolidSmem<T>*>(lbm_smem)[threadIdx.x >> 5];
+    const bool has0 = cov && pid.x >= 0, has1 = cov && pid.y >= 0;
+    const unsigned b0 = __ballot_sync(0xffffffffu, has0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, has1);
+    const unsigned below = (1u << lane) - 1u;
+    const int J0 = __popc(b0), J = J0 + __popc(b1);
+    const int j0 = __popc(b0 & below), j1 = J0 + __popc(b1 & below);
+    if (has0 || has1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        S.cu[lane][k] = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
+        S.am[lane][k] = a[k];
+      }
+    }
+    for (int c0 = 0; c0 < J; c0 += 32) {
+      // job set-up by the owner lanes: surface velocity (Eq. 20) and the
+      // per-job constants of the item arithmetic
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const bool has = sl ? has1 : has0;
+        const int jj = (sl ? j1 : j0) - c0;
+        if (has && jj >= 0 && jj < 32) {
+          const int p = sl ? pid.y : pid.x;
+          const T Bi = sl ? Bs.y : Bs.x;
+          T xp[3], up[3], op[3];
+          load_particle<T>(P, p, xp, up, op);
+          const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
+          const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
+          const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
+          const T Vx = up[0] + (op[1] * dz - op[2] * dy);
+          const T Vy = up[1] + (op[2] * dx - op[0] * dz);
+          const T Vz = up[2] + (op[0] * dy - op[1] * dx);
+          const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+          d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
+#pragma unroll
+          for (int k = 0; k < 9; ++k)
+            S.cv[jj][k] = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
+          const T BdU = Bi * dU2;
+          S.con[jj][0] = (T(4.5) * wk<T>(0)) * Bi;
+          S.con[jj][1] = (T(-1.5) * wk<T>(0)) * BdU;
+          S.con[jj][2] = (T(3) * wk<T>(0)) * Bi;
+          S.con[jj][3] = (T(4.5) * wk<T>(3)) * Bi;
+          S.con[jj][4] = (T(-1.5) * wk<T>(3)) * BdU;
+          S.con[jj][5] = (T(3) * wk<T>(3)) * Bi;
+          S.con[jj][6] = Bi;
+          S.owner[jj] = lane;
+        }
+      }
+      __syncwarp();
+      // items: job j, pair k.  C^s has symmetric part B_i w_k (9/2 (cv^2 -
+      // cu^2) - 3/2 dU2) and antisymmetric part B_i (3 w_k (cu + cv) - a_k)
+      const int nj = J - c0 < 32 ? J - c0 : 32;
+      for (int t = lane; t < 9 * nj; t += 32) {
+        const int j = t / 9, k = t - 9 * j;
+        const int L = S.owner[j];
+        const T cu = S.cu[L][k], cv = S.cv[j][k];
+        const int cl = k < 3 ? 0 : 3;
+        const T Dv = cv - cu, Sv = cv + cu;
+        const T BdS = S.con[j][cl] * (Dv * Sv) + S.con[j][cl + 1];
+        const T BA = S.con[j][cl + 2] * Sv - S.con[j][6] * S.am[L][k];
+        S.oq[j][k] = BdS + BA;
+        S.ob[j][k] = BdS - BA;
+        S.ba[j][k] = BA;
+      }
+      __syncwarp();
+      // owners fold the results in a fixed order; Eq. 21 per slot:
+      // B_i sum_q C^s_q c_qbar = -2 sum_k B_i A_k c_k
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const bool has = sl ? has1 : has0;
+        const int jj = (sl ? j1 : j0) - c0;
+        if (has && jj >= 0 && jj < 32) {
+          T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            d[2 * k + 1] += S.oq[jj][k];
+            d[2 * k + 2] += S.ob[jj][k];
+            const T A = S.ba[jj][k];
+            if (ckx(k) > 0) ax += A;
+            if (cky(k) > 0) ay += A;
+            if (cky(k) < 0) ay -= A;
+            if (ckz(k) > 0) az += A;
+            if (ckz(k) < 0) az -= A;
+          }
+          T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
+          o[0] = T(-2) * ax;
+          o[1] = T(-2) * ay;
+          o[2] = T(-2) * az;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (!live) return;
 
   // ---- store
-  dst[cell] = d[0];
+  DST(0)[cell] = d[0];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int cx = ckx(k), cy = cky(k), cz = ckz(k);
     const int qa = 2 * k + 1, qb = 2 * k + 2;
-    long long oa, ob;
     if (MODE == 0) {
-      oa = qa * NC + cell;
-      ob = qb * NC + cell;
+      DST(qa)[cell] = d[qa];
+      DST(qb)[cell] = d[qb];
     } else if (MODE == 1) {
-      oa = qb * NC + cell;
-      ob = qa * NC + cell;
+      DST(qb)[cell] = d[qa];
+      DST(qa)[cell] = d[qb];
     } else {
-      oa = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
-      ob = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
+      if (nb.ok(cx, cy, cz)) DST(qa)[nb.idx(cx, cy, cz)] = d[qa];
+      else DST(qb)[cell] = d[qa];
+      if (nb.ok(-cx, -cy, -cz)) DST(qb)[nb.idx(-cx, -cy, -cz)] = d[qb];
+      else DST(qa)[cell] = d[qb];
     }
-    dst[oa] = d[qa];
-    dst[ob] = d[qb];
   }
+#undef SRC
+#undef DST
 }
 
 // canonical FP64 f~ (unpadded, full f = w + delta) from the storage layout
@@ -485,19 +614,55 @@ __global__ void sums_final_kernel(int nparts, const double* __restrict__ partial
 
 }  // namespace
 
-int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s) {
-  const long long threads = P.g.nwords * 32;
-  const int block = 256;
-  const unsigned grid = (unsigned)((threads + block - 1) / block);
-  if (fp32) {
-    if (mode == 0) lbm_kernel<float, 0><<<grid, block, 0, s>>>(P);
-    else if (mode == 1) lbm_kernel<float, 1><<<grid, block, 0, s>>>(P);
-    else lbm_kernel<float, 2><<<grid, block, 0, s>>>(P);
-  } else {
-    if (mode == 0) lbm_kernel<double, 0><<<grid, block, 0, s>>>(P);
-    else if (mode == 1) lbm_kernel<double, 1><<<grid, block, 0, s>>>(P);
-    else lbm_kernel<double, 2><<<grid, block, 0, s>>>(P);
+template <typename T>
+size_t lbm_dyn_smem() {
+  return sizeof(T) == 8 ? lbm_smem_bytes<T>() : 0;
+}
+
+template <typename T, int W>
+int configure_walls() {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  const int sm = (int)lbm_dyn_smem<T>();
+  int bad = 0;
+  bad |= cudaFuncSetAttribute(lbm_kernel<T, 0, W>, a, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(lbm_kernel<T, 1, W>, a, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(lbm_kernel<T, 2, W>, a, sm) != cudaSuccess;
+  return bad;
+}
+
+int lbm_configure() {
+  return configure_walls<float, 0>() | configure_walls<float, 1>() | configure_walls<float, 7>() |
+         configure_walls<double, 0>() | configure_walls<double, 1>() |
+         configure_walls<double, 7>();
+}
+
+template <typename T, int W>
+void launch_lbm_t(const LbmParams& P, int mode, unsigned grid, cudaStream_t s) {
+  const size_t sm = lbm_dyn_smem<T>();
+  if (mode == 0) lbm_kernel<T, 0, W><<<grid, LBM_THREADS, sm, s>>>(P);
+  else if (mode == 1) lbm_kernel<T, 1, W><<<grid, LBM_THREADS, sm, s>>>(P);
+  else lbm_kernel<T, 2, W><<<grid, LBM_THREADS, sm, s>>>(P);
+}
+
+template <typename T>
+void launch_lbm_w(const LbmParams& P, int mode, unsigned grid, cudaStream_t s) {
+  const int w = P.g.wall[0] | (P.g.wall[1] << 1) | (P.g.wall[2] << 2);
+  if (w == 0) launch_lbm_t<T, 0>(P, mode, grid, s);
+  else if (w == 1) launch_lbm_t<T, 1>(P, mode, grid, s);
+  else launch_lbm_t<T, 7>(P, mode, grid, s);
+}
+
+int launch_lbm(const LbmParams& P0, int fp32, int mode, cudaStream_t s) {
+  LbmParams P = P0;
+  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  for (int q = 0; q < Q; ++q) {
+    P.srcq[q] = static_cast<const char*>(P.src) + esz * (size_t)q * P.g.ncell;
+    P.dstq[q] = static_cast<char*>(P.dst) + esz * (size_t)q * P.g.ncell;
   }
+  const long long threads = P.g.nwords * 32;
+  const unsigned grid = (unsigned)((threads + LBM_THREADS - 1) / LBM_THREADS);
+  if (fp32) launch_lbm_w<float>(P, mode, grid, s);
+  else launch_lbm_w<double>(P, mode, grid, s);
   return 1;
 }
 

@@ -409,6 +409,10 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "initialisation of device buffers failed");
   }
+  if (lbm_configure() != 0) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "could not set the shared-memory size of the collision kernel");
+  }
   launch_step_const(map_params(c), s);
   if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();

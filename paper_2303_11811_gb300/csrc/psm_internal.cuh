@@ -122,6 +122,8 @@ struct LbmParams {
   Grid g;
   const void* src;      // T*
   void* dst;            // T*
+  const void* srcq[19]; // per-direction planes (filled by the launcher)
+  void* dstq[19];
   const uint32_t* mask; // nullptr when there are no particles
   const int* base;
   const int2* slot_pid;
@@ -139,6 +141,7 @@ struct LbmParams {
 };
 
 // ---- launchers (stream-ordered; return the number of kernel launches) ----
+int lbm_configure();  // kernel attributes; call once before launching (returns != 0 on error)
 int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s);
 int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
                         double* out, cudaStream_t s);

@@ -14,7 +14,7 @@ particle bed is not public):
   sequential addition (surface gap >= 1), density ratio 2.5, gravity 2e-5 in
   -z, TRT (Lambda = 3/16) tau = 0.55, spring-dashpot DEM (k_n = 1e3, e = 0.9).
 * ``channel``    256x256x512 channel, walls at the x faces, periodic y/z,
-  12,816 fixed spheres r = 5 at solid fraction 0.20, TRT tau = 0.55, body
+  12,817 fixed spheres r = 5 at solid fraction 0.20, TRT tau = 0.55, body
   force 1e-5 along z.
 * ``settle512``  512x512x1024 periodic box, polydisperse spheres r in [3, 6]
   at solid fraction 0.15, settling under gravity 2e-5, density ratio 2.5.
