@@ -199,7 +199,7 @@ size_t lbm_smem_bytes() {
 // FP32 kernels are bandwidth bound and want resident warps (3 blocks per
 // SM); FP64 kernels are FP64-pipe bound and keep their registers
 template <typename T, int MODE, int WALLS>
-__global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 3 : 1) lbm_kernel(LbmParams P) {
+__global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kernel(LbmParams P) {
   using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char lbm_smem[];
   const Grid& g = P.g;

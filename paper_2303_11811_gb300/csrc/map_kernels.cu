@@ -313,7 +313,11 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
       const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
       const long long e = slot_index(P.cov, cell);
       if (e < P.s.cap) {
-        if (pos < lcap) P.list[loff + pos] = (int)e;
+        if (pos < lcap) {
+          P.list[loff + pos] = (int)e;
+          if (P.fp32)
+            P.listf[loff + pos] = make_float4((float)h.dx, (float)h.dy, (float)h.dz, 0.f);
+        }
         const int s = atomicAdd(&P.s.cnt[e], 1);
         if (s >= 2) {
           atomicOr(P.status, ST_SLOT_OVERFLOW);
@@ -500,6 +504,65 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
   }
 }
 
+// FP32 path: per-slot contributions are FP32, and so are the torque arms
+// stored by the mapping; every component is summed with an error-free
+// two-sum (a float pair carrying about 48 bits), then across the block in FP64
+// in a fixed order.  No FP64 arithmetic per entry: GB300 runs FP64 at 1/58 of
+// the FP32 rate.
+struct FloatPair {
+  float hi, lo;
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x;
+    const float bb = t - hi;
+    const float err = (hi - (t - bb)) + (x - bb);
+    hi = t;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams P) {
+  __shared__ double sh[6][RED_THREADS];
+  const int p = blockIdx.x;
+  const float* Fc = static_cast<const float*>(P.s.Fc);
+  const long long loff = P.list_off[p];
+  const int cnt = P.list_cnt[p];
+  FloatPair acc[6];
+  for (int i = 0; i < 6; ++i) acc[i] = FloatPair{0.f, 0.f};
+  for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
+    const int e = P.list[loff + k];
+    const float4 d = P.listf[loff + k];
+    const int2 pid = P.s.pid[e];
+    const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
+    if (s < 0) continue;
+    const float f0 = Fc[6LL * e + 3 * s];
+    const float f1 = Fc[6LL * e + 3 * s + 1];
+    const float f2 = Fc[6LL * e + 3 * s + 2];
+    acc[0].add(f0);
+    acc[1].add(f1);
+    acc[2].add(f2);
+    acc[3].add(d.y * f2 - d.z * f1);
+    acc[4].add(d.z * f0 - d.x * f2);
+    acc[5].add(d.x * f1 - d.y * f0);
+  }
+  for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] = acc[i].value();
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    bool finite = true;
+    for (int i = 0; i < 3; ++i) {
+      P.p.Fh[3 * p + i] = sh[i][0];
+      P.p.Th[3 * p + i] = sh[3 + i][0];
+      finite = finite && isfinite(sh[i][0]) && isfinite(sh[3 + i][0]);
+    }
+    if (!finite) atomicOr(P.status, ST_NONFINITE);
+  }
+}
+
 __global__ void pack_particles_kernel(Particles p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
@@ -608,7 +671,7 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
 
 int launch_force_reduce(MapParams P, cudaStream_t s) {
   if (P.p.n == 0) return 0;
-  if (P.fp32) force_reduce_kernel<float><<<P.p.n, RED_THREADS, 0, s>>>(P);
+  if (P.fp32) force_reduce_f32_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
   else force_reduce_kernel<double><<<P.p.n, RED_THREADS, 0, s>>>(P);
   return 1;
 }

@@ -58,6 +58,7 @@ struct psm_ctx {
   long long mlp_cap = 0;
   long long* list_off = nullptr;  // per-particle entry lists (force reduction)
   int* list = nullptr;
+  float4* listf = nullptr;
   int* list_cnt = nullptr;
   bool error_state = false;
   std::string err;
@@ -134,6 +135,7 @@ void free_particles(psm_ctx* c) {
   c->mlp_cap = 0;
   c->list_off = nullptr;
   c->list = nullptr;
+  c->listf = nullptr;
   c->list_cnt = nullptr;
 }
 
@@ -165,6 +167,7 @@ MapParams map_params(psm_ctx* c) {
   P.mlp_count = c->mlp_count;
   P.list_off = c->list_off;
   P.list = c->list;
+  P.listf = c->listf;
   P.list_cnt = c->list_cnt;
   return P;
 }
@@ -509,6 +512,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   S.Fc = alloc_n<unsigned char>(c, cp * 6 * (c->fp32 ? 4 : 8), c->palloc);
   c->list_off = alloc_n<long long>(c, (size_t)n + 1, c->palloc);
   c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
+  if (c->fp32) c->listf = alloc_n<float4>(c, (size_t)list_total, c->palloc);
   c->list_cnt = alloc_n<int>(c, n1, c->palloc);
   if (c->opt.eps_mode == PSM_EPS_MLP) {
     c->mlp_cap = (long long)cp;

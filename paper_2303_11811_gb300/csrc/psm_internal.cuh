@@ -114,6 +114,7 @@ struct MapParams {
   // fixed-order force/torque reduction
   const long long* list_off;   // n+1 offsets
   int* list;
+  float4* listf;               // FP32 path: cell-centre offset of each entry
   int* list_cnt;
 };
 constexpr int MAP_PARTIALS = 152 * 32;
