@@ -47,12 +47,14 @@ __global__ void dem_position_kernel(DemParams P) {
   P.p.xf[4 * i + 3] = (float)P.p.r[i];
 }
 
-// exact FP64 contact of i with j (j != i); adds to F when in contact
-__device__ __forceinline__ void pair_contact(const DemParams& P, int i, int j, double* F) {
+// exact FP64 contact of i with j (j != i); adds to F when in contact.
+// X and U are the positions and velocities of the current sub-step.
+__device__ __forceinline__ void pair_contact(const DemParams& P, const double* X,
+                                             const double* U, int i, int j, double* F) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   double d[3];
   for (int a = 0; a < 3; ++a) {
-    double v = P.p.x[3 * i + a] - P.p.x[3 * j + a];
+    double v = X[3 * i + a] - X[3 * j + a];
     if (!P.g.wall[a]) {
       if (v > 0.5 * dims[a]) v -= dims[a];
       else if (v < -0.5 * dims[a]) v += dims[a];
@@ -65,44 +67,54 @@ __device__ __forceinline__ void pair_contact(const DemParams& P, int i, int j, d
   const double dist = sqrt(dist2);
   const double delta = rs - dist;
   const double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
-  const double vrel[3] = {P.p.u[3 * i] - P.p.u[3 * j], P.p.u[3 * i + 1] - P.p.u[3 * j + 1],
-                          P.p.u[3 * i + 2] - P.p.u[3 * j + 2]};
+  const double vrel[3] = {U[3 * i] - U[3 * j], U[3 * i + 1] - U[3 * j + 1],
+                          U[3 * i + 2] - U[3 * j + 2]};
   const double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
   const double meff = P.p.m[i] * P.p.m[j] / (P.p.m[i] + P.p.m[j]);
   const double dn = damping(meff, P.kn, P.log_e);
   for (int a = 0; a < 3; ++a) F[a] += P.kn * delta * n[a] - dn * vn * n[a];
 }
 
-__device__ __forceinline__ void wall_contacts(const DemParams& P, int i, double* F) {
+__device__ __forceinline__ void wall_contacts(const DemParams& P, const double* X,
+                                              const double* U, int i, double* F) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   for (int a = 0; a < 3; ++a) {
     if (!P.g.wall[a]) continue;
     for (int side = 0; side < 2; ++side) {
-      const double delta = side == 0 ? P.p.r[i] - P.p.x[3 * i + a]
-                                     : P.p.x[3 * i + a] + P.p.r[i] - dims[a];
+      const double delta = side == 0 ? P.p.r[i] - X[3 * i + a]
+                                     : X[3 * i + a] + P.p.r[i] - dims[a];
       if (!(delta > 0.0)) continue;
       const double nn = side == 0 ? 1.0 : -1.0;
-      const double vn = P.p.u[3 * i + a] * nn;
+      const double vn = U[3 * i + a] * nn;
       const double dn = damping(P.p.m[i], P.kn, P.log_e);
       F[a] += P.kn * delta * nn - dn * vn * nn;
     }
   }
 }
 
-// one warp per particle, all other particles scanned with an FP32 prefilter
-__global__ void dem_contact_allpairs_kernel(DemParams P) {
+// One sub-step in one launch: one warp per particle scans all others with an
+// FP32 prefilter, sums its contacts in ascending j (Eq. 12), updates its
+// velocity (Eq. 16) and writes the positions of the next sub-step (Eq. 15).
+// Positions and velocities are double-buffered: every contact reads the
+// current sub-step's state (Xc, Uc, XFc) while the new state goes to
+// (Xn, Un, XFn).  On the last sub-step the positions are carried over.
+__global__ void dem_substep_kernel(DemParams P, const double* __restrict__ Xc,
+                                   const double* __restrict__ Uc,
+                                   const float4* __restrict__ XFc, double* __restrict__ Xn,
+                                   double* __restrict__ Un, float4* __restrict__ XFn,
+                                   int last) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= P.p.n) return;
   const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
-  const float4 xi = reinterpret_cast<const float4*>(P.p.xf)[i];
+  const float4 xi = XFc[i];
   double F[3] = {0.0, 0.0, 0.0};
   const int n = P.p.n;
   for (int base = 0; base < n; base += 32) {
     const int j = base + lane;
     bool cand = false;
     if (j < n && j != i) {
-      const float4 xj = reinterpret_cast<const float4*>(P.p.xf)[j];
+      const float4 xj = XFc[j];
       float d[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
       for (int a = 0; a < 3; ++a) {
         if (!P.g.wall[a]) {
@@ -117,46 +129,55 @@ __global__ void dem_contact_allpairs_kernel(DemParams P) {
     while (bits) {
       const int l = __ffs(bits) - 1;
       bits &= bits - 1;
-      pair_contact(P, i, base + l, F);  // same values on all lanes
+      pair_contact(P, Xc, Uc, i, base + l, F);  // same values on all lanes
     }
   }
-  if (lane == 0) {
-    wall_contacts(P, i, F);
-    for (int a = 0; a < 3; ++a) P.p.Fc[3 * i + a] = F[a];
-  }
-}
-
-// velocity update of one sub-step (Eq. 16) fused with the position update
-// of the next (Eq. 15): both only touch particle i
-__global__ void dem_velocity_position_kernel(DemParams P, int next_position) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+  if (lane != 0) return;
+  wall_contacts(P, Xc, Uc, i, F);
   const double dt = P.dt;
-  const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  const double ddims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
+  double u[3], x[3];
+  for (int a = 0; a < 3; ++a) {
+    u[a] = Uc[3 * i + a];
+    x[a] = Xc[3 * i + a];
+  }
   if (!P.p.fixed[i]) {
     for (int a = 0; a < 3; ++a) {
-      const double Fn = P.p.Fh[3 * i + a] + P.p.Fc[3 * i + a] +
-                        (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
+      const double Fn = P.p.Fh[3 * i + a] + F[a] + (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
       const double Tn = P.p.Th[3 * i + a];
-      P.p.u[3 * i + a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
+      u[a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
       P.p.om[3 * i + a] += dt * (P.p.Told[3 * i + a] + Tn) / (2.0 * P.p.I[i]);
       P.p.Fold[3 * i + a] = Fn;
       P.p.Told[3 * i + a] = Tn;
     }
-    if (next_position) {
+    if (!last) {
       for (int a = 0; a < 3; ++a) {
-        double xn = P.p.x[3 * i + a] + dt * P.p.u[3 * i + a] +
-                    dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
+        double xn = x[a] + dt * u[a] + dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
         if (!P.g.wall[a]) {
-          if (xn >= dims[a]) xn -= dims[a];
-          else if (xn < 0.0) xn += dims[a];
+          if (xn >= ddims[a]) xn -= ddims[a];
+          else if (xn < 0.0) xn += ddims[a];
         }
-        P.p.x[3 * i + a] = xn;
+        x[a] = xn;
       }
     }
   }
-  if (next_position)
-    for (int a = 0; a < 3; ++a) P.p.xf[4 * i + a] = (float)P.p.x[3 * i + a];
+  for (int a = 0; a < 3; ++a) {
+    Un[3 * i + a] = u[a];
+    Xn[3 * i + a] = x[a];
+  }
+  XFn[i] = make_float4((float)x[0], (float)x[1], (float)x[2], xi.w);
+}
+
+__global__ void dem_copy_back_kernel(DemParams P, const double* __restrict__ X,
+                                     const double* __restrict__ U,
+                                     const float4* __restrict__ XF) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n) return;
+  for (int a = 0; a < 3; ++a) {
+    P.p.x[3 * i + a] = X[3 * i + a];
+    P.p.u[3 * i + a] = U[3 * i + a];
+  }
+  reinterpret_cast<float4*>(P.p.xf)[i] = XF[i];
 }
 
 }  // namespace
@@ -170,10 +191,23 @@ int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
   int launches = 0;
   dem_position_kernel<<<gp, tb, 0, s>>>(P);
   ++launches;
+  const double* Xc = P.p.x;
+  const double* Uc = P.p.u;
+  const float4* XFc = reinterpret_cast<const float4*>(P.p.xf);
   for (int sc = 0; sc < subcycles; ++sc) {
-    dem_contact_allpairs_kernel<<<gw, tb, 0, s>>>(P);
-    dem_velocity_position_kernel<<<gp, tb, 0, s>>>(P, sc + 1 < subcycles);
-    launches += 2;
+    const bool to2 = (sc % 2) == 0;
+    double* Xn = to2 ? P.p.x2 : P.p.x;
+    double* Un = to2 ? P.p.u2 : P.p.u;
+    float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
+    dem_substep_kernel<<<gw, tb, 0, s>>>(P, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+    ++launches;
+    Xc = Xn;
+    Uc = Un;
+    XFc = XFn;
+  }
+  if (subcycles % 2 == 1) {
+    dem_copy_back_kernel<<<gp, tb, 0, s>>>(P, Xc, Uc, XFc);
+    ++launches;
   }
   return launches;
 }

@@ -58,6 +58,49 @@ __device__ inline int supersample_count_fast(double dx, double dy, double dz, do
   return count;
 }
 
+// the same count for a compile-time n (4 or 8): offsets are exact constants
+// and the squared x, y, z terms of the sample rows are formed once.  The
+// unrolled loop counts the samples certainly inside (S < lo) and those not
+// certainly outside (S <= hi); when the counts agree no sample lies in the
+// band, otherwise the cell is recounted with the FP64 test inside the band.
+template <int N>
+__device__ inline int supersample_count_n(double dx, double dy, double dz, double r) {
+  const float E = certified_band(r);
+  const float r2f = (float)(r * r);
+  const float lo = r2f - E, hi = r2f + E;
+  float X[N], Y[N], Z[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+    const float s = (float)((a + 0.5) / N - 0.5);
+    const float px = (float)dx + s, py = (float)dy + s, pz = (float)dz + s;
+    X[a] = px * px;
+    Y[a] = py * py;
+    Z[a] = pz * pz;
+  }
+  int in = 0, maybe = 0;
+#pragma unroll
+  for (int a = 0; a < N; ++a) {
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+      const float XY = X[a] + Y[b];
+#pragma unroll
+      for (int c = 0; c < N; ++c) {
+        const float S = XY + Z[c];
+        in += S < lo;
+        maybe += S <= hi;
+      }
+    }
+  }
+  if (in == maybe) return in;
+  double s64[N];
+  float s32[N];
+  for (int a = 0; a < N; ++a) {
+    s64[a] = sample_offset(a, N);
+    s32[a] = (float)s64[a];
+  }
+  return supersample_count_fast(dx, dy, dz, r, N, s64, s32);
+}
+
 // FP64 definition, all samples (reference for small counts and tests)
 __device__ inline int supersample_count(double dx, double dy, double dz, double r, int n) {
   const double r2 = r * r;

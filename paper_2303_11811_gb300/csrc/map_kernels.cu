@@ -23,7 +23,7 @@ namespace psm {
 namespace {
 
 constexpr double HALF_SQRT3 = kHalfSqrt3;
-constexpr int MAP_THREADS = 128;
+constexpr int MAP_THREADS = 256;
 constexpr int RED_THREADS = 128;
 constexpr int SCAN_THREADS = 1024;
 
@@ -270,7 +270,9 @@ __device__ double cell_eps(const MapParams& P, const Box& b, const CellHit& h, d
   }
   if (P.eps_mode == 2) return -1.0;
   const int n = P.eps_n;
-  const int cnt = supersample_count_fast(h.dx, h.dy, h.dz, r, n, s64, s32);
+  const int cnt = n == 4   ? supersample_count_n<4>(h.dx, h.dy, h.dz, r)
+                  : n == 8 ? supersample_count_n<8>(h.dx, h.dy, h.dz, r)
+                           : supersample_count_fast(h.dx, h.dy, h.dz, r, n, s64, s32);
   const int n3 = n * n * n;
   // count / n^3; for n^3 a power of two the product with the reciprocal is
   // the same IEEE result as the quotient
@@ -386,9 +388,6 @@ __global__ void apply_mlp_kernel(MapParams P) {
 
 __global__ void finish_kernel(MapParams P) {
   __shared__ double red[256];
-  __shared__ double s64[16];
-  __shared__ float s32[16];
-  load_offsets(8, s64, s32);
   const int n = slot_count(P);
   double accB = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -414,7 +413,7 @@ __global__ void finish_kernel(MapParams P) {
         const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
         const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
         const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-        const double eps = (double)supersample_count_fast(dx, dy, dz, r, 8, s64, s32) * (1.0 / 512.0);
+        const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
         Bs = weight(eps, P.tau, P.weighting);
       }
     }

@@ -73,13 +73,6 @@ __device__ __forceinline__ float4 network_input(double dx, double dy, double dz,
 __global__ void samples_kernel(unsigned long long seed, long long first, long long count,
                                float* __restrict__ X, float* __restrict__ eps,
                                float* __restrict__ resid) {
-  __shared__ double s64[8];
-  __shared__ float s32[8];
-  if (threadIdx.x < 8) {
-    s64[threadIdx.x] = sample_offset(threadIdx.x, 8);
-    s32[threadIdx.x] = (float)s64[threadIdx.x];
-  }
-  __syncthreads();
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
        t += (long long)gridDim.x * blockDim.x) {
     const unsigned long long i = (unsigned long long)(first + t);
@@ -94,7 +87,7 @@ __global__ void samples_kernel(unsigned long long seed, long long first, long lo
     const double rho = (r - kHalfSqrt3) + 1.7320508075688772935 * u[4];
     const double tt = rho / nv;
     const double d0 = v0 * tt, d1 = v1 * tt, d2 = v2 * tt;
-    const int cnt = supersample_count_fast(d0, d1, d2, r, 8, s64, s32);
+    const int cnt = supersample_count_n<8>(d0, d1, d2, r);
     reinterpret_cast<float4*>(X)[t] = network_input(d0, d1, d2, r);
     const double label = (double)cnt * (1.0 / 512.0);
     eps[t] = (float)label;

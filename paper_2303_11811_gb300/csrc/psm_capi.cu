@@ -502,6 +502,9 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   P.xf = alloc_n<float>(c, n4, c->palloc);
   P.uf = alloc_n<float>(c, n4, c->palloc);
   P.omf = alloc_n<float>(c, n4, c->palloc);
+  P.x2 = alloc_n<double>(c, n3, c->palloc);
+  P.u2 = alloc_n<double>(c, n3, c->palloc);
+  P.xf2 = alloc_n<float>(c, n4, c->palloc);
   Slots& S = c->slots;
   const size_t cp = cap > 0 ? (size_t)cap : 1;
   S.cap = (long long)cp;

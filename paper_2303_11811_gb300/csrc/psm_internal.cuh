@@ -70,6 +70,9 @@ struct Particles {
   float* xf;      // n*4 float copies for the FP32 collision
   float* uf;      // n*4
   float* omf;     // n*4
+  double* x2;     // second buffers of the DEM sub-steps
+  double* u2;
+  float* xf2;
 };
 
 struct Slots {
