@@ -37,6 +37,23 @@ __host__ __device__ constexpr T w0() {
   return T(1.0 / 3.0);
 }
 
+// c_k . (x, y, z) for a compile-time k, written without multiplications by 0
+// or 1 (IEEE rules keep 0 * x in the instruction stream)
+template <typename T>
+__device__ __forceinline__ T cdot(int k, T x, T y, T z) {
+  switch (k) {
+    case 0: return x;
+    case 1: return y;
+    case 2: return z;
+    case 3: return x + y;
+    case 4: return x - y;
+    case 5: return x + z;
+    case 6: return x - z;
+    case 7: return y + z;
+    default: return y - z;
+  }
+}
+
 // lattice weight of direction q in the canonical ordering
 __host__ __device__ inline double wq(int q) {
   return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -102,39 +119,14 @@ __device__ __forceinline__ T ld(const T* p) {
 }
 
 template <typename T>
-struct Coef {
-  T ffx, ffy, ffz, Gs[9], Fa[9], H0, H1, H2;
-};
-
-template <typename T>
-__device__ __forceinline__ void load_coef(const StepConst* sc, Coef<T>& c);
+__device__ __forceinline__ const CollideCoef<T>* coef_of(const StepConst* sc);
 template <>
-__device__ __forceinline__ void load_coef<double>(const StepConst* sc, Coef<double>& c) {
-  c.ffx = __ldg(&sc->fext[0]);
-  c.ffy = __ldg(&sc->fext[1]);
-  c.ffz = __ldg(&sc->fext[2]);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    c.Gs[k] = __ldg(&sc->Gs[k]);
-    c.Fa[k] = __ldg(&sc->Fa[k]);
-  }
-  c.H0 = __ldg(&sc->H[0]);
-  c.H1 = __ldg(&sc->H[1]);
-  c.H2 = __ldg(&sc->H[2]);
+__device__ __forceinline__ const CollideCoef<double>* coef_of<double>(const StepConst* sc) {
+  return &sc->d;
 }
 template <>
-__device__ __forceinline__ void load_coef<float>(const StepConst* sc, Coef<float>& c) {
-  c.ffx = __ldg(&sc->ffext[0]);
-  c.ffy = __ldg(&sc->ffext[1]);
-  c.ffz = __ldg(&sc->ffext[2]);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    c.Gs[k] = __ldg(&sc->fGs[k]);
-    c.Fa[k] = __ldg(&sc->fFa[k]);
-  }
-  c.H0 = __ldg(&sc->fH[0]);
-  c.H1 = __ldg(&sc->fH[1]);
-  c.H2 = __ldg(&sc->fH[2]);
+__device__ __forceinline__ const CollideCoef<float>* coef_of<float>(const StepConst* sc) {
+  return &sc->f;
 }
 
 // particle data for the solid operator
@@ -264,49 +256,46 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
   const T omB = T(1) - B;
 
   // ---- moments (Eqs. 6-7)
-  Coef<T> cf;
-  load_coef<T>(P.sc, cf);
-  T a[9];
-  T drho = d[0];
-  T jx = T(0), jy = T(0), jz = T(0);
+  const CollideCoef<T>* cf = coef_of<T>(P.sc);
+  T a[9], sk[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    const T s = d[2 * k + 1] + d[2 * k + 2];
+    sk[k] = d[2 * k + 1] + d[2 * k + 2];
     a[k] = d[2 * k + 1] - d[2 * k + 2];
-    drho += s;
-    if (ckx(k) > 0) jx += a[k];
-    if (cky(k) > 0) jy += a[k];
-    if (cky(k) < 0) jy -= a[k];
-    if (ckz(k) > 0) jz += a[k];
-    if (ckz(k) < 0) jz -= a[k];
   }
-  const T Ux = jx + T(0.5) * cf.ffx;
-  const T Uy = jy + T(0.5) * cf.ffy;
-  const T Uz = jz + T(0.5) * cf.ffz;
+  // pairwise sums: rho - 1 = delta_0 + sum s_k, j = sum a_k c_k
+  const T drho = ((d[0] + (sk[0] + sk[1])) + ((sk[2] + sk[3]) + (sk[4] + sk[5]))) +
+                 ((sk[6] + sk[7]) + sk[8]);
+  const T jx = ((a[0] + a[3]) + (a[4] + a[5])) + a[6];
+  const T jy = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
+  const T jz = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
+  const T Ux = jx + __ldg(&cf->hf[0]);
+  const T Uy = jy + __ldg(&cf->hf[1]);
+  const T Uz = jz + __ldg(&cf->hf[2]);
   const T uu = Ux * Ux + Uy * Uy + Uz * Uz;
-  const T Uf = Ux * cf.ffx + Uy * cf.ffy + Uz * cf.ffz;
+  const T Uf = Ux * __ldg(&cf->f[0]) + Uy * __ldg(&cf->f[1]) + Uz * __ldg(&cf->f[2]);
   const T base0 = drho - T(1.5) * uu;
-  const T wp = T(P.omega_p), wm = T(P.omega_m);
 
-  // ---- fluid relaxation + forcing, weighted by (1 - B)
+  // ---- fluid relaxation + forcing, weighted by (1 - B).  Per pair:
+  //   symmetric change  = -omega+/2 s_k + omega+ E_s,k + forcing
+  //                     = -omega+/2 s_k + ((9/2 omega+ w) c.U + G_k) c.U + C_c
+  //   antisymmetric     = -omega-/2 a_k + 3 omega- w c.U + F_k
+  // with C_c = omega+ w base0 + H_c U.f once per class.
   {
-    const T E0 = w0<T>() * base0;
-    T dl = -wp * (d[0] - E0) + cf.H0 * Uf;
+    const T dl = __ldg(&cf->nwp) * d[0] + (__ldg(&cf->wpw0) * base0 + __ldg(&cf->H[0]) * Uf);
     d[0] += omB * dl;
   }
+  const T C0 = __ldg(&cf->wpw[0]) * base0 + __ldg(&cf->H[1]) * Uf;
+  const T C1 = __ldg(&cf->wpw[1]) * base0 + __ldg(&cf->H[2]) * Uf;
+  const T mhwp = __ldg(&cf->mhwp), mhwm = __ldg(&cf->mhwm);
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    const T w = wk<T>(k);
-    const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
-    const T Es = (T(4.5) * w * cu) * cu + w * base0;
-    const T Fs = cf.Gs[k] * cu + (k < 3 ? cf.H1 : cf.H2) * Uf;
-    const T s = d[2 * k + 1] + d[2 * k + 2];
-    T ds = (T(-0.5) * wp) * s + (wp * Es + Fs);
-    T da = (T(-0.5) * wm) * a[k] + ((T(3) * w * wm) * cu + cf.Fa[k]);
-    ds *= omB;
-    da *= omB;
-    d[2 * k + 1] += ds + da;
-    d[2 * k + 2] += ds - da;
+    const int c = k < 3 ? 0 : 1;
+    const T cu = cdot<T>(k, Ux, Uy, Uz);
+    const T ds = mhwp * sk[k] + ((__ldg(&cf->A[c]) * cu + __ldg(&cf->Gs[k])) * cu + (c ? C1 : C0));
+    const T da = mhwm * a[k] + (__ldg(&cf->D[c]) * cu + __ldg(&cf->Fa[k]));
+    d[2 * k + 1] += omB * (ds + da);
+    d[2 * k + 2] += omB * (ds - da);
   }
 
   // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
@@ -333,8 +322,8 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const T w = wk<T>(k);
-        const T cu = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
-        const T cv = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
+        const T cu = cdot<T>(k, Ux, Uy, Uz);
+        const T cv = cdot<T>(k, Vx, Vy, Vz);
         const T Sv = cv + cu;
         const T BdS = (T(4.5) * w * Bi) * ((cv - cu) * Sv) + (T(-1.5) * w) * (Bi * dU2);
         const T BA = (T(3) * w * Bi) * Sv - Bi * a[k];
@@ -364,7 +353,7 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
     if (has0 || has1) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        S.cu[lane][k] = T(ckx(k)) * Ux + T(cky(k)) * Uy + T(ckz(k)) * Uz;
+        S.cu[lane][k] = cdot<T>(k, Ux, Uy, Uz);
         S.am[lane][k] = a[k];
       }
     }
@@ -390,7 +379,7 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
           d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
 #pragma unroll
           for (int k = 0; k < 9; ++k)
-            S.cv[jj][k] = T(ckx(k)) * Vx + T(cky(k)) * Vy + T(ckz(k)) * Vz;
+            S.cv[jj][k] = cdot<T>(k, Vx, Vy, Vz);
           const T BdU = Bi * dU2;
           S.con[jj][0] = (T(4.5) * wk<T>(0)) * Bi;
           S.con[jj][1] = (T(-1.5) * wk<T>(0)) * BdU;
@@ -713,30 +702,45 @@ int launch_sums(const Grid& g, const double* f, double* partials, int nparts, do
 
 // per-step constants: fluid force density (body force and the counter force
 // of the buoyancy-corrected gravity) and the forcing coefficients
+template <typename T>
+__device__ void fill_coef(CollideCoef<T>& c, const double* f, double wp, double wm) {
+  const double gp = 1.0 - 0.5 * wp, gm = 1.0 - 0.5 * wm;
+  for (int a = 0; a < 3; ++a) {
+    c.hf[a] = (T)(0.5 * f[a]);
+    c.f[a] = (T)f[a];
+  }
+  for (int k = 0; k < 9; ++k) {
+    const double cfk = ckx(k) * f[0] + cky(k) * f[1] + ckz(k) * f[2];
+    const double w = wk<double>(k);
+    c.Gs[k] = (T)(gp * 9.0 * w * cfk);
+    c.Fa[k] = (T)(gm * 3.0 * w * cfk);
+  }
+  c.H[0] = (T)(-3.0 * (1.0 / 3.0) * gp);
+  c.H[1] = (T)(-3.0 * (1.0 / 18.0) * gp);
+  c.H[2] = (T)(-3.0 * (1.0 / 36.0) * gp);
+  c.nwp = (T)(-wp);
+  c.mhwp = (T)(-0.5 * wp);
+  c.mhwm = (T)(-0.5 * wm);
+  c.wpw0 = (T)(wp * (1.0 / 3.0));
+  for (int cl = 0; cl < 2; ++cl) {
+    const double w = cl ? 1.0 / 36.0 : 1.0 / 18.0;
+    c.wpw[cl] = (T)(wp * w);
+    c.A[cl] = (T)(4.5 * w * wp);
+    c.D[cl] = (T)(3.0 * w * wm);
+  }
+}
+
 __global__ void step_const_kernel(MapParams P) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   StepConst* sc = P.sc;
   const double vf = sc->vfluid;
   double f[3];
-  for (int a = 0; a < 3; ++a)
-    f[a] = P.fbody[a] - ((P.G[a] != 0.0 && vf > 0.0) ? P.G[a] / vf : 0.0);
-  const double gp = 1.0 - 0.5 * P.omega_p, gm = 1.0 - 0.5 * P.omega_m;
   for (int a = 0; a < 3; ++a) {
+    f[a] = P.fbody[a] - ((P.G[a] != 0.0 && vf > 0.0) ? P.G[a] / vf : 0.0);
     sc->fext[a] = f[a];
-    sc->ffext[a] = (float)f[a];
   }
-  for (int k = 0; k < 9; ++k) {
-    const double cfk = ckx(k) * f[0] + cky(k) * f[1] + ckz(k) * f[2];
-    const double w = wk<double>(k);
-    sc->Gs[k] = gp * 9.0 * w * cfk;
-    sc->Fa[k] = gm * 3.0 * w * cfk;
-    sc->fGs[k] = (float)sc->Gs[k];
-    sc->fFa[k] = (float)sc->Fa[k];
-  }
-  sc->H[0] = -3.0 * (1.0 / 3.0) * gp;
-  sc->H[1] = -3.0 * (1.0 / 18.0) * gp;
-  sc->H[2] = -3.0 * (1.0 / 36.0) * gp;
-  for (int i = 0; i < 3; ++i) sc->fH[i] = (float)sc->H[i];
+  fill_coef<double>(sc->d, f, P.omega_p, P.omega_m);
+  fill_coef<float>(sc->f, f, P.omega_p, P.omega_m);
 }
 
 int launch_step_const(MapParams P, cudaStream_t s) {

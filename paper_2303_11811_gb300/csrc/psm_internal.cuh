@@ -39,16 +39,31 @@ struct Grid {
 };
 
 // Constants of one time step, computed on the device after the mapping
+// collision coefficients of one step in the storage precision: Eqs. 3-8
+// with the Guo prefactors (1 - omega/2) on the forcing, grouped so that the
+// relaxation of a pair is a chain of fused multiply-adds.  Class c = 0 holds
+// the face pairs (w = 1/18), c = 1 the edge pairs (w = 1/36).
+template <typename T>
+struct CollideCoef {
+  T hf[3];          // f_ext / 2, the velocity shift of Eq. 7
+  T f[3];           // f_ext
+  T Gs[9], Fa[9];   // forcing per pair: symmetric part / (c_k . U), antisymmetric part
+  T H[3];           // forcing, symmetric part / (U . f_ext): rest, faces, edges
+  T nwp;            // -omega+
+  T mhwp, mhwm;     // -omega+/2, -omega-/2
+  T wpw0;           // omega+ w_0
+  T wpw[2];         // omega+ w_c
+  T A[2];           // 9/2 omega+ w_c
+  T D[2];           // 3 omega- w_c
+};
+
 struct StepConst {
   double fext[3];       // fluid force density (body force + counter force)
   double vfluid;        // sum over cells of (1 - B)
   double sumB;          // sum over cells of min(B, 1), accumulated by the mapping
   double ncells;        // nx * ny * nz
-  // forcing coefficients (Eq. 8 with the Guo prefactors), per pair k:
-  //   symmetric part  = Gs[k] * (c_k . U) + H[class] * (U . f)
-  //   antisymmetric   = Fa[k]
-  double Gs[9], Fa[9], H[3];   // H[0] rest, H[1] faces, H[2] edges
-  float fGs[9], fFa[9], fH[3], ffext[3];
+  CollideCoef<double> d;
+  CollideCoef<float> f;
 };
 
 struct Particles {
