@@ -118,6 +118,17 @@ __device__ __forceinline__ T ld(const T* p) {
   return __ldg(p);
 }
 
+// four consecutive coefficients (16-byte aligned) in 16-byte loads
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+  const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
+}
+
 template <typename T>
 __device__ __forceinline__ const CollideCoef<T>* coef_of(const StepConst* sc);
 template <>
@@ -129,56 +140,19 @@ __device__ __forceinline__ const CollideCoef<float>* coef_of<float>(const StepCo
   return &sc->f;
 }
 
-// particle data for the solid operator
-template <typename T>
-__device__ __forceinline__ void load_particle(const LbmParams& P, int p, T* xp, T* up, T* op);
-template <>
-__device__ __forceinline__ void load_particle<double>(const LbmParams& P, int p, double* xp,
-                                                      double* up, double* op) {
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    xp[a] = __ldg(&P.px[3 * p + a]);
-    up[a] = __ldg(&P.pu[3 * p + a]);
-    op[a] = __ldg(&P.pom[3 * p + a]);
-  }
-}
-template <>
-__device__ __forceinline__ void load_particle<float>(const LbmParams& P, int p, float* xp,
-                                                     float* up, float* op) {
-  float4 a = __ldg(reinterpret_cast<const float4*>(P.pxf) + p);
-  float4 b = __ldg(reinterpret_cast<const float4*>(P.puf) + p);
-  float4 c = __ldg(reinterpret_cast<const float4*>(P.pomf) + p);
-  xp[0] = a.x; xp[1] = a.y; xp[2] = a.z;
-  up[0] = b.x; up[1] = b.y; up[2] = b.z;
-  op[0] = c.x; op[1] = c.y; op[2] = c.z;
-}
-
-// nearest-image offset of the cell centre from the particle centre
-template <typename T>
-__device__ __forceinline__ T image_offset(int i, T xp, int n, bool periodic) {
-  T d = (T(i) + T(0.5)) - xp;
-  if (periodic) {
-    if (d > T(0.5) * T(n)) d = (T(i - n) + T(0.5)) - xp;
-    else if (d < -T(0.5) * T(n)) d = (T(i + n) + T(0.5)) - xp;
-  }
-  return d;
-}
-
-// Shared memory of one warp for the solid operator.  Work is split in
-// "jobs" (one per covered cell and occupied slot, at most 32 per round) and
-// "items" (job x direction pair, 9 per job) spread over all 32 lanes, so that
-// the FP64 work of a warp with a few covered cells is not repeated by its
-// idle lanes.  The owner lane of a job folds the item results into its PDFs
-// and its force in a fixed order.
+// Shared memory of one warp for the FP64 solid operator.  Work is split in
+// "jobs" (one per covered cell and occupied slot) and "items" (job x
+// direction pair, 9 per job) spread over all 32 lanes, so that the FP64 work
+// of a warp with a few covered cells is not repeated by its idle lanes.  The
+// items add their results to a shared copy of the owner lane's PDFs, slot 0
+// before slot 1.
 template <typename T>
 struct SolidSmem {
   T cu[32][9];     // per lane: c_k . U_f of its cell
   T am[32][9];     // per lane: antisymmetric moments a_k of its cell
+  T dd[32][18];    // per lane: its PDFs 1..18 while the items add to them
   T cv[32][9];     // per job: c_k . U_p
   T con[32][7];    // per job: alpha, beta, gamma for faces and edges, B_i
-  T oq[32][9];     // per job and pair: change of f_q
-  T ob[32][9];     // per job and pair: change of f_qbar
-  T ba[32][9];     // per job and pair: B_i A_k (momentum exchange)
   int owner[32];
 };
 constexpr int LBM_THREADS = 256;
@@ -188,23 +162,240 @@ size_t lbm_smem_bytes() {
   return sizeof(SolidSmem<T>) * (LBM_THREADS / 32);
 }
 
-// FP32 kernels are bandwidth bound and want resident warps (3 blocks per
+// Force of one slot on its particle (Eq. 21): B_i sum_q C^s_q c_qbar =
+// -2 B_i sum_k A_k c_k over the pairs, with A_k = 3 w_k c_k.(U_f + U_p) - a_k.
+// The lattice sum over the pairs, sum_k w_k c_k c_k^T = I/6, reduces it
+// exactly to B_i ((U_f + U_p)/2 - j) (-2) = B_i (U_f - U_p - f_ext), since
+// j = U_f - f_ext/2 (Eq. 7).
+template <typename T>
+__device__ __forceinline__ void slot_force(const LbmParams& P, int e, int sl, T Bi, T dux, T duy,
+                                           T duz, const T* f) {
+  T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
+  o[0] = Bi * (dux - f[0]);
+  o[1] = Bi * (duy - f[1]);
+  o[2] = Bi * (duz - f[2]);
+}
+
+// Collision of one cell (Eqs. 3-8 and 17-21) on the PDFs d gathered by the
+// streaming step; the warp's 32 lanes hold the 32 cells of coverage word
+// `word` (padding lanes compute on a copy of a real cell).  FP64 kernels
+// pass the warp's SolidSmem.
+template <typename T>
+__device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, int lane, bool live,
+                                            T* d, SolidSmem<T>* solid, uint32_t m, int eb) {
+  // ---- coverage of this cell (m: coverage word, eb: slot of its first
+  // covered cell).  A slot holds, per particle, the surface velocity at the
+  // cell centre (Eq. 20) and the weight B_i, both written by the mapping; the
+  // loads depend only on the slot index and are issued together.
+  bool cov = live && ((m >> lane) & 1u);
+  int e = 0;
+  int2 pid = make_int2(-1, -1);
+  T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
+  if (cov) {
+    e = eb + __popc(m & ((1u << lane) - 1u));
+    if (e < P.slot_cap) {
+      pid = __ldg(&P.slot_pid[e]);
+      const T* R = static_cast<const T*>(P.slot_V) + 8LL * e;
+      ld4(R, r0);
+      ld4(R + 4, r1);
+    } else {
+      cov = false;
+    }
+  }
+  T B = r0[3] + r1[3];
+  if (B > T(1)) B = T(1);
+  const T omB = T(1) - B;
+
+  // ---- moments (Eqs. 6-7)
+  const CollideCoef<T>* cf = coef_of<T>(P.sc);
+  T a[9], sk[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    sk[k] = d[2 * k + 1] + d[2 * k + 2];
+    a[k] = d[2 * k + 1] - d[2 * k + 2];
+  }
+  // pairwise sums: rho - 1 = delta_0 + sum s_k, j = sum a_k c_k
+  const T drho = ((d[0] + (sk[0] + sk[1])) + ((sk[2] + sk[3]) + (sk[4] + sk[5]))) +
+                 ((sk[6] + sk[7]) + sk[8]);
+  const T jx = ((a[0] + a[3]) + (a[4] + a[5])) + a[6];
+  const T jy = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
+  const T jz = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
+  T h[16];
+  ld4(cf->head, h);
+  ld4(cf->head + 4, h + 4);
+  ld4(cf->head + 8, h + 8);
+  ld4(cf->head + 12, h + 12);
+  const T Ux = jx + h[CC_HF];
+  const T Uy = jy + h[CC_HF + 1];
+  const T Uz = jz + h[CC_HF + 2];
+  const T uu = Ux * Ux + Uy * Uy + Uz * Uz;
+  const T Uf = Ux * h[CC_F] + Uy * h[CC_F + 1] + Uz * h[CC_F + 2];
+  const T base0 = drho - T(1.5) * uu;
+
+  // ---- fluid relaxation + forcing, weighted by (1 - B).  Per pair:
+  //   symmetric change  = -omega+/2 s_k + omega+ E_s,k + forcing
+  //                     = -omega+/2 s_k + ((9/2 omega+ w) c.U + G_k) c.U + C_c
+  //   antisymmetric     = -omega-/2 a_k + 3 omega- w c.U + F_k
+  // with C_c = omega+ w base0 + H_c U.f once per class.
+  {
+    const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
+    d[0] += omB * dl;
+  }
+  const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
+  const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    T pk[4];
+    ld4(cf->pair[k], pk);
+    const T cu = cdot<T>(k, Ux, Uy, Uz);
+    const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
+    const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
+    d[2 * k + 1] += omB * (ds + da);
+    d[2 * k + 2] += omB * (ds - da);
+  }
+
+  // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
+  // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
+  // warp; in FP32 each covered lane does its own cell.
+  if (sizeof(T) == 4 && cov) {
+#pragma unroll 1
+    for (int sl = 0; sl < 2; ++sl) {
+      const int p = sl ? pid.y : pid.x;
+      if (p < 0) continue;
+      const T Vx = sl ? r1[0] : r0[0], Vy = sl ? r1[1] : r0[1], Vz = sl ? r1[2] : r0[2];
+      const T Bi = sl ? r1[3] : r0[3];
+      const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+      d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const T w = wk<T>(k);
+        const T cu = cdot<T>(k, Ux, Uy, Uz);
+        const T cv = cdot<T>(k, Vx, Vy, Vz);
+        const T Sv = cv + cu;
+        const T BdS = (T(4.5) * w * Bi) * ((cv - cu) * Sv) + (T(-1.5) * w) * (Bi * dU2);
+        const T BA = (T(3) * w * Bi) * Sv - Bi * a[k];
+        d[2 * k + 1] += BdS + BA;
+        d[2 * k + 2] += BdS - BA;
+      }
+      slot_force<T>(P, e, sl, Bi, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
+    }
+  }
+  if (sizeof(T) == 8 && m != 0u) {
+    SolidSmem<T>& S = *solid;
+    const bool has0 = cov && pid.x >= 0, has1 = cov && pid.y >= 0;
+    const unsigned b0 = __ballot_sync(0xffffffffu, has0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, has1);
+    const unsigned below = (1u << lane) - 1u;
+    if (has0 || has1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        S.cu[lane][k] = cdot<T>(k, Ux, Uy, Uz);
+        S.am[lane][k] = a[k];
+      }
+#pragma unroll
+      for (int q = 1; q < Q; ++q) S.dd[lane][q - 1] = d[q];
+    }
+    // the jobs of slot 0, then those of slot 1: within a pass each owner lane
+    // has at most one job, so no two items of a pass update the same PDF
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const unsigned bs = sl ? b1 : b0;
+      if (bs == 0u) continue;
+      const int Js = __popc(bs);
+      if (sl ? has1 : has0) {
+        // job set-up by the owner lane: the per-job constants of the item
+        // arithmetic and the slot's force (Eq. 21)
+        const int jj = __popc(bs & below);
+        const T Vx = sl ? r1[0] : r0[0], Vy = sl ? r1[1] : r0[1], Vz = sl ? r1[2] : r0[2];
+        const T Bi = sl ? r1[3] : r0[3];
+        const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+        d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) S.cv[jj][k] = cdot<T>(k, Vx, Vy, Vz);
+        const T BdU = Bi * dU2;
+        S.con[jj][0] = (T(4.5) * wk<T>(0)) * Bi;
+        S.con[jj][1] = (T(-1.5) * wk<T>(0)) * BdU;
+        S.con[jj][2] = (T(3) * wk<T>(0)) * Bi;
+        S.con[jj][3] = (T(4.5) * wk<T>(3)) * Bi;
+        S.con[jj][4] = (T(-1.5) * wk<T>(3)) * BdU;
+        S.con[jj][5] = (T(3) * wk<T>(3)) * Bi;
+        S.con[jj][6] = Bi;
+        S.owner[jj] = lane;
+        slot_force<T>(P, e, sl, Bi, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
+      }
+      __syncwarp();
+      // items: job j, pair k, added to the owner's PDFs.  C^s has symmetric
+      // part B_i w_k (9/2 (cv^2 - cu^2) - 3/2 dU2) and antisymmetric part
+      // B_i (3 w_k (cu + cv) - a_k)
+      for (int t = lane; t < 9 * Js; t += 32) {
+        const int j = t / 9, k = t - 9 * j;
+        const int L = S.owner[j];
+        const T cu = S.cu[L][k], cv = S.cv[j][k];
+        const int cl = k < 3 ? 0 : 3;
+        const T Dv = cv - cu, Sv = cv + cu;
+        const T BdS = S.con[j][cl] * (Dv * Sv) + S.con[j][cl + 1];
+        const T BA = S.con[j][cl + 2] * Sv - S.con[j][6] * S.am[L][k];
+        S.dd[L][2 * k] += BdS + BA;
+        S.dd[L][2 * k + 1] += BdS - BA;
+      }
+      __syncwarp();
+    }
+    if (has0 || has1) {
+#pragma unroll
+      for (int q = 1; q < Q; ++q) d[q] = S.dd[lane][q - 1];
+    }
+  }
+}
+
+// store of the collided PDFs (pull: own cell of the other buffer; AA even:
+// swapped slots of the own cell; AA odd: the neighbours' slots, or the own
+// cell's opposite slot across a wall)
+template <typename T, int MODE, int WALLS>
+__device__ __forceinline__ void store_pdfs(const LbmParams& P, const NbrT<WALLS>& nb, int cell,
+                                           const T* d) {
+#define DST(q) static_cast<T*>(P.dstq[q])
+  DST(0)[cell] = d[0];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+    const int qa = 2 * k + 1, qb = 2 * k + 2;
+    if (MODE == 0) {
+      DST(qa)[cell] = d[qa];
+      DST(qb)[cell] = d[qb];
+    } else if (MODE == 1) {
+      DST(qb)[cell] = d[qa];
+      DST(qa)[cell] = d[qb];
+    } else {
+      if (nb.ok(cx, cy, cz)) DST(qa)[nb.idx(cx, cy, cz)] = d[qa];
+      else DST(qb)[cell] = d[qa];
+      if (nb.ok(-cx, -cy, -cz)) DST(qb)[nb.idx(-cx, -cy, -cz)] = d[qb];
+      else DST(qa)[cell] = d[qb];
+    }
+  }
+#undef DST
+}
+
+// FP32 kernels are bandwidth bound and want resident warps (4 blocks per
 // SM); FP64 kernels are FP64-pipe bound and keep their registers
 template <typename T, int MODE, int WALLS>
 __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kernel(LbmParams P) {
-  using T2 = typename Vec2<T>::type;
   extern __shared__ __align__(16) unsigned char lbm_smem[];
   const Grid& g = P.g;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // the grid has fewer than 2^31 cells: 32-bit indices throughout
+  const unsigned warp = blockIdx.x * (LBM_THREADS / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (warp >= g.nwords) return;  // whole warps only
-  const int row = (int)(warp / g.wpr);
-  const int xr = (int)(warp - (long long)row * g.wpr) * 32 + lane;
+  if (warp >= (unsigned)g.nwords) return;  // whole warps only
+  const unsigned row = g.div_wpr.div(warp);
+  const int xr = (int)(warp - row * (unsigned)g.wpr) * 32 + lane;
   const bool live = xr < g.nx;   // padding lanes compute on a copy of a real cell
   const int x = live ? xr : g.nx - 1;
-  const int y = row % g.ny;
-  const int z = row / g.ny;
+  const int z = (int)g.div_ny.div(row);
+  const int y = (int)row - z * g.ny;
+
+  // coverage word and first slot: loaded ahead of the PDFs, the slot loads
+  // of the collision depend on them
   const uint32_t m = P.mask ? __ldg(&P.mask[warp]) : 0u;
+  const int eb = P.mask ? __ldg(&P.base[warp]) : 0;
 
   NbrT<WALLS> nb;
   nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
@@ -214,8 +405,6 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
   // the same array: every thread reads its whole set of locations before it
   // writes the same set.
 #define SRC(q) static_cast<const T*>(P.srcq[q])
-#define DST(q) static_cast<T*>(P.dstq[q])
-
   // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls)
   T d[Q];
   d[0] = ld(SRC(0) + cell);
@@ -235,230 +424,207 @@ __global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kerne
     }
   }
 
-  // ---- coverage of this cell
-  bool cov = live && ((m >> lane) & 1u);
-  int e = 0;
-  int2 pid = make_int2(-1, -1);
-  T2 Bs;
-  Bs.x = T(0);
-  Bs.y = T(0);
-  if (cov) {
-    e = __ldg(&P.base[warp]) + __popc(m & ((1u << lane) - 1u));
-    if (e < P.slot_cap) {
-      pid = __ldg(&P.slot_pid[e]);
-      Bs = __ldg(static_cast<const T2*>(P.slot_B) + e);
-    } else {
-      cov = false;
+#undef SRC
+  psm_collide<T>(P, warp, lane, live, d,
+                 reinterpret_cast<SolidSmem<T>*>(lbm_smem) + (threadIdx.x >> 5), m, eb);
+  if (live) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
+}
+
+// ---- staged variant.  Whole x-rows are copied into shared memory by bulk
+// copies (cp.async.bulk) that complete on mbarriers, in a ring of `stages`
+// tiles per block; a tile is tile_rows consecutive x-rows.  One producer warp
+// issues, per tile, the copy of each direction's source row (the row at
+// (y, z) - c_q; the own row in the even AA step); eight consumer warps take
+// the x-shift of a direction as an index offset within the staged row,
+// collide, and store to global memory.  Links across a wall read the own
+// cell from global memory.  The memory system thus sees the next tiles'
+// loads while the current one is computed, independent of warp scheduling.
+// Every wait is bounded (1 s); a wait that gives up sets ST_TIMEOUT, and the
+// producer waits for its copies in flight before the block exits.
+constexpr int BULK_CONSUMER_WARPS = 8;
+constexpr int BULK_THREADS = 32 * (BULK_CONSUMER_WARPS + 1);
+constexpr int BULK_MAX_STAGES = 8;
+constexpr int BULK_BAR_BYTES = 16 * BULK_MAX_STAGES;  // full[] and empty[] barriers
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// wait until the phase with the given parity has completed, at most kWaitLimitNs
+__device__ __noinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_test(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_test(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// components of c_q in the canonical ordering (q = 2k+1: +c_k, q = 2k+2: -c_k)
+__device__ __forceinline__ int qsign(int q) { return (q & 1) ? 1 : -1; }
+
+template <typename T, int MODE, int WALLS>
+__global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
+    lbm_bulk_kernel(LbmParams P) {
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  const Grid& g = P.g;
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bulk_smem);
+  unsigned long long* empty = full + BULK_MAX_STAGES;
+  const int S = P.stages, TR = P.tile_rows, nxp = g.nxp;
+  const int C = TR * nxp;  // elements per direction in a tile
+  const size_t stage_elems = (size_t)Q * C;
+  T* ring = reinterpret_cast<T*>(bulk_smem + BULK_BAR_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrows = g.ny * g.nz;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], BULK_CONSUMER_WARPS);
     }
+    mbar_fence_init();
   }
-  T B = Bs.x + Bs.y;
-  if (B > T(1)) B = T(1);
-  const T omB = T(1) - B;
+  __syncthreads();
 
-  // ---- moments (Eqs. 6-7)
-  const CollideCoef<T>* cf = coef_of<T>(P.sc);
-  T a[9], sk[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    sk[k] = d[2 * k + 1] + d[2 * k + 2];
-    a[k] = d[2 * k + 1] - d[2 * k + 2];
+  if (warp == BULK_CONSUMER_WARPS) {
+    // ---- producer
+    int issued = 0;
+    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+      const int s = issued % S;
+      const unsigned ph = (unsigned)(issued / S) & 1u;
+      if (issued >= S && !mbar_wait(&empty[s], ph ^ 1u)) {
+        if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+        break;
+      }
+      const int row0 = tile * TR;
+      const int nr = min(TR, nrows - row0);
+      if (lane == 0) mbar_expect_tx(&full[s], (unsigned)(Q * nr * nxp * sizeof(T)));
+      __syncwarp();
+      T* st = ring + s * stage_elems;
+      for (int j = lane; j < Q * nr; j += 32) {
+        const int q = j / nr, r = j - q * nr;
+        const int row = row0 + r;
+        const int z = (int)g.div_ny.div((unsigned)row);
+        const int y = row - z * g.ny;
+        int sy = y, sz = z, sq = q;
+        if (MODE != 1 && q > 0) {
+          const int k = (q - 1) >> 1, sg = qsign(q);
+          sy -= sg * cky(k);
+          sz -= sg * ckz(k);
+          sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+          sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
+          if (MODE == 2) sq = q + sg;  // AA odd: the opposite direction's array
+        }
+        const T* src = static_cast<const T*>(P.src) + (size_t)sq * g.ncell +
+                       ((size_t)sz * g.ny + sy) * nxp;
+        bulk_copy_g2s(st + ((size_t)q * TR + r) * nxp, src, (unsigned)(nxp * sizeof(T)),
+                      &full[s]);
+      }
+      ++issued;
+    }
+    // no copy may land after the block has exited
+    for (int j = issued - S < 0 ? 0 : issued - S; j < issued; ++j)
+      if (!mbar_wait(&full[j % S], (unsigned)(j / S) & 1u)) {
+        if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+      }
+    return;
   }
-  // pairwise sums: rho - 1 = delta_0 + sum s_k, j = sum a_k c_k
-  const T drho = ((d[0] + (sk[0] + sk[1])) + ((sk[2] + sk[3]) + (sk[4] + sk[5]))) +
-                 ((sk[6] + sk[7]) + sk[8]);
-  const T jx = ((a[0] + a[3]) + (a[4] + a[5])) + a[6];
-  const T jy = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
-  const T jz = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
-  const T Ux = jx + __ldg(&cf->hf[0]);
-  const T Uy = jy + __ldg(&cf->hf[1]);
-  const T Uz = jz + __ldg(&cf->hf[2]);
-  const T uu = Ux * Ux + Uy * Uy + Uz * Uz;
-  const T Uf = Ux * __ldg(&cf->f[0]) + Uy * __ldg(&cf->f[1]) + Uz * __ldg(&cf->f[2]);
-  const T base0 = drho - T(1.5) * uu;
 
-  // ---- fluid relaxation + forcing, weighted by (1 - B).  Per pair:
-  //   symmetric change  = -omega+/2 s_k + omega+ E_s,k + forcing
-  //                     = -omega+/2 s_k + ((9/2 omega+ w) c.U + G_k) c.U + C_c
-  //   antisymmetric     = -omega-/2 a_k + 3 omega- w c.U + F_k
-  // with C_c = omega+ w base0 + H_c U.f once per class.
-  {
-    const T dl = __ldg(&cf->nwp) * d[0] + (__ldg(&cf->wpw0) * base0 + __ldg(&cf->H[0]) * Uf);
-    d[0] += omB * dl;
-  }
-  const T C0 = __ldg(&cf->wpw[0]) * base0 + __ldg(&cf->H[1]) * Uf;
-  const T C1 = __ldg(&cf->wpw[1]) * base0 + __ldg(&cf->H[2]) * Uf;
-  const T mhwp = __ldg(&cf->mhwp), mhwm = __ldg(&cf->mhwm);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int c = k < 3 ? 0 : 1;
-    const T cu = cdot<T>(k, Ux, Uy, Uz);
-    const T ds = mhwp * sk[k] + ((__ldg(&cf->A[c]) * cu + __ldg(&cf->Gs[k])) * cu + (c ? C1 : C0));
-    const T da = mhwm * a[k] + (__ldg(&cf->D[c]) * cu + __ldg(&cf->Fa[k]));
-    d[2 * k + 1] += omB * (ds + da);
-    d[2 * k + 2] += omB * (ds - da);
-  }
-
-  // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
-  // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
-  // warp; in FP32 each covered lane does its own cell.
-  if (sizeof(T) == 4 && cov) {
-#pragma unroll 1
-    for (int sl = 0; sl < 2; ++sl) {
-      const int p = sl ? pid.y : pid.x;
-      if (p < 0) continue;
-      const T Bi = sl ? Bs.y : Bs.x;
-      T xp[3], up[3], op[3];
-      load_particle<T>(P, p, xp, up, op);
-      const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
-      const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
-      const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
-      // Eq. 20: surface velocity at the cell centre
-      const T Vx = up[0] + (op[1] * dz - op[2] * dy);
-      const T Vy = up[1] + (op[2] * dx - op[0] * dz);
-      const T Vz = up[2] + (op[0] * dy - op[1] * dx);
-      const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
-      d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
-      T ax = T(0), ay = T(0), az = T(0);
+  // ---- consumers
+  SolidSmem<T>* solid = reinterpret_cast<SolidSmem<T>*>(
+                            bulk_smem + BULK_BAR_BYTES + S * stage_elems * sizeof(T)) + warp;
+#define SRC(q) static_cast<const T*>(P.srcq[q])
+  int it = 0;
+  for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++it) {
+    const int s = it % S;
+    if (!mbar_wait(&full[s], (unsigned)(it / S) & 1u)) {
+      if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+      break;
+    }
+    const T* st = ring + s * stage_elems;
+    const int row0 = tile * TR;
+    const int nw = min(TR, nrows - row0) * g.wpr;  // coverage words of the tile
+    for (int w = warp; w < nw; w += BULK_CONSUMER_WARPS) {
+      const int r = (int)g.div_wpr.div((unsigned)w);
+      const int wr = w - r * g.wpr;
+      const int xr = wr * 32 + lane;
+      const bool live = xr < g.nx;  // padding lanes compute on a copy of a real cell
+      const int x = live ? xr : g.nx - 1;
+      const int row = row0 + r;
+      const unsigned word = (unsigned)(row * g.wpr + wr);
+      const uint32_t m = P.mask ? __ldg(&P.mask[word]) : 0u;
+      const int eb = P.mask ? __ldg(&P.base[word]) : 0;
+      const int z = (int)g.div_ny.div((unsigned)row);
+      const int y = row - z * g.ny;
+      NbrT<WALLS> nb;
+      nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
+      const int cell = nb.idx(0, 0, 0);
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xq = x == g.nx - 1 ? 0 : x + 1;
+      const T* sr = st + (size_t)r * nxp;  // direction q of this row at sr[q * C]
+      T d[Q];
+      d[0] = sr[x];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        const T w = wk<T>(k);
-        const T cu = cdot<T>(k, Ux, Uy, Uz);
-        const T cv = cdot<T>(k, Vx, Vy, Vz);
-        const T Sv = cv + cu;
-        const T BdS = (T(4.5) * w * Bi) * ((cv - cu) * Sv) + (T(-1.5) * w) * (Bi * dU2);
-        const T BA = (T(3) * w * Bi) * Sv - Bi * a[k];
-        d[2 * k + 1] += BdS + BA;
-        d[2 * k + 2] += BdS - BA;
-        if (ckx(k) > 0) ax += BA;
-        if (cky(k) > 0) ay += BA;
-        if (cky(k) < 0) ay -= BA;
-        if (ckz(k) > 0) az += BA;
-        if (ckz(k) < 0) az -= BA;
-      }
-      // Eq. 21: B_i sum_q C^s_q c_qbar = -2 sum_k B_i A_k c_k
-      T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
-      o[0] = T(-2) * ax;
-      o[1] = T(-2) * ay;
-      o[2] = T(-2) * az;
-    }
-  }
-  if (sizeof(T) == 8 && m != 0u) {
-    SolidSmem<T>& S = reinterpret_cast<SolidSmem<T>*>(lbm_smem)[threadIdx.x >> 5];
-    const bool has0 = cov && pid.x >= 0, has1 = cov && pid.y >= 0;
-    const unsigned b0 = __ballot_sync(0xffffffffu, has0);
-    const unsigned b1 = __ballot_sync(0xffffffffu, has1);
-    const unsigned below = (1u << lane) - 1u;
-    const int J0 = __popc(b0), J = J0 + __popc(b1);
-    const int j0 = __popc(b0 & below), j1 = J0 + __popc(b1 & below);
-    if (has0 || has1) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        S.cu[lane][k] = cdot<T>(k, Ux, Uy, Uz);
-        S.am[lane][k] = a[k];
-      }
-    }
-    for (int c0 = 0; c0 < J; c0 += 32) {
-      // job set-up by the owner lanes: surface velocity (Eq. 20) and the
-      // per-job constants of the item arithmetic
-#pragma unroll
-      for (int sl = 0; sl < 2; ++sl) {
-        const bool has = sl ? has1 : has0;
-        const int jj = (sl ? j1 : j0) - c0;
-        if (has && jj >= 0 && jj < 32) {
-          const int p = sl ? pid.y : pid.x;
-          const T Bi = sl ? Bs.y : Bs.x;
-          T xp[3], up[3], op[3];
-          load_particle<T>(P, p, xp, up, op);
-          const T dx = image_offset<T>(x, xp[0], g.nx, !g.wall[0]);
-          const T dy = image_offset<T>(y, xp[1], g.ny, !g.wall[1]);
-          const T dz = image_offset<T>(z, xp[2], g.nz, !g.wall[2]);
-          const T Vx = up[0] + (op[1] * dz - op[2] * dy);
-          const T Vy = up[1] + (op[2] * dx - op[0] * dz);
-          const T Vz = up[2] + (op[0] * dy - op[1] * dx);
-          const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
-          d[0] += Bi * (T(-1.5) * w0<T>() * dU2);
-#pragma unroll
-          for (int k = 0; k < 9; ++k)
-            S.cv[jj][k] = cdot<T>(k, Vx, Vy, Vz);
-          const T BdU = Bi * dU2;
-          S.con[jj][0] = (T(4.5) * wk<T>(0)) * Bi;
-          S.con[jj][1] = (T(-1.5) * wk<T>(0)) * BdU;
-          S.con[jj][2] = (T(3) * wk<T>(0)) * Bi;
-          S.con[jj][3] = (T(4.5) * wk<T>(3)) * Bi;
-          S.con[jj][4] = (T(-1.5) * wk<T>(3)) * BdU;
-          S.con[jj][5] = (T(3) * wk<T>(3)) * Bi;
-          S.con[jj][6] = Bi;
-          S.owner[jj] = lane;
+        const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+        const int qa = 2 * k + 1, qb = 2 * k + 2;
+        const int xa = cx > 0 ? xm : (cx < 0 ? xq : x);  // x - c_x
+        const int xb = cx > 0 ? xq : (cx < 0 ? xm : x);  // x + c_x
+        if (MODE == 0) {
+          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qb) + cell);
+          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qa) + cell);
+        } else if (MODE == 1) {
+          d[qa] = sr[qa * C + x];
+          d[qb] = sr[qb * C + x];
+        } else {
+          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qa) + cell);
+          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qb) + cell);
         }
       }
-      __syncwarp();
-      // items: job j, pair k.  C^s has symmetric part B_i w_k (9/2 (cv^2 -
-      // cu^2) - 3/2 dU2) and antisymmetric part B_i (3 w_k (cu + cv) - a_k)
-      const int nj = J - c0 < 32 ? J - c0 : 32;
-      for (int t = lane; t < 9 * nj; t += 32) {
-        const int j = t / 9, k = t - 9 * j;
-        const int L = S.owner[j];
-        const T cu = S.cu[L][k], cv = S.cv[j][k];
-        const int cl = k < 3 ? 0 : 3;
-        const T Dv = cv - cu, Sv = cv + cu;
-        const T BdS = S.con[j][cl] * (Dv * Sv) + S.con[j][cl + 1];
-        const T BA = S.con[j][cl + 2] * Sv - S.con[j][6] * S.am[L][k];
-        S.oq[j][k] = BdS + BA;
-        S.ob[j][k] = BdS - BA;
-        S.ba[j][k] = BA;
-      }
-      __syncwarp();
-      // owners fold the results in a fixed order; Eq. 21 per slot:
-      // B_i sum_q C^s_q c_qbar = -2 sum_k B_i A_k c_k
-#pragma unroll
-      for (int sl = 0; sl < 2; ++sl) {
-        const bool has = sl ? has1 : has0;
-        const int jj = (sl ? j1 : j0) - c0;
-        if (has && jj >= 0 && jj < 32) {
-          T ax = T(0), ay = T(0), az = T(0);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            d[2 * k + 1] += S.oq[jj][k];
-            d[2 * k + 2] += S.ob[jj][k];
-            const T A = S.ba[jj][k];
-            if (ckx(k) > 0) ax += A;
-            if (cky(k) > 0) ay += A;
-            if (cky(k) < 0) ay -= A;
-            if (ckz(k) > 0) az += A;
-            if (ckz(k) < 0) az -= A;
-          }
-          T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
-          o[0] = T(-2) * ax;
-          o[1] = T(-2) * ay;
-          o[2] = T(-2) * az;
-        }
-      }
-      __syncwarp();
+      psm_collide<T>(P, word, lane, live, d, solid, m, eb);
+      if (live) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
     }
-  }
-  if (!live) return;
-
-  // ---- store
-  DST(0)[cell] = d[0];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const int cx = ckx(k), cy = cky(k), cz = ckz(k);
-    const int qa = 2 * k + 1, qb = 2 * k + 2;
-    if (MODE == 0) {
-      DST(qa)[cell] = d[qa];
-      DST(qb)[cell] = d[qb];
-    } else if (MODE == 1) {
-      DST(qb)[cell] = d[qa];
-      DST(qa)[cell] = d[qb];
-    } else {
-      if (nb.ok(cx, cy, cz)) DST(qa)[nb.idx(cx, cy, cz)] = d[qa];
-      else DST(qb)[cell] = d[qa];
-      if (nb.ok(-cx, -cy, -cz)) DST(qb)[nb.idx(-cx, -cy, -cz)] = d[qb];
-      else DST(qa)[cell] = d[qb];
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
 #undef SRC
-#undef DST
 }
 
 // canonical FP64 f~ (unpadded, full f = w + delta) from the storage layout
@@ -609,24 +775,94 @@ size_t lbm_dyn_smem() {
 }
 
 template <typename T, int W>
-int configure_walls() {
+int configure_walls(int optin) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   const int sm = (int)lbm_dyn_smem<T>();
   int bad = 0;
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 0, W>, a, sm) != cudaSuccess;
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 1, W>, a, sm) != cudaSuccess;
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 2, W>, a, sm) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 0, W>, a, optin) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 1, W>, a, optin) != cudaSuccess;
+  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 2, W>, a, optin) != cudaSuccess;
   return bad;
 }
 
+static int smem_optin() {
+  int dev = 0, v = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return 0;
+  return v;
+}
+
 int lbm_configure() {
-  return configure_walls<float, 0>() | configure_walls<float, 1>() | configure_walls<float, 7>() |
-         configure_walls<double, 0>() | configure_walls<double, 1>() |
-         configure_walls<double, 7>();
+  const int o = smem_optin();
+  if (o <= 0) return 1;
+  return configure_walls<float, 0>(o) | configure_walls<float, 1>(o) |
+         configure_walls<float, 7>(o) | configure_walls<double, 0>(o) |
+         configure_walls<double, 1>(o) | configure_walls<double, 7>(o);
+}
+
+// tiles of whole x-rows: 256 cells (tile_rows rows) when the padded row
+// divides 256, else one row; as many stages as fit the per-block budget
+// (FP32: two blocks per SM; FP64: one block next to the solid-operator
+// scratch).  The staged kernel serves FP64 (FP64-pipe bound: it frees the
+// warps from load latency) and the FP32 AA pattern; FP32 pull streaming runs
+// faster on the one-cell-per-thread kernel, whose 32 resident warps per SM
+// keep enough loads in flight.  Returns 0 and leaves plan.stages = 0 when
+// the one-cell-per-thread kernel is to be used.
+int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan) {
+  *plan = LbmPlan{};
+  if (fp32 && !aa) return 0;
+  const int optin = smem_optin();
+  if (optin <= 0) return 1;
+  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  const int TR = (g.nxp <= 256 && 256 % g.nxp == 0) ? 256 / g.nxp : 1;
+  const size_t stage = (size_t)Q * TR * g.nxp * esz;
+  const size_t extra = BULK_BAR_BYTES + (fp32 ? 0 : BULK_CONSUMER_WARPS * sizeof(SolidSmem<double>));
+  const size_t budget = fp32 ? (size_t)100 * 1024 : (size_t)optin;
+  if (budget <= extra) return 0;
+  size_t S = (budget - extra) / stage;
+  if (S > BULK_MAX_STAGES) S = BULK_MAX_STAGES;
+  if (S < 2) {
+    if (extra + 2 * stage > (size_t)optin) return 0;
+    S = 2;
+  }
+  const size_t smem = extra + S * stage;
+  const int w = g.wall[0] | (g.wall[1] << 1) | (g.wall[2] << 2);
+  const void* fn = fp32 ? (w == 0 ? (const void*)lbm_bulk_kernel<float, 0, 0>
+                                  : (w == 1 ? (const void*)lbm_bulk_kernel<float, 0, 1>
+                                            : (const void*)lbm_bulk_kernel<float, 0, 7>))
+                        : (w == 0 ? (const void*)lbm_bulk_kernel<double, 0, 0>
+                                  : (w == 1 ? (const void*)lbm_bulk_kernel<double, 0, 1>
+                                            : (const void*)lbm_bulk_kernel<double, 0, 7>));
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BULK_THREADS, smem) !=
+          cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  if (per_sm < 1) return 0;
+  const long long nrows = (long long)g.ny * g.nz;
+  plan->tile_rows = TR;
+  plan->ntiles = (int)((nrows + TR - 1) / TR);
+  plan->stages = (int)S;
+  plan->smem = smem;
+  const long long blocks = (long long)nsm * per_sm;
+  plan->blocks = (int)(blocks < plan->ntiles ? blocks : plan->ntiles);
+  return 0;
 }
 
 template <typename T, int W>
 void launch_lbm_t(const LbmParams& P, int mode, unsigned grid, cudaStream_t s) {
+  if (P.stages > 0) {
+    const size_t sm = P.smem;
+    if (mode == 0) lbm_bulk_kernel<T, 0, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    else if (mode == 1) lbm_bulk_kernel<T, 1, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    else lbm_bulk_kernel<T, 2, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    return;
+  }
   const size_t sm = lbm_dyn_smem<T>();
   if (mode == 0) lbm_kernel<T, 0, W><<<grid, LBM_THREADS, sm, s>>>(P);
   else if (mode == 1) lbm_kernel<T, 1, W><<<grid, LBM_THREADS, sm, s>>>(P);
@@ -706,27 +942,26 @@ template <typename T>
 __device__ void fill_coef(CollideCoef<T>& c, const double* f, double wp, double wm) {
   const double gp = 1.0 - 0.5 * wp, gm = 1.0 - 0.5 * wm;
   for (int a = 0; a < 3; ++a) {
-    c.hf[a] = (T)(0.5 * f[a]);
-    c.f[a] = (T)f[a];
+    c.head[CC_HF + a] = (T)(0.5 * f[a]);
+    c.head[CC_F + a] = (T)f[a];
   }
+  c.head[CC_NWP] = (T)(-wp);
+  c.head[CC_WPW0] = (T)(wp * (1.0 / 3.0));
+  c.head[CC_H] = (T)(-3.0 * (1.0 / 3.0) * gp);
+  c.head[CC_H + 1] = (T)(-3.0 * (1.0 / 18.0) * gp);
+  c.head[CC_H + 2] = (T)(-3.0 * (1.0 / 36.0) * gp);
+  c.head[CC_MHWP] = (T)(-0.5 * wp);
+  c.head[CC_WPW] = (T)(wp * (1.0 / 18.0));
+  c.head[CC_WPW + 1] = (T)(wp * (1.0 / 36.0));
+  c.head[CC_MHWM] = (T)(-0.5 * wm);
+  c.head[15] = (T)0;
   for (int k = 0; k < 9; ++k) {
     const double cfk = ckx(k) * f[0] + cky(k) * f[1] + ckz(k) * f[2];
     const double w = wk<double>(k);
-    c.Gs[k] = (T)(gp * 9.0 * w * cfk);
-    c.Fa[k] = (T)(gm * 3.0 * w * cfk);
-  }
-  c.H[0] = (T)(-3.0 * (1.0 / 3.0) * gp);
-  c.H[1] = (T)(-3.0 * (1.0 / 18.0) * gp);
-  c.H[2] = (T)(-3.0 * (1.0 / 36.0) * gp);
-  c.nwp = (T)(-wp);
-  c.mhwp = (T)(-0.5 * wp);
-  c.mhwm = (T)(-0.5 * wm);
-  c.wpw0 = (T)(wp * (1.0 / 3.0));
-  for (int cl = 0; cl < 2; ++cl) {
-    const double w = cl ? 1.0 / 36.0 : 1.0 / 18.0;
-    c.wpw[cl] = (T)(wp * w);
-    c.A[cl] = (T)(4.5 * w * wp);
-    c.D[cl] = (T)(3.0 * w * wm);
+    c.pair[k][0] = (T)(gp * 9.0 * w * cfk);
+    c.pair[k][1] = (T)(gm * 3.0 * w * cfk);
+    c.pair[k][2] = (T)(4.5 * w * wp);
+    c.pair[k][3] = (T)(3.0 * w * wm);
   }
 }
 

@@ -129,10 +129,13 @@ __device__ __forceinline__ long long padded_cell(const Grid& g, int x, int y, in
   return (long long)x + (long long)g.nxp * ((long long)y + (long long)g.ny * z);
 }
 
+// padded cell index -> (x, y, z); nxp is a multiple of 32, so the row is the
+// coverage word divided by the words per row
 __device__ __forceinline__ void cell_xyz(const Grid& g, int cell, int& x, int& y, int& z) {
-  x = cell % g.nxp;
-  y = (cell / g.nxp) % g.ny;
-  z = cell / (g.nxp * g.ny);
+  const unsigned row = g.div_wpr.div((unsigned)cell >> 5);
+  x = cell - (int)row * g.nxp;
+  z = (int)g.div_ny.div(row);
+  y = (int)row - z * g.ny;
 }
 
 // B(eps); for eps = 0 and eps = 1 the FP64 formula gives exactly 0 and 1
@@ -427,6 +430,32 @@ __global__ void finish_kernel(MapParams P) {
     store_B(P, e, 0, B0);
     store_B(P, e, 1, B1);
     accB += B;
+    // per slot: the particle's surface velocity at the cell centre (Eq. 20)
+    // and its weight, read by the collision
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
+    for (int s = 0; s < 2; ++s) {
+      const int p = s ? pid.y : pid.x;
+      double v[4] = {0.0, 0.0, 0.0, s ? B1 : B0};
+      if (p >= 0) {
+        const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+        const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+        const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+        const double* u = P.p.u + 3 * p;
+        const double* om = P.p.om + 3 * p;
+        v[0] = u[0] + (om[1] * dz - om[2] * dy);
+        v[1] = u[1] + (om[2] * dx - om[0] * dz);
+        v[2] = u[2] + (om[0] * dy - om[1] * dx);
+      }
+      if (P.fp32) {
+        float4* o = static_cast<float4*>(P.s.V) + 2 * e + s;
+        *o = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+      } else {
+        double2* o = static_cast<double2*>(P.s.V) + 4 * e + 2 * s;
+        o[0] = make_double2(v[0], v[1]);
+        o[1] = make_double2(v[2], v[3]);
+      }
+    }
   }
   red[threadIdx.x] = accB;
   __syncthreads();

@@ -28,6 +28,7 @@ struct psm_ctx {
   Grid g{};
   double tau = 0.6, omega_p = 0, omega_m = 0;
   int relax = 0, fp32 = 0, aa = 0;
+  LbmPlan plan{};       // staged collision kernel (plan.stages = 0: not used)
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
   std::vector<void*> allocs;
@@ -110,7 +111,7 @@ void dfree(psm_ctx* c, void* p) {
 template <typename T>
 T* alloc_n(psm_ctx* c, size_t n, std::vector<void*>& owner) {
   void* p = dalloc(c, sizeof(T) * n);
-  if (p) owner.push_back(p);
+  owner.push_back(p);  // NULL too: callers scan `owner` for failed allocations
   return static_cast<T*>(p);
 }
 
@@ -212,17 +213,18 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
     L.slot_pid = c->slots.pid;
     L.slot_B = c->slots.B;
     L.slot_Fc = c->slots.Fc;
+    L.slot_V = c->slots.V;
     L.slot_cap = c->slots.cap;
   }
-  L.px = c->p.x;
-  L.pu = c->p.u;
-  L.pom = c->p.om;
-  L.pxf = c->p.xf;
-  L.puf = c->p.uf;
-  L.pomf = c->p.omf;
   L.sc = c->sc;
   L.omega_p = c->omega_p;
   L.omega_m = c->omega_m;
+  L.status = c->status;
+  L.tile_rows = c->plan.tile_rows;
+  L.ntiles = c->plan.ntiles;
+  L.stages = c->plan.stages;
+  L.blocks = c->plan.blocks;
+  L.smem = c->plan.smem;
   n += launch_lbm(L, c->fp32, mode, s);
   if (c->timing) cudaEventRecord(c->ev[2], s);
   if (c->p.n > 0) n += launch_force_reduce(MP, s);
@@ -292,6 +294,8 @@ psm_status read_status(psm_ctx* c) {
     if (st & ST_SLOT_OVERFLOW)
       return fail(c, PSM_ERR_SLOT_OVERFLOW, "a cell lies within reach of more than two particles");
     if (st & ST_NONFINITE) return fail(c, PSM_ERR_NONFINITE, "non-finite hydrodynamic force");
+    if (st & ST_TIMEOUT)
+      return fail(c, PSM_ERR_TIMEOUT, "a bounded wait in the collision kernel gave up");
     return fail(c, PSM_ERR_STATE, "device status " + std::to_string(st));
   }
   return PSM_OK;
@@ -370,6 +374,8 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   g.wpr = (int)(nxp / 32);
   g.ncell = ncell;
   g.nwords = ncell / 32;
+  g.div_wpr = make_fastdiv((unsigned)g.wpr);
+  g.div_ny = make_fastdiv((unsigned)g.ny);
 
   auto bail = [&](psm_status st, const char* msg) {
     psm_status r = st;
@@ -415,6 +421,10 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   if (lbm_configure() != 0) {
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "could not set the shared-memory size of the collision kernel");
+  }
+  if (lbm_plan(g, c->fp32, c->aa, &c->plan) != 0) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "occupancy query of the collision kernel failed");
   }
   launch_step_const(map_params(c), s);
   if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
@@ -513,6 +523,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   S.B = alloc_n<unsigned char>(c, cp * 2 * (c->fp32 ? 4 : 8), c->palloc);
   S.cnt = alloc_n<int>(c, cp, c->palloc);
   S.Fc = alloc_n<unsigned char>(c, cp * 6 * (c->fp32 ? 4 : 8), c->palloc);
+  S.V = alloc_n<unsigned char>(c, cp * 8 * (c->fp32 ? 4 : 8), c->palloc);
   c->list_off = alloc_n<long long>(c, (size_t)n + 1, c->palloc);
   c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
   if (c->fp32) c->listf = alloc_n<float4>(c, (size_t)list_total, c->palloc);

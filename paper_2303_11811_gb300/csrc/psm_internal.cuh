@@ -28,33 +28,64 @@ enum : unsigned {
   ST_SLOT_OVERFLOW = 1u,
   ST_NONFINITE = 2u,
   ST_CONTACT_OVERFLOW = 4u,
+  ST_TIMEOUT = 8u,   // a bounded device wait gave up
 };
+
+// unsigned division by an invariant d for 0 <= n < 2^32 (Granlund and
+// Montgomery, PLDI 1994, Sec. 4): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n) gives
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+#ifdef __CUDACC__
+  __device__ __forceinline__ unsigned div(unsigned n) const {
+    const unsigned t = __umulhi(n, m);
+    return (t + ((n - t) >> s1)) >> s2;
+  }
+#endif
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.m = (unsigned)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
 
 struct Grid {
   int nx, ny, nz, nxp;
   int wall[3];          // 1 = walls on both faces of that axis
   int wpr;              // warps (coverage words) per x-row = nxp / 32
-  long long ncell;      // nxp * ny * nz
+  long long ncell;      // nxp * ny * nz (< 2^31)
   long long nwords;     // ncell / 32
+  FastDiv div_wpr, div_ny;
 };
 
 // Constants of one time step, computed on the device after the mapping
 // collision coefficients of one step in the storage precision: Eqs. 3-8
 // with the Guo prefactors (1 - omega/2) on the forcing, grouped so that the
-// relaxation of a pair is a chain of fused multiply-adds.  Class c = 0 holds
-// the face pairs (w = 1/18), c = 1 the edge pairs (w = 1/36).
+// relaxation of a pair is a chain of fused multiply-adds, and packed in
+// groups of four for 16-byte loads.  Class c = 0 holds the face pairs
+// (w = 1/18), c = 1 the edge pairs (w = 1/36).
+enum {
+  CC_HF = 0,      // f_ext / 2 (3 values), the velocity shift of Eq. 7
+  CC_NWP = 3,     // -omega+
+  CC_F = 4,       // f_ext (3 values)
+  CC_WPW0 = 7,    // omega+ w_0
+  CC_H = 8,       // forcing, symmetric part / (U . f_ext): rest, faces, edges
+  CC_MHWP = 11,   // -omega+/2
+  CC_WPW = 12,    // omega+ w_c (2 values)
+  CC_MHWM = 14    // -omega-/2
+};
 template <typename T>
-struct CollideCoef {
-  T hf[3];          // f_ext / 2, the velocity shift of Eq. 7
-  T f[3];           // f_ext
-  T Gs[9], Fa[9];   // forcing per pair: symmetric part / (c_k . U), antisymmetric part
-  T H[3];           // forcing, symmetric part / (U . f_ext): rest, faces, edges
-  T nwp;            // -omega+
-  T mhwp, mhwm;     // -omega+/2, -omega-/2
-  T wpw0;           // omega+ w_0
-  T wpw[2];         // omega+ w_c
-  T A[2];           // 9/2 omega+ w_c
-  T D[2];           // 3 omega- w_c
+struct alignas(16) CollideCoef {
+  T head[16];
+  // per pair k: symmetric forcing / (c_k . U), antisymmetric forcing,
+  // 9/2 omega+ w_c, 3 omega- w_c
+  T pair[9][4];
 };
 
 struct StepConst {
@@ -96,6 +127,9 @@ struct Slots {
   void* B;        // T2
   int* cnt;
   void* Fc;       // T[6] per entry
+  // T[8] per entry: for slots 0 and 1 the particle's surface velocity at the
+  // cell centre (Eq. 20) and the slot's normalised weight B_i
+  void* V;
   long long cap;
 };
 
@@ -148,19 +182,26 @@ struct LbmParams {
   const int2* slot_pid;
   const void* slot_B;   // T2
   void* slot_Fc;        // T[6] per entry
+  const void* slot_V;   // T[8] per entry (Slots::V)
   long long slot_cap;   // entries allocated
-  const double* px;     // FP64 path
-  const double* pu;
-  const double* pom;
-  const float* pxf;     // FP32 path (n*4)
-  const float* puf;
-  const float* pomf;
   const StepConst* sc;
   double omega_p, omega_m;
+  unsigned* status;     // device status word (ST_* bits)
+  // staged kernel (stages > 0): tiles of tile_rows x-rows, `stages` tiles in
+  // flight per block, `blocks` persistent blocks with `smem` bytes each
+  int tile_rows, ntiles, stages, blocks;
+  size_t smem;
+};
+
+struct LbmPlan {
+  int tile_rows, ntiles, stages, blocks;
+  size_t smem;
 };
 
 // ---- launchers (stream-ordered; return the number of kernel launches) ----
 int lbm_configure();  // kernel attributes; call once before launching (returns != 0 on error)
+// staged-kernel plan for a grid (stages = 0: use the one-cell-per-thread kernel)
+int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan);
 int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s);
 int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
                         double* out, cudaStream_t s);
