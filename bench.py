@@ -34,11 +34,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "LBM-PSM MLUPS and % of HBM roofline; FP32+MLP-eps vs FP64 at drag err<=0.5%"
-WORKLOAD = ("settle128: 128^3 periodic box, 400 spheres r=6 (random sequential addition, "
-            "gap>=1, seed 20230321), density ratio 2.5, gravity 2e-5 in -z, D3Q19 TRT "
-            "(Lambda=3/16) tau=0.55, 4^3 sub-division sampling, Noble-Torczynski B, "
-            "spring-dashpot DEM k_n=1e3 e=0.9 x10 sub-cycles, FP64 PDFs, pull streaming")
+WORKLOADS = {
+    "settle128": ("settle128: 128^3 periodic box, 400 spheres r=6 (random sequential addition, "
+                  "gap>=1, seed 20230321), density ratio 2.5, gravity 2e-5 in -z, D3Q19 TRT "
+                  "(Lambda=3/16) tau=0.55, 4^3 sub-division sampling, Noble-Torczynski B, "
+                  "spring-dashpot DEM k_n=1e3 e=0.9 x10 sub-cycles"),
+    "channel": ("channel: 256x256x512, walls at the x faces, 12,817 fixed spheres r=5 (random "
+                "sequential addition, solid fraction 0.20, seed 20230321), D3Q19 TRT "
+                "(Lambda=3/16) tau=0.55, body force 1e-5 along z, 4^3 sub-division sampling, "
+                "Noble-Torczynski B"),
+}
 HBM_FALLBACK_GBS = 6800.0
+SM_COUNT = 152
+# FP64 arithmetic peak of the GPU: 2 FP64 fused multiply-adds per clock per SM
+FP64_FMA_PER_CLK_SM = 2
+# algorithmic FP64 flops of the collision (adds and multiplies, a fused
+# multiply-add counts 2): per cell (moments, equilibrium, TRT relaxation with
+# forcing, (1 - B) weighting) and per occupied slot (solid operator and force)
+FLOP_PER_CELL = 219
+FLOP_PER_SLOT = 139
 
 
 def peaks():
@@ -105,10 +119,14 @@ def source_hash(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def profiled_traffic(kernel_src, workload):
+def fp64_peak_tflops(sm_max_mhz):
+    return SM_COUNT * FP64_FMA_PER_CLK_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
+def profiled_traffic(kernel_src, name):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     source is unchanged since the capture; else None."""
-    path = os.path.join(ROOT, "profiles", f"lbm_kernel_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(path):
         return None
     want = source_hash(kernel_src)
@@ -174,9 +192,9 @@ def run_reference(args, w, world, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / n * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "config": {"workload": describe(args), "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} full steps of settle128 (of {args.steps} requested; "
+                         "sample": f"{n} full steps of {args.workload} (of {args.steps} requested; "
                                    f"capped at {budget:.0f} s of host time)"},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -236,25 +254,38 @@ def forms_comparison(capi, torch, steps, seed=20230321):
     return out
 
 
+def describe(args):
+    prec = {"fp64": "FP64 PDFs", "fp32": "FP32 deviation PDFs"}[args.precision]
+    return f"{WORKLOADS[args.workload]}, {prec}, {args.streaming} streaming"
+
+
+def make_workload(name):
+    from paper_2303_11811_gb300 import inputs
+    return inputs.settle128() if name == "settle128" else inputs.channel()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="settle128")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--streaming", choices=["pull", "aa"], default="pull")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
+    default_run = (args.workload, args.precision, args.streaming) == ("settle128", "fp64", "pull")
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
-    from paper_2303_11811_gb300 import inputs
-    w = inputs.settle128()
+    w = make_workload(args.workload)
 
     if args.impl == "reference":
         import oracle
@@ -274,7 +305,7 @@ def main():
     if dist:
         dist.barrier()
 
-    e = make_engine(w, capi)
+    e = make_engine(w, capi, precision=args.precision, streaming=args.streaming)
     e.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -302,21 +333,45 @@ def main():
     t = e.timings()
     e.set_timing(False)
     lbm_ms = t[1] / t[4]
-    p0, _, _, _ = e.slots()
+    p0, _, p1, _ = e.slots()
     ncov = int((p0 >= 0).sum())
-    bytes_lbm = cells * 19 * 2 * 8
-    bytes_psm = bytes_lbm + ncov * 24
+    nslot = ncov + int((p1 >= 0).sum())
+    fp64 = args.precision == "fp64"
+    esz = 8 if fp64 else 4
+    bytes_lbm = cells * 19 * 2 * esz
+    bytes_psm = bytes_lbm + ncov * (24 if fp64 else 16)
     hbm, peak_kind = peaks()
-    achieved = bytes_psm / (lbm_ms * 1e-3) / 1e9
+    hbm_achieved = bytes_psm / (lbm_ms * 1e-3) / 1e9
+    staged = fp64 or args.streaming == "aa"
+    kname = ("lbm_bulk_kernel" if staged else "lbm_kernel") + \
+        f"<{'double' if fp64 else 'float'},{args.streaming}>"
     traffic = profiled_traffic(os.path.join(ROOT, "paper_2303_11811_gb300", "csrc",
-                                            "lbm_kernels.cu"), "settle128")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic,
-                "kernel": "lbm_kernel<double,pull>", "peak_source": peak_kind,
-                "bytes_per_launch": bytes_psm, "lbm_only_bytes_per_launch": bytes_lbm,
-                "covered_cells": ncov, "avg_launch_ms": lbm_ms,
-                "class_ms_per_step": {"mapping": t[0] / t[4], "stream_collide": lbm_ms,
-                                      "force_reduce": t[2] / t[4], "dem": t[3] / t[4]}}
+                                            "lbm_kernels.cu"),
+                               f"{'lbm_bulk_kernel' if staged else 'lbm_kernel'}_"
+                               f"{args.precision}{args.streaming}_{args.workload}")
+    hbm_part = {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                "frac": hbm_achieved / hbm, "peak_source": peak_kind,
+                "bytes_per_launch": bytes_psm, "lbm_only_bytes_per_launch": bytes_lbm}
+    common = {"kernel": kname, "traffic": traffic, "covered_cells": ncov, "slots": nslot,
+              "avg_launch_ms": lbm_ms,
+              "class_ms_per_step": {"mapping": t[0] / t[4], "stream_collide": lbm_ms,
+                                    "force_reduce": t[2] / t[4], "dem": t[3] / t[4]}}
+    if fp64:
+        # FP64 runs at 1/64 of the FP32 rate on this GPU: the FP64 pipe binds
+        sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
+        peak = fp64_peak_tflops(sm_max)
+        flops = FLOP_PER_CELL * cells + FLOP_PER_SLOT * nslot
+        achieved = flops / (lbm_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_source": f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk "
+                                   f"x 2 flop x {sm_max:.0f} MHz",
+                    "flops_per_launch": flops, "hbm": hbm_part, **common}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm, "peak_source": peak_kind,
+                    "bytes_per_launch": bytes_psm, "lbm_only_bytes_per_launch": bytes_lbm,
+                    **common}
 
     # end to end through the C ABI with host buffers in pinned memory
     n = w.particles["r"].size
@@ -342,7 +397,7 @@ def main():
     e.close()
 
     forms = None
-    if not args.no_forms and rank == 0:
+    if default_run and not args.no_forms and rank == 0:
         forms = forms_comparison(capi, torch, max(50, min(args.steps, 300)))
 
     cpu = None
@@ -351,16 +406,17 @@ def main():
         oracle.build()
         v, nst, dt = oracle_rate(w, args.cpu_seconds, 1000)
         cpu = {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-               "sample": f"{nst} full steps of settle128 on one host core ({dt:.1f} s)"}
+               "sample": f"{nst} full steps of {args.workload} on one host core ({dt:.1f} s)"}
 
     if rank == 0:
+        ws = cells * 19 * esz * (1 if args.streaming == "aa" else 2) / 1e6
         line = {
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": cells,
-                       "l2": "working set 638 MB (two FP64 PDF buffers) > 126 MB L2",
+            "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+            "config": {"workload": describe(args), "cells": cells,
+                       "l2": f"working set {ws:.0f} MB of PDFs > 126 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
             "cpu_baseline": cpu, "forms": forms,

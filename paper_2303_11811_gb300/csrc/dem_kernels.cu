@@ -4,18 +4,22 @@
 // gravity and the hydrodynamic force/torque of the last LBM step held fixed
 // over the sub-steps.
 //
-// Per sub-step: positions (all particles), then contact forces (every
-// particle reads the new positions and the old velocities of the others),
-// then velocities.  Contacts of particle i are summed in ascending j, then the
-// walls -x,+x,-y,+y,-z,+z, with plain IEEE FP64 operations (this file is
-// compiled with -fmad=false), so the sums are bitwise reproducible.
+// Once per LBM step the particles are binned (bin edge >= largest diameter +
+// skin) and each particle gets the list of partners within contact distance
+// plus the skin, in ascending index order.  A particle that moves more than
+// half the skin within the step could miss a contact: the sub-steps check the
+// displacement and set ST_DEM_SKIN; a list longer than its capacity sets
+// ST_CONTACT_OVERFLOW.
 //
-// Per sub-step two launches: contacts (one warp per particle scanning all
-// others with an FP32 prefilter -- float positions differ from FP64 by far
-// less than the 1e-2 margin -- and evaluating candidates in FP64, ascending
-// j), then the velocity update fused with the next sub-step's positions.
-// FP64 runs at 1/58 of the FP32 rate here, so the per-particle FP64 work is
-// spread over many SMs rather than run in one block.
+// Per sub-step one launch, one thread per particle: positions of the current
+// sub-step are read, contacts are summed over the list in ascending j (FP32
+// prefilter -- float positions differ from FP64 by far less than the 1e-2
+// margin -- then the exact FP64 contact), then the walls -x,+x,-y,+y,-z,+z,
+// with plain IEEE FP64 operations (this file is compiled with -fmad=false),
+// so the sums are bitwise reproducible; then the velocity update and the next
+// sub-step's positions.  FP64 runs at 1/64 of the FP32 rate here, so each
+// FP64 instruction works on 32 particles and the blocks (32 threads) spread
+// over many SMs.
 #include "psm_internal.cuh"
 
 namespace psm {
@@ -49,7 +53,7 @@ __global__ void dem_position_kernel(DemParams P) {
 
 // exact FP64 contact of i with j (j != i); adds to F when in contact.
 // X and U are the positions and velocities of the current sub-step.
-__device__ __forceinline__ void pair_contact(const DemParams& P, const double* X,
+__device__ __noinline__ void pair_contact(const DemParams& P, const double* X,
                                              const double* U, int i, int j, double* F) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   double d[3];
@@ -92,47 +96,164 @@ __device__ __forceinline__ void wall_contacts(const DemParams& P, const double* 
   }
 }
 
-// One sub-step in one launch: one warp per particle scans all others with an
-// FP32 prefilter, sums its contacts in ascending j (Eq. 12), updates its
-// velocity (Eq. 16) and writes the positions of the next sub-step (Eq. 15).
-// Positions and velocities are double-buffered: every contact reads the
-// current sub-step's state (Xc, Uc, XFc) while the new state goes to
-// (Xn, Un, XFn).  On the last sub-step the positions are carried over.
+// ---- neighbour lists, once per LBM step
+__device__ __forceinline__ int bin_of(const DemParams& P, float x, int a) {
+  int b = (int)(x / P.h[a]);
+  return b < 0 ? 0 : (b >= P.nc[a] ? P.nc[a] - 1 : b);
+}
+
+__global__ void dem_bin_kernel(DemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n) return;
+  const float x = (float)P.p.x[3 * i], y = (float)P.p.x[3 * i + 1], z = (float)P.p.x[3 * i + 2];
+  P.xbuild[i] = make_float4(x, y, z, (float)P.p.r[i]);
+  const int b = bin_of(P, x, 0) + P.nc[0] * (bin_of(P, y, 1) + P.nc[1] * bin_of(P, z, 2));
+  P.pbin[i] = b;
+  atomicAdd(&P.bin_count[b], 1);
+}
+
+// exclusive scan of the bin counts, one block
+constexpr int SCAN_THREADS = 1024;
+__global__ void dem_scan_kernel(DemParams P) {
+  __shared__ int part[SCAN_THREADS];
+  const int n = P.nbins, t = threadIdx.x;
+  const int chunk = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+  const int lo = t * chunk, hi = min(n, lo + chunk);
+  int s = 0;
+  for (int b = lo; b < hi; ++b) s += P.bin_count[b];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+    const int v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - s;
+  for (int b = lo; b < hi; ++b) {
+    P.bin_start[b] = run;
+    P.bin_cursor[b] = run;
+    run += P.bin_count[b];
+  }
+}
+
+__global__ void dem_fill_kernel(DemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n) return;
+  P.bin_items[atomicAdd(&P.bin_cursor[P.pbin[i]], 1)] = i;
+}
+
+// the bins next to bin b along one axis (periodic wrap or none at walls)
+__device__ __forceinline__ int axis_bins(const DemParams& P, int a, int b, int* out) {
+  const int nc = P.nc[a];
+  if (nc < 3) {
+    for (int k = 0; k < nc; ++k) out[k] = k;
+    return nc;
+  }
+  int m = 0;
+  for (int o = -1; o <= 1; ++o) {
+    int v = b + o;
+    if (v < 0 || v >= nc) {
+      if (P.g.wall[a]) continue;
+      v = v < 0 ? v + nc : v - nc;
+    }
+    out[m++] = v;
+  }
+  return m;
+}
+
+__device__ __forceinline__ float min_image(float d, float dim, int periodic) {
+  if (periodic) {
+    if (d > 0.5f * dim) d -= dim;
+    else if (d < -0.5f * dim) d += dim;
+  }
+  return d;
+}
+
+__global__ void dem_nbr_kernel(DemParams P) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.p.n) return;
+  const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
+  const float4 xi = P.xbuild[i];
+  const float xa[3] = {xi.x, xi.y, xi.z};
+  int bx[3], by[3], bz[3];
+  const int nbx = axis_bins(P, 0, bin_of(P, xi.x, 0), bx);
+  const int nby = axis_bins(P, 1, bin_of(P, xi.y, 1), by);
+  const int nbz = axis_bins(P, 2, bin_of(P, xi.z, 2), bz);
+  int* L = P.nbr + (size_t)i * P.K;
+  int cnt = 0;
+  bool over = false;
+  for (int c = 0; c < nbz; ++c)
+    for (int bb = 0; bb < nby; ++bb)
+      for (int aa = 0; aa < nbx; ++aa) {
+        const int b = bx[aa] + P.nc[0] * (by[bb] + P.nc[1] * bz[c]);
+        const int e = P.bin_start[b] + P.bin_count[b];
+        for (int k = P.bin_start[b]; k < e; ++k) {
+          const int j = P.bin_items[k];
+          if (j == i) continue;
+          const float4 xj = P.xbuild[j];
+          const float xb[3] = {xj.x, xj.y, xj.z};
+          float d2 = 0.0f;
+          for (int a = 0; a < 3; ++a) {
+            const float d = min_image(xa[a] - xb[a], dims[a], !P.g.wall[a]);
+            d2 += d * d;
+          }
+          const float reach = xi.w + xj.w + P.skin;
+          if (!(d2 < reach * reach)) continue;
+          if (cnt == P.K) {
+            over = true;
+            continue;
+          }
+          // insertion keeps the list in ascending index order
+          int pos = cnt++;
+          while (pos > 0 && L[pos - 1] > j) {
+            L[pos] = L[pos - 1];
+            --pos;
+          }
+          L[pos] = j;
+        }
+      }
+  P.nbr_cnt[i] = cnt;
+  if (over) atomicOr(P.status, ST_CONTACT_OVERFLOW);
+}
+
+// One sub-step in one launch, one thread per particle: contacts over the
+// neighbour list in ascending j (Eq. 12), velocity update (Eq. 16) and the
+// positions of the next sub-step (Eq. 15).  Positions and velocities are
+// double-buffered: every contact reads the current sub-step's state (Xc, Uc,
+// XFc) while the new state goes to (Xn, Un, XFn).  On the last sub-step the
+// positions are carried over.
+constexpr int DEM_BATCH = 8;
 __global__ void dem_substep_kernel(DemParams P, const double* __restrict__ Xc,
                                    const double* __restrict__ Uc,
                                    const float4* __restrict__ XFc, double* __restrict__ Xn,
                                    double* __restrict__ Un, float4* __restrict__ XFn,
                                    int last) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P.p.n) return;
   const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
   const float4 xi = XFc[i];
   double F[3] = {0.0, 0.0, 0.0};
-  const int n = P.p.n;
-  for (int base = 0; base < n; base += 32) {
-    const int j = base + lane;
-    bool cand = false;
-    if (j < n && j != i) {
-      const float4 xj = XFc[j];
-      float d[3] = {xi.x - xj.x, xi.y - xj.y, xi.z - xj.z};
-      for (int a = 0; a < 3; ++a) {
-        if (!P.g.wall[a]) {
-          if (d[a] > 0.5f * dims[a]) d[a] -= dims[a];
-          else if (d[a] < -0.5f * dims[a]) d[a] += dims[a];
-        }
-      }
-      const float rs = xi.w + xj.w + 1e-2f;
-      cand = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < rs * rs;
-    }
-    unsigned bits = __ballot_sync(0xffffffffu, cand);
-    while (bits) {
-      const int l = __ffs(bits) - 1;
-      bits &= bits - 1;
-      pair_contact(P, Xc, Uc, i, base + l, F);  // same values on all lanes
+  const int cnt = P.nbr_cnt[i];
+  const int* L = P.nbr + (size_t)i * P.K;
+  for (int k0 = 0; k0 < cnt; k0 += DEM_BATCH) {
+    // the batch's partners and positions are loaded before any is used
+    int jj[DEM_BATCH];
+    float4 xj[DEM_BATCH];
+#pragma unroll
+    for (int u = 0; u < DEM_BATCH; ++u) jj[u] = k0 + u < cnt ? L[k0 + u] : -1;
+#pragma unroll
+    for (int u = 0; u < DEM_BATCH; ++u) xj[u] = jj[u] >= 0 ? XFc[jj[u]] : xi;
+#pragma unroll
+    for (int u = 0; u < DEM_BATCH; ++u) {
+      if (jj[u] < 0) continue;
+      const float dx = min_image(xi.x - xj[u].x, dims[0], !P.g.wall[0]);
+      const float dy = min_image(xi.y - xj[u].y, dims[1], !P.g.wall[1]);
+      const float dz = min_image(xi.z - xj[u].z, dims[2], !P.g.wall[2]);
+      const float rs = xi.w + xj[u].w + 1e-2f;
+      if (dx * dx + dy * dy + dz * dz < rs * rs) pair_contact(P, Xc, Uc, i, jj[u], F);
     }
   }
-  if (lane != 0) return;
   wall_contacts(P, Xc, Uc, i, F);
   const double dt = P.dt;
   const double ddims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
@@ -160,6 +281,12 @@ __global__ void dem_substep_kernel(DemParams P, const double* __restrict__ Xc,
         x[a] = xn;
       }
     }
+    // the lists stay valid while every particle moves less than skin / 2
+    const float4 xb = P.xbuild[i];
+    const float ex = min_image((float)x[0] - xb.x, dims[0], !P.g.wall[0]);
+    const float ey = min_image((float)x[1] - xb.y, dims[1], !P.g.wall[1]);
+    const float ez = min_image((float)x[2] - xb.z, dims[2], !P.g.wall[2]);
+    if (ex * ex + ey * ey + ez * ez > 0.25f * P.skin * P.skin) atomicOr(P.status, ST_DEM_SKIN);
   }
   for (int a = 0; a < 3; ++a) {
     Un[3 * i + a] = u[a];
@@ -185,10 +312,16 @@ __global__ void dem_copy_back_kernel(DemParams P, const double* __restrict__ X,
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
   const int n = P.p.n;
   if (n == 0) return 0;
-  const int tb = 128;
+  const int tb = 32;
   const unsigned gp = (n + tb - 1) / tb;
-  const unsigned gw = (unsigned)(((long long)n * 32 + tb - 1) / tb);
   int launches = 0;
+  // neighbour lists from the positions at the start of the step
+  cudaMemsetAsync(P.bin_count, 0, sizeof(int) * (size_t)P.nbins, s);
+  dem_bin_kernel<<<gp, tb, 0, s>>>(P);
+  dem_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(P);
+  dem_fill_kernel<<<gp, tb, 0, s>>>(P);
+  dem_nbr_kernel<<<gp, tb, 0, s>>>(P);
+  launches += 4;
   dem_position_kernel<<<gp, tb, 0, s>>>(P);
   ++launches;
   const double* Xc = P.p.x;
@@ -199,7 +332,7 @@ int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
     double* Xn = to2 ? P.p.x2 : P.p.x;
     double* Un = to2 ? P.p.u2 : P.p.u;
     float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
-    dem_substep_kernel<<<gw, tb, 0, s>>>(P, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+    dem_substep_kernel<<<gp, tb, 0, s>>>(P, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
     ++launches;
     Xc = Xn;
     Uc = Un;

@@ -2,6 +2,7 @@
 // the kernels within one time step, CUDA-graph replay, error and status
 // handling.  Host arithmetic that feeds the device (particle volume, mass,
 // inertia, f(r) of Eq. 26) is compiled with -ffp-contract=off.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -22,6 +23,11 @@ using namespace psm;
 struct Alloc {
   void* ptr;
 };
+
+// DEM neighbour lists: margin beyond contact (lattice units; a particle may
+// move up to half of it within one LBM step) and capacity per particle
+constexpr float kDemSkin = 1.0f;
+constexpr int kDemListCap = 64;
 
 struct psm_ctx {
   psm_options opt{};
@@ -47,8 +53,13 @@ struct psm_ctx {
   bool need_pack = false;
   double G[3] = {0, 0, 0};
   double log_e = 0;
-  int dem_nc[3] = {1, 1, 1};   // DEM cell list
+  int dem_nc[3] = {1, 1, 1};   // DEM bins per axis
   float dem_h[3] = {1, 1, 1};
+  int dem_nbins = 1;
+  int* dem_bins = nullptr;       // count, start, cursor (3 * dem_nbins)
+  int* dem_items = nullptr;      // bin_items, pbin, nbr_cnt (3 * n)
+  int* dem_nbr = nullptr;        // n * kDemListCap
+  float4* dem_xbuild = nullptr;  // n
   float* mlp = nullptr;   // FP32 parameters on the device
   bool have_mlp = false;
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
@@ -137,6 +148,10 @@ void free_particles(psm_ctx* c) {
   c->list_off = nullptr;
   c->list = nullptr;
   c->listf = nullptr;
+  c->dem_bins = nullptr;
+  c->dem_items = nullptr;
+  c->dem_nbr = nullptr;
+  c->dem_xbuild = nullptr;
   c->list_cnt = nullptr;
 }
 
@@ -242,6 +257,17 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
       D.h[a] = c->dem_h[a];
     }
     D.status = c->status;
+    D.skin = kDemSkin;
+    D.K = kDemListCap;
+    D.nbins = c->dem_nbins;
+    D.bin_count = c->dem_bins;
+    D.bin_start = c->dem_bins + c->dem_nbins;
+    D.bin_cursor = c->dem_bins + 2 * c->dem_nbins;
+    D.bin_items = c->dem_items;
+    D.pbin = c->dem_items + c->p.n;
+    D.nbr_cnt = c->dem_items + 2 * c->p.n;
+    D.nbr = c->dem_nbr;
+    D.xbuild = c->dem_xbuild;
     n += launch_dem_step(D, c->opt.dem_subcycles, s);
   }
   if (c->timing) cudaEventRecord(c->ev[4], s);
@@ -294,6 +320,11 @@ psm_status read_status(psm_ctx* c) {
     if (st & ST_SLOT_OVERFLOW)
       return fail(c, PSM_ERR_SLOT_OVERFLOW, "a cell lies within reach of more than two particles");
     if (st & ST_NONFINITE) return fail(c, PSM_ERR_NONFINITE, "non-finite hydrodynamic force");
+    if (st & ST_CONTACT_OVERFLOW)
+      return fail(c, PSM_ERR_STATE, "more DEM neighbours than the list holds");
+    if (st & ST_DEM_SKIN)
+      return fail(c, PSM_ERR_STATE,
+                  "a particle moved more than half the DEM neighbour-list skin in one step");
     if (st & ST_TIMEOUT)
       return fail(c, PSM_ERR_TIMEOUT, "a bounded wait in the collision kernel gave up");
     return fail(c, PSM_ERR_STATE, "device status " + std::to_string(st));
@@ -488,6 +519,25 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
     cap += ci;
     loff[i + 1] = loff[i] + ci;
   }
+  // DEM bins: edge >= the largest diameter plus the skin, at least three
+  // bins along an axis or a single one, at most max(4096, 8 n) bins
+  double rmax = 0.0;
+  for (int i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
+  int nc[3];
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = (int)std::floor(dims[a] / (2.0 * rmax + kDemSkin + 0.01));
+    if (nc[a] < 3) nc[a] = 1;
+  }
+  const long long bin_cap = std::max(4096LL, 8LL * n);
+  while ((long long)nc[0] * nc[1] * nc[2] > bin_cap) {
+    const int a = nc[0] >= nc[1] && nc[0] >= nc[2] ? 0 : (nc[1] >= nc[2] ? 1 : 2);
+    nc[a] = nc[a] / 2 < 3 ? 1 : nc[a] / 2;
+  }
+  for (int a = 0; a < 3; ++a) {
+    c->dem_nc[a] = nc[a];
+    c->dem_h[a] = (float)((double)dims[a] / nc[a]);
+  }
+  c->dem_nbins = nc[0] * nc[1] * nc[2];
   const long long list_total = cap > 0 ? cap : 1;
   if (cap > c->g.ncell) cap = c->g.ncell;
   free_graphs(c);
@@ -528,6 +578,10 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
   if (c->fp32) c->listf = alloc_n<float4>(c, (size_t)list_total, c->palloc);
   c->list_cnt = alloc_n<int>(c, n1, c->palloc);
+  c->dem_bins = alloc_n<int>(c, 3 * (size_t)c->dem_nbins, c->palloc);
+  c->dem_items = alloc_n<int>(c, 3 * n1, c->palloc);
+  c->dem_nbr = alloc_n<int>(c, n1 * kDemListCap, c->palloc);
+  c->dem_xbuild = alloc_n<float4>(c, n1, c->palloc);
   if (c->opt.eps_mode == PSM_EPS_MLP) {
     c->mlp_cap = (long long)cp;
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
@@ -561,17 +615,6 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   CK(cudaMemcpyAsync(c->list_off, loff.data(), sizeof(long long) * (n + 1),
                      cudaMemcpyHostToDevice, s));
   for (int a = 0; a < 3; ++a) c->G[a] = G[a];
-  // DEM cell list: edge >= the largest diameter (plus the prefilter margin),
-  // at least three cells along an axis or a single one
-  double rmax = 0.0;
-  for (int i = 0; i < n; ++i) rmax = r[i] > rmax ? r[i] : rmax;
-  for (int a = 0; a < 3; ++a) {
-    int nc = (int)std::floor(dims[a] / (2.0 * rmax + 0.05));
-    if (nc < 3) nc = 1;
-    if (nc > 1024) nc = 1024;
-    c->dem_nc[a] = nc;
-    c->dem_h[a] = (float)((double)dims[a] / nc);
-  }
   c->any_free = any_free;
   c->need_map = true;
   c->error_state = false;

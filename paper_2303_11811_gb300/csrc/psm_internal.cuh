@@ -29,6 +29,7 @@ enum : unsigned {
   ST_NONFINITE = 2u,
   ST_CONTACT_OVERFLOW = 4u,
   ST_TIMEOUT = 8u,   // a bounded device wait gave up
+  ST_DEM_SKIN = 16u, // a particle moved more than half the neighbour-list skin in one step
 };
 
 // unsigned division by an invariant d for 0 <= n < 2^32 (Granlund and
@@ -227,8 +228,19 @@ struct DemParams {
   double kn, log_e, dt;
   double gravity[3];
   unsigned* status;
-  int nc[3];          // cell-list cells per axis (edge >= largest diameter)
-  float h[3];         // cell edges
+  int nc[3];          // bins per axis (edge >= largest diameter + skin)
+  float h[3];         // bin edges
+  float skin;         // neighbour-list margin beyond contact
+  int K;              // neighbour-list capacity per particle
+  int nbins;
+  int* bin_count;     // nbins
+  int* bin_start;     // nbins
+  int* bin_cursor;    // nbins
+  int* bin_items;     // n, particle indices grouped by bin
+  int* pbin;          // n, bin of each particle
+  int* nbr;           // n*K, candidate partners in ascending order
+  int* nbr_cnt;       // n
+  float4* xbuild;     // n, positions when the lists were built
 };
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
 
