@@ -172,15 +172,55 @@ __device__ __forceinline__ void load_offsets(int n, double* s64, float* s32) {
   __syncthreads();
 }
 
+// Cells in reach of one particle (one block per particle): the coverage bits
+// (one atomicOr per distinct word of a warp) and the particle's list of its
+// cells in box order, as box indices t; the fill pass replaces them by slot
+// indices.
 __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
+  __shared__ int warp_tot[MAP_THREADS / 32];
+  __shared__ int running;
   const int p = blockIdx.x;
   const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
-  for (int t = threadIdx.x; t < b.count; t += MAP_THREADS) {
+  const long long loff = P.list_off[p];
+  const int lcap = (int)(P.list_off[p + 1] - loff);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
+    const int t = t0 + threadIdx.x;
     CellHit h;
-    box_coords(P.g, b, t, h);
-    if (!reach_test(b, h)) continue;
-    const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-    atomicOr(&P.cov.mask[cell >> 5], 1u << (cell & 31));
+    bool in = false;
+    if (t < b.count) {
+      box_coords(P.g, b, t, h);
+      in = reach_test(b, h);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, in);
+    if (lane == 0) warp_tot[wid] = __popc(bal);
+    const long long cell = in ? padded_cell(P.g, h.ix, h.iy, h.iz) : 0;
+    unsigned pend = bal;
+    while (pend) {
+      const int leader = __ffs(pend) - 1;
+      const long long w0 = __shfl_sync(0xffffffffu, cell >> 5, leader);
+      const bool mine = in && (cell >> 5) == w0;
+      const unsigned bits = __reduce_or_sync(0xffffffffu, mine ? 1u << (cell & 31) : 0u);
+      if (lane == leader) atomicOr(&P.cov.mask[w0], bits);
+      pend &= ~__ballot_sync(0xffffffffu, mine);
+    }
+    __syncthreads();
+    int before = running, chunk = 0;
+    for (int w = 0; w < MAP_THREADS / 32; ++w) {
+      if (w < wid) before += warp_tot[w];
+      chunk += warp_tot[w];
+    }
+    const int pos = before + __popc(bal & ((1u << lane) - 1u));
+    if (in && pos < lcap) P.list[loff + pos] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) running += chunk;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    P.list_cnt[p] = running < lcap ? running : lcap;
+    if (running > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
   }
 }
 
@@ -254,6 +294,20 @@ __global__ void clear_slots_kernel(MapParams P) {
   }
 }
 
+// sampled count of a cell for one particle (n^3 for a cell inside by the
+// margin sqrt(3)/2, which the sampling would also give)
+__device__ int cell_count(const MapParams& P, const Box& b, const CellHit& h, const double* s64,
+                          const float* s32) {
+  const int n = P.eps_n;
+  if (b.rin2 >= 0.0) {
+    if (h.d2f < b.rin2f - b.E) return n * n * n;
+    if (h.d2f <= b.rin2f + b.E && h.d2 <= b.rin2) return n * n * n;
+  }
+  return n == 4   ? supersample_count_n<4>(h.dx, h.dy, h.dz, b.r)
+         : n == 8 ? supersample_count_n<8>(h.dx, h.dy, h.dz, b.r)
+                  : supersample_count_fast(h.dx, h.dy, h.dz, b.r, n, s64, s32);
+}
+
 // eps of a cell for one particle; -1 means "resolved in a later pass".  The
 // inside test d2 <= (r - sqrt(3)/2)^2 is taken in FP32 outside the band.
 __device__ double cell_eps(const MapParams& P, const Box& b, const CellHit& h, double fr,
@@ -283,64 +337,82 @@ __device__ double cell_eps(const MapParams& P, const Box& b, const CellHit& h, d
   return (double)cnt / (double)n3;
 }
 
-// claims the slots of one particle's cells and lists them in box order
+// eps of a sampled count: count / n^3; for n^3 a power of two the product
+// with the reciprocal is the same IEEE result as the quotient
+__device__ __forceinline__ double count_eps(int cnt, int n3) {
+  if ((n3 & (n3 - 1)) == 0) return (double)cnt * (1.0 / (double)n3);
+  return (double)cnt / (double)n3;
+}
+
+constexpr int WTAB = 513;  // B of every sampled count up to 8^3
+
+// Slots of one particle's cells (one block per particle, over the list the
+// mark pass wrote): claims a slot per cell, writes B (Eq. 16, from a table
+// of the n^3 + 1 sampled values when eps is a count), and the particle's
+// surface velocity at the cell centre (Eq. 20); the list entry becomes the
+// slot index (and, for the FP32 path, the float offset from the centre).
 __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
   __shared__ double s64[16];
   __shared__ float s32[16];
-  __shared__ int warp_tot[MAP_THREADS / 32];
-  __shared__ int running;
+  __shared__ double wtab[WTAB];
   const int p = blockIdx.x;
   const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const double fr = P.p.fr[p];
-  if (threadIdx.x == 0) running = 0;
-  load_offsets(P.eps_n, s64, s32);
+  const int n = P.eps_n, n3 = n * n * n;
+  const bool tab = P.eps_mode == 0 && n3 < WTAB;
+  if (tab)
+    for (int c = threadIdx.x; c <= n3; c += MAP_THREADS)
+      wtab[c] = weight(count_eps(c, n3), P.tau, P.weighting);
+  load_offsets(P.eps_n, s64, s32);  // ends with __syncthreads
+  const double u0 = P.p.u[3 * p], u1 = P.p.u[3 * p + 1], u2 = P.p.u[3 * p + 2];
+  const double o0 = P.p.om[3 * p], o1 = P.p.om[3 * p + 1], o2 = P.p.om[3 * p + 2];
   const long long loff = P.list_off[p];
-  const int lcap = (int)(P.list_off[p + 1] - loff);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
-    const int t = t0 + threadIdx.x;
+  const int cnt = P.list_cnt[p];
+  for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
     CellHit h;
-    bool in = false;
-    if (t < b.count) {
-      box_coords(P.g, b, t, h);
-      in = reach_test(b, h);
+    box_coords(P.g, b, P.list[loff + k], h);
+    const float dxf = (float)(h.kx - b.ip[0]) + (0.5f - b.fpf[0]);
+    const float dyf = (float)(h.ky - b.ip[1]) + (0.5f - b.fpf[1]);
+    const float dzf = (float)(h.kz - b.ip[2]) + (0.5f - b.fpf[2]);
+    h.d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+    h.dx = ((double)h.kx + 0.5) - b.xp[0];
+    h.dy = ((double)h.ky + 0.5) - b.xp[1];
+    h.dz = ((double)h.kz + 0.5) - b.xp[2];
+    h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
+    const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
+    const long long e = slot_index(P.cov, cell);
+    if (e >= P.s.cap) {
+      P.list[loff + k] = 0;  // the step reports the slot overflow
+      continue;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, in);
-    if (lane == 0) warp_tot[wid] = __popc(bal);
-    __syncthreads();
-    int before = running, chunk = 0;
-    for (int w = 0; w < MAP_THREADS / 32; ++w) {
-      if (w < wid) before += warp_tot[w];
-      chunk += warp_tot[w];
+    P.list[loff + k] = (int)e;
+    if (P.fp32) P.listf[loff + k] = make_float4((float)h.dx, (float)h.dy, (float)h.dz, 0.f);
+    const int s = atomicAdd(&P.s.cnt[e], 1);
+    if (s >= 2) {
+      atomicOr(P.status, ST_SLOT_OVERFLOW);
+      continue;
     }
-    const int pos = before + __popc(bal & ((1u << lane) - 1u));
-    if (in) {
-      const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-      const long long e = slot_index(P.cov, cell);
-      if (e < P.s.cap) {
-        if (pos < lcap) {
-          P.list[loff + pos] = (int)e;
-          if (P.fp32)
-            P.listf[loff + pos] = make_float4((float)h.dx, (float)h.dy, (float)h.dz, 0.f);
-        }
-        const int s = atomicAdd(&P.s.cnt[e], 1);
-        if (s >= 2) {
-          atomicOr(P.status, ST_SLOT_OVERFLOW);
-        } else {
-          P.s.cell[e] = (int)cell;
-          reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
-          const double eps = cell_eps(P, b, h, fr, s64, s32);
-          store_B(P, e, s, eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting));
-        }
-      }
+    P.s.cell[e] = (int)cell;
+    reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
+    double B;
+    if (tab) {
+      const int c = cell_count(P, b, h, s64, s32);
+      B = wtab[c];
+    } else {
+      const double eps = cell_eps(P, b, h, fr, s64, s32);
+      B = eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) running += chunk;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    P.list_cnt[p] = running < lcap ? running : lcap;
-    if (running > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
+    store_B(P, e, s, B);
+    const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
+    const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
+    const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
+    if (P.fp32) {
+      static_cast<float4*>(P.s.V)[2 * e + s] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+    } else {
+      double2* R = static_cast<double2*>(P.s.V) + 4 * e + 2 * s;
+      R[0] = make_double2(v0, v1);
+      R[1] = make_double2(v2, 0.0);
+    }
   }
 }
 
@@ -396,7 +468,8 @@ __global__ void finish_kernel(MapParams P) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int2 pid = P.s.pid[e];
     double B0 = load_B(P, e, 0), B1 = load_B(P, e, 1);
-    if (pid.y >= 0 && pid.y < pid.x) {
+    const bool swapped = pid.y >= 0 && pid.y < pid.x;
+    if (swapped) {
       const int t = pid.x;
       pid.x = pid.y;
       pid.y = t;
@@ -430,31 +503,37 @@ __global__ void finish_kernel(MapParams P) {
     store_B(P, e, 0, B0);
     store_B(P, e, 1, B1);
     accB += B;
-    // per slot: the particle's surface velocity at the cell centre (Eq. 20)
-    // and its weight, read by the collision
-    int x, y, z;
-    cell_xyz(P.g, P.s.cell[e], x, y, z);
-    for (int s = 0; s < 2; ++s) {
-      const int p = s ? pid.y : pid.x;
-      double v[4] = {0.0, 0.0, 0.0, s ? B1 : B0};
-      if (p >= 0) {
-        const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-        const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-        const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-        const double* u = P.p.u + 3 * p;
-        const double* om = P.p.om + 3 * p;
-        v[0] = u[0] + (om[1] * dz - om[2] * dy);
-        v[1] = u[1] + (om[2] * dx - om[0] * dz);
-        v[2] = u[2] + (om[0] * dy - om[1] * dx);
+    // slot records (surface velocity from the fill pass): in slot order,
+    // with the final weights
+    if (P.fp32) {
+      float4* R = static_cast<float4*>(P.s.V) + 2 * e;
+      float4 r0 = R[0], r1 = R[1];
+      if (swapped) {
+        const float4 t = r0;
+        r0 = r1;
+        r1 = t;
       }
-      if (P.fp32) {
-        float4* o = static_cast<float4*>(P.s.V) + 2 * e + s;
-        *o = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-      } else {
-        double2* o = static_cast<double2*>(P.s.V) + 4 * e + 2 * s;
-        o[0] = make_double2(v[0], v[1]);
-        o[1] = make_double2(v[2], v[3]);
+      r0.w = (float)B0;
+      r1.w = (float)B1;
+      R[0] = r0;
+      R[1] = r1;
+    } else {
+      double2* R = static_cast<double2*>(P.s.V) + 4 * e;
+      double2 a0 = R[0], a1 = R[1], c0 = R[2], c1 = R[3];
+      if (swapped) {
+        double2 t = a0;
+        a0 = c0;
+        c0 = t;
+        t = a1;
+        a1 = c1;
+        c1 = t;
       }
+      a1.y = B0;
+      c1.y = B1;
+      R[0] = a0;
+      R[1] = a1;
+      R[2] = c0;
+      R[3] = c1;
     }
   }
   red[threadIdx.x] = accB;
