@@ -31,9 +31,7 @@ __device__ __forceinline__ double damping(double meff, double kn, double le) {
   return -2.0 * le * sqrt(meff * kn) / sqrt(PI * PI + le * le);
 }
 
-__global__ void dem_position_kernel(DemParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_position(const DemParams& P, int i) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   if (!P.p.fixed[i]) {
     const double dt = P.dt;
@@ -102,9 +100,7 @@ __device__ __forceinline__ int bin_of(const DemParams& P, float x, int a) {
   return b < 0 ? 0 : (b >= P.nc[a] ? P.nc[a] - 1 : b);
 }
 
-__global__ void dem_bin_kernel(DemParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_bin(const DemParams& P, int i) {
   const float x = (float)P.p.x[3 * i], y = (float)P.p.x[3 * i + 1], z = (float)P.p.x[3 * i + 2];
   P.xbuild[i] = make_float4(x, y, z, (float)P.p.r[i]);
   const int b = bin_of(P, x, 0) + P.nc[0] * (bin_of(P, y, 1) + P.nc[1] * bin_of(P, z, 2));
@@ -112,18 +108,17 @@ __global__ void dem_bin_kernel(DemParams P) {
   atomicAdd(&P.bin_count[b], 1);
 }
 
-// exclusive scan of the bin counts, one block
-constexpr int SCAN_THREADS = 1024;
-__global__ void dem_scan_kernel(DemParams P) {
-  __shared__ int part[SCAN_THREADS];
-  const int n = P.nbins, t = threadIdx.x;
-  const int chunk = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+// exclusive scan of the bin counts by one block (part: blockDim ints of
+// shared memory)
+__device__ void dem_scan(const DemParams& P, int* part) {
+  const int n = P.nbins, t = threadIdx.x, nt = blockDim.x;
+  const int chunk = (n + nt - 1) / nt;
   const int lo = t * chunk, hi = min(n, lo + chunk);
   int s = 0;
   for (int b = lo; b < hi; ++b) s += P.bin_count[b];
   part[t] = s;
   __syncthreads();
-  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+  for (int off = 1; off < nt; off <<= 1) {
     const int v = t >= off ? part[t - off] : 0;
     __syncthreads();
     part[t] += v;
@@ -137,9 +132,7 @@ __global__ void dem_scan_kernel(DemParams P) {
   }
 }
 
-__global__ void dem_fill_kernel(DemParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_fill(const DemParams& P, int i) {
   P.bin_items[atomicAdd(&P.bin_cursor[P.pbin[i]], 1)] = i;
 }
 
@@ -170,9 +163,7 @@ __device__ __forceinline__ float min_image(float d, float dim, int periodic) {
   return d;
 }
 
-__global__ void dem_nbr_kernel(DemParams P) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_nbr(const DemParams& P, int i) {
   const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
   const float4 xi = P.xbuild[i];
   const float xa[3] = {xi.x, xi.y, xi.z};
@@ -224,13 +215,10 @@ __global__ void dem_nbr_kernel(DemParams P) {
 // XFc) while the new state goes to (Xn, Un, XFn).  On the last sub-step the
 // positions are carried over.
 constexpr int DEM_BATCH = 8;
-__global__ void dem_substep_kernel(DemParams P, const double* __restrict__ Xc,
-                                   const double* __restrict__ Uc,
-                                   const float4* __restrict__ XFc, double* __restrict__ Xn,
-                                   double* __restrict__ Un, float4* __restrict__ XFn,
-                                   int last) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_substep(const DemParams& P, int i, const double* __restrict__ Xc,
+                            const double* __restrict__ Uc, const float4* __restrict__ XFc,
+                            double* __restrict__ Xn, double* __restrict__ Un,
+                            float4* __restrict__ XFn, int last) {
   const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
   const float4 xi = XFc[i];
   double F[3] = {0.0, 0.0, 0.0};
@@ -295,11 +283,8 @@ __global__ void dem_substep_kernel(DemParams P, const double* __restrict__ Xc,
   XFn[i] = make_float4((float)x[0], (float)x[1], (float)x[2], xi.w);
 }
 
-__global__ void dem_copy_back_kernel(DemParams P, const double* __restrict__ X,
-                                     const double* __restrict__ U,
-                                     const float4* __restrict__ XF) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P.p.n) return;
+__device__ void dem_copy_back(const DemParams& P, int i, const double* __restrict__ X,
+                              const double* __restrict__ U, const float4* __restrict__ XF) {
   for (int a = 0; a < 3; ++a) {
     P.p.x[3 * i + a] = X[3 * i + a];
     P.p.u[3 * i + a] = U[3 * i + a];
@@ -307,23 +292,63 @@ __global__ void dem_copy_back_kernel(DemParams P, const double* __restrict__ X,
   reinterpret_cast<float4*>(P.p.xf)[i] = XF[i];
 }
 
-}  // namespace
+// ---- one DEM step in one launch: the phases above separated by a grid
+// barrier (all blocks resident: cooperative launch).  The barrier's wait is
+// bounded (1 s); a block that gives up sets ST_TIMEOUT and leaves.
+constexpr int DEM_THREADS = 32;
+constexpr unsigned long long kBarrierLimitNs = 1000000000ull;
 
-int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
+__device__ __forceinline__ unsigned long long dem_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// sense by generation: the last block to arrive resets the count and bumps
+// the generation the others wait on
+__device__ bool grid_barrier(const DemParams& P, unsigned& gen) {
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&P.bar[0], 1u) == gridDim.x - 1) {
+      atomicExch(&P.bar[0], 0u);
+      __threadfence();
+      atomicAdd(&P.bar[1], 1u);
+    } else {
+      volatile unsigned* g = &P.bar[1];
+      const unsigned long long t0 = dem_ns();
+      while (*g == gen) {
+        if (dem_ns() - t0 > kBarrierLimitNs) {
+          ok = 0;
+          atomicOr(P.status, ST_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  ++gen;
+  return __syncthreads_and(ok) != 0;
+}
+
+__global__ void __launch_bounds__(DEM_THREADS) dem_step_kernel(DemParams P, int subcycles) {
+  __shared__ int part[DEM_THREADS];
+  unsigned gen = *(volatile unsigned*)&P.bar[1];
   const int n = P.p.n;
-  if (n == 0) return 0;
-  const int tb = 32;
-  const unsigned gp = (n + tb - 1) / tb;
-  int launches = 0;
-  // neighbour lists from the positions at the start of the step
-  cudaMemsetAsync(P.bin_count, 0, sizeof(int) * (size_t)P.nbins, s);
-  dem_bin_kernel<<<gp, tb, 0, s>>>(P);
-  dem_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(P);
-  dem_fill_kernel<<<gp, tb, 0, s>>>(P);
-  dem_nbr_kernel<<<gp, tb, 0, s>>>(P);
-  launches += 4;
-  dem_position_kernel<<<gp, tb, 0, s>>>(P);
-  ++launches;
+  const int stride = gridDim.x * blockDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int b = i0; b < P.nbins; b += stride) P.bin_count[b] = 0;
+  if (!grid_barrier(P, gen)) return;
+  for (int i = i0; i < n; i += stride) dem_bin(P, i);
+  if (!grid_barrier(P, gen)) return;
+  if (blockIdx.x == 0) dem_scan(P, part);
+  if (!grid_barrier(P, gen)) return;
+  for (int i = i0; i < n; i += stride) dem_fill(P, i);
+  if (!grid_barrier(P, gen)) return;
+  for (int i = i0; i < n; i += stride) dem_nbr(P, i);
+  for (int i = i0; i < n; i += stride) dem_position(P, i);
+  if (!grid_barrier(P, gen)) return;
   const double* Xc = P.p.x;
   const double* Uc = P.p.u;
   const float4* XFc = reinterpret_cast<const float4*>(P.p.xf);
@@ -332,17 +357,46 @@ int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
     double* Xn = to2 ? P.p.x2 : P.p.x;
     double* Un = to2 ? P.p.u2 : P.p.u;
     float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
-    dem_substep_kernel<<<gp, tb, 0, s>>>(P, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
-    ++launches;
+    for (int i = i0; i < n; i += stride)
+      dem_substep(P, i, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+    if (!grid_barrier(P, gen)) return;
     Xc = Xn;
     Uc = Un;
     XFc = XFn;
   }
-  if (subcycles % 2 == 1) {
-    dem_copy_back_kernel<<<gp, tb, 0, s>>>(P, Xc, Uc, XFc);
-    ++launches;
-  }
-  return launches;
+  if (subcycles % 2 == 1)
+    for (int i = i0; i < n; i += stride) dem_copy_back(P, i, Xc, Uc, XFc);
+}
+
+}  // namespace
+
+int dem_max_blocks() {
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dem_step_kernel, DEM_THREADS, 0) !=
+          cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return per_sm * nsm;
+}
+
+int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {
+  const int n = P.p.n;
+  if (n == 0) return 0;
+  int blocks = (n + DEM_THREADS - 1) / DEM_THREADS;
+  if (blocks > P.max_blocks) blocks = P.max_blocks;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(DEM_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, dem_step_kernel, P, subcycles);
+  return 1;
 }
 
 }  // namespace psm

@@ -60,6 +60,8 @@ struct psm_ctx {
   int* dem_items = nullptr;      // bin_items, pbin, nbr_cnt (3 * n)
   int* dem_nbr = nullptr;        // n * kDemListCap
   float4* dem_xbuild = nullptr;  // n
+  unsigned* dem_bar = nullptr;   // grid barrier of the DEM step kernel
+  int dem_blocks = 0;            // resident blocks of the DEM step kernel
   float* mlp = nullptr;   // FP32 parameters on the device
   bool have_mlp = false;
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
@@ -268,6 +270,8 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
     D.nbr_cnt = c->dem_items + 2 * c->p.n;
     D.nbr = c->dem_nbr;
     D.xbuild = c->dem_xbuild;
+    D.bar = c->dem_bar;
+    D.max_blocks = c->dem_blocks;
     n += launch_dem_step(D, c->opt.dem_subcycles, s);
   }
   if (c->timing) cudaEventRecord(c->ev[4], s);
@@ -430,8 +434,9 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->partials = alloc_n<double>(c, MAP_PARTIALS * 4, c->allocs);
   c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
   c->mlp_count = alloc_n<int>(c, 1, c->allocs);
+  c->dem_bar = alloc_n<unsigned>(c, 2, c->allocs);
   if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
-      !c->status || !c->partials || !c->mlp || !c->mlp_count)
+      !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar)
     return bail(PSM_ERR_OOM, "allocator returned NULL");
   cudaStream_t s = c->stream;
   bool ok = true;
@@ -439,6 +444,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     ok = ok && cudaMemsetAsync(c->buf[b], 0, esz * Q * (size_t)ncell, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.mask, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->dem_bar, 0, 2 * sizeof(unsigned), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.ncov, 0, sizeof(int), s) == cudaSuccess;
   StepConst h{};
   h.ncells = (double)g.nx * g.ny * g.nz;
@@ -452,6 +458,11 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   if (lbm_configure() != 0) {
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "could not set the shared-memory size of the collision kernel");
+  }
+  c->dem_blocks = dem_max_blocks();
+  if (c->dem_blocks <= 0) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "occupancy query of the DEM kernel failed");
   }
   if (lbm_plan(g, c->fp32, c->aa, &c->plan) != 0) {
     cudaGetLastError();
@@ -619,6 +630,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->need_map = true;
   c->error_state = false;
   CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(c->dem_bar, 0, 2 * sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
   return PSM_OK;
 }

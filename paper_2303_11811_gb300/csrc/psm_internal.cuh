@@ -241,7 +241,10 @@ struct DemParams {
   int* nbr;           // n*K, candidate partners in ascending order
   int* nbr_cnt;       // n
   float4* xbuild;     // n, positions when the lists were built
+  unsigned* bar;      // grid barrier of the step kernel: arrival count, generation
+  int max_blocks;     // blocks that can be resident at once (cooperative launch)
 };
+int dem_max_blocks();
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
 
 // MLP
