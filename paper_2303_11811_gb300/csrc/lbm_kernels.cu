@@ -170,7 +170,7 @@ size_t lbm_smem_bytes() {
 template <typename T>
 __device__ __forceinline__ void slot_force(const LbmParams& P, int e, int sl, T Bi, T dux, T duy,
                                            T duz, const T* f) {
-  T* o = static_cast<T*>(P.slot_Fc) + 6LL * e + 3 * sl;
+  T* o = static_cast<T*>(P.slot_Fc) + 3 * ((long long)sl * P.slot_cap + e);
   o[0] = Bi * (dux - f[0]);
   o[1] = Bi * (duy - f[1]);
   o[2] = Bi * (duz - f[2]);
@@ -184,20 +184,21 @@ template <typename T>
 __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, int lane, bool live,
                                             T* d, SolidSmem<T>* solid, uint32_t m, int eb) {
   // ---- coverage of this cell (m: coverage word, eb: slot of its first
-  // covered cell).  A slot holds, per particle, the surface velocity at the
-  // cell centre (Eq. 20) and the weight B_i, both written by the mapping; the
-  // loads depend only on the slot index and are issued together.
+  // covered cell).  A slot record holds the particle's surface velocity at
+  // the cell centre (Eq. 20) and the weight B_i, both written by the mapping;
+  // the sign of slot 0's weight tells whether a second particle shares the
+  // cell, whose record is read only then.
   bool cov = live && ((m >> lane) & 1u);
+  bool has1 = false;
   int e = 0;
-  int2 pid = make_int2(-1, -1);
   T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
   if (cov) {
     e = eb + __popc(m & ((1u << lane) - 1u));
     if (e < P.slot_cap) {
-      pid = __ldg(&P.slot_pid[e]);
-      const T* R = static_cast<const T*>(P.slot_V) + 8LL * e;
-      ld4(R, r0);
-      ld4(R + 4, r1);
+      ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
+      has1 = signbit(r0[3]);
+      r0[3] = fabs(r0[3]);
+      if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
     } else {
       cov = false;
     }
@@ -260,8 +261,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   if (sizeof(T) == 4 && cov) {
 #pragma unroll 1
     for (int sl = 0; sl < 2; ++sl) {
-      const int p = sl ? pid.y : pid.x;
-      if (p < 0) continue;
+      if (sl && !has1) continue;
       const T Vx = sl ? r1[0] : r0[0], Vy = sl ? r1[1] : r0[1], Vz = sl ? r1[2] : r0[2];
       const T Bi = sl ? r1[3] : r0[3];
       const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
@@ -282,11 +282,11 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   }
   if (sizeof(T) == 8 && m != 0u) {
     SolidSmem<T>& S = *solid;
-    const bool has0 = cov && pid.x >= 0, has1 = cov && pid.y >= 0;
+    const bool has0 = cov, hs1 = cov && has1;
     const unsigned b0 = __ballot_sync(0xffffffffu, has0);
-    const unsigned b1 = __ballot_sync(0xffffffffu, has1);
+    const unsigned b1 = __ballot_sync(0xffffffffu, hs1);
     const unsigned below = (1u << lane) - 1u;
-    if (has0 || has1) {
+    if (has0) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         S.cu[lane][k] = cdot<T>(k, Ux, Uy, Uz);
@@ -302,7 +302,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
       const unsigned bs = sl ? b1 : b0;
       if (bs == 0u) continue;
       const int Js = __popc(bs);
-      if (sl ? has1 : has0) {
+      if (sl ? hs1 : has0) {
         // job set-up by the owner lane: the per-job constants of the item
         // arithmetic and the slot's force (Eq. 21)
         const int jj = __popc(bs & below);
@@ -340,7 +340,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
       }
       __syncwarp();
     }
-    if (has0 || has1) {
+    if (has0) {
 #pragma unroll
       for (int q = 1; q < Q; ++q) d[q] = S.dd[lane][q - 1];
     }

@@ -406,10 +406,11 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
     const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
     const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
     const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
+    const long long rec = s * P.s.cap + e;  // slot s's record array
     if (P.fp32) {
-      static_cast<float4*>(P.s.V)[2 * e + s] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+      static_cast<float4*>(P.s.V)[rec] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
     } else {
-      double2* R = static_cast<double2*>(P.s.V) + 4 * e + 2 * s;
+      double2* R = static_cast<double2*>(P.s.V) + 2 * rec;
       R[0] = make_double2(v0, v1);
       R[1] = make_double2(v2, 0.0);
     }
@@ -504,22 +505,30 @@ __global__ void finish_kernel(MapParams P) {
     store_B(P, e, 1, B1);
     accB += B;
     // slot records (surface velocity from the fill pass): in slot order,
-    // with the final weights
+    // with the final weights; slot 0's weight carries a negative sign when a
+    // second particle shares the cell (-0.0 for a zero weight)
+    const bool two = pid.y >= 0;
+    const long long e1 = P.s.cap + e;
     if (P.fp32) {
-      float4* R = static_cast<float4*>(P.s.V) + 2 * e;
-      float4 r0 = R[0], r1 = R[1];
+      float4* R = static_cast<float4*>(P.s.V);
+      float4 r0 = R[e], r1 = two ? R[e1] : make_float4(0.f, 0.f, 0.f, 0.f);
       if (swapped) {
         const float4 t = r0;
         r0 = r1;
         r1 = t;
       }
-      r0.w = (float)B0;
+      r0.w = two ? -(float)B0 : (float)B0;
       r1.w = (float)B1;
-      R[0] = r0;
-      R[1] = r1;
+      R[e] = r0;
+      if (two) R[e1] = r1;
     } else {
-      double2* R = static_cast<double2*>(P.s.V) + 4 * e;
-      double2 a0 = R[0], a1 = R[1], c0 = R[2], c1 = R[3];
+      double2* R = static_cast<double2*>(P.s.V);
+      double2 a0 = R[2 * e], a1 = R[2 * e + 1];
+      double2 c0 = make_double2(0.0, 0.0), c1 = make_double2(0.0, 0.0);
+      if (two) {
+        c0 = R[2 * e1];
+        c1 = R[2 * e1 + 1];
+      }
       if (swapped) {
         double2 t = a0;
         a0 = c0;
@@ -528,12 +537,14 @@ __global__ void finish_kernel(MapParams P) {
         a1 = c1;
         c1 = t;
       }
-      a1.y = B0;
+      a1.y = two ? -B0 : B0;
       c1.y = B1;
-      R[0] = a0;
-      R[1] = a1;
-      R[2] = c0;
-      R[3] = c1;
+      R[2 * e] = a0;
+      R[2 * e + 1] = a1;
+      if (two) {
+        R[2 * e1] = c0;
+        R[2 * e1 + 1] = c1;
+      }
     }
   }
   red[threadIdx.x] = accB;
@@ -583,9 +594,10 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
     const double dx = image_d(x, xp0, P.g.nx, !P.g.wall[0]);
     const double dy = image_d(y, xp1, P.g.ny, !P.g.wall[1]);
     const double dz = image_d(z, xp2, P.g.nz, !P.g.wall[2]);
-    const double f0 = (double)Fc[6LL * e + 3 * s];
-    const double f1 = (double)Fc[6LL * e + 3 * s + 1];
-    const double f2 = (double)Fc[6LL * e + 3 * s + 2];
+    const long long fo = 3 * (s * P.s.cap + e);
+    const double f0 = (double)Fc[fo];
+    const double f1 = (double)Fc[fo + 1];
+    const double f2 = (double)Fc[fo + 2];
     acc[0] += f0;
     acc[1] += f1;
     acc[2] += f2;
@@ -642,9 +654,10 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams
     const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
-    const float f0 = Fc[6LL * e + 3 * s];
-    const float f1 = Fc[6LL * e + 3 * s + 1];
-    const float f2 = Fc[6LL * e + 3 * s + 2];
+    const long long fo = 3 * (s * P.s.cap + e);
+    const float f0 = Fc[fo];
+    const float f1 = Fc[fo + 1];
+    const float f2 = Fc[fo + 2];
     acc[0].add(f0);
     acc[1].add(f1);
     acc[2].add(f2);

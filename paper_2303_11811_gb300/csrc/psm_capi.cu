@@ -227,8 +227,6 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   if (c->p.n > 0) {
     L.mask = c->cov.mask;
     L.base = c->cov.base;
-    L.slot_pid = c->slots.pid;
-    L.slot_B = c->slots.B;
     L.slot_Fc = c->slots.Fc;
     L.slot_V = c->slots.V;
     L.slot_cap = c->slots.cap;

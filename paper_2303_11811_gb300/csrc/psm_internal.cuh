@@ -127,9 +127,10 @@ struct Slots {
   int2* pid;
   void* B;        // T2
   int* cnt;
-  void* Fc;       // T[6] per entry
-  // T[8] per entry: for slots 0 and 1 the particle's surface velocity at the
-  // cell centre (Eq. 20) and the slot's normalised weight B_i
+  void* Fc;       // slot s's force of entry e at T[3 (s cap + e)]
+  // slot s's record of entry e at T[4 (s cap + e)]: the particle's surface
+  // velocity at the cell centre (Eq. 20) and the slot's normalised weight
+  // B_i, negated in slot 0 when the cell has a second particle
   void* V;
   long long cap;
 };
@@ -180,10 +181,8 @@ struct LbmParams {
   void* dstq[19];
   const uint32_t* mask; // nullptr when there are no particles
   const int* base;
-  const int2* slot_pid;
-  const void* slot_B;   // T2
-  void* slot_Fc;        // T[6] per entry
-  const void* slot_V;   // T[8] per entry (Slots::V)
+  void* slot_Fc;        // Slots::Fc
+  const void* slot_V;   // Slots::V
   long long slot_cap;   // entries allocated
   const StepConst* sc;
   double omega_p, omega_m;
