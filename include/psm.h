@@ -157,6 +157,20 @@ psm_status psm_get_particles(psm_ctx* ctx, double* x, double* u, double* omega);
  * in the canonical layout above, whatever the storage precision/pattern. */
 psm_status psm_get_pdfs(psm_ctx* ctx, double* f);
 
+/* The same for a box of bx*by*bz cells with origin (x0, y0, z0): 19*bx*by*bz
+ * FP64 values, layout f[q][z][y][x] over the box.  Along a periodic axis the
+ * box wraps around (origin in [-n, 2n)); along an axis with walls it must lie
+ * inside the grid.  PSM_ERR_ARG otherwise. */
+psm_status psm_get_pdfs_box(psm_ctx* ctx, int x0, int y0, int z0, int bx, int by, int bz,
+                            double* f);
+
+/* Fluid force density applied in the last step (3 values): the body force
+ * plus, with gravity and free particles, the counter force
+ * -sum_i (m_i - V_i) g / V_fluid that keeps the periodic system from
+ * accelerating (buoyancy-corrected gravity, Sec. 2.2), and V_fluid =
+ * sum_x (1 - B) from the mapping it used (vfluid may be NULL). */
+psm_status psm_get_fluid_force(psm_ctx* ctx, double* f, double* vfluid);
+
 /* Replaces the PDF field (canonical layout, 19*N FP64) and clears a device
  * error state. */
 psm_status psm_set_pdfs(psm_ctx* ctx, const double* f);

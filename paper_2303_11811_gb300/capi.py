@@ -32,6 +32,7 @@ EXPORTS = [
     "psm_default_options", "psm_create", "psm_set_particles", "psm_update_particles",
     "psm_step",
     "psm_get_force_torque", "psm_get_macroscopic", "psm_get_particles", "psm_get_pdfs",
+    "psm_get_pdfs_box", "psm_get_fluid_force",
     "psm_set_pdfs", "psm_get_slots", "psm_check", "psm_set_mlp", "psm_get_mlp",
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
     "psm_set_timing", "psm_get_timings", "psm_last_launch_count", "psm_last_error",
@@ -84,6 +85,10 @@ def lib():
     L.psm_update_particles.restype = st
     L.psm_step.argtypes = [P, C.c_int]
     L.psm_step.restype = st
+    L.psm_get_pdfs_box.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]
+    L.psm_get_pdfs_box.restype = st
+    L.psm_get_fluid_force.argtypes = [P, dp, C.POINTER(C.c_double)]
+    L.psm_get_fluid_force.restype = st
     for name in ("psm_get_force_torque",):
         getattr(L, name).argtypes = [P, dp, dp]
         getattr(L, name).restype = st
@@ -314,6 +319,20 @@ class Engine:
         f = np.empty(Q * self.N)
         self._check(self._L.psm_get_pdfs(self.h, _dp(f)))
         return f.reshape((Q,) + self.shape)
+
+    def pdfs_box(self, x0, y0, z0, bx, by, bz):
+        """Post-collision PDFs of a box of cells, shape (19, bz, by, bx)."""
+        f = np.empty(Q * bx * by * bz)
+        self._check(self._L.psm_get_pdfs_box(self.h, int(x0), int(y0), int(z0), int(bx),
+                                             int(by), int(bz), _dp(f)))
+        return f.reshape((Q, bz, by, bx))
+
+    def fluid_force(self):
+        """(fluid force density of the last step (3,), fluid volume)."""
+        f = np.empty(3)
+        v = C.c_double(0.0)
+        self._check(self._L.psm_get_fluid_force(self.h, _dp(f), C.byref(v)))
+        return f, v.value
 
     def set_pdfs(self, f):
         f = _f64(f, Q * self.N)

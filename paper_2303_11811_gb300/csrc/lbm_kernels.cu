@@ -630,13 +630,13 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
 // canonical FP64 f~ (unpadded, full f = w + delta) from the storage layout
 template <typename T>
 __global__ void to_canonical_kernel(Grid g, const T* __restrict__ buf, int aa, int parity,
-                                    double* __restrict__ out) {
-  const long long N = (long long)g.nx * g.ny * g.nz;
+                                    BoxSel B, double* __restrict__ out) {
+  const long long N = (long long)B.bx * B.by * B.bz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % g.nx);
-    const int y = (int)((c / g.nx) % g.ny);
-    const int z = (int)(c / ((long long)g.nx * g.ny));
+    const int x = (int)((B.x0 + c % B.bx) % g.nx);
+    const int y = (int)((B.y0 + (c / B.bx) % B.by) % g.ny);
+    const int z = (int)((B.z0 + c / ((long long)B.bx * B.by)) % g.nz);
     Nbr nb;
     nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
     const int cell = nb.idx(0, 0, 0);
@@ -898,14 +898,14 @@ static unsigned grid_for(long long n, int block) {
 }
 
 int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
-                        double* out, cudaStream_t s) {
-  const long long N = (long long)g.nx * g.ny * g.nz;
+                        const BoxSel& B, double* out, cudaStream_t s) {
+  const long long N = (long long)B.bx * B.by * B.bz;
   if (fp32)
     to_canonical_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
-        g, static_cast<const float*>(buf), aa, aa_parity, out);
+        g, static_cast<const float*>(buf), aa, aa_parity, B, out);
   else
     to_canonical_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
-        g, static_cast<const double*>(buf), aa, aa_parity, out);
+        g, static_cast<const double*>(buf), aa, aa_parity, B, out);
   return 1;
 }
 

@@ -334,11 +334,12 @@ psm_status read_status(psm_ctx* c) {
   return PSM_OK;
 }
 
-psm_status canonical(psm_ctx* c, double** out) {
-  const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
+psm_status canonical(psm_ctx* c, double** out, const BoxSel* box = nullptr) {
+  const BoxSel B = box ? *box : BoxSel{0, 0, 0, c->g.nx, c->g.ny, c->g.nz};
+  const size_t N = (size_t)B.bx * B.by * B.bz;
   double* f = static_cast<double*>(dalloc(c, sizeof(double) * Q * N));
   if (!f) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
-  launch_to_canonical(c->g, c->aa ? c->buf[0] : c->buf[c->cur], c->fp32, c->parity, c->aa, f,
+  launch_to_canonical(c->g, c->aa ? c->buf[0] : c->buf[c->cur], c->fp32, c->parity, c->aa, B, f,
                       c->stream);
   *out = f;
   CK(cudaGetLastError());
@@ -706,6 +707,38 @@ psm_status psm_get_pdfs(psm_ctx* c, double* f) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   dfree(c, d);
   if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_get_pdfs_box(psm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz,
+                            double* f) {
+  if (!c || !f) return PSM_ERR_ARG;
+  const int n[3] = {c->g.nx, c->g.ny, c->g.nz};
+  const int o[3] = {x0, y0, z0}, b[3] = {bx, by, bz};
+  for (int a = 0; a < 3; ++a) {
+    if (b[a] < 1 || b[a] > n[a]) return fail(c, PSM_ERR_ARG, "box extent outside 1..n");
+    if (c->g.wall[a] ? (o[a] < 0 || o[a] + b[a] > n[a]) : (o[a] < -n[a] || o[a] >= 2 * n[a]))
+      return fail(c, PSM_ERR_ARG, "box origin outside the grid");
+  }
+  BoxSel B{(x0 + n[0]) % n[0], (y0 + n[1]) % n[1], (z0 + n[2]) % n[2], bx, by, bz};
+  double* d = nullptr;
+  psm_status st = canonical(c, &d, &B);
+  if (st != PSM_OK) return st;
+  const size_t N = (size_t)bx * by * bz;
+  cudaError_t e = cudaMemcpyAsync(f, d, sizeof(double) * Q * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  dfree(c, d);
+  if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));
+  return PSM_OK;
+}
+
+psm_status psm_get_fluid_force(psm_ctx* c, double* f, double* vfluid) {
+  if (!c || !f) return PSM_ERR_ARG;
+  StepConst h;
+  CK(cudaMemcpyAsync(&h, c->sc, sizeof(StepConst), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int a = 0; a < 3; ++a) f[a] = h.fext[a];
+  if (vfluid) *vfluid = h.vfluid;
   return PSM_OK;
 }
 

@@ -203,8 +203,13 @@ int lbm_configure();  // kernel attributes; call once before launching (returns 
 // staged-kernel plan for a grid (stages = 0: use the one-cell-per-thread kernel)
 int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan);
 int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s);
+// a box of cells, origin (x0, y0, z0) (non-negative, taken modulo the grid) and
+// extent (bx, by, bz); output layout [q][z][y][x] over the box
+struct BoxSel {
+  int x0, y0, z0, bx, by, bz;
+};
 int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
-                        double* out, cudaStream_t s);
+                        const BoxSel& B, double* out, cudaStream_t s);
 int launch_from_canonical(const Grid& g, const double* in, void* buf, int fp32, int aa,
                           cudaStream_t s);
 int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,

@@ -62,37 +62,58 @@ def rsa_spheres(dims, walls, radii, gap, seed, max_tries=100000):
     ``radii`` is the list of radii in placement order; each sphere is drawn
     uniformly in the box (kept r away from wall faces) and accepted when its
     surface is at least ``gap`` from every sphere already placed (nearest image
-    along periodic axes).  Returns centres (n x 3).
+    along periodic axes).  Returns centres (n x 3).  The candidates come from
+    one generator stream, three uniforms per try; the overlap test runs on
+    plain floats over a bucket grid of edge >= 2 r_max + gap.
     """
     rng = np.random.default_rng(seed)
-    dims = np.asarray(dims, dtype=np.float64)
-    per = np.array([not walls[0], not walls[2], not walls[4]])
+    dims = [float(v) for v in dims]
+    per = [not walls[0], not walls[2], not walls[4]]
     radii = np.asarray(radii, dtype=np.float64)
     rmax = float(radii.max()) if radii.size else 1.0
     h = 2.0 * rmax + gap
-    ncell = np.maximum(1, np.floor(dims / h).astype(int))
-    csize = dims / ncell
+    ncell = [max(1, int(np.floor(dims[a] / h))) for a in range(3)]
+    csize = [dims[a] / ncell[a] for a in range(3)]
+    half = [0.5 * dims[a] for a in range(3)]
+    # neighbour buckets per axis offset, wrapped or clipped, without repeats
+    def around(c, a):
+        out = []
+        for o in (-1, 0, 1):
+            k = c + o
+            if k < 0 or k >= ncell[a]:
+                if not per[a]:
+                    continue
+                k %= ncell[a]
+            if k not in out:
+                out.append(k)
+        return out
     grid: dict = {}
+    pos = []          # accepted centres as float triples
     out = np.zeros((radii.size, 3))
-    for i, r in enumerate(radii):
-        lo = np.where(per, 0.0, r)
-        hi = np.where(per, dims, dims - r)
+    for i, r in enumerate(radii.tolist()):
+        lo = [0.0 if per[a] else r for a in range(3)]
+        hi = [dims[a] if per[a] else dims[a] - r for a in range(3)]
         for _ in range(max_tries):
-            p = lo + (hi - lo) * rng.random(3)
-            c = np.minimum((p // csize).astype(int), ncell - 1)
+            u = rng.random(3)
+            p = [lo[a] + (hi[a] - lo[a]) * float(u[a]) for a in range(3)]
+            c = [min(int(p[a] // csize[a]), ncell[a] - 1) for a in range(3)]
             ok = True
-            for dz in (-1, 0, 1):
-                for dy in (-1, 0, 1):
-                    for dx in (-1, 0, 1):
-                        k = c + (dx, dy, dz)
-                        if np.any((~per) & ((k < 0) | (k >= ncell))):
-                            continue
-                        k = tuple(np.mod(k, ncell))
-                        for j in grid.get(k, ()):
-                            d = p - out[j]
-                            d = np.where(per & (d > 0.5 * dims), d - dims, d)
-                            d = np.where(per & (d < -0.5 * dims), d + dims, d)
-                            if d @ d < (r + radii[j] + gap) ** 2:
+            for kz in around(c[2], 2):
+                for ky in around(c[1], 1):
+                    for kx in around(c[0], 0):
+                        for j in grid.get((kx, ky, kz), ()):
+                            q = pos[j]
+                            d2 = 0.0
+                            for a in range(3):
+                                d = p[a] - q[a]
+                                if per[a]:
+                                    if d > half[a]:
+                                        d -= dims[a]
+                                    elif d < -half[a]:
+                                        d += dims[a]
+                                d2 += d * d
+                            s = r + radii[j] + gap
+                            if d2 < s * s:
                                 ok = False
                                 break
                         if not ok:
@@ -103,6 +124,7 @@ def rsa_spheres(dims, walls, radii, gap, seed, max_tries=100000):
                     break
             if ok:
                 out[i] = p
+                pos.append(p)
                 grid.setdefault(tuple(c), []).append(i)
                 break
         else:
