@@ -39,6 +39,10 @@ WORKLOADS = {
                   "gap>=1, seed 20230321), density ratio 2.5, gravity 2e-5 in -z, D3Q19 TRT "
                   "(Lambda=3/16) tau=0.55, 4^3 sub-division sampling, Noble-Torczynski B, "
                   "spring-dashpot DEM k_n=1e3 e=0.9 x10 sub-cycles"),
+    "settle512": ("settle512: 512x512x1024 periodic box (268M cells), 94,692 spheres r in [3,6] "
+                  "(random sequential addition, solid fraction 0.15, seed 20230321), density "
+                  "ratio 2.5, gravity 2e-5 in -z, D3Q19 TRT (Lambda=3/16) tau=0.55, 4^3 "
+                  "sub-division sampling, Noble-Torczynski B, spring-dashpot DEM x10 sub-cycles"),
     "channel": ("channel: 256x256x512, walls at the x faces, 12,817 fixed spheres r=5 (random "
                 "sequential addition, solid fraction 0.20, seed 20230321), D3Q19 TRT "
                 "(Lambda=3/16) tau=0.55, body force 1e-5 along z, 4^3 sub-division sampling, "
@@ -237,6 +241,7 @@ def forms_comparison(capi, torch, steps, seed=20230321):
     trainer.close()
     out["surrogate_training"] = {"samples": 1 << 21, "epochs": 10, "batch": 1024,
                                  "final_mse": loss, "seconds": time.perf_counter() - t0}
+    out["_params"] = params
     hbm, _ = peaks()
     res = {}
     for name, prec, stream, mode, n in FORMS:
@@ -287,6 +292,62 @@ def forms_comparison(capi, torch, steps, seed=20230321):
     return out
 
 
+SETTLE_FORMS = (
+    ("fp64_8cubed", "fp64", "pull", "supersample"),
+    ("fp32_8cubed_aa", "fp32", "aa", "supersample"),
+    ("fp32_mlp_aa", "fp32", "aa", "mlp"),
+)
+
+
+def forms_settling(capi, torch, params, steps):
+    """The moving-particle form of the metric on the 512x512x1024 periodic box
+    (268M cells, 94,692 spheres r in [3, 6] at solid fraction 0.15, density
+    ratio 2.5, gravity, DEM): the plain FP64 method (8^3 sampling, pull)
+    beside FP32 AA storage with 8^3 sampling and with the trained surrogate.
+    The spheres move, so the mapping runs every step and the surrogate's
+    mapping time counts per step.  The flow is chaotic: the forms are compared
+    on the mean settling velocity and the mean drag over all spheres after
+    the same number of steps from rest."""
+    from paper_2303_11811_gb300 import inputs
+    w = inputs.settle512()
+    w.eps_n = 8
+    n = w.particles["r"].size
+    out = {"workload": "settle512: 512x512x1024 periodic, %d spheres r in [3,6] (solid "
+           "fraction 0.15), density ratio 2.5, gravity 2e-5 in -z, TRT tau=0.55, DEM" % n,
+           "steps": steps}
+    m = w.particles["density"] * 4.0 / 3.0 * math.pi * w.particles["r"] ** 3
+    res = {}
+    for name, prec, stream, mode in SETTLE_FORMS:
+        e = make_engine(w, capi, precision=prec, streaming=stream, eps_mode=mode)
+        if mode == "mlp":
+            e.set_mlp(params)
+        e.step(2)
+        ms = timed_steps(e, torch, steps)
+        e.set_timing(True)
+        e.step(3)
+        t = e.timings()
+        e.set_timing(False)
+        _, u, _ = e.particles()
+        F, _ = e.force_torque()
+        r = {"mlups": w.cells * steps / (ms * 1e-3) / 1e6, "ms_per_step": ms / steps,
+             "mapping_ms_per_step": t[0] / t[4], "collide_ms": t[1] / t[4],
+             "mean_settling_velocity": float(np.sum(m * u[:, 2]) / np.sum(m)),
+             "mean_drag_z": float(np.mean(F[:, 2]))}
+        res[name] = r
+        e.close()
+        torch.cuda.empty_cache()
+    ref = res["fp64_8cubed"]
+    for name, _, _, _ in SETTLE_FORMS:
+        r = res[name]
+        if name != "fp64_8cubed":
+            r["speedup_vs_fp64"] = r["mlups"] / ref["mlups"]
+            r["settling_velocity_rel_diff"] = abs(r["mean_settling_velocity"] /
+                                                  ref["mean_settling_velocity"] - 1.0)
+            r["mean_drag_rel_diff"] = abs(r["mean_drag_z"] / ref["mean_drag_z"] - 1.0)
+        out[name] = r
+    return out
+
+
 def describe(args):
     prec = {"fp64": "FP64 PDFs", "fp32": "FP32 deviation PDFs"}[args.precision]
     return f"{WORKLOADS[args.workload]}, {prec}, {args.streaming} streaming"
@@ -294,7 +355,8 @@ def describe(args):
 
 def make_workload(name):
     from paper_2303_11811_gb300 import inputs
-    return inputs.settle128() if name == "settle128" else inputs.channel()
+    return {"settle128": inputs.settle128, "channel": inputs.channel,
+            "settle512": inputs.settle512}[name]()
 
 
 def main():
@@ -432,6 +494,7 @@ def main():
     forms = None
     if default_run and not args.no_forms and rank == 0:
         forms = forms_comparison(capi, torch, max(50, min(args.steps, 300)))
+        forms["settling"] = forms_settling(capi, torch, forms.pop("_params"), 20)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

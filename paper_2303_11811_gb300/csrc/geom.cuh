@@ -63,16 +63,17 @@ __device__ inline int supersample_count_fast(double dx, double dy, double dz, do
 // unrolled loop counts the samples certainly inside (S < lo) and those not
 // certainly outside (S <= hi); when the counts agree no sample lies in the
 // band, otherwise the cell is recounted with the FP64 test inside the band.
+// dxf, dyf, dzf: the FP32 roundings of dx, dy, dz; r2f = (float)(r * r);
+// E = certified_band(r) (callers with many cells of one sphere form them once)
 template <int N>
-__device__ inline int supersample_count_n(double dx, double dy, double dz, double r) {
-  const float E = certified_band(r);
-  const float r2f = (float)(r * r);
+__device__ inline int supersample_count_n(double dx, double dy, double dz, double r, float dxf,
+                                          float dyf, float dzf, float r2f, float E) {
   const float lo = r2f - E, hi = r2f + E;
   float X[N], Y[N], Z[N];
 #pragma unroll
   for (int a = 0; a < N; ++a) {
     const float s = (float)((a + 0.5) / N - 0.5);
-    const float px = (float)dx + s, py = (float)dy + s, pz = (float)dz + s;
+    const float px = dxf + s, py = dyf + s, pz = dzf + s;
     X[a] = px * px;
     Y[a] = py * py;
     Z[a] = pz * pz;
@@ -99,6 +100,12 @@ __device__ inline int supersample_count_n(double dx, double dy, double dz, doubl
     s32[a] = (float)s64[a];
   }
   return supersample_count_fast(dx, dy, dz, r, N, s64, s32);
+}
+
+template <int N>
+__device__ inline int supersample_count_n(double dx, double dy, double dz, double r) {
+  return supersample_count_n<N>(dx, dy, dz, r, (float)dx, (float)dy, (float)dz, (float)(r * r),
+                                certified_band(r));
 }
 
 // FP64 definition, all samples (reference for small counts and tests)

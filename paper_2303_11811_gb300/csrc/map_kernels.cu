@@ -38,6 +38,8 @@ struct Box {
   double r;
   double reach2;      // (r + sqrt(3)/2)^2 in FP64
   float reach2f, E;   // its FP32 value and the certified band of geom.cuh
+  float r2f;          // (float)(r * r)
+  FastDiv div_n0, div_nxy;  // box index t -> (kx, ky, kz)
 };
 
 __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, double r) {
@@ -59,20 +61,18 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
     b.fpf[a] = (float)(xp - fl);
   }
   b.count = b.n[0] * b.n[1] * b.n[2];
+  b.div_n0 = make_fastdiv((unsigned)(b.n[0] > 0 ? b.n[0] : 1));
+  b.div_nxy = make_fastdiv((unsigned)(b.n[0] * b.n[1] > 0 ? b.n[0] * b.n[1] : 1));
   b.r = r;
   const double reach = r + HALF_SQRT3;
   b.reach2 = reach * reach;
   b.reach2f = (float)b.reach2;
   b.E = certified_band(r);
+  b.r2f = (float)(r * r);
   const double rin = r - HALF_SQRT3;
   b.rin2 = rin > 0.0 ? rin * rin : -1.0;
   b.rin2f = (float)b.rin2;
   return b;
-}
-
-__device__ __forceinline__ int wrap(int k, int n) {
-  const int i = k % n;
-  return i < 0 ? i + n : i;
 }
 
 // nearest image of cell coordinate i relative to xp (integer shifted first)
@@ -93,23 +93,27 @@ struct CellHit {
   int kx, ky, kz;
   double dx, dy, dz, d2;
   float d2f;
+  float dxf, dyf, dzf;  // FP32 roundings of dx, dy, dz
 };
 
+// box coordinates lie within one period of the grid (the box is narrower
+// than half a periodic extent)
+__device__ __forceinline__ int wrap1(int k, int n) { return k < 0 ? k + n : (k >= n ? k - n : k); }
+
 __device__ __forceinline__ void box_coords(const Grid& g, const Box& b, int t, CellHit& h) {
-  const int nxy = b.n[0] * b.n[1];
-  const int kz = t / nxy;
-  const int rem = t - kz * nxy;
-  const int ky = rem / b.n[0];
+  const int kz = (int)b.div_nxy.div((unsigned)t);
+  const int rem = t - kz * (b.n[0] * b.n[1]);
+  const int ky = (int)b.div_n0.div((unsigned)rem);
   h.kx = b.lo[0] + (rem - ky * b.n[0]);
   h.ky = b.lo[1] + ky;
   h.kz = b.lo[2] + kz;
-  h.ix = wrap(h.kx, g.nx);
-  h.iy = wrap(h.ky, g.ny);
-  h.iz = wrap(h.kz, g.nz);
+  h.ix = wrap1(h.kx, g.nx);
+  h.iy = wrap1(h.ky, g.ny);
+  h.iz = wrap1(h.kz, g.nz);
 }
 
 // reach test of the FP64 definition, evaluated in FP32 outside the certified
-// band; fills the FP64 offsets and squared distance of a cell in reach
+// band (FP64 offsets only inside the band)
 __device__ __forceinline__ bool reach_test(const Box& b, CellHit& h) {
   const float dxf = (float)(h.kx - b.ip[0]) + (0.5f - b.fpf[0]);
   const float dyf = (float)(h.ky - b.ip[1]) + (0.5f - b.fpf[1]);
@@ -117,12 +121,11 @@ __device__ __forceinline__ bool reach_test(const Box& b, CellHit& h) {
   const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
   h.d2f = d2f;
   if (d2f > b.reach2f + b.E) return false;
-  h.dx = ((double)h.kx + 0.5) - b.xp[0];
-  h.dy = ((double)h.ky + 0.5) - b.xp[1];
-  h.dz = ((double)h.kz + 0.5) - b.xp[2];
-  h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
   if (d2f < b.reach2f - b.E) return true;
-  return h.d2 < b.reach2;
+  const double dx = ((double)h.kx + 0.5) - b.xp[0];
+  const double dy = ((double)h.ky + 0.5) - b.xp[1];
+  const double dz = ((double)h.kz + 0.5) - b.xp[2];
+  return dx * dx + dy * dy + dz * dz < b.reach2;
 }
 
 __device__ __forceinline__ long long padded_cell(const Grid& g, int x, int y, int z) {
@@ -179,13 +182,17 @@ __device__ __forceinline__ void load_offsets(int n, double* s64, float* s32) {
 __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   __shared__ int warp_tot[MAP_THREADS / 32];
   __shared__ int running;
+  __shared__ Box sbox;
   const int p = blockIdx.x;
-  const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const long long loff = P.list_off[p];
   const int lcap = (int)(P.list_off[p + 1] - loff);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) running = 0;
+  if (threadIdx.x == 0) {
+    running = 0;
+    sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);  // FP64 set-up once per block
+  }
   __syncthreads();
+  const Box b = sbox;
   for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
     const int t = t0 + threadIdx.x;
     CellHit h;
@@ -301,10 +308,11 @@ __device__ int cell_count(const MapParams& P, const Box& b, const CellHit& h, co
   const int n = P.eps_n;
   if (b.rin2 >= 0.0) {
     if (h.d2f < b.rin2f - b.E) return n * n * n;
-    if (h.d2f <= b.rin2f + b.E && h.d2 <= b.rin2) return n * n * n;
+    if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
+      return n * n * n;
   }
-  return n == 4   ? supersample_count_n<4>(h.dx, h.dy, h.dz, b.r)
-         : n == 8 ? supersample_count_n<8>(h.dx, h.dy, h.dz, b.r)
+  return n == 4   ? supersample_count_n<4>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f, b.E)
+         : n == 8 ? supersample_count_n<8>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f, b.E)
                   : supersample_count_fast(h.dx, h.dy, h.dz, b.r, n, s64, s32);
 }
 
@@ -345,6 +353,13 @@ __device__ __forceinline__ double count_eps(int cnt, int n3) {
 }
 
 constexpr int WTAB = 513;  // B of every sampled count up to 8^3
+constexpr int FILL_AXIS = 64;  // box extent per axis with offset tables (r < 30)
+
+// B of every sampled count (Eq. 16 of each eps = c / n^3), once per context
+__global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
+  for (int c = threadIdx.x; c <= n3; c += blockDim.x)
+    out[c] = weight(count_eps(c, n3), tau, weighting);
+}
 
 // Slots of one particle's cells (one block per particle, over the list the
 // mark pass wrote): claims a slot per cell, writes B (Eq. 16, from a table
@@ -354,16 +369,30 @@ constexpr int WTAB = 513;  // B of every sampled count up to 8^3
 __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
   __shared__ double s64[16];
   __shared__ float s32[16];
-  __shared__ double wtab[WTAB];
+  __shared__ Box sbox;
+  // per-axis offsets (k + 1/2) - x_p of the box columns, FP64 and their FP32
+  // roundings, formed once per block
+  __shared__ double toff[3][FILL_AXIS];
+  __shared__ float toff32[3][FILL_AXIS];
   const int p = blockIdx.x;
-  const Box b = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
+  if (threadIdx.x == 0) sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const double fr = P.p.fr[p];
-  const int n = P.eps_n, n3 = n * n * n;
-  const bool tab = P.eps_mode == 0 && n3 < WTAB;
-  if (tab)
-    for (int c = threadIdx.x; c <= n3; c += MAP_THREADS)
-      wtab[c] = weight(count_eps(c, n3), P.tau, P.weighting);
+  const bool tab = P.eps_mode == 0 && P.wtab != nullptr;
+  const double* wtab = P.wtab;
   load_offsets(P.eps_n, s64, s32);  // ends with __syncthreads
+  const Box b = sbox;
+  const bool tables = b.n[0] <= FILL_AXIS && b.n[1] <= FILL_AXIS && b.n[2] <= FILL_AXIS;
+  if (tables) {
+    for (int t = threadIdx.x; t < 3 * FILL_AXIS; t += MAP_THREADS) {
+      const int a = t / FILL_AXIS, k = t - a * FILL_AXIS;
+      if (k < b.n[a]) {
+        const double d = ((double)(b.lo[a] + k) + 0.5) - b.xp[a];
+        toff[a][k] = d;
+        toff32[a][k] = (float)d;
+      }
+    }
+  }
+  __syncthreads();
   const double u0 = P.p.u[3 * p], u1 = P.p.u[3 * p + 1], u2 = P.p.u[3 * p + 2];
   const double o0 = P.p.om[3 * p], o1 = P.p.om[3 * p + 1], o2 = P.p.om[3 * p + 2];
   const long long loff = P.list_off[p];
@@ -371,14 +400,26 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
   for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
     CellHit h;
     box_coords(P.g, b, P.list[loff + k], h);
-    const float dxf = (float)(h.kx - b.ip[0]) + (0.5f - b.fpf[0]);
-    const float dyf = (float)(h.ky - b.ip[1]) + (0.5f - b.fpf[1]);
-    const float dzf = (float)(h.kz - b.ip[2]) + (0.5f - b.fpf[2]);
-    h.d2f = dxf * dxf + dyf * dyf + dzf * dzf;
-    h.dx = ((double)h.kx + 0.5) - b.xp[0];
-    h.dy = ((double)h.ky + 0.5) - b.xp[1];
-    h.dz = ((double)h.kz + 0.5) - b.xp[2];
-    h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
+    if (tables) {
+      const int i0 = h.kx - b.lo[0], i1 = h.ky - b.lo[1], i2 = h.kz - b.lo[2];
+      h.dx = toff[0][i0];
+      h.dy = toff[1][i1];
+      h.dz = toff[2][i2];
+      h.dxf = toff32[0][i0];
+      h.dyf = toff32[1][i1];
+      h.dzf = toff32[2][i2];
+    } else {
+      h.dx = ((double)h.kx + 0.5) - b.xp[0];
+      h.dy = ((double)h.ky + 0.5) - b.xp[1];
+      h.dz = ((double)h.kz + 0.5) - b.xp[2];
+      h.dxf = (float)h.dx;
+      h.dyf = (float)h.dy;
+      h.dzf = (float)h.dz;
+    }
+    // FP32 squared distance of the inside test (its band is certified for
+    // the components rounded from FP64 as well as for the box-local form)
+    h.d2f = h.dxf * h.dxf + h.dyf * h.dyf + h.dzf * h.dzf;
+    h.d2 = -1.0;  // formed where a decision needs it
     const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
     const long long e = slot_index(P.cov, cell);
     if (e >= P.s.cap) {
@@ -386,7 +427,7 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
       continue;
     }
     P.list[loff + k] = (int)e;
-    if (P.fp32) P.listf[loff + k] = make_float4((float)h.dx, (float)h.dy, (float)h.dz, 0.f);
+    if (P.fp32) P.listf[loff + k] = make_float4(h.dxf, h.dyf, h.dzf, 0.f);
     const int s = atomicAdd(&P.s.cnt[e], 1);
     if (s >= 2) {
       atomicOr(P.status, ST_SLOT_OVERFLOW);
@@ -397,19 +438,25 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
     double B;
     if (tab) {
       const int c = cell_count(P, b, h, s64, s32);
-      B = wtab[c];
+      B = __ldg(&wtab[c]);
     } else {
+      h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
       const double eps = cell_eps(P, b, h, fr, s64, s32);
       B = eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting);
     }
     store_B(P, e, s, B);
-    const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
-    const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
-    const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
     const long long rec = s * P.s.cap + e;  // slot s's record array
     if (P.fp32) {
-      static_cast<float4*>(P.s.V)[rec] = make_float4((float)v0, (float)v1, (float)v2, 0.f);
+      // the FP32 collision takes the surface velocity in FP32
+      const float fx = h.dxf, fy = h.dyf, fz = h.dzf;
+      const float f0 = (float)o0, f1 = (float)o1, f2 = (float)o2;
+      static_cast<float4*>(P.s.V)[rec] =
+          make_float4((float)u0 + (f1 * fz - f2 * fy), (float)u1 + (f2 * fx - f0 * fz),
+                      (float)u2 + (f0 * fy - f1 * fx), 0.f);
     } else {
+      const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
+      const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
+      const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
       double2* R = static_cast<double2*>(P.s.V) + 2 * rec;
       R[0] = make_double2(v0, v1);
       R[1] = make_double2(v2, 0.0);
@@ -787,6 +834,13 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
     launches += 2;
   }
   return launches + map_finish(P, s);
+}
+
+int launch_weight_table(int n, double tau, int weighting, double* out, cudaStream_t s) {
+  const int n3 = n * n * n;
+  if (n3 >= WTAB) return 0;
+  wtab_kernel<<<1, 256, 0, s>>>(n3, tau, weighting, out);
+  return 1;
 }
 
 int launch_force_reduce(MapParams P, cudaStream_t s) {

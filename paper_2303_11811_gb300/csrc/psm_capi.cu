@@ -60,6 +60,8 @@ struct psm_ctx {
   int* dem_items = nullptr;      // bin_items, pbin, nbr_cnt (3 * n)
   int* dem_nbr = nullptr;        // n * kDemListCap
   float4* dem_xbuild = nullptr;  // n
+  double* wtab = nullptr;        // B of the sampled counts (eps_n^3 < 513)
+  bool have_wtab = false;
   unsigned* dem_bar = nullptr;   // grid barrier of the DEM step kernel
   int dem_blocks = 0;            // resident blocks of the DEM step kernel
   float* mlp = nullptr;   // FP32 parameters on the device
@@ -177,6 +179,7 @@ MapParams map_params(psm_ctx* c) {
   P.omega_p = c->omega_p;
   P.omega_m = c->omega_m;
   P.mlp = c->have_mlp ? c->mlp : nullptr;
+  P.wtab = c->have_wtab ? c->wtab : nullptr;
   P.partials = c->partials;
   P.mlp_X = c->mlp_X;
   P.mlp_eps = c->mlp_eps;
@@ -434,8 +437,9 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
   c->mlp_count = alloc_n<int>(c, 1, c->allocs);
   c->dem_bar = alloc_n<unsigned>(c, 2, c->allocs);
+  c->wtab = alloc_n<double>(c, 513, c->allocs);
   if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
-      !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar)
+      !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar || !c->wtab)
     return bail(PSM_ERR_OOM, "allocator returned NULL");
   cudaStream_t s = c->stream;
   bool ok = true;
@@ -468,6 +472,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     return bail(PSM_ERR_CUDA, "occupancy query of the collision kernel failed");
   }
   launch_step_const(map_params(c), s);
+  c->have_wtab = launch_weight_table(c->opt.eps_n, c->tau, c->opt.weighting, c->wtab, s) > 0;
   if (cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "cudaStreamCreate failed");

@@ -46,7 +46,7 @@ struct FastDiv {
   }
 #endif
 };
-inline FastDiv make_fastdiv(unsigned d) {
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
   int l = 0;
   while ((1ull << l) < d) ++l;
   FastDiv f;
@@ -156,6 +156,7 @@ struct MapParams {
   double G[3];          // sum over free particles of (m - V) g
   double fbody[3];
   double omega_p, omega_m;
+  const double* wtab;   // B of each sampled count c = 0..n^3 (n^3 < 513), or NULL
   const float* mlp;     // FP32 parameters (PSM_MLP_PARAMS)
   double* partials;     // >= MAP_PARTIALS doubles of scratch
   // surrogate worklist (eps mode 2): inputs, outputs, slot entry, count
@@ -219,7 +220,9 @@ int launch_sums(const Grid& g, const double* f, double* partials, int nparts, do
 int launch_step_const(MapParams P, cudaStream_t s);
 
 int launch_map(MapParams P, cudaStream_t s);                   // full mapping
-int launch_force_reduce(MapParams P, cudaStream_t s);          // fixed-order F/T
+int launch_force_reduce(MapParams P, cudaStream_t s);
+// table of B for the n^3 + 1 sampled counts (n^3 < 513); returns launches
+int launch_weight_table(int n, double tau, int weighting, double* out, cudaStream_t s);          // fixed-order F/T
 int launch_force_reduce_atomic_finish(MapParams P, cudaStream_t s);
 int launch_pack_particles(Particles p, cudaStream_t s);
 int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s);
