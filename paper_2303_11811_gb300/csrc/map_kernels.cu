@@ -17,6 +17,8 @@
 // with a certified band and FP64 inside the band (geom.cuh); this file is
 // compiled with -fmad=false.
 #include "geom.cuh"
+#include <type_traits>
+
 #include "psm_internal.cuh"
 
 namespace psm {
@@ -147,13 +149,20 @@ __device__ __forceinline__ double weight(double eps, double tau, int nt) {
   return eps * (tau - 0.5) / ((1.0 - eps) + (tau - 0.5));
 }
 
+// the weight of slot s of entry e lives in the last component of its record
+// (during the mapping: raw, -1 for "resolved in a later pass"; after the
+// finish pass: normalised, slot 0's negated when the cell has a second
+// particle)
+__device__ __forceinline__ long long rec_w(const MapParams& P, long long e, int s) {
+  return 4 * (s * P.s.cap + e) + 3;
+}
 __device__ __forceinline__ void store_B(const MapParams& P, long long e, int s, double B) {
-  if (P.fp32) reinterpret_cast<float*>(static_cast<float2*>(P.s.B) + e)[s] = (float)B;
-  else reinterpret_cast<double*>(static_cast<double2*>(P.s.B) + e)[s] = B;
+  if (P.fp32) static_cast<float*>(P.s.V)[rec_w(P, e, s)] = (float)B;
+  else static_cast<double*>(P.s.V)[rec_w(P, e, s)] = B;
 }
 __device__ __forceinline__ double load_B(const MapParams& P, long long e, int s) {
-  if (P.fp32) return (double)reinterpret_cast<const float*>(static_cast<float2*>(P.s.B) + e)[s];
-  return reinterpret_cast<const double*>(static_cast<double2*>(P.s.B) + e)[s];
+  if (P.fp32) return (double)static_cast<const float*>(P.s.V)[rec_w(P, e, s)];
+  return static_cast<const double*>(P.s.V)[rec_w(P, e, s)];
 }
 
 __device__ __forceinline__ long long slot_index(const Coverage& cov, long long cell) {
@@ -296,13 +305,12 @@ __global__ void clear_slots_kernel(MapParams P) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     P.s.pid[e] = make_int2(-1, -1);
     P.s.cnt[e] = 0;
-    if (P.fp32) static_cast<float2*>(P.s.B)[e] = make_float2(0.f, 0.f);
-    else static_cast<double2*>(P.s.B)[e] = make_double2(0.0, 0.0);
   }
 }
 
 // sampled count of a cell for one particle (n^3 for a cell inside by the
 // margin sqrt(3)/2, which the sampling would also give)
+template <int NS>
 __device__ int cell_count(const MapParams& P, const Box& b, const CellHit& h, const double* s64,
                           const float* s32) {
   const int n = P.eps_n;
@@ -311,9 +319,10 @@ __device__ int cell_count(const MapParams& P, const Box& b, const CellHit& h, co
     if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
       return n * n * n;
   }
-  return n == 4   ? supersample_count_n<4>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f, b.E)
-         : n == 8 ? supersample_count_n<8>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f, b.E)
-                  : supersample_count_fast(h.dx, h.dy, h.dz, b.r, n, s64, s32);
+  if (NS > 0)
+    return supersample_count_n<(NS > 0 ? NS : 1)>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf,
+                                                  b.r2f, b.E);
+  return supersample_count_fast(h.dx, h.dy, h.dz, b.r, n, s64, s32);
 }
 
 // eps of a cell for one particle; -1 means "resolved in a later pass".  The
@@ -366,7 +375,8 @@ __global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
 // of the n^3 + 1 sampled values when eps is a count), and the particle's
 // surface velocity at the cell centre (Eq. 20); the list entry becomes the
 // slot index (and, for the FP32 path, the float offset from the centre).
-__global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
+template <int NS>
+__global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   __shared__ double s64[16];
   __shared__ float s32[16];
   __shared__ Box sbox;
@@ -427,7 +437,6 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
       continue;
     }
     P.list[loff + k] = (int)e;
-    if (P.fp32) P.listf[loff + k] = make_float4(h.dxf, h.dyf, h.dzf, 0.f);
     const int s = atomicAdd(&P.s.cnt[e], 1);
     if (s >= 2) {
       atomicOr(P.status, ST_SLOT_OVERFLOW);
@@ -437,29 +446,28 @@ __global__ void __launch_bounds__(MAP_THREADS) fill_kernel(MapParams P) {
     reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
     double B;
     if (tab) {
-      const int c = cell_count(P, b, h, s64, s32);
+      const int c = cell_count<NS>(P, b, h, s64, s32);
       B = __ldg(&wtab[c]);
     } else {
       h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
       const double eps = cell_eps(P, b, h, fr, s64, s32);
       B = eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting);
     }
-    store_B(P, e, s, B);
-    const long long rec = s * P.s.cap + e;  // slot s's record array
+    const long long rec = s * P.s.cap + e;  // slot s's record: velocity and B
     if (P.fp32) {
       // the FP32 collision takes the surface velocity in FP32
       const float fx = h.dxf, fy = h.dyf, fz = h.dzf;
       const float f0 = (float)o0, f1 = (float)o1, f2 = (float)o2;
       static_cast<float4*>(P.s.V)[rec] =
           make_float4((float)u0 + (f1 * fz - f2 * fy), (float)u1 + (f2 * fx - f0 * fz),
-                      (float)u2 + (f0 * fy - f1 * fx), 0.f);
+                      (float)u2 + (f0 * fy - f1 * fx), (float)B);
     } else {
       const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
       const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
       const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
       double2* R = static_cast<double2*>(P.s.V) + 2 * rec;
       R[0] = make_double2(v0, v1);
-      R[1] = make_double2(v2, 0.0);
+      R[1] = make_double2(v2, B);
     }
   }
 }
@@ -509,91 +517,68 @@ __global__ void apply_mlp_kernel(MapParams P) {
   }
 }
 
+// one slot entry of the finish pass in the storage precision T: order the
+// two slots by particle index, sample cells left pending with 8^3 points,
+// normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
+// weight; returns min(B, 1)
+template <typename T>
+__device__ double finish_entry(const MapParams& P, int e) {
+  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+  int2 pid = P.s.pid[e];
+  const bool two = pid.y >= 0;
+  const long long e1 = P.s.cap + e;
+  T* V = static_cast<T*>(P.s.V);
+  T r0[4], r1[4] = {T(0), T(0), T(0), T(0)};
+  for (int a = 0; a < 4; ++a) r0[a] = V[4 * e + a];
+  if (two)
+    for (int a = 0; a < 4; ++a) r1[a] = V[4 * e1 + a];
+  if (two && pid.y < pid.x) {
+    const int t = pid.x;
+    pid.x = pid.y;
+    pid.y = t;
+    for (int a = 0; a < 4; ++a) {
+      const T v = r0[a];
+      r0[a] = r1[a];
+      r1[a] = v;
+    }
+  }
+  if (r0[3] < T(0) || r1[3] < T(0)) {
+    // cells left for the surrogate and not taken by it: 8^3 sampling
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
+    for (int sl = 0; sl < 2; ++sl) {
+      const int p = sl ? pid.y : pid.x;
+      T& Bs = sl ? r1[3] : r0[3];
+      if (p < 0 || Bs >= T(0)) continue;
+      const double r = P.p.r[p];
+      const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+      const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+      const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+      const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
+      Bs = (T)weight(eps, P.tau, P.weighting);
+    }
+  }
+  T B = r0[3] + r1[3];
+  if (B > T(1)) {
+    r0[3] = r0[3] / B;
+    r1[3] = r1[3] / B;
+    B = T(1);
+  }
+  P.s.pid[e] = pid;
+  r0[3] = two ? -r0[3] : r0[3];
+  for (int a = 0; a < 4; ++a) V[4 * e + a] = r0[a];
+  if (two)
+    for (int a = 0; a < 4; ++a) V[4 * e1 + a] = r1[a];
+  (void)sizeof(T2);
+  return (double)B;
+}
+
 __global__ void finish_kernel(MapParams P) {
   __shared__ double red[256];
   const int n = slot_count(P);
   double accB = 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    int2 pid = P.s.pid[e];
-    double B0 = load_B(P, e, 0), B1 = load_B(P, e, 1);
-    const bool swapped = pid.y >= 0 && pid.y < pid.x;
-    if (swapped) {
-      const int t = pid.x;
-      pid.x = pid.y;
-      pid.y = t;
-      const double tb = B0;
-      B0 = B1;
-      B1 = tb;
-    }
-    if (B0 < 0.0 || B1 < 0.0) {
-      // cells left for the surrogate and not taken by it: 8^3 sampling
-      int x, y, z;
-      cell_xyz(P.g, P.s.cell[e], x, y, z);
-      for (int s = 0; s < 2; ++s) {
-        const int p = s ? pid.y : pid.x;
-        double& Bs = s ? B1 : B0;
-        if (p < 0 || Bs >= 0.0) continue;
-        const double r = P.p.r[p];
-        const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-        const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-        const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-        const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
-        Bs = weight(eps, P.tau, P.weighting);
-      }
-    }
-    double B = B0 + B1;
-    if (B > 1.0) {
-      B0 = B0 / B;
-      B1 = B1 / B;
-      B = 1.0;
-    }
-    P.s.pid[e] = pid;
-    store_B(P, e, 0, B0);
-    store_B(P, e, 1, B1);
-    accB += B;
-    // slot records (surface velocity from the fill pass): in slot order,
-    // with the final weights; slot 0's weight carries a negative sign when a
-    // second particle shares the cell (-0.0 for a zero weight)
-    const bool two = pid.y >= 0;
-    const long long e1 = P.s.cap + e;
-    if (P.fp32) {
-      float4* R = static_cast<float4*>(P.s.V);
-      float4 r0 = R[e], r1 = two ? R[e1] : make_float4(0.f, 0.f, 0.f, 0.f);
-      if (swapped) {
-        const float4 t = r0;
-        r0 = r1;
-        r1 = t;
-      }
-      r0.w = two ? -(float)B0 : (float)B0;
-      r1.w = (float)B1;
-      R[e] = r0;
-      if (two) R[e1] = r1;
-    } else {
-      double2* R = static_cast<double2*>(P.s.V);
-      double2 a0 = R[2 * e], a1 = R[2 * e + 1];
-      double2 c0 = make_double2(0.0, 0.0), c1 = make_double2(0.0, 0.0);
-      if (two) {
-        c0 = R[2 * e1];
-        c1 = R[2 * e1 + 1];
-      }
-      if (swapped) {
-        double2 t = a0;
-        a0 = c0;
-        c0 = t;
-        t = a1;
-        a1 = c1;
-        c1 = t;
-      }
-      a1.y = two ? -B0 : B0;
-      c1.y = B1;
-      R[2 * e] = a0;
-      R[2 * e + 1] = a1;
-      if (two) {
-        R[2 * e1] = c0;
-        R[2 * e1 + 1] = c1;
-      }
-    }
-  }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    accB += P.fp32 ? finish_entry<float>(P, e) : finish_entry<double>(P, e);
   red[threadIdx.x] = accB;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -689,15 +674,38 @@ struct FloatPair {
 
 __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams P) {
   __shared__ double sh[6][RED_THREADS];
+  __shared__ int sip[3];
+  __shared__ float sfp[3];
   const int p = blockIdx.x;
   const float* Fc = static_cast<const float*>(P.s.Fc);
   const long long loff = P.list_off[p];
   const int cnt = P.list_cnt[p];
+  if (threadIdx.x < 3) {  // centre = floor + fraction, once per block in FP64
+    const double xp = P.p.x[3 * p + threadIdx.x];
+    const double fl = floor(xp);
+    sip[threadIdx.x] = (int)fl;
+    sfp[threadIdx.x] = (float)(xp - fl);
+  }
+  __syncthreads();
+  const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
   FloatPair acc[6];
   for (int i = 0; i < 6; ++i) acc[i] = FloatPair{0.f, 0.f};
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
     const int e = P.list[loff + k];
-    const float4 d = P.listf[loff + k];
+    // torque arm: the cell centre's nearest-image offset, in FP32 from the
+    // integer and fractional parts of the centre
+    int c3[3];
+    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    float d3[3];
+    for (int a = 0; a < 3; ++a) {
+      int k0 = c3[a] - sip[a];
+      if (!P.g.wall[a]) {
+        if (2 * k0 > dims[a]) k0 -= dims[a];
+        else if (2 * k0 < -dims[a]) k0 += dims[a];
+      }
+      d3[a] = (float)k0 + (0.5f - sfp[a]);
+    }
+    const float4 d = make_float4(d3[0], d3[1], d3[2], 0.f);
     const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
@@ -775,8 +783,8 @@ __global__ void dense_scatter_kernel(MapParams P, int* pid0, double* B0, int* pi
     const int2 pid = P.s.pid[e];
     pid0[c] = pid.x;
     pid1[c] = pid.y;
-    B0[c] = load_B(P, e, 0);
-    B1[c] = load_B(P, e, 1);
+    B0[c] = fabs(load_B(P, e, 0));
+    B1[c] = pid.y >= 0 ? load_B(P, e, 1) : 0.0;
   }
 }
 
@@ -801,7 +809,9 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
   clear_slots_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
   launches += 4;
   if (P.p.n > 0) {
-    fill_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    else fill_kernel<0><<<P.p.n, MAP_THREADS, 0, s>>>(P);
     ++launches;
   }
   return launches;

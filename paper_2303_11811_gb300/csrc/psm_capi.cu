@@ -74,7 +74,6 @@ struct psm_ctx {
   long long mlp_cap = 0;
   long long* list_off = nullptr;  // per-particle entry lists (force reduction)
   int* list = nullptr;
-  float4* listf = nullptr;
   int* list_cnt = nullptr;
   bool error_state = false;
   std::string err;
@@ -151,7 +150,6 @@ void free_particles(psm_ctx* c) {
   c->mlp_cap = 0;
   c->list_off = nullptr;
   c->list = nullptr;
-  c->listf = nullptr;
   c->dem_bins = nullptr;
   c->dem_items = nullptr;
   c->dem_nbr = nullptr;
@@ -188,7 +186,6 @@ MapParams map_params(psm_ctx* c) {
   P.mlp_count = c->mlp_count;
   P.list_off = c->list_off;
   P.list = c->list;
-  P.listf = c->listf;
   P.list_cnt = c->list_cnt;
   return P;
 }
@@ -585,13 +582,11 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   S.cap = (long long)cp;
   S.cell = alloc_n<int>(c, cp, c->palloc);
   S.pid = alloc_n<int2>(c, cp, c->palloc);
-  S.B = alloc_n<unsigned char>(c, cp * 2 * (c->fp32 ? 4 : 8), c->palloc);
   S.cnt = alloc_n<int>(c, cp, c->palloc);
   S.Fc = alloc_n<unsigned char>(c, cp * 6 * (c->fp32 ? 4 : 8), c->palloc);
   S.V = alloc_n<unsigned char>(c, cp * 8 * (c->fp32 ? 4 : 8), c->palloc);
   c->list_off = alloc_n<long long>(c, (size_t)n + 1, c->palloc);
   c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
-  if (c->fp32) c->listf = alloc_n<float4>(c, (size_t)list_total, c->palloc);
   c->list_cnt = alloc_n<int>(c, n1, c->palloc);
   c->dem_bins = alloc_n<int>(c, 3 * (size_t)c->dem_nbins, c->palloc);
   c->dem_items = alloc_n<int>(c, 3 * n1, c->palloc);

@@ -125,7 +125,6 @@ struct Particles {
 struct Slots {
   int* cell;      // padded cell index of each entry
   int2* pid;
-  void* B;        // T2
   int* cnt;
   void* Fc;       // slot s's force of entry e at T[3 (s cap + e)]
   // slot s's record of entry e at T[4 (s cap + e)]: the particle's surface
@@ -169,7 +168,6 @@ struct MapParams {
   // fixed-order force/torque reduction
   const long long* list_off;   // n+1 offsets
   int* list;
-  float4* listf;               // FP32 path: cell-centre offset of each entry
   int* list_cnt;
 };
 constexpr int MAP_PARTIALS = 152 * 32;
