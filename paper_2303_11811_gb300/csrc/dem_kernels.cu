@@ -4,12 +4,15 @@
 // gravity and the hydrodynamic force/torque of the last LBM step held fixed
 // over the sub-steps.
 //
-// Once per LBM step the particles are binned (bin edge >= largest diameter +
-// skin) and each particle gets the list of partners within contact distance
-// plus the skin, in ascending index order.  A particle that moves more than
-// half the skin within the step could miss a contact: the sub-steps check the
-// displacement and set ST_DEM_SKIN; a list longer than its capacity sets
-// ST_CONTACT_OVERFLOW.
+// The particles are binned (bin edge >= largest diameter + skin) and each
+// particle gets the list of partners within contact distance plus the skin,
+// in ascending index order.  The lists are rebuilt at the start of a step
+// once a particle has moved more than a quarter of the skin since they were
+// built (or the host changed the particles); a particle that moves more than
+// half the skin could miss a contact: the sub-steps check the displacement
+// and set ST_DEM_SKIN.  A list longer than its capacity sets
+// ST_CONTACT_OVERFLOW.  When every list is empty no contact can occur within
+// the step and each particle runs its sub-steps alone.
 //
 // Per sub-step one launch, one thread per particle: positions of the current
 // sub-step are read, contacts are summed over the list in ascending j (FP32
@@ -205,6 +208,7 @@ __device__ void dem_nbr(const DemParams& P, int i) {
         }
       }
   P.nbr_cnt[i] = cnt;
+  if (cnt > 0) atomicAdd(&P.bar[3], 1u);
   if (over) atomicOr(P.status, ST_CONTACT_OVERFLOW);
 }
 
@@ -274,7 +278,9 @@ __device__ void dem_substep(const DemParams& P, int i, const double* __restrict_
     const float ex = min_image((float)x[0] - xb.x, dims[0], !P.g.wall[0]);
     const float ey = min_image((float)x[1] - xb.y, dims[1], !P.g.wall[1]);
     const float ez = min_image((float)x[2] - xb.z, dims[2], !P.g.wall[2]);
-    if (ex * ex + ey * ey + ez * ez > 0.25f * P.skin * P.skin) atomicOr(P.status, ST_DEM_SKIN);
+    const float e2 = ex * ex + ey * ey + ez * ez;
+    if (e2 > 0.25f * P.skin * P.skin) atomicOr(P.status, ST_DEM_SKIN);
+    if (last && e2 > 0.0625f * P.skin * P.skin) P.bar[2] = 0u;  // rebuild next step
   }
   for (int a = 0; a < 3; ++a) {
     Un[3 * i + a] = u[a];
@@ -335,23 +341,55 @@ __device__ bool grid_barrier(const DemParams& P, unsigned& gen) {
 __global__ void __launch_bounds__(DEM_THREADS) dem_step_kernel(DemParams P, int subcycles) {
   __shared__ int part[DEM_THREADS];
   unsigned gen = *(volatile unsigned*)&P.bar[1];
+  // lists are rebuilt when a particle has moved more than a quarter of the
+  // skin since they were built, or the host changed the particles
+  const bool rebuild = *(volatile unsigned*)&P.bar[2] == 0u;
   const int n = P.p.n;
   const int stride = gridDim.x * blockDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int b = i0; b < P.nbins; b += stride) P.bin_count[b] = 0;
-  if (!grid_barrier(P, gen)) return;
-  for (int i = i0; i < n; i += stride) dem_bin(P, i);
-  if (!grid_barrier(P, gen)) return;
-  if (blockIdx.x == 0) dem_scan(P, part);
-  if (!grid_barrier(P, gen)) return;
-  for (int i = i0; i < n; i += stride) dem_fill(P, i);
-  if (!grid_barrier(P, gen)) return;
-  for (int i = i0; i < n; i += stride) dem_nbr(P, i);
+  if (rebuild) {
+    for (int b = i0; b < P.nbins; b += stride) P.bin_count[b] = 0;
+    if (i0 == 0) P.bar[3] = 0u;
+    if (!grid_barrier(P, gen)) return;
+    for (int i = i0; i < n; i += stride) dem_bin(P, i);
+    if (!grid_barrier(P, gen)) return;
+    if (blockIdx.x == 0) dem_scan(P, part);
+    if (!grid_barrier(P, gen)) return;
+    for (int i = i0; i < n; i += stride) dem_fill(P, i);
+    if (!grid_barrier(P, gen)) return;
+    for (int i = i0; i < n; i += stride) dem_nbr(P, i);
+    if (i0 == 0) P.bar[2] = 1u;  // every block read the flag before its first barrier
+  }
   for (int i = i0; i < n; i += stride) dem_position(P, i);
   if (!grid_barrier(P, gen)) return;
-  const double* Xc = P.p.x;
-  const double* Uc = P.p.u;
-  const float4* XFc = reinterpret_cast<const float4*>(P.p.xf);
+  const double* X0 = P.p.x;
+  const double* U0 = P.p.u;
+  const float4* XF0 = reinterpret_cast<const float4*>(P.p.xf);
+  if (*(volatile unsigned*)&P.bar[3] == 0u) {
+    // no particle has a partner within contact distance plus the skin: no
+    // contact can occur this step, each particle's sub-steps need only its
+    // own state (same arithmetic, no barriers)
+    for (int i = i0; i < n; i += stride) {
+      const double* Xc = X0;
+      const double* Uc = U0;
+      const float4* XFc = XF0;
+      for (int sc = 0; sc < subcycles; ++sc) {
+        const bool to2 = (sc % 2) == 0;
+        double* Xn = to2 ? P.p.x2 : P.p.x;
+        double* Un = to2 ? P.p.u2 : P.p.u;
+        float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
+        dem_substep(P, i, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+        Xc = Xn;
+        Uc = Un;
+        XFc = XFn;
+      }
+      if (subcycles % 2 == 1) dem_copy_back(P, i, Xc, Uc, XFc);
+    }
+    return;
+  }
+  const double* Xc = X0;
+  const double* Uc = U0;
+  const float4* XFc = XF0;
   for (int sc = 0; sc < subcycles; ++sc) {
     const bool to2 = (sc % 2) == 0;
     double* Xn = to2 ? P.p.x2 : P.p.x;

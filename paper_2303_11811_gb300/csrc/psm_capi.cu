@@ -433,7 +433,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->partials = alloc_n<double>(c, MAP_PARTIALS * 4, c->allocs);
   c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
   c->mlp_count = alloc_n<int>(c, 1, c->allocs);
-  c->dem_bar = alloc_n<unsigned>(c, 2, c->allocs);
+  c->dem_bar = alloc_n<unsigned>(c, 4, c->allocs);
   c->wtab = alloc_n<double>(c, 513, c->allocs);
   if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
       !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar || !c->wtab)
@@ -444,7 +444,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     ok = ok && cudaMemsetAsync(c->buf[b], 0, esz * Q * (size_t)ncell, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.mask, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) == cudaSuccess;
-  ok = ok && cudaMemsetAsync(c->dem_bar, 0, 2 * sizeof(unsigned), s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->dem_bar, 0, 4 * sizeof(unsigned), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.ncov, 0, sizeof(int), s) == cudaSuccess;
   StepConst h{};
   h.ncells = (double)g.nx * g.ny * g.nz;
@@ -629,7 +629,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->need_map = true;
   c->error_state = false;
   CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), s));
-  CK(cudaMemsetAsync(c->dem_bar, 0, 2 * sizeof(unsigned), s));
+  CK(cudaMemsetAsync(c->dem_bar, 0, 4 * sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
   return PSM_OK;
 }
@@ -1003,6 +1003,7 @@ psm_status psm_update_particles(psm_ctx* c, const double* x, const double* u, co
   CK(cudaMemcpyAsync(c->p.u, u, b3, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(c->p.om, om, b3, cudaMemcpyHostToDevice, c->stream));
   launch_wrap_particles(c->g, c->p, c->stream);
+  CK(cudaMemsetAsync(c->dem_bar + 2, 0, sizeof(unsigned), c->stream));  // new DEM lists
   CK(cudaGetLastError());
   c->need_map = true;
   return PSM_OK;

@@ -246,7 +246,8 @@ struct DemParams {
   int* nbr;           // n*K, candidate partners in ascending order
   int* nbr_cnt;       // n
   float4* xbuild;     // n, positions when the lists were built
-  unsigned* bar;      // grid barrier of the step kernel: arrival count, generation
+  unsigned* bar;      // [0] barrier arrivals, [1] barrier generation, [2] lists valid
+                      // (0: rebuild), [3] particles with a non-empty list
   int max_blocks;     // blocks that can be resident at once (cooperative launch)
 };
 int dem_max_blocks();
