@@ -20,7 +20,8 @@
 // margin -- then the exact FP64 contact), then the walls -x,+x,-y,+y,-z,+z,
 // with plain IEEE FP64 operations (this file is compiled with -fmad=false),
 // so the sums are bitwise reproducible; then the velocity update and the next
-// sub-step's positions.  FP64 runs at 1/64 of the FP32 rate here, so each
+// sub-step's positions (Eqs. 15-16 with dt/(2m), dt/(2I) formed once per
+// sub-step: equal to the quotients up to rounding).  FP64 runs at 1/64 of the FP32 rate here, so each
 // FP64 instruction works on 32 particles and the blocks (32 threads) spread
 // over many SMs.
 #include "psm_internal.cuh"
@@ -38,9 +39,9 @@ __device__ void dem_position(const DemParams& P, int i) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   if (!P.p.fixed[i]) {
     const double dt = P.dt;
+    const double h2m = dt * dt / (2.0 * P.p.m[i]);
     for (int a = 0; a < 3; ++a) {
-      double xn = P.p.x[3 * i + a] + dt * P.p.u[3 * i + a] +
-                  dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
+      double xn = P.p.x[3 * i + a] + dt * P.p.u[3 * i + a] + h2m * P.p.Fold[3 * i + a];
       if (!P.g.wall[a]) {
         if (xn >= dims[a]) xn -= dims[a];
         else if (xn < 0.0) xn += dims[a];
@@ -255,17 +256,20 @@ __device__ void dem_substep(const DemParams& P, int i, const double* __restrict_
     x[a] = Xc[3 * i + a];
   }
   if (!P.p.fixed[i]) {
+    // FP64 division is a long instruction sequence here: the three
+    // reciprocal factors once per sub-step
+    const double hm = dt / (2.0 * P.p.m[i]), hI = dt / (2.0 * P.p.I[i]), h2m = dt * hm;
     for (int a = 0; a < 3; ++a) {
       const double Fn = P.p.Fh[3 * i + a] + F[a] + (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
       const double Tn = P.p.Th[3 * i + a];
-      u[a] += dt * (P.p.Fold[3 * i + a] + Fn) / (2.0 * P.p.m[i]);
-      P.p.om[3 * i + a] += dt * (P.p.Told[3 * i + a] + Tn) / (2.0 * P.p.I[i]);
+      u[a] += hm * (P.p.Fold[3 * i + a] + Fn);
+      P.p.om[3 * i + a] += hI * (P.p.Told[3 * i + a] + Tn);
       P.p.Fold[3 * i + a] = Fn;
       P.p.Told[3 * i + a] = Tn;
     }
     if (!last) {
       for (int a = 0; a < 3; ++a) {
-        double xn = x[a] + dt * u[a] + dt * dt * P.p.Fold[3 * i + a] / (2.0 * P.p.m[i]);
+        double xn = x[a] + dt * u[a] + h2m * P.p.Fold[3 * i + a];
         if (!P.g.wall[a]) {
           if (xn >= ddims[a]) xn -= ddims[a];
           else if (xn < 0.0) xn += ddims[a];
