@@ -17,8 +17,6 @@
 // with a certified band and FP64 inside the band (geom.cuh); this file is
 // compiled with -fmad=false.
 #include "geom.cuh"
-#include <type_traits>
-
 #include "psm_internal.cuh"
 
 namespace psm {
@@ -41,6 +39,7 @@ struct Box {
   double reach2;      // (r + sqrt(3)/2)^2 in FP64
   float reach2f, E;   // its FP32 value and the certified band of geom.cuh
   float r2f;          // (float)(r * r)
+  bool has_in;        // rin2 >= 0: cells can lie inside by the margin
   FastDiv div_n0, div_nxy;  // box index t -> (kx, ky, kz)
 };
 
@@ -73,6 +72,7 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
   b.r2f = (float)(r * r);
   const double rin = r - HALF_SQRT3;
   b.rin2 = rin > 0.0 ? rin * rin : -1.0;
+  b.has_in = rin > 0.0;
   b.rin2f = (float)b.rin2;
   return b;
 }
@@ -314,7 +314,7 @@ template <int NS>
 __device__ int cell_count(const MapParams& P, const Box& b, const CellHit& h, const double* s64,
                           const float* s32) {
   const int n = P.eps_n;
-  if (b.rin2 >= 0.0) {
+  if (b.has_in) {
     if (h.d2f < b.rin2f - b.E) return n * n * n;
     if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
       return n * n * n;
@@ -365,9 +365,14 @@ constexpr int WTAB = 513;  // B of every sampled count up to 8^3
 constexpr int FILL_AXIS = 64;  // box extent per axis with offset tables (r < 30)
 
 // B of every sampled count (Eq. 16 of each eps = c / n^3), once per context
+// (doubles at out[0..n3], their FP32 roundings after WTAB doubles)
 __global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
-  for (int c = threadIdx.x; c <= n3; c += blockDim.x)
-    out[c] = weight(count_eps(c, n3), tau, weighting);
+  float* outf = reinterpret_cast<float*>(out + WTAB);
+  for (int c = threadIdx.x; c <= n3; c += blockDim.x) {
+    const double B = weight(count_eps(c, n3), tau, weighting);
+    out[c] = B;
+    outf[c] = (float)B;
+  }
 }
 
 // Slots of one particle's cells (one block per particle, over the list the
@@ -405,6 +410,9 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   __syncthreads();
   const double u0 = P.p.u[3 * p], u1 = P.p.u[3 * p + 1], u2 = P.p.u[3 * p + 2];
   const double o0 = P.p.om[3 * p], o1 = P.p.om[3 * p + 1], o2 = P.p.om[3 * p + 2];
+  const float uf0 = (float)u0, uf1 = (float)u1, uf2 = (float)u2;
+  const float of0 = (float)o0, of1 = (float)o1, of2 = (float)o2;
+  const float* wtabf = reinterpret_cast<const float*>(wtab + WTAB);  // FP32 copy
   const long long loff = P.list_off[p];
   const int cnt = P.list_cnt[p];
   for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
@@ -445,22 +453,24 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     P.s.cell[e] = (int)cell;
     reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
     double B;
+    float Bf = 0.f;
     if (tab) {
       const int c = cell_count<NS>(P, b, h, s64, s32);
-      B = __ldg(&wtab[c]);
+      if (P.fp32) Bf = __ldg(&wtabf[c]);
+      else B = __ldg(&wtab[c]);
     } else {
       h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
       const double eps = cell_eps(P, b, h, fr, s64, s32);
       B = eps < 0.0 ? -1.0 : weight(eps, P.tau, P.weighting);
+      Bf = (float)B;
     }
     const long long rec = s * P.s.cap + e;  // slot s's record: velocity and B
     if (P.fp32) {
       // the FP32 collision takes the surface velocity in FP32
       const float fx = h.dxf, fy = h.dyf, fz = h.dzf;
-      const float f0 = (float)o0, f1 = (float)o1, f2 = (float)o2;
       static_cast<float4*>(P.s.V)[rec] =
-          make_float4((float)u0 + (f1 * fz - f2 * fy), (float)u1 + (f2 * fx - f0 * fz),
-                      (float)u2 + (f0 * fy - f1 * fx), (float)B);
+          make_float4(uf0 + (of1 * fz - of2 * fy), uf1 + (of2 * fx - of0 * fz),
+                      uf2 + (of0 * fy - of1 * fx), Bf);
     } else {
       const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
       const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
@@ -521,17 +531,51 @@ __global__ void apply_mlp_kernel(MapParams P) {
 // two slots by particle index, sample cells left pending with 8^3 points,
 // normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
 // weight; returns min(B, 1)
+__device__ __forceinline__ void rec_load(const float* p, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void rec_load(const double* p, double* o) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0];
+  const double2 v = reinterpret_cast<const double2*>(p)[1];
+  o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
+}
+__device__ __forceinline__ void rec_store(float* p, const float* o) {
+  *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
+}
+__device__ __forceinline__ void rec_store(double* p, const double* o) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
+}
+
+// cells left for the surrogate and not taken by it: 8^3 sampling (rare;
+// kept out of line so that its registers do not weigh on the common path)
+template <typename T>
+__device__ __noinline__ void pending_weights(const MapParams& P, int e, int2 pid, T& B0, T& B1) {
+  int x, y, z;
+  cell_xyz(P.g, P.s.cell[e], x, y, z);
+  for (int sl = 0; sl < 2; ++sl) {
+    const int p = sl ? pid.y : pid.x;
+    T& Bs = sl ? B1 : B0;
+    if (p < 0 || Bs >= T(0)) continue;
+    const double r = P.p.r[p];
+    const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+    const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+    const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+    const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
+    Bs = (T)weight(eps, P.tau, P.weighting);
+  }
+}
+
 template <typename T>
 __device__ double finish_entry(const MapParams& P, int e) {
-  using T2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
   int2 pid = P.s.pid[e];
   const bool two = pid.y >= 0;
   const long long e1 = P.s.cap + e;
   T* V = static_cast<T*>(P.s.V);
   T r0[4], r1[4] = {T(0), T(0), T(0), T(0)};
-  for (int a = 0; a < 4; ++a) r0[a] = V[4 * e + a];
-  if (two)
-    for (int a = 0; a < 4; ++a) r1[a] = V[4 * e1 + a];
+  rec_load(V + 4 * e, r0);
+  if (two) rec_load(V + 4 * e1, r1);
   if (two && pid.y < pid.x) {
     const int t = pid.x;
     pid.x = pid.y;
@@ -542,38 +586,23 @@ __device__ double finish_entry(const MapParams& P, int e) {
       r1[a] = v;
     }
   }
-  if (r0[3] < T(0) || r1[3] < T(0)) {
-    // cells left for the surrogate and not taken by it: 8^3 sampling
-    int x, y, z;
-    cell_xyz(P.g, P.s.cell[e], x, y, z);
-    for (int sl = 0; sl < 2; ++sl) {
-      const int p = sl ? pid.y : pid.x;
-      T& Bs = sl ? r1[3] : r0[3];
-      if (p < 0 || Bs >= T(0)) continue;
-      const double r = P.p.r[p];
-      const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-      const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-      const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-      const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
-      Bs = (T)weight(eps, P.tau, P.weighting);
-    }
-  }
+  if (r0[3] < T(0) || r1[3] < T(0)) pending_weights<T>(P, e, pid, r0[3], r1[3]);
   T B = r0[3] + r1[3];
   if (B > T(1)) {
     r0[3] = r0[3] / B;
     r1[3] = r1[3] / B;
     B = T(1);
   }
-  P.s.pid[e] = pid;
   r0[3] = two ? -r0[3] : r0[3];
-  for (int a = 0; a < 4; ++a) V[4 * e + a] = r0[a];
-  if (two)
-    for (int a = 0; a < 4; ++a) V[4 * e1 + a] = r1[a];
-  (void)sizeof(T2);
+  rec_store(V + 4 * e, r0);
+  if (two) {
+    P.s.pid[e] = pid;
+    rec_store(V + 4 * e1, r1);
+  }
   return (double)B;
 }
 
-__global__ void finish_kernel(MapParams P) {
+__global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   __shared__ double red[256];
   const int n = slot_count(P);
   double accB = 0.0;

@@ -434,7 +434,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
   c->mlp_count = alloc_n<int>(c, 1, c->allocs);
   c->dem_bar = alloc_n<unsigned>(c, 4, c->allocs);
-  c->wtab = alloc_n<double>(c, 513, c->allocs);
+  c->wtab = alloc_n<double>(c, 513 + 257, c->allocs);  // 513 doubles + 513 floats
   if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
       !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar || !c->wtab)
     return bail(PSM_ERR_OOM, "allocator returned NULL");

@@ -155,7 +155,8 @@ struct MapParams {
   double G[3];          // sum over free particles of (m - V) g
   double fbody[3];
   double omega_p, omega_m;
-  const double* wtab;   // B of each sampled count c = 0..n^3 (n^3 < 513), or NULL
+  const double* wtab;   // B of each sampled count c = 0..n^3 (n^3 < 513), or NULL;
+                        // their FP32 roundings follow at (const float*)(wtab + 513)
   const float* mlp;     // FP32 parameters (PSM_MLP_PARAMS)
   double* partials;     // >= MAP_PARTIALS doubles of scratch
   // surrogate worklist (eps mode 2): inputs, outputs, slot entry, count
