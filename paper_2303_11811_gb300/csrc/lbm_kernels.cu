@@ -203,9 +203,12 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
       cov = false;
     }
   }
-  T B = r0[3] + r1[3];
-  if (B > T(1)) B = T(1);
-  const T omB = T(1) - B;
+  T omB = T(1);  // 1 - B; the FP64 operations only where a lane is covered
+  if (cov) {
+    T B = r0[3] + r1[3];
+    if (B > T(1)) B = T(1);
+    omB = T(1) - B;
+  }
 
   // ---- moments (Eqs. 6-7)
   const CollideCoef<T>* cf = coef_of<T>(P.sc);

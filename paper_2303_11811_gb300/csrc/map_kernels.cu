@@ -638,23 +638,39 @@ __global__ void vfluid_kernel(MapParams P, int nparts) {
 // ---- fixed-order force and torque reduction over each particle's list
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) {
-  __shared__ double sh[6][RED_THREADS];
+  __shared__ double sh[6][RED_THREADS / 32];
+  __shared__ int sip[3];
+  __shared__ double sfr[3];
   const int p = blockIdx.x;
-  const double xp0 = P.p.x[3 * p], xp1 = P.p.x[3 * p + 1], xp2 = P.p.x[3 * p + 2];
   const T* Fc = static_cast<const T*>(P.s.Fc);
   const long long loff = P.list_off[p];
   const int cnt = P.list_cnt[p];
+  if (threadIdx.x < 3) {  // centre = integer part + (1/2 - fraction), once per block
+    const double xp = P.p.x[3 * p + threadIdx.x];
+    const double fl = floor(xp);
+    sip[threadIdx.x] = (int)fl;
+    sfr[threadIdx.x] = 0.5 - (xp - fl);
+  }
+  __syncthreads();
+  const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
     const int e = P.list[loff + k];
     const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
-    int x, y, z;
-    cell_xyz(P.g, P.s.cell[e], x, y, z);
-    const double dx = image_d(x, xp0, P.g.nx, !P.g.wall[0]);
-    const double dy = image_d(y, xp1, P.g.ny, !P.g.wall[1]);
-    const double dz = image_d(z, xp2, P.g.nz, !P.g.wall[2]);
+    // torque arm: nearest-image offset of the cell centre, (k - i_p) + (1/2 - frac)
+    int c3[3];
+    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    double d3[3];
+    for (int a = 0; a < 3; ++a) {
+      int k0 = c3[a] - sip[a];
+      if (!P.g.wall[a]) {
+        if (2 * k0 > dims[a]) k0 -= dims[a];
+        else if (2 * k0 < -dims[a]) k0 += dims[a];
+      }
+      d3[a] = (double)k0 + sfr[a];
+    }
     const long long fo = 3 * (s * P.s.cap + e);
     const double f0 = (double)Fc[fo];
     const double f1 = (double)Fc[fo + 1];
@@ -662,33 +678,39 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
     acc[0] += f0;
     acc[1] += f1;
     acc[2] += f2;
-    acc[3] += dy * f2 - dz * f1;
-    acc[4] += dz * f0 - dx * f2;
-    acc[5] += dx * f1 - dy * f0;
+    acc[3] += d3[1] * f2 - d3[2] * f1;
+    acc[4] += d3[2] * f0 - d3[0] * f2;
+    acc[5] += d3[0] * f1 - d3[1] * f0;
   }
-  for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] = acc[i];
+  // fixed-order tree: within each warp by shuffles, then over the warps
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1)
+    for (int i = 0; i < 6; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
+  if (lane == 0)
+    for (int i = 0; i < 6; ++i) sh[i][wid] = acc[i];
   __syncthreads();
-  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + s];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
+    double tot[6];
+    for (int i = 0; i < 6; ++i) {
+      tot[i] = sh[i][0];
+      for (int w = 1; w < RED_THREADS / 32; ++w) tot[i] += sh[i][w];
+    }
     bool finite = true;
     for (int i = 0; i < 3; ++i) {
-      P.p.Fh[3 * p + i] = sh[i][0];
-      P.p.Th[3 * p + i] = sh[3 + i][0];
-      finite = finite && isfinite(sh[i][0]) && isfinite(sh[3 + i][0]);
+      P.p.Fh[3 * p + i] = tot[i];
+      P.p.Th[3 * p + i] = tot[3 + i];
+      finite = finite && isfinite(tot[i]) && isfinite(tot[3 + i]);
     }
     if (!finite) atomicOr(P.status, ST_NONFINITE);
   }
 }
 
 // FP32 path: per-slot contributions are FP32, and so are the torque arms
-// stored by the mapping; every component is summed with an error-free
-// two-sum (a float pair carrying about 48 bits), then across the block in FP64
-// in a fixed order.  No FP64 arithmetic per entry: GB300 runs FP64 at 1/58 of
-// the FP32 rate.
+// (formed from the cell index and the centre's integer and fractional
+// parts); every component is summed with an error-free two-sum (a float pair
+// carrying about 48 bits), across the block by shuffles in a fixed order, and
+// converted to FP64 once.  No FP64 arithmetic per entry: GB300 runs FP64 at
+// 1/58 of the FP32 rate.
 struct FloatPair {
   float hi, lo;
   __device__ __forceinline__ void add(float x) {
@@ -698,11 +720,17 @@ struct FloatPair {
     hi = t;
     lo += err;
   }
+  // merges another pair: its high part through the two-sum, its low part
+  // into the low word
+  __device__ __forceinline__ void merge(const FloatPair& o) {
+    add(o.hi);
+    lo += o.lo;
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams P) {
-  __shared__ double sh[6][RED_THREADS];
+  __shared__ FloatPair sh[6][RED_THREADS / 32];
   __shared__ int sip[3];
   __shared__ float sfp[3];
   const int p = blockIdx.x;
@@ -749,19 +777,31 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams
     acc[4].add(d.z * f0 - d.x * f2);
     acc[5].add(d.x * f1 - d.y * f0);
   }
-  for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] = acc[i].value();
+  // fixed-order tree of the pairs: within each warp by shuffles, then over
+  // the warps; one conversion to FP64 per component at the end
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1)
+    for (int i = 0; i < 6; ++i) {
+      FloatPair q;
+      q.hi = __shfl_down_sync(0xffffffffu, acc[i].hi, o);
+      q.lo = __shfl_down_sync(0xffffffffu, acc[i].lo, o);
+      acc[i].merge(q);
+    }
+  if (lane == 0)
+    for (int i = 0; i < 6; ++i) sh[i][wid] = acc[i];
   __syncthreads();
-  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int i = 0; i < 6; ++i) sh[i][threadIdx.x] += sh[i][threadIdx.x + s];
-    __syncthreads();
-  }
   if (threadIdx.x == 0) {
+    double tot[6];
+    for (int i = 0; i < 6; ++i) {
+      FloatPair t = sh[i][0];
+      for (int w = 1; w < RED_THREADS / 32; ++w) t.merge(sh[i][w]);
+      tot[i] = t.value();
+    }
     bool finite = true;
     for (int i = 0; i < 3; ++i) {
-      P.p.Fh[3 * p + i] = sh[i][0];
-      P.p.Th[3 * p + i] = sh[3 + i][0];
-      finite = finite && isfinite(sh[i][0]) && isfinite(sh[3 + i][0]);
+      P.p.Fh[3 * p + i] = tot[i];
+      P.p.Th[3 * p + i] = tot[3 + i];
+      finite = finite && isfinite(tot[i]) && isfinite(tot[3 + i]);
     }
     if (!finite) atomicOr(P.status, ST_NONFINITE);
   }
