@@ -221,6 +221,20 @@ FORMS = (
 )
 
 
+def train_surrogate(capi, seed=20230321):
+    """The surrogate, trained on the device by the engine's own kernels on
+    2^21 samples labelled by 8^3 sub-division sampling."""
+    from paper_2303_11811_gb300 import inputs
+    t0 = time.perf_counter()
+    trainer = capi.Engine(32, 8, 8, 0.6)
+    trainer.set_mlp(capi.pack_mlp(inputs.mlp_init(1)))
+    loss = trainer.train_surrogate(1 << 21, seed, epochs=10, batch=1024, lr=3e-3)
+    params = trainer.get_mlp()
+    trainer.close()
+    return params, {"samples": 1 << 21, "epochs": 10, "batch": 1024, "final_mse": loss,
+                    "seconds": time.perf_counter() - t0}
+
+
 def forms_comparison(capi, torch, steps, seed=20230321):
     """The metric's second half on the channel workload (256x256x512, walls at
     the x faces, 12,817 fixed spheres r=5, TRT tau=0.55, body force 1e-5 along
@@ -236,15 +250,7 @@ def forms_comparison(capi, torch, steps, seed=20230321):
     out = {"workload": "channel 256x256x512, walls at the x faces, %d fixed spheres r=5 "
            "(solid fraction 0.20), TRT tau=0.55, body force 1e-5 along z"
            % w.particles["r"].size, "steps": steps}
-    # surrogate: trained on the device by the engine's own kernels
-    t0 = time.perf_counter()
-    trainer = capi.Engine(32, 8, 8, 0.6)
-    trainer.set_mlp(capi.pack_mlp(inputs.mlp_init(1)))
-    loss = trainer.train_surrogate(1 << 21, seed, epochs=10, batch=1024, lr=3e-3)
-    params = trainer.get_mlp()
-    trainer.close()
-    out["surrogate_training"] = {"samples": 1 << 21, "epochs": 10, "batch": 1024,
-                                 "final_mse": loss, "seconds": time.perf_counter() - t0}
+    params, out["surrogate_training"] = train_surrogate(capi, seed)
     out["_params"] = params
     hbm, _ = peaks()
     res = {}
@@ -354,7 +360,13 @@ def forms_settling(capi, torch, params, steps):
 
 def describe(args):
     prec = {"fp64": "FP64 PDFs", "fp32": "FP32 deviation PDFs"}[args.precision]
-    return f"{WORKLOADS[args.workload]}, {prec}, {args.streaming} streaming"
+    d = f"{WORKLOADS[args.workload]}, {prec}, {args.streaming} streaming"
+    if args.eps != "supersample" or args.eps_n:
+        eps = {"supersample": f"{args.eps_n or 4}^3 sub-division sampling",
+               "linear": "linear approximation (Eqs. 25-27)",
+               "mlp": "trained surrogate with 8^3 fallback"}[args.eps]
+        d += f", eps by {eps}"
+    return d
 
 
 def make_workload(name):
@@ -374,19 +386,29 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="settle128")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
     ap.add_argument("--streaming", choices=["pull", "aa"], default="pull")
+    ap.add_argument("--eps", choices=["supersample", "linear", "mlp"], default="supersample",
+                    help="solid-fraction mode of the main line (default: the workload's)")
+    ap.add_argument("--eps-n", type=int, default=0,
+                    help="sub-division sampling points per axis (default: the workload's)")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    default_run = (args.workload, args.precision, args.streaming) == ("settle128", "fp64", "pull")
+    default_run = ((args.workload, args.precision, args.streaming, args.eps, args.eps_n) ==
+                   ("settle128", "fp64", "pull", "supersample", 0))
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     w = make_workload(args.workload)
+    w.eps_mode = args.eps
+    if args.eps_n:
+        w.eps_n = args.eps_n
+    elif args.eps == "mlp":
+        w.eps_n = 8
 
     if args.impl == "reference":
         import oracle
@@ -407,6 +429,9 @@ def main():
         dist.barrier()
 
     e = make_engine(w, capi, precision=args.precision, streaming=args.streaming)
+    if args.eps == "mlp":
+        params, _ = train_surrogate(capi)
+        e.set_mlp(params)
     e.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -503,7 +528,7 @@ def main():
         forms["settling"] = forms_settling(capi, torch, forms.pop("_params"), 20)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w.eps_mode != "mlp":
         import oracle
         oracle.build()
         v, nst, dt = oracle_rate(w, args.cpu_seconds, 1000)

@@ -69,21 +69,25 @@ template <int N>
 __device__ inline int supersample_count_n(double dx, double dy, double dz, double r, float dxf,
                                           float dyf, float dzf, float r2f, float E) {
   const float lo = r2f - E, hi = r2f + E;
-  float X[N], Y[N], Z[N];
+  float Y[N], Z[N];
 #pragma unroll
   for (int a = 0; a < N; ++a) {
     const float s = (float)((a + 0.5) / N - 0.5);
-    const float px = dxf + s, py = dyf + s, pz = dzf + s;
-    X[a] = px * px;
+    const float py = dyf + s, pz = dzf + s;
     Y[a] = py * py;
     Z[a] = pz * pz;
   }
   int in = 0, maybe = 0;
-#pragma unroll
+  // the x samples stay a loop for N = 8 (64 samples per pass): the fully
+  // unrolled 512 samples overflow the instruction cache
+#pragma unroll(N <= 4 ? N : 1)
   for (int a = 0; a < N; ++a) {
+    // (a + 1/2)/N - 1/2 is exact in FP32 for N a power of two
+    const float px = dxf + (((float)a + 0.5f) * (1.0f / N) - 0.5f);
+    const float Xa = px * px;
 #pragma unroll
     for (int b = 0; b < N; ++b) {
-      const float XY = X[a] + Y[b];
+      const float XY = Xa + Y[b];
 #pragma unroll
       for (int c = 0; c < N; ++c) {
         const float S = XY + Z[c];

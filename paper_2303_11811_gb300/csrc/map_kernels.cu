@@ -156,10 +156,6 @@ __device__ __forceinline__ double weight(double eps, double tau, int nt) {
 __device__ __forceinline__ long long rec_w(const MapParams& P, long long e, int s) {
   return 4 * (s * P.s.cap + e) + 3;
 }
-__device__ __forceinline__ void store_B(const MapParams& P, long long e, int s, double B) {
-  if (P.fp32) static_cast<float*>(P.s.V)[rec_w(P, e, s)] = (float)B;
-  else static_cast<double*>(P.s.V)[rec_w(P, e, s)] = B;
-}
 __device__ __forceinline__ double load_B(const MapParams& P, long long e, int s) {
   if (P.fp32) return (double)static_cast<const float*>(P.s.V)[rec_w(P, e, s)];
   return static_cast<const double*>(P.s.V)[rec_w(P, e, s)];
@@ -375,6 +371,49 @@ __global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
   }
 }
 
+// a cell of a particle's box (box index t): coordinates, FP64 offsets from
+// the centre and their FP32 roundings (from the per-block tables when the
+// box fits them), FP32 squared distance
+__device__ __forceinline__ void cell_hit(const Grid& g, const Box& b, int t, bool tables,
+                                         const double (*toff)[FILL_AXIS],
+                                         const float (*toff32)[FILL_AXIS], CellHit& h) {
+  box_coords(g, b, t, h);
+  if (tables) {
+    const int i0 = h.kx - b.lo[0], i1 = h.ky - b.lo[1], i2 = h.kz - b.lo[2];
+    h.dx = toff[0][i0];
+    h.dy = toff[1][i1];
+    h.dz = toff[2][i2];
+    h.dxf = toff32[0][i0];
+    h.dyf = toff32[1][i1];
+    h.dzf = toff32[2][i2];
+  } else {
+    h.dx = ((double)h.kx + 0.5) - b.xp[0];
+    h.dy = ((double)h.ky + 0.5) - b.xp[1];
+    h.dz = ((double)h.kz + 0.5) - b.xp[2];
+    h.dxf = (float)h.dx;
+    h.dyf = (float)h.dy;
+    h.dzf = (float)h.dz;
+  }
+  // FP32 squared distance of the inside test (its band is certified for
+  // the components rounded from FP64 as well as for the box-local form)
+  h.d2f = h.dxf * h.dxf + h.dyf * h.dyf + h.dzf * h.dzf;
+  h.d2 = -1.0;  // formed where a decision needs it
+}
+
+// surrogate mode (reading I): 1 = inside by the margin (eps = 1), 2 = a
+// partial cell next to a wall face (8^3 sampling), 0 = any other partial
+// cell (the network)
+__device__ __forceinline__ int net_class(const Grid& g, const Box& b, const CellHit& h) {
+  if (b.has_in) {
+    if (h.d2f < b.rin2f - b.E) return 1;
+    if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2) return 1;
+  }
+  const bool wallcell = (g.wall[0] && (h.ix == 0 || h.ix == g.nx - 1)) ||
+                        (g.wall[1] && (h.iy == 0 || h.iy == g.ny - 1)) ||
+                        (g.wall[2] && (h.iz == 0 || h.iz == g.nz - 1));
+  return wallcell ? 2 : 0;
+}
+
 // Slots of one particle's cells (one block per particle, over the list the
 // mark pass wrote): claims a slot per cell, writes B (Eq. 16, from a table
 // of the n^3 + 1 sampled values when eps is a count), and the particle's
@@ -413,31 +452,34 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   const float uf0 = (float)u0, uf1 = (float)u1, uf2 = (float)u2;
   const float of0 = (float)o0, of1 = (float)o1, of2 = (float)o2;
   const float* wtabf = reinterpret_cast<const float*>(wtab + WTAB);  // FP32 copy
+  const float rf = (float)b.r, rinvf = 1.0f / rf, frf = (float)fr;  // surrogate inputs
   const long long loff = P.list_off[p];
   const int cnt = P.list_cnt[p];
+  // surrogate mode: the block's network cells, its worklist range and next free index
+  __shared__ int net_cnt, net_base, net_next;
+  if constexpr (NS < 0) {
+    // count the block's network cells first and reserve their worklist
+    // range with one atomic (a counter shared by every block would serialise)
+    if (threadIdx.x == 0) net_cnt = 0;
+    __syncthreads();
+    int mine = 0;
+    for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
+      CellHit h;
+      cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
+      mine += net_class(P.g, b, h) == 0;
+    }
+    mine = __reduce_add_sync(0xffffffffu, mine);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&net_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      net_base = net_cnt ? atomicAdd(P.mlp_count, net_cnt) : 0;
+      net_next = net_base;
+    }
+    __syncthreads();
+  }
   for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
     CellHit h;
-    box_coords(P.g, b, P.list[loff + k], h);
-    if (tables) {
-      const int i0 = h.kx - b.lo[0], i1 = h.ky - b.lo[1], i2 = h.kz - b.lo[2];
-      h.dx = toff[0][i0];
-      h.dy = toff[1][i1];
-      h.dz = toff[2][i2];
-      h.dxf = toff32[0][i0];
-      h.dyf = toff32[1][i1];
-      h.dzf = toff32[2][i2];
-    } else {
-      h.dx = ((double)h.kx + 0.5) - b.xp[0];
-      h.dy = ((double)h.ky + 0.5) - b.xp[1];
-      h.dz = ((double)h.kz + 0.5) - b.xp[2];
-      h.dxf = (float)h.dx;
-      h.dyf = (float)h.dy;
-      h.dzf = (float)h.dz;
-    }
-    // FP32 squared distance of the inside test (its band is certified for
-    // the components rounded from FP64 as well as for the box-local form)
-    h.d2f = h.dxf * h.dxf + h.dyf * h.dyf + h.dzf * h.dzf;
-    h.d2 = -1.0;  // formed where a decision needs it
+    cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
     const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
     const long long e = slot_index(P.cov, cell);
     if (e >= P.s.cap) {
@@ -454,7 +496,24 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
     double B;
     float Bf = 0.f;
-    if (tab) {
+    bool want = false;  // surrogate mode: the cell goes to the network's worklist
+    if constexpr (NS < 0) {
+      // surrogate mode (reading I): inside by the margin -> 1; a partial
+      // cell next to a wall face -> 8^3 sampling; any other partial cell ->
+      // the network (B stays -1 until the inference writes it)
+      const int cls = net_class(P.g, b, h);
+      if (cls == 1) {
+        B = 1.0;
+      } else if (cls == 2) {
+        const int c = supersample_count_n<8>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f,
+                                             b.E);
+        B = weight((double)c * (1.0 / 512.0), P.tau, P.weighting);
+      } else {
+        B = -1.0;
+        want = true;
+      }
+      Bf = (float)B;
+    } else if (tab) {
       const int c = cell_count<NS>(P, b, h, s64, s32);
       if (P.fp32) Bf = __ldg(&wtabf[c]);
       else B = __ldg(&wtab[c]);
@@ -479,51 +538,44 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       R[0] = make_double2(v0, v1);
       R[1] = make_double2(v2, B);
     }
+    if constexpr (NS < 0) {
+      // worklist append within the block's range, one shared-memory atomic
+      // per group of converged lanes: the
+      // network's inputs (|d/r| components in decreasing order, r), the
+      // linear approximation of Eqs. 25-27, and 2 * entry + slot.  Items
+      // beyond the worklist's capacity keep B = -1 (8^3 sampling later).
+      const unsigned grp = __activemask();
+      const unsigned wm = __ballot_sync(grp, want);
+      if (want) {
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(wm) - 1;
+        int first = 0;
+        if (lane == leader) first = atomicAdd(&net_next, __popc(wm));
+        first = __shfl_sync(wm, first, leader);
+        const long long k = (long long)first + __popc(wm & ((1u << lane) - 1u));
+        if (k < P.mlp_cap) {
+          float a0 = fabsf(h.dxf) * rinvf, a1 = fabsf(h.dyf) * rinvf, a2 = fabsf(h.dzf) * rinvf;
+          float t;
+          if (a1 > a0) { t = a0; a0 = a1; a1 = t; }
+          if (a2 > a0) { t = a0; a0 = a2; a2 = t; }
+          if (a2 > a1) { t = a1; a1 = a2; a2 = t; }
+          reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4(a0, a1, a2, rf);
+          const float lin = (rf - sqrtf(h.d2f)) + frf;
+          P.mlp_lin[k] = lin < 0.f ? 0.f : (lin > 1.f ? 1.f : lin);
+          P.mlp_work[k] = (int)(2 * e + s);
+        }
+      }
+    }
   }
-}
-
-// surrogate mode: a partial cell within reach of exactly one particle and not
-// next to a wall face goes to the network's worklist with its inputs (|d/r|
-// in decreasing order, r) and its linear approximation (Eqs. 25-27); the
-// finish pass samples every other pending cell with 8^3 points
-__global__ void classify_kernel(MapParams P) {
-  const int n = slot_count(P);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    if (P.s.cnt[e] != 1) continue;
-    const int2 pid = P.s.pid[e];
-    if (pid.x < 0 || load_B(P, e, 0) >= 0.0) continue;
-    int x, y, z;
-    cell_xyz(P.g, P.s.cell[e], x, y, z);
-    const bool wall = (P.g.wall[0] && (x == 0 || x == P.g.nx - 1)) ||
-                      (P.g.wall[1] && (y == 0 || y == P.g.ny - 1)) ||
-                      (P.g.wall[2] && (z == 0 || z == P.g.nz - 1));
-    if (wall) continue;
-    const int p = pid.x;
-    const double r = P.p.r[p];
-    const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-    const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-    const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-    double a = fabs(dx / r), b = fabs(dy / r), c = fabs(dz / r), t;
-    if (b > a) { t = a; a = b; b = t; }
-    if (c > a) { t = a; a = c; c = t; }
-    if (c > b) { t = b; b = c; c = t; }
-    const double dist = sqrt(dx * dx + dy * dy + dz * dz);
-    double lin = -(dist - r) + P.p.fr[p];
-    lin = lin < 0.0 ? 0.0 : (lin > 1.0 ? 1.0 : lin);
-    const int k = atomicAdd(P.mlp_count, 1);
-    reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4((float)a, (float)b, (float)c, (float)r);
-    P.mlp_lin[k] = lin;
-    P.mlp_work[k] = e;
-  }
-}
-
-__global__ void apply_mlp_kernel(MapParams P) {
-  const int n = *P.mlp_count;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-    const int e = P.mlp_work[k];
-    double eps = P.mlp_lin[k] + (double)P.mlp_eps[k];
-    eps = eps < 0.0 ? 0.0 : (eps > 1.0 ? 1.0 : eps);
-    store_B(P, e, 0, weight(eps, P.tau, P.weighting));
+  if constexpr (NS < 0) {
+    // cells counted but not listed (slot overflow) leave empty items
+    __syncthreads();
+    const long long end = (long long)net_base + net_cnt;
+    for (long long k = net_next + threadIdx.x; k < end && k < P.mlp_cap; k += MAP_THREADS) {
+      reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      P.mlp_lin[k] = 0.f;
+      P.mlp_work[k] = -1;
+    }
   }
 }
 
@@ -548,45 +600,116 @@ __device__ __forceinline__ void rec_store(double* p, const double* o) {
   reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
 }
 
-// cells left for the surrogate and not taken by it: 8^3 sampling (rare;
-// kept out of line so that its registers do not weigh on the common path)
-template <typename T>
-__device__ __noinline__ void pending_weights(const MapParams& P, int e, int2 pid, T& B0, T& B1) {
-  int x, y, z;
-  cell_xyz(P.g, P.s.cell[e], x, y, z);
-  for (int sl = 0; sl < 2; ++sl) {
-    const int p = sl ? pid.y : pid.x;
-    T& Bs = sl ? B1 : B0;
-    if (p < 0 || Bs >= T(0)) continue;
-    const double r = P.p.r[p];
-    const double dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-    const double dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-    const double dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-    const double eps = (double)supersample_count_n<8>(dx, dy, dz, r) * (1.0 / 512.0);
-    Bs = (T)weight(eps, P.tau, P.weighting);
+// 8^3 sampled count of a cell for one sphere by a whole warp (every lane
+// passes the same arguments): lane l takes the sample columns (a, b) =
+// (l / 4, 2 (l % 4) + {0, 1}), 16 samples, with the certified FP32 test of
+// geom.cuh; if any lane has a sample inside the band, every lane recounts
+// its samples with the FP64 definition inside the band.  Same count as the
+// FP64 definition.
+__device__ int warp_count8(double dx, double dy, double dz, double r) {
+  const int lane = threadIdx.x & 31;
+  const float dxf = (float)dx, dyf = (float)dy, dzf = (float)dz;
+  const double r2 = r * r;
+  const float r2f = (float)r2, E = certified_band(r);
+  const float lo = r2f - E, hi = r2f + E;
+  const int a = lane >> 2;
+  const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
+  const float Xa = px * px;
+  float Z[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+    Z[c] = pz * pz;
   }
-}
-
-template <typename T>
-__device__ double finish_entry(const MapParams& P, int e) {
-  int2 pid = P.s.pid[e];
-  const bool two = pid.y >= 0;
-  const long long e1 = P.s.cap + e;
-  T* V = static_cast<T*>(P.s.V);
-  T r0[4], r1[4] = {T(0), T(0), T(0), T(0)};
-  rec_load(V + 4 * e, r0);
-  if (two) rec_load(V + 4 * e1, r1);
-  if (two && pid.y < pid.x) {
-    const int t = pid.x;
-    pid.x = pid.y;
-    pid.y = t;
-    for (int a = 0; a < 4; ++a) {
-      const T v = r0[a];
-      r0[a] = r1[a];
-      r1[a] = v;
+  float XY[2];
+  int in = 0, maybe = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int bb = 2 * (lane & 3) + j;
+    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+    XY[j] = Xa + py * py;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float S = XY[j] + Z[c];
+      in += S < lo;
+      maybe += S <= hi;
     }
   }
-  if (r0[3] < T(0) || r1[3] < T(0)) pending_weights<T>(P, e, pid, r0[3], r1[3]);
+  if (__any_sync(0xffffffffu, in != maybe)) {
+    in = 0;
+    for (int j = 0; j < 2; ++j) {
+      const int bb = 2 * (lane & 3) + j;
+      for (int c = 0; c < 8; ++c) {
+        const float S = XY[j] + Z[c];
+        if (S < lo) ++in;
+        else if (S <= hi && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
+                                               sample_offset(bb, 8), sample_offset(c, 8), r2))
+          ++in;
+      }
+    }
+  }
+  return __reduce_add_sync(0xffffffffu, in);
+}
+
+// one slot entry of the finish pass in the storage precision T, taken by a
+// whole warp (lanes with e >= n take part in the sampling only): order the two
+// slots by particle index, sample the slots left pending (B < 0: cells of two
+// particles in surrogate mode, worklist overflow, no network) with 8^3 points,
+// normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
+// weight; returns min(B, 1) (0 for lanes without an entry)
+template <typename T>
+__device__ double finish_entry(const MapParams& P, int e, int n) {
+  const bool live = e < n;
+  int2 pid = make_int2(-1, -1);
+  T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
+  T* V = static_cast<T*>(P.s.V);
+  const long long e1 = P.s.cap + e;
+  bool two = false;
+  if (live) {
+    pid = P.s.pid[e];
+    two = pid.y >= 0;
+    rec_load(V + 4 * e, r0);
+    if (two) rec_load(V + 4 * e1, r1);
+    if (two && pid.y < pid.x) {
+      const int t = pid.x;
+      pid.x = pid.y;
+      pid.y = t;
+      for (int a = 0; a < 4; ++a) {
+        const T v = r0[a];
+        r0[a] = r1[a];
+        r1[a] = v;
+      }
+    }
+  }
+  // pending slots, one warp-wide count each
+  const unsigned full = 0xffffffffu;
+  unsigned pend = __ballot_sync(full, live && r0[3] < T(0));          // slot 0 pending
+  unsigned pend1 = __ballot_sync(full, live && two && r1[3] < T(0));  // slot 1 pending
+  while (pend | pend1) {
+    const bool s1 = pend == 0u;
+    const int L = __ffs(s1 ? pend1 : pend) - 1;
+    if (s1) pend1 &= pend1 - 1u; else pend &= pend - 1u;
+    double dx = 0.0, dy = 0.0, dz = 0.0, r = 0.0;
+    if ((threadIdx.x & 31) == L) {
+      int x, y, z;
+      cell_xyz(P.g, P.s.cell[e], x, y, z);
+      const int p = s1 ? pid.y : pid.x;
+      r = P.p.r[p];
+      dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+      dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+      dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+    }
+    dx = __shfl_sync(full, dx, L);
+    dy = __shfl_sync(full, dy, L);
+    dz = __shfl_sync(full, dz, L);
+    r = __shfl_sync(full, r, L);
+    const int cnt = warp_count8(dx, dy, dz, r);
+    if ((threadIdx.x & 31) == L) {
+      const T B = (T)weight((double)cnt * (1.0 / 512.0), P.tau, P.weighting);
+      if (s1) r1[3] = B; else r0[3] = B;
+    }
+  }
+  if (!live) return 0.0;
   T B = r0[3] + r1[3];
   if (B > T(1)) {
     r0[3] = r0[3] / B;
@@ -606,8 +729,12 @@ __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   __shared__ double red[256];
   const int n = slot_count(P);
   double accB = 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    accB += P.fp32 ? finish_entry<float>(P, e) : finish_entry<double>(P, e);
+  // warp-uniform loop: every lane of a warp runs the same iterations
+  const int stride = gridDim.x * blockDim.x;
+  for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += stride) {
+    const int e = e0 + (threadIdx.x & 31);
+    accB += P.fp32 ? finish_entry<float>(P, e, n) : finish_entry<double>(P, e, n);
+  }
   red[threadIdx.x] = accB;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -878,7 +1005,8 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
   clear_slots_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
   launches += 4;
   if (P.p.n > 0) {
-    if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    if (mlp) fill_kernel<-1><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    else if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4><<<P.p.n, MAP_THREADS, 0, s>>>(P);
     else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8><<<P.p.n, MAP_THREADS, 0, s>>>(P);
     else fill_kernel<0><<<P.p.n, MAP_THREADS, 0, s>>>(P);
     ++launches;
@@ -895,22 +1023,27 @@ int map_finish(MapParams P, cudaStream_t s) {
 
 }  // namespace
 
-int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
-                         const float* X, float* eps, cudaStream_t s);
-
 int launch_map(MapParams P, cudaStream_t s) {
   return map_common(P, s, false) + map_finish(P, s);
 }
 
-// mapping with the surrogate: the network runs on the tensor cores for the
-// worklist between the fill and finish passes
+// mapping with the surrogate: the fill pass lists the network's cells, the
+// network runs on the tensor cores and writes their B, the finish pass
+// samples what is left (cells of two particles, worklist overflow, no
+// network set) with 8^3 points
 int launch_map_mlp(MapParams P, cudaStream_t s) {
   int launches = map_common(P, s, true);
-  if (P.mlp) {
-    classify_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
-    launches += launch_mlp_infer_dev(P.mlp, P.mlp_count, P.s.cap, P.mlp_X, P.mlp_eps, s);
-    apply_mlp_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
-    launches += 2;
+  if (P.mlp && P.mlp_cap > 0) {
+    InferSink out{};
+    out.V = P.s.V;
+    out.cnt = P.s.cnt;
+    out.lin = P.mlp_lin;
+    out.work = P.mlp_work;
+    out.cap = P.s.cap;
+    out.fp32 = P.fp32;
+    out.nt = P.weighting;
+    out.tau = P.tau;
+    launches += launch_mlp_infer(P.mlp, -1, P.mlp_count, P.mlp_cap, P.mlp_X, out, P.status, s);
   }
   return launches + map_finish(P, s);
 }

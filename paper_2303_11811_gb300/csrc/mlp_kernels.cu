@@ -23,10 +23,10 @@
 // tiles are reduced in a fixed order; Adam (Kingma and Ba, 2015) updates the
 // FP32 master weights.
 //
-// Inference: per warp, tiles of 16 inputs; layer 1 (K = 4) in FP32, layer 2
-// on the tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation,
-// the layer-1 accumulator fragments reused as the A operand), layer 3 (N = 1)
-// as FP32 dot products reduced across the quad of lanes that holds a row.
+// Inference: tiles of 128 inputs per CTA; layer 1 (K = 4) in FP32, layer 2
+// on the 5th-generation tensor cores (tcgen05.mma, BF16 operands from shared
+// memory, FP32 accumulator in tensor memory), layer 3 (N = 1) in FP32 after
+// tcgen05.ld; in the mapping the same kernel turns the outputs into B.
 #include <cuda_bf16.h>
 
 #include "geom.cuh"
@@ -219,99 +219,266 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g,
   p[i] -= lr * mh / (sqrtf(vh) + 1e-8f);
 }
 
-// ---- inference
+// ---- inference on the 5th-generation tensor cores.  One CTA of 128
+// threads takes tiles of 128 inputs: each thread computes its row's layer 1
+// in FP32 and writes the ReLU activations as BF16 into shared memory in the
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix); one thread
+// issues the layer-2 product h1 (128 x 32) x W2^T (32 x 32) as two
+// tcgen05.mma (K = 16 each, BF16 operands) with the FP32 accumulator in
+// tensor memory (32 columns); after the commit arrives on the mbarrier each
+// warp reads its 32 rows back with tcgen05.ld and finishes layer 3 (bias,
+// ReLU, dot with W3) in FP32.  Waits are bounded: a wait that gives up sets
+// ST_TIMEOUT, waits once more for the tensor core and frees its tensor memory.
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
+constexpr int INF_M = 128;         // rows per tile: the MMA's M
+constexpr int INF_THREADS = 128;   // thread t owns row t; warp w reads TMEM lanes 32w..32w+31
+constexpr unsigned INF_TMEM_COLS = 32;  // FP32 accumulator, N = 32 columns
+constexpr unsigned long long kInferWaitNs = 1000000000ull;
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N / 8 at
+// bits 17-22, M / 16 at bits 24-28
+constexpr uint32_t kInferIdesc =
+    (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((unsigned)(INF_M >> 4) << 24);
+
+struct InferSmem {
+  alignas(128) unsigned char a[INF_M * 32 * 2];  // layer-1 activations, BF16
+  alignas(128) unsigned char b[32 * 32 * 2];     // W2 (N = 32 rows of K = 32), BF16
+  float4 w1[32];
+  float b1[32], b2[32], w3[32];
+  float b3;
+  unsigned tmem;
+  unsigned long long bar;
+};
+
+// byte offset of the 16-byte chunk kc (elements 8kc..8kc+7) of row `row` in
+// the K-major layout without swizzle: core matrices of 8 rows x 16 bytes, the
+// K direction's four core matrices 128 bytes apart (leading byte offset),
+// successive groups of 8 rows 512 bytes apart (stride byte offset)
+__device__ __forceinline__ int kmajor_off(int row, int kc) {
+  return (row >> 3) * 512 + kc * 128 + (row & 7) * 16;
+}
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+// shared-memory matrix descriptor of tcgen05: start address >> 4 (bits 0-13),
+// leading byte offset >> 4 (bits 16-29), stride byte offset >> 4 (bits
+// 32-45), the fixed value 1 at bits 46-48, base offset 0, no swizzle
+__device__ __forceinline__ uint64_t kmajor_desc(const void* p) {
+  return (uint64_t)((smem_addr(p) & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
+         ((uint64_t)(512 >> 4) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ bool inf_mbar_test(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __noinline__ bool inf_mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (inf_mbar_test(bar, parity)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    for (int i = 0; i < 64; ++i)
+      if (inf_mbar_test(bar, parity)) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kInferWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tc_mma_bf16(unsigned d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(kInferIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes, one lane per thread
+__device__ __forceinline__ void tc_ld32(unsigned taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// raw network outputs for inputs X; count: number of inputs, read from
-// *count_dev when count < 0
-__global__ void __launch_bounds__(128) infer_kernel(const float* __restrict__ P, long long count,
-                                                   const int* __restrict__ count_dev,
-                                                   const float4* __restrict__ X,
-                                                   float* __restrict__ eps) {
-  const long long n = count >= 0 ? count : (long long)*count_dev;
-  const int lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  // layer-1 neurons this lane produces: j = 8c + 2t + {0,1}, c = 0..3
-  float w1[8][4], b1[8];
-  for (int c = 0; c < 4; ++c)
-    for (int h = 0; h < 2; ++h) {
-      const int j = 8 * c + 2 * t + h;
-      for (int k = 0; k < 4; ++k) w1[2 * c + h][k] = P[j * 4 + k];
-      b1[2 * c + h] = P[OFF_B1 + j];
+// B(eps) of Eq. 16 in the storage precision of the slot records
+__device__ __forceinline__ void apply_weight(const InferSink& o, long long rec, float epsf) {
+  if (o.fp32) {
+    float B = epsf;
+    if (o.nt && epsf != 0.f && epsf != 1.f) {
+      const float tm = (float)(o.tau - 0.5);
+      B = epsf * tm / ((1.f - epsf) + tm);
     }
-  // layer-2 B fragments: n-tile nt (outputs 8nt + g), k-step ks
-  uint32_t bw[4][2][2];
-  for (int nt = 0; nt < 4; ++nt)
-    for (int ks = 0; ks < 2; ++ks) {
-      const float* row = P + OFF_W2 + (8 * nt + g) * 32 + 16 * ks;
-      bw[nt][ks][0] = pack_bf16(row[2 * t], row[2 * t + 1]);
-      bw[nt][ks][1] = pack_bf16(row[8 + 2 * t], row[8 + 2 * t + 1]);
-    }
-  float b2[8], w3[8];
-  for (int nt = 0; nt < 4; ++nt)
-    for (int h = 0; h < 2; ++h) {
-      b2[2 * nt + h] = P[OFF_B2 + 8 * nt + 2 * t + h];
-      w3[2 * nt + h] = P[OFF_W3 + 8 * nt + 2 * t + h];
-    }
-  const float b3 = P[OFF_B3];
+    static_cast<float*>(o.V)[4 * rec + 3] = B;
+  } else {
+    const double eps = (double)epsf;
+    double B = eps;
+    if (o.nt && eps != 0.0 && eps != 1.0) B = eps * (o.tau - 0.5) / ((1.0 - eps) + (o.tau - 0.5));
+    static_cast<double*>(o.V)[4 * rec + 3] = B;
+  }
+}
 
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  const long long ntiles = (n + 15) / 16;
-  for (long long tile = warp; tile < ntiles; tile += nwarps) {
-    const long long r0 = tile * 16 + g, r1 = r0 + 8;
-    const float4 x0 = r0 < n ? X[r0] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 x1 = r1 < n ? X[r1] : make_float4(0.f, 0.f, 0.f, 0.f);
-    // layer 1 in FP32, ReLU, packed as the A fragments of layer 2
-    float h0[8], h1v[8];
-    for (int i = 0; i < 8; ++i) {
-      float a = b1[i], b = b1[i];
-      a = fmaf(w1[i][0], x0.x, a); a = fmaf(w1[i][1], x0.y, a);
-      a = fmaf(w1[i][2], x0.z, a); a = fmaf(w1[i][3], x0.w, a);
-      b = fmaf(w1[i][0], x1.x, b); b = fmaf(w1[i][1], x1.y, b);
-      b = fmaf(w1[i][2], x1.z, b); b = fmaf(w1[i][3], x1.w, b);
-      h0[i] = a > 0.f ? a : 0.f;
-      h1v[i] = b > 0.f ? b : 0.f;
+// raw network outputs (o.eps != NULL) or, in the mapping, eps = clamp(linear
+// approximation + output, 0, 1) and its weight B into the item's slot record
+// when the cell is within reach of this particle only (cells shared by two
+// particles keep B = -1 and are sampled by the finish pass).  count: number
+// of inputs, read from *count_dev when count < 0, at most cap.
+__global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
+    const float* __restrict__ P, long long count, const int* __restrict__ count_dev,
+    long long cap, const float4* __restrict__ X, InferSink o, unsigned* status) {
+  __shared__ InferSmem S;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  long long n = count >= 0 ? count : (long long)*count_dev;
+  if (n > cap) n = cap;
+  // W2 as the B operand (row j = output neuron, K = input neuron), the
+  // other parameters in FP32
+  for (int i = tid; i < 32 * 4; i += INF_THREADS) {
+    const int j = i >> 2, kc = i & 3;
+    const float* w = P + OFF_W2 + j * 32 + kc * 8;
+    *reinterpret_cast<uint4*>(S.b + kmajor_off(j, kc)) =
+        make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                   pack_bf16(w[6], w[7]));
+  }
+  if (tid < 32) {
+    S.w1[tid] = make_float4(P[4 * tid], P[4 * tid + 1], P[4 * tid + 2], P[4 * tid + 3]);
+    S.b1[tid] = P[OFF_B1 + tid];
+    S.b2[tid] = P[OFF_B2 + tid];
+    S.w3[tid] = P[OFF_W3 + tid];
+  }
+  if (tid == 0) {
+    S.b3 = P[OFF_B3];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&S.bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&S.tmem)),
+                 "r"(INF_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();  // W2 was written by the generic proxy, the MMA reads it
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = S.tmem;
+  const uint64_t ad0 = kmajor_desc(S.a), ad1 = kmajor_desc(S.a + 256);
+  const uint64_t bd0 = kmajor_desc(S.b), bd1 = kmajor_desc(S.b + 256);
+  const long long ntiles = (n + INF_M - 1) / INF_M;
+  unsigned phase = 0;
+  bool in_flight = false;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long row = tile * INF_M + tid;
+    const bool live = row < n;
+    const float4 x = live ? X[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // layer 1 (FP32), ReLU, BF16 activations into the A operand
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        float v[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int j = 8 * kc + 2 * h + e;
+          const float4 wj = S.w1[j];
+          float a = S.b1[j];
+          a = fmaf(wj.x, x.x, a);
+          a = fmaf(wj.y, x.y, a);
+          a = fmaf(wj.z, x.z, a);
+          a = fmaf(wj.w, x.w, a);
+          v[e] = a > 0.f ? a : 0.f;
+        }
+        w[h] = pack_bf16(v[0], v[1]);
+      }
+      *reinterpret_cast<uint4*>(S.a + kmajor_off(tid, kc)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
-    uint32_t A[2][4];
-    for (int ks = 0; ks < 2; ++ks) {
-      // k = 16ks + 2t (+1) -> neuron index i = 2*(2ks) + h; k + 8 -> 2*(2ks+1) + h
-      A[ks][0] = pack_bf16(h0[4 * ks + 0], h0[4 * ks + 1]);
-      A[ks][1] = pack_bf16(h1v[4 * ks + 0], h1v[4 * ks + 1]);
-      A[ks][2] = pack_bf16(h0[4 * ks + 2], h0[4 * ks + 3]);
-      A[ks][3] = pack_bf16(h1v[4 * ks + 2], h1v[4 * ks + 3]);
+    fence_async_smem();
+    __syncthreads();
+    bool done = true;
+    if (tid == 0) {
+      tc_fence_after();
+      tc_mma_bf16(tmem, ad0, bd0, 0);
+      tc_mma_bf16(tmem, ad1, bd1, 1);
+      tc_commit(&S.bar);
+      done = inf_mbar_wait(&S.bar, phase);
     }
-    float y0 = 0.f, y1 = 0.f;
-    for (int nt = 0; nt < 4; ++nt) {
-      float c[4] = {0.f, 0.f, 0.f, 0.f};
-      mma_bf16(c, A[0], bw[nt][0]);
-      mma_bf16(c, A[1], bw[nt][1]);
-      for (int h = 0; h < 2; ++h) {
-        const float v0 = c[h] + b2[2 * nt + h];
-        const float v1 = c[2 + h] + b2[2 * nt + h];
-        y0 = fmaf(w3[2 * nt + h], v0 > 0.f ? v0 : 0.f, y0);
-        y1 = fmaf(w3[2 * nt + h], v1 > 0.f ? v1 : 0.f, y1);
+    in_flight = true;
+    if (!__syncthreads_and(done)) {
+      if (tid == 0) atomicOr(status, ST_TIMEOUT);
+      break;
+    }
+    in_flight = false;
+    phase ^= 1u;
+    tc_fence_after();
+    float acc[32];
+    tc_ld32(tmem + ((unsigned)(warp * 32) << 16), acc);
+    float y = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float v = acc[j] + S.b2[j];
+      y = fmaf(S.w3[j], v > 0.f ? v : 0.f, y);
+    }
+    y += S.b3;
+    if (live) {
+      if (o.eps) {
+        o.eps[row] = y;
+      } else {
+        const int item = o.work[row];  // -1: an empty item
+        const long long e = item >> 1;
+        if (item >= 0 && __ldg(&o.cnt[e]) == 1) {
+          float eps = o.lin[row] + y;
+          eps = eps < 0.f ? 0.f : (eps > 1.f ? 1.f : eps);
+          apply_weight(o, (item & 1) * o.cap + e, eps);
+        }
       }
     }
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 1);
-    y0 += __shfl_xor_sync(0xffffffffu, y0, 2);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 1);
-    y1 += __shfl_xor_sync(0xffffffffu, y1, 2);
-    if (t == 0) {
-      if (r0 < n) eps[r0] = y0 + b3;
-      if (r1 < n) eps[r1] = y1 + b3;
-    }
+    tc_fence_before();
+    __syncthreads();  // the A tile and the accumulator are free again
+  }
+  if (in_flight && tid == 0) inf_mbar_wait(&S.bar, phase);  // the MMA of a wait that gave up
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(INF_TMEM_COLS)
+                 : "memory");
   }
 }
 
@@ -351,25 +518,16 @@ int launch_adam(float* params, const float* grad, float* mstate, float* vstate, 
   return 1;
 }
 
-int launch_mlp_infer(const float* params, long long m, const float* X, float* eps,
-                     cudaStream_t s) {
-  if (m <= 0) return 0;
-  long long tiles = (m + 15) / 16;
-  long long blocks = (tiles + 3) / 4;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(params, m, nullptr,
-                                               reinterpret_cast<const float4*>(X), eps);
-  return 1;
-}
-
-int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
-                         const float* X, float* eps, cudaStream_t s) {
-  long long tiles = (cap + 15) / 16;
-  long long blocks = (tiles + 3) / 4;
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  if (blocks < 1) blocks = 1;
-  infer_kernel<<<(unsigned)blocks, 128, 0, s>>>(params, -1, count_dev,
-                                               reinterpret_cast<const float4*>(X), eps);
+// network outputs for m inputs (m_dev: count on the device, m < 0), at most
+// cap; results to the sink
+int launch_mlp_infer(const float* params, long long m, const int* m_dev, long long cap,
+                     const float* X, const InferSink& out, unsigned* status, cudaStream_t s) {
+  const long long rows = m >= 0 ? (m < cap ? m : cap) : cap;
+  if (rows <= 0) return 0;
+  long long blocks = (rows + INF_M - 1) / INF_M;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  infer_tc_kernel<<<(unsigned)blocks, INF_THREADS, 0, s>>>(
+      params, m, m_dev, cap, reinterpret_cast<const float4*>(X), out, status);
   return 1;
 }
 

@@ -13,8 +13,6 @@
 #include "psm_internal.cuh"
 
 namespace psm {
-int launch_mlp_infer_dev(const float* params, const int* count_dev, long long cap,
-                         const float* X, float* eps, cudaStream_t s);
 int launch_map_mlp(MapParams P, cudaStream_t s);
 }
 
@@ -67,8 +65,7 @@ struct psm_ctx {
   float* mlp = nullptr;   // FP32 parameters on the device
   bool have_mlp = false;
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
-  float* mlp_eps = nullptr;
-  double* mlp_lin = nullptr; // linear approximation per worklist item
+  float* mlp_lin = nullptr;  // linear approximation per worklist item
   int* mlp_work = nullptr;   // entry index per worklist item
   int* mlp_count = nullptr;
   long long mlp_cap = 0;
@@ -144,7 +141,6 @@ void free_particles(psm_ctx* c) {
   c->p = Particles{};
   c->slots = Slots{};
   c->mlp_X = nullptr;
-  c->mlp_eps = nullptr;
   c->mlp_lin = nullptr;
   c->mlp_work = nullptr;
   c->mlp_cap = 0;
@@ -180,8 +176,8 @@ MapParams map_params(psm_ctx* c) {
   P.wtab = c->have_wtab ? c->wtab : nullptr;
   P.partials = c->partials;
   P.mlp_X = c->mlp_X;
-  P.mlp_eps = c->mlp_eps;
   P.mlp_lin = c->mlp_lin;
+  P.mlp_cap = c->mlp_cap;
   P.mlp_work = c->mlp_work;
   P.mlp_count = c->mlp_count;
   P.list_off = c->list_off;
@@ -595,8 +591,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   if (c->opt.eps_mode == PSM_EPS_MLP) {
     c->mlp_cap = (long long)cp;
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
-    c->mlp_eps = alloc_n<float>(c, cp, c->palloc);
-    c->mlp_lin = alloc_n<double>(c, cp, c->palloc);
+    c->mlp_lin = alloc_n<float>(c, cp, c->palloc);
     c->mlp_work = alloc_n<int>(c, cp, c->palloc);
   }
   for (void* q : c->palloc)
@@ -911,7 +906,9 @@ psm_status psm_mlp_infer(psm_ctx* c, const float* params, long m, const float* X
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dX, X, sizeof(float) * 4 * m, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
-    launch_mlp_infer(dp, m, dX, de, c->stream);
+    InferSink out{};
+    out.eps = de;
+    launch_mlp_infer(dp, m, nullptr, m, dX, out, c->status, c->stream);
     e = cudaMemcpyAsync(eps, de, sizeof(float) * m, cudaMemcpyDeviceToHost, c->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

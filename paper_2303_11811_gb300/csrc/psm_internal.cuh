@@ -159,12 +159,13 @@ struct MapParams {
                         // their FP32 roundings follow at (const float*)(wtab + 513)
   const float* mlp;     // FP32 parameters (PSM_MLP_PARAMS)
   double* partials;     // >= MAP_PARTIALS doubles of scratch
-  // surrogate worklist (eps mode 2): inputs, outputs, slot entry, count
+  // surrogate worklist (eps mode 2): network inputs, linear approximation,
+  // 2 * slot entry + slot, item count (at most mlp_cap items)
   float* mlp_X;
-  float* mlp_eps;
-  double* mlp_lin;      // linear approximation of each worklist cell
+  float* mlp_lin;
   int* mlp_work;
   int* mlp_count;
+  long long mlp_cap;
   // per-particle lists of covered slot entries (box order) for the
   // fixed-order force/torque reduction
   const long long* list_off;   // n+1 offsets
@@ -262,8 +263,20 @@ int launch_mlp_loss_grad(const float* params, long long m, const float* X, const
                          cudaStream_t s);
 int launch_adam(float* params, const float* grad, float* mstate, float* vstate, int step,
                 float lr, cudaStream_t s);
-int launch_mlp_infer(const float* params, long long m, const float* X, float* eps,
-                     cudaStream_t s);
+// where the network's outputs go: raw outputs (eps != NULL), or, in the
+// mapping, B of each worklist item's slot record
+struct InferSink {
+  float* eps;          // raw outputs, or NULL
+  void* V;             // Slots::V
+  const int* cnt;      // Slots::cnt
+  const float* lin;    // linear approximation (Eqs. 25-27) per item
+  const int* work;     // item -> 2 * slot entry + slot
+  long long cap;       // slot entries allocated
+  int fp32, nt;        // record precision; Noble-Torczynski weighting
+  double tau;
+};
+int launch_mlp_infer(const float* params, long long m, const int* m_dev, long long cap,
+                     const float* X, const InferSink& out, unsigned* status, cudaStream_t s);
 int mlp_grad_blocks(long long m);
 
 }  // namespace psm
