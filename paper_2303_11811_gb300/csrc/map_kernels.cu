@@ -371,6 +371,60 @@ __global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
   }
 }
 
+// 8^3 sampled count of a cell for one sphere by a whole warp: every lane
+// passes the same FP32 roundings of the offset d (dxf, dyf, dzf), of r^2
+// (r2f) and the certified band E of geom.cuh; the FP64 offset and r^2 are
+// taken from lane L.  Lane l takes the sample columns (a, b) = (l / 4,
+// 2 (l % 4) + {0, 1}), 16 samples, with the certified FP32 test; if any lane
+// has a sample inside the band, every lane recounts its samples with the FP64
+// definition inside the band.  Same count as the FP64 definition.
+__device__ int warp_count8(float dxf, float dyf, float dzf, float r2f, float E, int L, double dx,
+                           double dy, double dz, double r2) {
+  const int lane = threadIdx.x & 31;
+  const float lo = r2f - E, hi = r2f + E;
+  const int a = lane >> 2;
+  const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
+  const float Xa = px * px;
+  float Z[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+    Z[c] = pz * pz;
+  }
+  float XY[2];
+  int in = 0, maybe = 0;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int bb = 2 * (lane & 3) + j;
+    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+    XY[j] = Xa + py * py;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float S = XY[j] + Z[c];
+      in += S < lo;
+      maybe += S <= hi;
+    }
+  }
+  if (__any_sync(0xffffffffu, in != maybe)) {
+    dx = __shfl_sync(0xffffffffu, dx, L);
+    dy = __shfl_sync(0xffffffffu, dy, L);
+    dz = __shfl_sync(0xffffffffu, dz, L);
+    r2 = __shfl_sync(0xffffffffu, r2, L);
+    in = 0;
+    for (int j = 0; j < 2; ++j) {
+      const int bb = 2 * (lane & 3) + j;
+      for (int c = 0; c < 8; ++c) {
+        const float S = XY[j] + Z[c];
+        if (S < lo) ++in;
+        else if (S <= hi && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
+                                               sample_offset(bb, 8), sample_offset(c, 8), r2))
+          ++in;
+      }
+    }
+  }
+  return __reduce_add_sync(0xffffffffu, in);
+}
+
 // a cell of a particle's box (box index t): coordinates, FP64 offsets from
 // the centre and their FP32 roundings (from the per-block tables when the
 // box fits them), FP32 squared distance
@@ -477,23 +531,64 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     }
     __syncthreads();
   }
-  for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
+  // warp-uniform loop: every lane of a warp runs the same iterations (the
+  // 8^3 count is taken by the whole warp), lanes past the list idle
+  const int lane = threadIdx.x & 31;
+  const double r2 = b.r * b.r;
+  for (int k0 = threadIdx.x & ~31; k0 < cnt; k0 += MAP_THREADS) {
+    const int k = k0 + lane;
+    bool ok = k < cnt;
     CellHit h;
-    cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
-    const long long cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-    const long long e = slot_index(P.cov, cell);
-    if (e >= P.s.cap) {
-      P.list[loff + k] = 0;  // the step reports the slot overflow
-      continue;
+    h.dx = h.dy = h.dz = 0.0;
+    h.dxf = h.dyf = h.dzf = 0.f;
+    long long cell = 0, e = 0;
+    int s = 0;
+    if (ok) {
+      cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
+      cell = padded_cell(P.g, h.ix, h.iy, h.iz);
+      e = slot_index(P.cov, cell);
+      if (e >= P.s.cap) {
+        P.list[loff + k] = 0;  // the step reports the slot overflow
+        ok = false;
+      } else {
+        P.list[loff + k] = (int)e;
+        s = atomicAdd(&P.s.cnt[e], 1);
+        if (s >= 2) {
+          atomicOr(P.status, ST_SLOT_OVERFLOW);
+          ok = false;
+        } else {
+          P.s.cell[e] = (int)cell;
+          reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
+        }
+      }
     }
-    P.list[loff + k] = (int)e;
-    const int s = atomicAdd(&P.s.cnt[e], 1);
-    if (s >= 2) {
-      atomicOr(P.status, ST_SLOT_OVERFLOW);
-      continue;
+    // 8^3 sampling: a cell inside by the margin counts 512 without
+    // sampling; the partial cells of the warp are counted one after the
+    // other by all 32 lanes
+    int count8 = 512;
+    if constexpr (NS == 8) {
+      bool partial = false;
+      if (ok && tab) {
+        partial = true;
+        if (b.has_in) {
+          if (h.d2f < b.rin2f - b.E) partial = false;
+          else if (h.d2f <= b.rin2f + b.E &&
+                   h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
+            partial = false;
+        }
+      }
+      unsigned need = __ballot_sync(0xffffffffu, partial);
+      while (need) {
+        const int L = __ffs(need) - 1;
+        need &= need - 1u;
+        const float dxf = __shfl_sync(0xffffffffu, h.dxf, L);
+        const float dyf = __shfl_sync(0xffffffffu, h.dyf, L);
+        const float dzf = __shfl_sync(0xffffffffu, h.dzf, L);
+        const int c = warp_count8(dxf, dyf, dzf, b.r2f, b.E, L, h.dx, h.dy, h.dz, r2);
+        if (lane == L) count8 = c;
+      }
     }
-    P.s.cell[e] = (int)cell;
-    reinterpret_cast<int*>(&P.s.pid[e])[s] = p;
+    if (!ok) continue;
     double B;
     float Bf = 0.f;
     bool want = false;  // surrogate mode: the cell goes to the network's worklist
@@ -514,7 +609,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       }
       Bf = (float)B;
     } else if (tab) {
-      const int c = cell_count<NS>(P, b, h, s64, s32);
+      const int c = NS == 8 ? count8 : cell_count<NS>(P, b, h, s64, s32);
       if (P.fp32) Bf = __ldg(&wtabf[c]);
       else B = __ldg(&wtab[c]);
     } else {
@@ -600,57 +695,6 @@ __device__ __forceinline__ void rec_store(double* p, const double* o) {
   reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
 }
 
-// 8^3 sampled count of a cell for one sphere by a whole warp (every lane
-// passes the same arguments): lane l takes the sample columns (a, b) =
-// (l / 4, 2 (l % 4) + {0, 1}), 16 samples, with the certified FP32 test of
-// geom.cuh; if any lane has a sample inside the band, every lane recounts
-// its samples with the FP64 definition inside the band.  Same count as the
-// FP64 definition.
-__device__ int warp_count8(double dx, double dy, double dz, double r) {
-  const int lane = threadIdx.x & 31;
-  const float dxf = (float)dx, dyf = (float)dy, dzf = (float)dz;
-  const double r2 = r * r;
-  const float r2f = (float)r2, E = certified_band(r);
-  const float lo = r2f - E, hi = r2f + E;
-  const int a = lane >> 2;
-  const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
-  const float Xa = px * px;
-  float Z[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
-    Z[c] = pz * pz;
-  }
-  float XY[2];
-  int in = 0, maybe = 0;
-#pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int bb = 2 * (lane & 3) + j;
-    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
-    XY[j] = Xa + py * py;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float S = XY[j] + Z[c];
-      in += S < lo;
-      maybe += S <= hi;
-    }
-  }
-  if (__any_sync(0xffffffffu, in != maybe)) {
-    in = 0;
-    for (int j = 0; j < 2; ++j) {
-      const int bb = 2 * (lane & 3) + j;
-      for (int c = 0; c < 8; ++c) {
-        const float S = XY[j] + Z[c];
-        if (S < lo) ++in;
-        else if (S <= hi && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
-                                               sample_offset(bb, 8), sample_offset(c, 8), r2))
-          ++in;
-      }
-    }
-  }
-  return __reduce_add_sync(0xffffffffu, in);
-}
-
 // one slot entry of the finish pass in the storage precision T, taken by a
 // whole warp (lanes with e >= n take part in the sampling only): order the two
 // slots by particle index, sample the slots left pending (B < 0: cells of two
@@ -689,21 +733,26 @@ __device__ double finish_entry(const MapParams& P, int e, int n) {
     const bool s1 = pend == 0u;
     const int L = __ffs(s1 ? pend1 : pend) - 1;
     if (s1) pend1 &= pend1 - 1u; else pend &= pend - 1u;
-    double dx = 0.0, dy = 0.0, dz = 0.0, r = 0.0;
+    double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0;
+    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if ((threadIdx.x & 31) == L) {
       int x, y, z;
       cell_xyz(P.g, P.s.cell[e], x, y, z);
       const int p = s1 ? pid.y : pid.x;
-      r = P.p.r[p];
+      const double r = P.p.r[p];
       dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
       dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
       dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+      r2 = r * r;
+      f[0] = (float)dx;
+      f[1] = (float)dy;
+      f[2] = (float)dz;
+      f[3] = (float)r2;
+      f[4] = certified_band(r);
     }
-    dx = __shfl_sync(full, dx, L);
-    dy = __shfl_sync(full, dy, L);
-    dz = __shfl_sync(full, dz, L);
-    r = __shfl_sync(full, r, L);
-    const int cnt = warp_count8(dx, dy, dz, r);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = __shfl_sync(full, f[i], L);
+    const int cnt = warp_count8(f[0], f[1], f[2], f[3], f[4], L, dx, dy, dz, r2);
     if ((threadIdx.x & 31) == L) {
       const T B = (T)weight((double)cnt * (1.0 / 512.0), P.tau, P.weighting);
       if (s1) r1[3] = B; else r0[3] = B;
