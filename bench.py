@@ -213,6 +213,7 @@ def run_reference(args, w, world, rank):
 FORMS = (
     # name, PDF precision, streaming, eps mode, sampling n
     ("fp64_8cubed", "fp64", "pull", "supersample", 8),
+    ("df64_8cubed", "df64", "pull", "supersample", 8),
     ("fp32_8cubed", "fp32", "pull", "supersample", 8),
     ("fp32_mlp", "fp32", "pull", "mlp", 8),
     ("fp32_mlp_aa", "fp32", "aa", "mlp", 8),
@@ -241,7 +242,8 @@ def forms_comparison(capi, torch, steps, seed=20230321):
     z): FP64 PDFs with 8^3 sub-division sampling (the reference) against FP32
     deviation storage with the trained surrogate (8^3 fallback), and, for the
     surrogate's gain, FP32 with 8^3 sampling, 4^3 sampling and the linear
-    approximation of Eqs. 25-27.  Same number of steps from rest on the same
+    approximation of Eqs. 25-27; beside them the double-float form (FP64
+    accuracy on the FP32 pipes) with 8^3 sampling.  Same number of steps from rest on the same
     GPU; drag error = ||F - F_ref|| / ||F_ref|| over all particles, velocity
     error likewise over the field.  Per form: whole-step MLUPS, the one-off
     mapping time (fixed spheres) and the collision kernel's roofline fraction."""
@@ -279,8 +281,9 @@ def forms_comparison(capi, torch, steps, seed=20230321):
         _, u = e.macroscopic()
         r = {"mlups": w.cells * steps / (ms * 1e-3) / 1e6, "mapping_ms_once": map_ms,
              "collide_ms": coll_ms}
-        if prec == "fp32":
-            gbs = (152 * w.cells + 16 * ncov) / (coll_ms * 1e-3) / 1e9
+        if prec != "fp64":
+            b = (152 * w.cells + 16 * ncov) if prec == "fp32" else (304 * w.cells + 24 * ncov)
+            gbs = b / (coll_ms * 1e-3) / 1e9
             r["collide_hbm_gbs"] = gbs
             r["collide_hbm_frac"] = gbs / hbm
         else:
@@ -304,6 +307,7 @@ def forms_comparison(capi, torch, steps, seed=20230321):
 
 SETTLE_FORMS = (
     ("fp64_8cubed", "fp64", "pull", "supersample"),
+    ("df64_8cubed", "df64", "pull", "supersample"),
     ("fp32_8cubed_aa", "fp32", "aa", "supersample"),
     ("fp32_mlp_aa", "fp32", "aa", "mlp"),
 )
@@ -359,7 +363,8 @@ def forms_settling(capi, torch, params, steps):
 
 
 def describe(args):
-    prec = {"fp64": "FP64 PDFs", "fp32": "FP32 deviation PDFs"}[args.precision]
+    prec = {"fp64": "FP64 PDFs", "fp32": "FP32 deviation PDFs",
+            "df64": "double-float deviation PDFs (FP32 pairs, 8 B)"}[args.precision]
     d = f"{WORKLOADS[args.workload]}, {prec}, {args.streaming} streaming"
     if args.eps != "supersample" or args.eps_n:
         eps = {"supersample": f"{args.eps_n or 4}^3 sub-division sampling",
@@ -384,7 +389,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="settle128")
-    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32", "df64"], default="fp64")
     ap.add_argument("--streaming", choices=["pull", "aa"], default="pull")
     ap.add_argument("--eps", choices=["supersample", "linear", "mlp"], default="supersample",
                     help="solid-fraction mode of the main line (default: the workload's)")
@@ -463,14 +468,14 @@ def main():
     ncov = int((p0 >= 0).sum())
     nslot = ncov + int((p1 >= 0).sum())
     fp64 = args.precision == "fp64"
-    esz = 8 if fp64 else 4
+    esz = 4 if args.precision == "fp32" else 8
     bytes_lbm = cells * 19 * 2 * esz
-    bytes_psm = bytes_lbm + ncov * (24 if fp64 else 16)
+    bytes_psm = bytes_lbm + ncov * (24 if esz == 8 else 16)
     hbm, peak_kind = peaks()
     hbm_achieved = bytes_psm / (lbm_ms * 1e-3) / 1e9
-    staged = fp64 or args.streaming == "aa"
+    staged = fp64 or (args.precision == "fp32" and args.streaming == "aa")
     kname = ("lbm_bulk_kernel" if staged else "lbm_kernel") + \
-        f"<{'double' if fp64 else 'float'},{args.streaming}>"
+        f"<{ {'fp64': 'double', 'fp32': 'float', 'df64': 'df'}[args.precision] },{args.streaming}>"
     traffic = profiled_traffic(os.path.join(ROOT, "paper_2303_11811_gb300", "csrc",
                                             "lbm_kernels.cu"),
                                f"{'lbm_bulk_kernel' if staged else 'lbm_kernel'}_"
@@ -541,7 +546,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if fp64 else "f32", "data": "synthetic",
+            "dtype": {"fp64": "f64", "fp32": "f32", "df64": "f32x2 (double-float)"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": describe(args), "cells": cells,
                        "l2": f"working set {ws:.0f} MB of PDFs > 126 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -74,8 +74,13 @@ typedef struct {
 typedef enum { PSM_SRT = 0, PSM_TRT = 1 } psm_relax;
 
 enum { PSM_FP64 = 0,       /* PDFs stored and collided in FP64 */
-       PSM_FP32_DEV = 1 }; /* PDFs stored as FP32 deviations f_q - w_q,
+       PSM_FP32_DEV = 1,   /* PDFs stored as FP32 deviations f_q - w_q,
                               collided in FP32; forces and checks in FP64 */
+       PSM_FP64_DF = 2 };  /* PDFs stored as deviations in double-float form
+                              (a pair of FP32 values hi + lo, 8 bytes, a
+                              48-bit significand) and collided in double-float
+                              arithmetic on the FP32 pipes; mapping, forces,
+                              DEM and checks in FP64 */
 enum { PSM_PULL = 0,       /* two buffers, pull streaming */
        PSM_AA = 1 };       /* one buffer, AA-pattern in-place streaming */
 enum { PSM_EPS_SUPERSAMPLE = 0, /* eps from eps_n^3 sub-cell sample points */
@@ -89,7 +94,7 @@ enum { PSM_W_EPS = 0,      /* B = eps (Sec. 2.3) */
 
 typedef struct {
   double magic;          /* TRT magic parameter Lambda (default 3/16) */
-  int precision;         /* PSM_FP64 | PSM_FP32_DEV */
+  int precision;         /* PSM_FP64 | PSM_FP32_DEV | PSM_FP64_DF */
   int streaming;         /* PSM_PULL | PSM_AA */
   int eps_mode;          /* PSM_EPS_* */
   int eps_n;             /* samples per axis for PSM_EPS_SUPERSAMPLE (1..16) */

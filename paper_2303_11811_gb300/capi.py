@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "PSM_OK", 1: "PSM_ERR_ARG", 2: "PSM_ERR_CUDA", 3: "PSM_ERR_OO
                 4: "PSM_ERR_SLOT_OVERFLOW", 5: "PSM_ERR_NONFINITE", 6: "PSM_ERR_TIMEOUT",
                 7: "PSM_ERR_STATE"}
 PSM_SRT, PSM_TRT = 0, 1
-PSM_FP64, PSM_FP32_DEV = 0, 1
+PSM_FP64, PSM_FP32_DEV, PSM_FP64_DF = 0, 1, 2
 PSM_PULL, PSM_AA = 0, 1
 PSM_EPS_SUPERSAMPLE, PSM_EPS_LINEAR, PSM_EPS_MLP = 0, 1, 2
 PSM_W_EPS, PSM_W_NT = 0, 1
@@ -192,7 +192,8 @@ class Engine:
     grid (nx, ny, nz), ``walls`` six 0/1 flags (-x,+x,-y,+y,-z,+z), ``tau``,
     ``relax`` "srt"/"trt", ``magic``, ``fbody``, ``weighting`` "eps"/"nt",
     ``eps_mode`` "supersample"/"linear"/"mlp", ``eps_n``, DEM parameters,
-    ``precision`` "fp64"/"fp32", ``streaming`` "pull"/"aa"."""
+    ``precision`` "fp64"/"fp32"/"df64" (FP64, FP32 deviations, double-float
+    pairs), ``streaming`` "pull"/"aa"."""
 
     def __init__(self, nx, ny, nz, tau, relax="srt", magic=3.0 / 16.0,
                  walls=(0, 0, 0, 0, 0, 0), fbody=(0.0, 0.0, 0.0), weighting="eps",
@@ -205,7 +206,7 @@ class Engine:
         opt = PsmOptions()
         L.psm_default_options(C.byref(opt))
         opt.magic = magic
-        opt.precision = {"fp64": PSM_FP64, "fp32": PSM_FP32_DEV}[precision]
+        opt.precision = {"fp64": PSM_FP64, "fp32": PSM_FP32_DEV, "df64": PSM_FP64_DF}[precision]
         opt.streaming = {"pull": PSM_PULL, "aa": PSM_AA}[streaming]
         opt.eps_mode = {"supersample": 0, "linear": 1, "mlp": 2}[eps_mode]
         opt.eps_n = eps_n

@@ -14,10 +14,39 @@
 // weighted by (1 - B) and each particle i adds B_i C^s_i (Eq. 19), whose
 // symmetric part per pair is E_s(U_p) - E_s(U_f) and antisymmetric part
 // E_a(U_f) + E_a(U_p) - a_k; its momentum gives the force of Eq. 21.
+#include "df.cuh"
 #include "psm_internal.cuh"
 
 namespace psm {
 namespace {
+
+// element traits: FP64 (the warp-shared solid operator, FP64-pipe bound), or
+// a form that runs on the FP32 pipes (FP32 deviations, double-float pairs)
+template <typename T>
+constexpr bool kFP64 = false;
+template <>
+constexpr bool kFP64<double> = true;
+// slot records and per-slot forces come from the mapping in FP32 (FP32 form)
+// or FP64 (FP64 and double-float forms)
+template <typename T>
+struct RecOf {
+  using type = T;
+};
+template <>
+struct RecOf<df> {
+  using type = double;
+};
+__device__ __forceinline__ double as_double(double v) { return v; }
+__device__ __forceinline__ double as_double(float v) { return (double)v; }
+__device__ __forceinline__ double as_double(df v) { return to_double(v); }
+template <typename T>
+__device__ __forceinline__ T from_double(double v) {
+  return (T)v;
+}
+template <>
+__device__ __forceinline__ df from_double<df>(double v) {
+  return df(v);
+}
 
 __host__ __device__ constexpr int ckx(int k) {
   return (k == 0 || k == 3 || k == 4 || k == 5 || k == 6) ? 1 : 0;
@@ -117,6 +146,10 @@ template <typename T>
 __device__ __forceinline__ T ld(const T* p) {
   return __ldg(p);
 }
+__device__ __forceinline__ df ld(const df* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df(v.x, v.y);
+}
 
 // four consecutive coefficients (16-byte aligned) in 16-byte loads
 __device__ __forceinline__ void ld4(const float* p, float* o) {
@@ -128,6 +161,11 @@ __device__ __forceinline__ void ld4(const double* p, double* o) {
   const double2 v = __ldg(reinterpret_cast<const double2*>(p) + 1);
   o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
 }
+__device__ __forceinline__ void ld4(const df* p, df* o) {
+  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  o[0] = df(u.x, u.y); o[1] = df(u.z, u.w); o[2] = df(v.x, v.y); o[3] = df(v.z, v.w);
+}
 
 template <typename T>
 __device__ __forceinline__ const CollideCoef<T>* coef_of(const StepConst* sc);
@@ -138,6 +176,10 @@ __device__ __forceinline__ const CollideCoef<double>* coef_of<double>(const Step
 template <>
 __device__ __forceinline__ const CollideCoef<float>* coef_of<float>(const StepConst* sc) {
   return &sc->f;
+}
+template <>
+__device__ __forceinline__ const CollideCoef<df>* coef_of<df>(const StepConst* sc) {
+  return &sc->x;
 }
 
 // Shared memory of one warp for the FP64 solid operator.  Work is split in
@@ -170,10 +212,11 @@ size_t lbm_smem_bytes() {
 template <typename T>
 __device__ __forceinline__ void slot_force(const LbmParams& P, int e, int sl, T Bi, T dux, T duy,
                                            T duz, const T* f) {
-  T* o = static_cast<T*>(P.slot_Fc) + 3 * ((long long)sl * P.slot_cap + e);
-  o[0] = Bi * (dux - f[0]);
-  o[1] = Bi * (duy - f[1]);
-  o[2] = Bi * (duz - f[2]);
+  using R = typename RecOf<T>::type;  // the force reduction's precision
+  R* o = static_cast<R*>(P.slot_Fc) + 3 * ((long long)sl * P.slot_cap + e);
+  o[0] = (R)as_double(Bi * (dux - f[0]));
+  o[1] = (R)as_double(Bi * (duy - f[1]));
+  o[2] = (R)as_double(Bi * (duz - f[2]));
 }
 
 // Collision of one cell (Eqs. 3-8 and 17-21) on the PDFs d gathered by the
@@ -188,6 +231,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   // the cell centre (Eq. 20) and the weight B_i, both written by the mapping;
   // the sign of slot 0's weight tells whether a second particle shares the
   // cell, whose record is read only then.
+  using R = typename RecOf<T>::type;
   bool cov = live && ((m >> lane) & 1u);
   bool has1 = false;
   int e = 0;
@@ -195,10 +239,17 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   if (cov) {
     e = eb + __popc(m & ((1u << lane) - 1u));
     if (e < P.slot_cap) {
-      ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
-      has1 = signbit(r0[3]);
-      r0[3] = fabs(r0[3]);
-      if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
+      R v[4];
+      ld4(static_cast<const R*>(P.slot_V) + 4LL * e, v);
+      has1 = signbit(v[3]);
+      v[3] = fabs(v[3]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) r0[i] = from_double<T>(v[i]);
+      if (has1) {
+        ld4(static_cast<const R*>(P.slot_V) + 4LL * (P.slot_cap + e), v);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r1[i] = from_double<T>(v[i]);
+      }
     } else {
       cov = false;
     }
@@ -261,7 +312,8 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
   // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
   // warp; in FP32 each covered lane does its own cell.
-  if (sizeof(T) == 4 && cov) {
+  if constexpr (!kFP64<T>) {
+  if (cov) {
 #pragma unroll 1
     for (int sl = 0; sl < 2; ++sl) {
       if (sl && !has1) continue;
@@ -283,7 +335,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
       slot_force<T>(P, e, sl, Bi, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
     }
   }
-  if (sizeof(T) == 8 && m != 0u) {
+  } else if (m != 0u) {
     SolidSmem<T>& S = *solid;
     const bool has0 = cov, hs1 = cov && has1;
     const unsigned b0 = __ballot_sync(0xffffffffu, has0);
@@ -381,7 +433,8 @@ __device__ __forceinline__ void store_pdfs(const LbmParams& P, const NbrT<WALLS>
 // FP32 kernels are bandwidth bound and want resident warps (4 blocks per
 // SM); FP64 kernels are FP64-pipe bound and keep their registers
 template <typename T, int MODE, int WALLS>
-__global__ void __launch_bounds__(LBM_THREADS, sizeof(T) == 4 ? 4 : 1) lbm_kernel(LbmParams P) {
+__global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 4 : 2))
+    lbm_kernel(LbmParams P) {
   extern __shared__ __align__(16) unsigned char lbm_smem[];
   const Grid& g = P.g;
   // the grid has fewer than 2^31 cells: 32-bit indices throughout
@@ -644,7 +697,7 @@ __global__ void to_canonical_kernel(Grid g, const T* __restrict__ buf, int aa, i
     nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
     const int cell = nb.idx(0, 0, 0);
     const long long NC = g.ncell;
-    out[c] = wq(0) + (double)buf[cell];
+    out[c] = wq(0) + as_double(buf[cell]);
     for (int k = 0; k < 9; ++k) {
       const int cx = ckx(k), cy = cky(k), cz = ckz(k);
       const int qa = 2 * k + 1, qb = 2 * k + 2;
@@ -659,8 +712,8 @@ __global__ void to_canonical_kernel(Grid g, const T* __restrict__ buf, int aa, i
         ia = nb.ok(cx, cy, cz) ? qa * NC + nb.idx(cx, cy, cz) : qb * NC + cell;
         ib = nb.ok(-cx, -cy, -cz) ? qb * NC + nb.idx(-cx, -cy, -cz) : qa * NC + cell;
       }
-      out[qa * N + c] = wq(qa) + (double)buf[ia];
-      out[qb * N + c] = wq(qb) + (double)buf[ib];
+      out[qa * N + c] = wq(qa) + as_double(buf[ia]);
+      out[qb * N + c] = wq(qb) + as_double(buf[ib]);
     }
   }
 }
@@ -680,7 +733,7 @@ __global__ void from_canonical_kernel(Grid g, const double* __restrict__ in, int
     nc.init(x, y, z, g.nx, g.ny, g.nz, g.nx, g.wall);
     const long long cell = (long long)x + (long long)g.nxp * (y + (long long)g.ny * z);
     const long long NC = g.ncell;
-    buf[cell] = (T)(in[c] - wq(0));
+    buf[cell] = from_double<T>(in[c] - wq(0));
     for (int k = 0; k < 9; ++k) {
       const int cx = ckx(k), cy = cky(k), cz = ckz(k);
       const int qa = 2 * k + 1, qb = 2 * k + 2;
@@ -692,8 +745,8 @@ __global__ void from_canonical_kernel(Grid g, const double* __restrict__ in, int
         va = nc.ok(-cx, -cy, -cz) ? in[qa * N + nc.idx(-cx, -cy, -cz)] : in[qb * N + c];
         vb = nc.ok(cx, cy, cz) ? in[qb * N + nc.idx(cx, cy, cz)] : in[qa * N + c];
       }
-      buf[qa * NC + cell] = (T)(va - wq(qa));
-      buf[qb * NC + cell] = (T)(vb - wq(qb));
+      buf[qa * NC + cell] = from_double<T>(va - wq(qa));
+      buf[qb * NC + cell] = from_double<T>(vb - wq(qb));
     }
   }
 }
@@ -774,7 +827,7 @@ __global__ void sums_final_kernel(int nparts, const double* __restrict__ partial
 
 template <typename T>
 size_t lbm_dyn_smem() {
-  return sizeof(T) == 8 ? lbm_smem_bytes<T>() : 0;
+  return kFP64<T> ? lbm_smem_bytes<T>() : 0;
 }
 
 template <typename T, int W>
@@ -804,7 +857,8 @@ int lbm_configure() {
   if (o <= 0) return 1;
   return configure_walls<float, 0>(o) | configure_walls<float, 1>(o) |
          configure_walls<float, 7>(o) | configure_walls<double, 0>(o) |
-         configure_walls<double, 1>(o) | configure_walls<double, 7>(o);
+         configure_walls<double, 1>(o) | configure_walls<double, 7>(o) |
+         configure_walls<df, 0>(o) | configure_walls<df, 1>(o) | configure_walls<df, 7>(o);
 }
 
 // tiles of whole x-rows: 256 cells (tile_rows rows) when the padded row
@@ -815,16 +869,32 @@ int lbm_configure() {
 // faster on the one-cell-per-thread kernel, whose 32 resident warps per SM
 // keep enough loads in flight.  Returns 0 and leaves plan.stages = 0 when
 // the one-cell-per-thread kernel is to be used.
-int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan) {
+template <typename T, int W>
+const void* bulk_fn() {
+  return (const void*)lbm_bulk_kernel<T, 0, W>;
+}
+template <typename T>
+const void* bulk_fn_w(int w) {
+  return w == 0 ? bulk_fn<T, 0>() : (w == 1 ? bulk_fn<T, 1>() : bulk_fn<T, 7>());
+}
+
+int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan) {
   *plan = LbmPlan{};
+  const int fp32 = prec == PREC_FP32;
   if (fp32 && !aa) return 0;
+  // the double-float form is bound by the FP32 pipes: it takes the
+  // one-cell-per-thread kernel (two blocks of eight warps per SM; the staged
+  // kernel fits one block of nine warps next to its ring)
+  if (prec == PREC_DF) return 0;
   const int optin = smem_optin();
   if (optin <= 0) return 1;
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
   const int TR = (g.nxp <= 256 && 256 % g.nxp == 0) ? 256 / g.nxp : 1;
   const size_t stage = (size_t)Q * TR * g.nxp * esz;
-  const size_t extra = BULK_BAR_BYTES + (fp32 ? 0 : BULK_CONSUMER_WARPS * sizeof(SolidSmem<double>));
-  const size_t budget = fp32 ? (size_t)100 * 1024 : (size_t)optin;
+  const size_t extra = BULK_BAR_BYTES + (prec == PREC_FP64 ? BULK_CONSUMER_WARPS *
+                                                                 sizeof(SolidSmem<double>)
+                                                           : 0);
+  const size_t budget = prec == PREC_FP64 ? (size_t)optin : (size_t)100 * 1024;
   if (budget <= extra) return 0;
   size_t S = (budget - extra) / stage;
   if (S > BULK_MAX_STAGES) S = BULK_MAX_STAGES;
@@ -834,12 +904,9 @@ int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan) {
   }
   const size_t smem = extra + S * stage;
   const int w = g.wall[0] | (g.wall[1] << 1) | (g.wall[2] << 2);
-  const void* fn = fp32 ? (w == 0 ? (const void*)lbm_bulk_kernel<float, 0, 0>
-                                  : (w == 1 ? (const void*)lbm_bulk_kernel<float, 0, 1>
-                                            : (const void*)lbm_bulk_kernel<float, 0, 7>))
-                        : (w == 0 ? (const void*)lbm_bulk_kernel<double, 0, 0>
-                                  : (w == 1 ? (const void*)lbm_bulk_kernel<double, 0, 1>
-                                            : (const void*)lbm_bulk_kernel<double, 0, 7>));
+  const void* fn = prec == PREC_FP32 ? bulk_fn_w<float>(w)
+                   : prec == PREC_DF ? bulk_fn_w<df>(w)
+                                     : bulk_fn_w<double>(w);
   int per_sm = 0, dev = 0, nsm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BULK_THREADS, smem) !=
           cudaSuccess ||
@@ -880,16 +947,17 @@ void launch_lbm_w(const LbmParams& P, int mode, unsigned grid, cudaStream_t s) {
   else launch_lbm_t<T, 7>(P, mode, grid, s);
 }
 
-int launch_lbm(const LbmParams& P0, int fp32, int mode, cudaStream_t s) {
+int launch_lbm(const LbmParams& P0, int prec, int mode, cudaStream_t s) {
   LbmParams P = P0;
-  const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  const size_t esz = prec == PREC_FP32 ? sizeof(float) : sizeof(double);
   for (int q = 0; q < Q; ++q) {
     P.srcq[q] = static_cast<const char*>(P.src) + esz * (size_t)q * P.g.ncell;
     P.dstq[q] = static_cast<char*>(P.dst) + esz * (size_t)q * P.g.ncell;
   }
   const long long threads = P.g.nwords * 32;
   const unsigned grid = (unsigned)((threads + LBM_THREADS - 1) / LBM_THREADS);
-  if (fp32) launch_lbm_w<float>(P, mode, grid, s);
+  if (prec == PREC_FP32) launch_lbm_w<float>(P, mode, grid, s);
+  else if (prec == PREC_DF) launch_lbm_w<df>(P, mode, grid, s);
   else launch_lbm_w<double>(P, mode, grid, s);
   return 1;
 }
@@ -900,24 +968,29 @@ static unsigned grid_for(long long n, int block) {
   return (unsigned)(b > 0 ? b : 1);
 }
 
-int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
+int launch_to_canonical(const Grid& g, const void* buf, int prec, int aa_parity, int aa,
                         const BoxSel& B, double* out, cudaStream_t s) {
   const long long N = (long long)B.bx * B.by * B.bz;
-  if (fp32)
+  if (prec == PREC_FP32)
     to_canonical_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(
         g, static_cast<const float*>(buf), aa, aa_parity, B, out);
+  else if (prec == PREC_DF)
+    to_canonical_kernel<df><<<grid_for(N, 256), 256, 0, s>>>(g, static_cast<const df*>(buf), aa,
+                                                              aa_parity, B, out);
   else
     to_canonical_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(
         g, static_cast<const double*>(buf), aa, aa_parity, B, out);
   return 1;
 }
 
-int launch_from_canonical(const Grid& g, const double* in, void* buf, int fp32, int aa,
-                             cudaStream_t s) {
+int launch_from_canonical(const Grid& g, const double* in, void* buf, int prec, int aa,
+                          cudaStream_t s) {
   const long long N = (long long)g.nx * g.ny * g.nz;
-  if (fp32)
+  if (prec == PREC_FP32)
     from_canonical_kernel<float><<<grid_for(N, 256), 256, 0, s>>>(g, in, aa,
                                                                   static_cast<float*>(buf));
+  else if (prec == PREC_DF)
+    from_canonical_kernel<df><<<grid_for(N, 256), 256, 0, s>>>(g, in, aa, static_cast<df*>(buf));
   else
     from_canonical_kernel<double><<<grid_for(N, 256), 256, 0, s>>>(g, in, aa,
                                                                    static_cast<double*>(buf));
@@ -979,6 +1052,7 @@ __global__ void step_const_kernel(MapParams P) {
   }
   fill_coef<double>(sc->d, f, P.omega_p, P.omega_m);
   fill_coef<float>(sc->f, f, P.omega_p, P.omega_m);
+  fill_coef<df>(sc->x, f, P.omega_p, P.omega_m);
 }
 
 int launch_step_const(MapParams P, cudaStream_t s) {

@@ -32,6 +32,7 @@ struct psm_ctx {
   Grid g{};
   double tau = 0.6, omega_p = 0, omega_m = 0;
   int relax = 0, fp32 = 0, aa = 0;
+  int prec = PREC_FP64;  // PDF storage and collision arithmetic (PREC_*)
   LbmPlan plan{};       // staged collision kernel (plan.stages = 0: not used)
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
@@ -236,7 +237,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   L.stages = c->plan.stages;
   L.blocks = c->plan.blocks;
   L.smem = c->plan.smem;
-  n += launch_lbm(L, c->fp32, mode, s);
+  n += launch_lbm(L, c->prec, mode, s);
   if (c->timing) cudaEventRecord(c->ev[2], s);
   if (c->p.n > 0) n += launch_force_reduce(MP, s);
   if (c->timing) cudaEventRecord(c->ev[3], s);
@@ -335,7 +336,7 @@ psm_status canonical(psm_ctx* c, double** out, const BoxSel* box = nullptr) {
   const size_t N = (size_t)B.bx * B.by * B.bz;
   double* f = static_cast<double*>(dalloc(c, sizeof(double) * Q * N));
   if (!f) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
-  launch_to_canonical(c->g, c->aa ? c->buf[0] : c->buf[c->cur], c->fp32, c->parity, c->aa, B, f,
+  launch_to_canonical(c->g, c->aa ? c->buf[0] : c->buf[c->cur], c->prec, c->parity, c->aa, B, f,
                       c->stream);
   *out = f;
   CK(cudaGetLastError());
@@ -372,7 +373,9 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     if (grid->wall[2 * a] != grid->wall[2 * a + 1]) return PSM_ERR_ARG;
   if (!(tau > 0.5) || !std::isfinite(tau)) return PSM_ERR_ARG;
   if (relax != PSM_SRT && relax != PSM_TRT) return PSM_ERR_ARG;
-  if (opt->precision != PSM_FP64 && opt->precision != PSM_FP32_DEV) return PSM_ERR_ARG;
+  if (opt->precision != PSM_FP64 && opt->precision != PSM_FP32_DEV &&
+      opt->precision != PSM_FP64_DF)
+    return PSM_ERR_ARG;
   if (opt->streaming != PSM_PULL && opt->streaming != PSM_AA) return PSM_ERR_ARG;
   if (opt->eps_mode < 0 || opt->eps_mode > 2) return PSM_ERR_ARG;
   if (opt->eps_n < 1 || opt->eps_n > 16) return PSM_ERR_ARG;
@@ -390,6 +393,9 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->tau = tau;
   c->relax = relax;
   c->fp32 = opt->precision == PSM_FP32_DEV;
+  c->prec = opt->precision == PSM_FP32_DEV ? PREC_FP32
+            : opt->precision == PSM_FP64_DF ? PREC_DF
+                                             : PREC_FP64;
   c->aa = opt->streaming == PSM_AA;
   c->stream = static_cast<cudaStream_t>(opt->stream);
   c->omega_p = 1.0 / tau;
@@ -460,7 +466,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "occupancy query of the DEM kernel failed");
   }
-  if (lbm_plan(g, c->fp32, c->aa, &c->plan) != 0) {
+  if (lbm_plan(g, c->prec, c->aa, &c->plan) != 0) {
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "occupancy query of the collision kernel failed");
   }
@@ -745,7 +751,7 @@ psm_status psm_set_pdfs(psm_ctx* c, const double* f) {
   cudaError_t e = cudaMemcpyAsync(d, f, sizeof(double) * Q * N, cudaMemcpyHostToDevice, c->stream);
   void* target = c->aa ? c->buf[0] : c->buf[c->cur];
   if (e == cudaSuccess) {
-    launch_from_canonical(c->g, d, target, c->fp32, c->aa, c->stream);
+    launch_from_canonical(c->g, d, target, c->prec, c->aa, c->stream);
     e = cudaStreamSynchronize(c->stream);
   }
   dfree(c, d);

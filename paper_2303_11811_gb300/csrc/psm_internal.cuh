@@ -19,9 +19,15 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df.cuh"
+
 namespace psm {
 
 constexpr int Q = 19;
+
+// storage and arithmetic of the PDFs: FP64; FP32 deviations; double-float
+// pairs (FP32 hi + lo, 8 bytes per value, arithmetic on the FP32 pipes)
+enum : int { PREC_FP64 = 0, PREC_FP32 = 1, PREC_DF = 2 };
 
 // Status bits raised on the device
 enum : unsigned {
@@ -96,6 +102,7 @@ struct StepConst {
   double ncells;        // nx * ny * nz
   CollideCoef<double> d;
   CollideCoef<float> f;
+  CollideCoef<df> x;
 };
 
 struct Particles {
@@ -202,16 +209,16 @@ struct LbmPlan {
 // ---- launchers (stream-ordered; return the number of kernel launches) ----
 int lbm_configure();  // kernel attributes; call once before launching (returns != 0 on error)
 // staged-kernel plan for a grid (stages = 0: use the one-cell-per-thread kernel)
-int lbm_plan(const Grid& g, int fp32, int aa, LbmPlan* plan);
-int launch_lbm(const LbmParams& P, int fp32, int mode, cudaStream_t s);
+int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan);
+int launch_lbm(const LbmParams& P, int prec, int mode, cudaStream_t s);
 // a box of cells, origin (x0, y0, z0) (non-negative, taken modulo the grid) and
 // extent (bx, by, bz); output layout [q][z][y][x] over the box
 struct BoxSel {
   int x0, y0, z0, bx, by, bz;
 };
-int launch_to_canonical(const Grid& g, const void* buf, int fp32, int aa_parity, int aa,
+int launch_to_canonical(const Grid& g, const void* buf, int prec, int aa_parity, int aa,
                         const BoxSel& B, double* out, cudaStream_t s);
-int launch_from_canonical(const Grid& g, const double* in, void* buf, int fp32, int aa,
+int launch_from_canonical(const Grid& g, const double* in, void* buf, int prec, int aa,
                           cudaStream_t s);
 int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,
                        double* u, cudaStream_t s);
