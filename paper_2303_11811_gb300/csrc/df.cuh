@@ -1,12 +1,20 @@
 // df.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo of
-// two FP32 numbers with |lo| <= ulp(hi)/2, a 48-bit significand.  GB300
-// executes FP64 at 1/64 of its FP32 rate; the collision in this form runs on
-// the FP32 pipes while keeping the PDFs to about 2^-47 relative precision.
+// two FP32 numbers.  GB300 executes FP64 at 1/64 of its FP32 rate; the
+// collision in this form runs on the FP32 pipes while keeping the PDFs to
+// about 2^-47 relative precision.
 //
 // The operations are the error-free transformations of Knuth (TwoSum, 1969)
-// and Dekker (Fast2Sum and the exact product, 1971), with the product's error
-// term taken from a fused multiply-add: the "sloppy" double-float addition
-// and multiplication of Hida, Li and Bailey (QD library, ARITH 2001).  Every
+// and Dekker (Fast2Sum and the exact product, 1971), the product's error term
+// taken from a fused multiply-add, as in the double-float arithmetic of Hida,
+// Li and Bailey (QD library, ARITH 2001), but without renormalising each
+// result (the compensated form of Ogita, Rump and Oishi, SIAM J. Sci. Comput.
+// 2005): a sum keeps the exact error of its high parts plus the sum of the low
+// parts, a product the exact error of the high product plus the cross terms.
+// Each operation then errs by about 2^-47 of its operands' magnitude rather
+// than of its result; the collision's inputs and outputs are deviations from
+// the lattice weights, small next to the PDFs themselves, so this stays far
+// below the FP64 path's bound on the PDFs.  Stored values are renormalised
+// (renorm) so that the low part never accumulates over time steps.  Every
 // FP32 step is an explicitly rounded intrinsic, so the compiler cannot
 // contract or reassociate them.
 #pragma once
@@ -36,7 +44,7 @@ __device__ __forceinline__ df fast_two_sum(float a, float b) {
 }
 __device__ __forceinline__ df operator+(df a, df b) {
   const df s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  return df(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
 __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
@@ -45,10 +53,14 @@ __device__ __forceinline__ df operator*(df a, df b) {
   float e = __fmaf_rn(a.hi, b.hi, -p);
   e = __fmaf_rn(a.hi, b.lo, e);
   e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
+  return df(p, e);
 }
+// canonical pair: hi the FP32 rounding of hi + lo (valid for any magnitudes)
+__device__ __forceinline__ df renorm(df a) { return two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 __device__ __forceinline__ bool operator>(df a, df b) {
+  a = renorm(a);
+  b = renorm(b);
   return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
 }
 __device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }

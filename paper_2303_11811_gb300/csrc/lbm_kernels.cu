@@ -14,6 +14,8 @@
 // weighted by (1 - B) and each particle i adds B_i C^s_i (Eq. 19), whose
 // symmetric part per pair is E_s(U_p) - E_s(U_f) and antisymmetric part
 // E_a(U_f) + E_a(U_p) - a_k; its momentum gives the force of Eq. 21.
+#include <type_traits>
+
 #include "df.cuh"
 #include "psm_internal.cuh"
 
@@ -26,16 +28,12 @@ template <typename T>
 constexpr bool kFP64 = false;
 template <>
 constexpr bool kFP64<double> = true;
-// slot records and per-slot forces come from the mapping in FP32 (FP32 form)
-// or FP64 (FP64 and double-float forms)
 template <typename T>
-struct RecOf {
-  using type = T;
-};
+constexpr bool kDF = false;
 template <>
-struct RecOf<df> {
-  using type = double;
-};
+constexpr bool kDF<df> = true;
+// slot records and per-slot forces are stored in the form's own precision
+// (FP32, FP64, double-float pairs)
 __device__ __forceinline__ double as_double(double v) { return v; }
 __device__ __forceinline__ double as_double(float v) { return (double)v; }
 __device__ __forceinline__ double as_double(df v) { return to_double(v); }
@@ -47,6 +45,14 @@ template <>
 __device__ __forceinline__ df from_double<df>(double v) {
   return df(v);
 }
+// sign flag and magnitude of a record's weight (slot 0's weight is negated
+// when a second particle shares the cell)
+__device__ __forceinline__ bool neg_flag(float v) { return signbit(v); }
+__device__ __forceinline__ bool neg_flag(double v) { return signbit(v); }
+__device__ __forceinline__ bool neg_flag(df v) { return signbit(v.hi); }
+__device__ __forceinline__ float magnitude(float v) { return fabsf(v); }
+__device__ __forceinline__ double magnitude(double v) { return fabs(v); }
+__device__ __forceinline__ df magnitude(df v) { return signbit(v.hi) ? -v : v; }
 
 __host__ __device__ constexpr int ckx(int k) {
   return (k == 0 || k == 3 || k == 4 || k == 5 || k == 6) ? 1 : 0;
@@ -212,11 +218,10 @@ size_t lbm_smem_bytes() {
 template <typename T>
 __device__ __forceinline__ void slot_force(const LbmParams& P, int e, int sl, T Bi, T dux, T duy,
                                            T duz, const T* f) {
-  using R = typename RecOf<T>::type;  // the force reduction's precision
-  R* o = static_cast<R*>(P.slot_Fc) + 3 * ((long long)sl * P.slot_cap + e);
-  o[0] = (R)as_double(Bi * (dux - f[0]));
-  o[1] = (R)as_double(Bi * (duy - f[1]));
-  o[2] = (R)as_double(Bi * (duz - f[2]));
+  T* o = static_cast<T*>(P.slot_Fc) + 3 * ((long long)sl * P.slot_cap + e);
+  o[0] = Bi * (dux - f[0]);
+  o[1] = Bi * (duy - f[1]);
+  o[2] = Bi * (duz - f[2]);
 }
 
 // Collision of one cell (Eqs. 3-8 and 17-21) on the PDFs d gathered by the
@@ -231,7 +236,6 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   // the cell centre (Eq. 20) and the weight B_i, both written by the mapping;
   // the sign of slot 0's weight tells whether a second particle shares the
   // cell, whose record is read only then.
-  using R = typename RecOf<T>::type;
   bool cov = live && ((m >> lane) & 1u);
   bool has1 = false;
   int e = 0;
@@ -239,17 +243,10 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   if (cov) {
     e = eb + __popc(m & ((1u << lane) - 1u));
     if (e < P.slot_cap) {
-      R v[4];
-      ld4(static_cast<const R*>(P.slot_V) + 4LL * e, v);
-      has1 = signbit(v[3]);
-      v[3] = fabs(v[3]);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) r0[i] = from_double<T>(v[i]);
-      if (has1) {
-        ld4(static_cast<const R*>(P.slot_V) + 4LL * (P.slot_cap + e), v);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) r1[i] = from_double<T>(v[i]);
-      }
+      ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
+      has1 = neg_flag(r0[3]);
+      r0[3] = magnitude(r0[3]);
+      if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
     } else {
       cov = false;
     }
@@ -292,22 +289,29 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   //                     = -omega+/2 s_k + ((9/2 omega+ w) c.U + G_k) c.U + C_c
   //   antisymmetric     = -omega-/2 a_k + 3 omega- w c.U + F_k
   // with C_c = omega+ w base0 + H_c U.f once per class.
-  {
-    const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
-    d[0] += omB * dl;
-  }
   const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
   const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
+  // the (1 - B) weight is a multiply-add in FP32/FP64; in double-float it is
+  // a product of its own, skipped in warps without a covered cell
+  auto relax = [&](auto weighted) {
+    constexpr bool W = decltype(weighted)::value;
+    {
+      const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
+      d[0] += W ? omB * dl : dl;
+    }
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    T pk[4];
-    ld4(cf->pair[k], pk);
-    const T cu = cdot<T>(k, Ux, Uy, Uz);
-    const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
-    const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
-    d[2 * k + 1] += omB * (ds + da);
-    d[2 * k + 2] += omB * (ds - da);
-  }
+    for (int k = 0; k < 9; ++k) {
+      T pk[4];
+      ld4(cf->pair[k], pk);
+      const T cu = cdot<T>(k, Ux, Uy, Uz);
+      const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
+      const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
+      d[2 * k + 1] += W ? omB * (ds + da) : ds + da;
+      d[2 * k + 2] += W ? omB * (ds - da) : ds - da;
+    }
+  };
+  if (kDF<T> && m == 0u) relax(std::false_type{});
+  else relax(std::true_type{});
 
   // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
   // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
@@ -399,6 +403,11 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
 #pragma unroll
       for (int q = 1; q < Q; ++q) d[q] = S.dd[lane][q - 1];
     }
+  }
+  if constexpr (kDF<T>) {
+    // stored pairs are canonical, so their low parts do not grow over steps
+#pragma unroll
+    for (int q = 0; q < Q; ++q) d[q] = renorm(d[q]);
   }
 }
 

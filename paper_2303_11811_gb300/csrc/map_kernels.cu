@@ -158,6 +158,7 @@ __device__ __forceinline__ long long rec_w(const MapParams& P, long long e, int 
 }
 __device__ __forceinline__ double load_B(const MapParams& P, long long e, int s) {
   if (P.fp32) return (double)static_cast<const float*>(P.s.V)[rec_w(P, e, s)];
+  if (P.dfrec) return to_double(static_cast<const df*>(P.s.V)[rec_w(P, e, s)]);
   return static_cast<const double*>(P.s.V)[rec_w(P, e, s)];
 }
 
@@ -358,16 +359,20 @@ __device__ __forceinline__ double count_eps(int cnt, int n3) {
 }
 
 constexpr int WTAB = 513;  // B of every sampled count up to 8^3
+constexpr int WTAB_DF = WTAB + 257;  // their double-float pairs (after the FP32 copy)
 constexpr int FILL_AXIS = 64;  // box extent per axis with offset tables (r < 30)
 
 // B of every sampled count (Eq. 16 of each eps = c / n^3), once per context
-// (doubles at out[0..n3], their FP32 roundings after WTAB doubles)
+// (doubles at out[0..n3], their FP32 roundings after WTAB doubles, their
+// double-float pairs after WTAB_DF doubles)
 __global__ void wtab_kernel(int n3, double tau, int weighting, double* out) {
   float* outf = reinterpret_cast<float*>(out + WTAB);
+  df* outd = reinterpret_cast<df*>(out + WTAB_DF);
   for (int c = threadIdx.x; c <= n3; c += blockDim.x) {
     const double B = weight(count_eps(c, n3), tau, weighting);
     out[c] = B;
     outf[c] = (float)B;
+    outd[c] = df(B);
   }
 }
 
@@ -482,6 +487,8 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   // roundings, formed once per block
   __shared__ double toff[3][FILL_AXIS];
   __shared__ float toff32[3][FILL_AXIS];
+  __shared__ df toffd[3][FILL_AXIS];  // double-float records: offsets as pairs
+  __shared__ df sud[6];               // and the particle's u, omega
   const int p = blockIdx.x;
   if (threadIdx.x == 0) sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const double fr = P.p.fr[p];
@@ -497,15 +504,20 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
         const double d = ((double)(b.lo[a] + k) + 0.5) - b.xp[a];
         toff[a][k] = d;
         toff32[a][k] = (float)d;
+        if (P.dfrec) toffd[a][k] = df(d);
       }
     }
   }
+  if (P.dfrec && threadIdx.x < 6)
+    sud[threadIdx.x] = df(threadIdx.x < 3 ? P.p.u[3 * p + threadIdx.x]
+                                          : P.p.om[3 * p + threadIdx.x - 3]);
   __syncthreads();
   const double u0 = P.p.u[3 * p], u1 = P.p.u[3 * p + 1], u2 = P.p.u[3 * p + 2];
   const double o0 = P.p.om[3 * p], o1 = P.p.om[3 * p + 1], o2 = P.p.om[3 * p + 2];
   const float uf0 = (float)u0, uf1 = (float)u1, uf2 = (float)u2;
   const float of0 = (float)o0, of1 = (float)o1, of2 = (float)o2;
   const float* wtabf = reinterpret_cast<const float*>(wtab + WTAB);  // FP32 copy
+  const df* wtabd = reinterpret_cast<const df*>(wtab + WTAB_DF);      // double-float copy
   const float rf = (float)b.r, rinvf = 1.0f / rf, frf = (float)fr;  // surrogate inputs
   const long long loff = P.list_off[p];
   const int cnt = P.list_cnt[p];
@@ -591,6 +603,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     if (!ok) continue;
     double B;
     float Bf = 0.f;
+    int cidx = -1;      // sampled count when B comes from the table
     bool want = false;  // surrogate mode: the cell goes to the network's worklist
     if constexpr (NS < 0) {
       // surrogate mode (reading I): inside by the margin -> 1; a partial
@@ -610,6 +623,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       Bf = (float)B;
     } else if (tab) {
       const int c = NS == 8 ? count8 : cell_count<NS>(P, b, h, s64, s32);
+      cidx = c;
       if (P.fp32) Bf = __ldg(&wtabf[c]);
       else B = __ldg(&wtab[c]);
     } else {
@@ -625,6 +639,26 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       static_cast<float4*>(P.s.V)[rec] =
           make_float4(uf0 + (of1 * fz - of2 * fy), uf1 + (of2 * fx - of0 * fz),
                       uf2 + (of0 * fy - of1 * fx), Bf);
+    } else if (P.dfrec) {
+      // the double-float form: surface velocity (Eq. 20) in double-float from
+      // the pairs of the offsets and of u, omega; B from the table's pairs
+      df dx, dy, dz;
+      if (tables) {
+        dx = toffd[0][h.kx - b.lo[0]];
+        dy = toffd[1][h.ky - b.lo[1]];
+        dz = toffd[2][h.kz - b.lo[2]];
+      } else {
+        dx = df(h.dx);
+        dy = df(h.dy);
+        dz = df(h.dz);
+      }
+      const df v0 = sud[0] + (sud[4] * dz - sud[5] * dy);
+      const df v1 = sud[1] + (sud[5] * dx - sud[3] * dz);
+      const df v2 = sud[2] + (sud[3] * dy - sud[4] * dx);
+      const df w = cidx >= 0 ? wtabd[cidx] : df(B);
+      float4* R = static_cast<float4*>(P.s.V) + 2 * rec;
+      R[0] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
+      R[1] = make_float4(v2.hi, v2.lo, w.hi, w.lo);
     } else {
       const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
       const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
@@ -690,6 +724,25 @@ __device__ __forceinline__ void rec_load(const double* p, double* o) {
 __device__ __forceinline__ void rec_store(float* p, const float* o) {
   *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
 }
+// double-float records: the finish pass only moves the velocity pairs (their
+// 8 bytes travel as the bits of a double) and computes with the weight
+__device__ __forceinline__ void rec_load(const df* p, double* o) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0];
+  const float4 v = reinterpret_cast<const float4*>(p)[1];
+  o[0] = u.x;
+  o[1] = u.y;
+  o[2] = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(v.y) << 32) |
+                                          __float_as_uint(v.x)));
+  o[3] = to_double(df(v.z, v.w));
+}
+__device__ __forceinline__ void rec_store(df* p, const double* o) {
+  const df w(o[3]);
+  const unsigned long long b2 = (unsigned long long)__double_as_longlong(o[2]);
+  reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
+  reinterpret_cast<float4*>(p)[1] =
+      make_float4(__uint_as_float((unsigned)b2), __uint_as_float((unsigned)(b2 >> 32)), w.hi,
+                  w.lo);
+}
 __device__ __forceinline__ void rec_store(double* p, const double* o) {
   reinterpret_cast<double2*>(p)[0] = make_double2(o[0], o[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
@@ -701,12 +754,12 @@ __device__ __forceinline__ void rec_store(double* p, const double* o) {
 // particles in surrogate mode, worklist overflow, no network) with 8^3 points,
 // normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
 // weight; returns min(B, 1) (0 for lanes without an entry)
-template <typename T>
+template <typename T, typename S>  // arithmetic in T, records stored as S
 __device__ double finish_entry(const MapParams& P, int e, int n) {
   const bool live = e < n;
   int2 pid = make_int2(-1, -1);
   T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
-  T* V = static_cast<T*>(P.s.V);
+  S* V = static_cast<S*>(P.s.V);
   const long long e1 = P.s.cap + e;
   bool two = false;
   if (live) {
@@ -782,7 +835,9 @@ __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   const int stride = gridDim.x * blockDim.x;
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
-    accB += P.fp32 ? finish_entry<float>(P, e, n) : finish_entry<double>(P, e, n);
+    accB += P.fp32    ? finish_entry<float, float>(P, e, n)
+            : P.dfrec ? finish_entry<double, df>(P, e, n)
+                      : finish_entry<double, double>(P, e, n);
   }
   red[threadIdx.x] = accB;
   __syncthreads();
@@ -983,6 +1038,84 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams
   }
 }
 
+// The same reduction for the double-float form: slot forces arrive as FP32
+// pairs, torque arms are formed as (integer offset) + (1/2 - fraction of the
+// centre) in double-float, products and sums in double-float on the FP32
+// pipes (df.cuh), the same fixed-order tree, one conversion to FP64 per
+// component at the end.
+__global__ void __launch_bounds__(RED_THREADS) force_reduce_df_kernel(MapParams P) {
+  __shared__ df sh[6][RED_THREADS / 32];
+  __shared__ int sip[3];
+  __shared__ df sfr[3];
+  const int p = blockIdx.x;
+  const df* Fc = static_cast<const df*>(P.s.Fc);
+  const long long loff = P.list_off[p];
+  const int cnt = P.list_cnt[p];
+  if (threadIdx.x < 3) {  // centre = integer part + (1/2 - fraction), once per block
+    const double xp = P.p.x[3 * p + threadIdx.x];
+    const double fl = floor(xp);
+    sip[threadIdx.x] = (int)fl;
+    sfr[threadIdx.x] = df(0.5 - (xp - fl));
+  }
+  __syncthreads();
+  const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
+  df acc[6];
+  for (int i = 0; i < 6; ++i) acc[i] = df(0.f, 0.f);
+  for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
+    const int e = P.list[loff + k];
+    const int2 pid = P.s.pid[e];
+    const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
+    if (s < 0) continue;
+    int c3[3];
+    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    df d3[3];
+    for (int a = 0; a < 3; ++a) {
+      int k0 = c3[a] - sip[a];
+      if (!P.g.wall[a]) {
+        if (2 * k0 > dims[a]) k0 -= dims[a];
+        else if (2 * k0 < -dims[a]) k0 += dims[a];
+      }
+      d3[a] = df((float)k0, 0.f) + sfr[a];
+    }
+    const long long fo = 3 * (s * P.s.cap + e);
+    const float2 u = reinterpret_cast<const float2*>(Fc)[fo];
+    const float2 v = reinterpret_cast<const float2*>(Fc)[fo + 1];
+    const float2 w = reinterpret_cast<const float2*>(Fc)[fo + 2];
+    const df f0(u.x, u.y), f1(v.x, v.y), f2(w.x, w.y);
+    acc[0] = renorm(acc[0] + f0);
+    acc[1] = renorm(acc[1] + f1);
+    acc[2] = renorm(acc[2] + f2);
+    acc[3] = renorm(acc[3] + (d3[1] * f2 - d3[2] * f1));
+    acc[4] = renorm(acc[4] + (d3[2] * f0 - d3[0] * f2));
+    acc[5] = renorm(acc[5] + (d3[0] * f1 - d3[1] * f0));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1)
+    for (int i = 0; i < 6; ++i) {
+      const df q(__shfl_down_sync(0xffffffffu, acc[i].hi, o),
+                 __shfl_down_sync(0xffffffffu, acc[i].lo, o));
+      acc[i] = renorm(acc[i] + q);
+    }
+  if (lane == 0)
+    for (int i = 0; i < 6; ++i) sh[i][wid] = acc[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[6];
+    for (int i = 0; i < 6; ++i) {
+      df t = sh[i][0];
+      for (int w = 1; w < RED_THREADS / 32; ++w) t = renorm(t + sh[i][w]);
+      tot[i] = to_double(t);
+    }
+    bool finite = true;
+    for (int i = 0; i < 3; ++i) {
+      P.p.Fh[3 * p + i] = tot[i];
+      P.p.Th[3 * p + i] = tot[3 + i];
+      finite = finite && isfinite(tot[i]) && isfinite(tot[3 + i]);
+    }
+    if (!finite) atomicOr(P.status, ST_NONFINITE);
+  }
+}
+
 __global__ void pack_particles_kernel(Particles p) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.n) return;
@@ -1090,6 +1223,7 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
     out.work = P.mlp_work;
     out.cap = P.s.cap;
     out.fp32 = P.fp32;
+    out.dfrec = P.dfrec;
     out.nt = P.weighting;
     out.tau = P.tau;
     launches += launch_mlp_infer(P.mlp, -1, P.mlp_count, P.mlp_cap, P.mlp_X, out, P.status, s);
@@ -1107,6 +1241,7 @@ int launch_weight_table(int n, double tau, int weighting, double* out, cudaStrea
 int launch_force_reduce(MapParams P, cudaStream_t s) {
   if (P.p.n == 0) return 0;
   if (P.fp32) force_reduce_f32_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
+  else if (P.dfrec) force_reduce_df_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
   else force_reduce_kernel<double><<<P.p.n, RED_THREADS, 0, s>>>(P);
   return 1;
 }

@@ -349,7 +349,8 @@ __device__ __forceinline__ void apply_weight(const InferSink& o, long long rec, 
     const double eps = (double)epsf;
     double B = eps;
     if (o.nt && eps != 0.0 && eps != 1.0) B = eps * (o.tau - 0.5) / ((1.0 - eps) + (o.tau - 0.5));
-    static_cast<double*>(o.V)[4 * rec + 3] = B;
+    if (o.dfrec) static_cast<df*>(o.V)[4 * rec + 3] = df(B);
+    else static_cast<double*>(o.V)[4 * rec + 3] = B;
   }
 }
 

@@ -161,6 +161,7 @@ MapParams map_params(psm_ctx* c) {
   P.cov = c->cov;
   P.s = c->slots;
   P.fp32 = c->fp32;
+  P.dfrec = c->prec == PREC_DF;
   P.eps_mode = c->opt.eps_mode;
   P.eps_n = c->opt.eps_n;
   P.weighting = c->opt.weighting;
@@ -436,7 +437,8 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->mlp = alloc_n<float>(c, PSM_MLP_PARAMS, c->allocs);
   c->mlp_count = alloc_n<int>(c, 1, c->allocs);
   c->dem_bar = alloc_n<unsigned>(c, 4, c->allocs);
-  c->wtab = alloc_n<double>(c, 513 + 257, c->allocs);  // 513 doubles + 513 floats
+  // 513 doubles, 513 floats, 513 double-float pairs
+  c->wtab = alloc_n<double>(c, 513 + 257 + 513, c->allocs);
   if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
       !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar || !c->wtab)
     return bail(PSM_ERR_OOM, "allocator returned NULL");

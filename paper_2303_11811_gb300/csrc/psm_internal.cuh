@@ -154,7 +154,8 @@ struct MapParams {
   Particles p;
   Coverage cov;
   Slots s;
-  int fp32;             // slot B stored as float2 (1) or double2 (0)
+  int fp32;             // slot records and forces in FP32 (1), else FP64 or double-float
+  int dfrec;            // slot records and forces as double-float pairs (the df form)
   int eps_mode, eps_n, weighting;
   double tau;
   unsigned* status;
@@ -279,7 +280,7 @@ struct InferSink {
   const float* lin;    // linear approximation (Eqs. 25-27) per item
   const int* work;     // item -> 2 * slot entry + slot
   long long cap;       // slot entries allocated
-  int fp32, nt;        // record precision; Noble-Torczynski weighting
+  int fp32, dfrec, nt; // record precision (FP32, double-float, else FP64); weighting
   double tau;
 };
 int launch_mlp_infer(const float* params, long long m, const int* m_dev, long long cap,

@@ -134,3 +134,30 @@ def test_df64_settle128_full_size_three_steps(capi):
     xo, _, _ = o.particles()
     assert np.max(np.abs(xg - xo)) < 1e-12
     e.close()
+
+
+@pytest.mark.parametrize("eps_mode,eps_n", [("supersample", 8), ("mlp", 8)])
+def test_df64_mapping_records(capi, eps_mode, eps_n):
+    """The double-float form keeps its slot records as FP32 pairs: the same
+    slots as the FP64 form and the same weights to the pairs' precision
+    (surrogate mode included: its weights are written by the inference)."""
+    shape = (48, 40, 36)
+    kw = dict(tau=0.6, relax="srt", weighting="nt", eps_mode=eps_mode, eps_n=eps_n)
+    a = capi.Engine(*shape, precision="df64", **kw)
+    b = capi.Engine(*shape, precision="fp64", **kw)
+    x = np.array([[1.2, 39.4, 17.9], [24.25, 20.0, 18.0], [24.25 + 9.4, 20.3, 18.5],
+                  [46.9, 3.3, 35.2]])
+    r = np.array([5.5, 4.0, 5.0, 3.3])
+    params = capi.pack_mlp(inputs.mlp_init(4))
+    for s in (a, b):
+        if eps_mode == "mlp":
+            s.set_mlp(params)
+        s.set_particles(x, r)
+        s.step(1)
+    pa0, ba0, pa1, ba1 = a.slots()
+    pb0, bb0, pb1, bb1 = b.slots()
+    assert np.array_equal(pa0, pb0) and np.array_equal(pa1, pb1)
+    assert np.max(np.abs(ba0 - bb0)) < 1e-14 and np.max(np.abs(ba1 - bb1)) < 1e-14
+    assert (pa1 >= 0).sum() > 0
+    a.close()
+    b.close()
