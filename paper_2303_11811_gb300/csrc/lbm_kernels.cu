@@ -14,8 +14,6 @@
 // weighted by (1 - B) and each particle i adds B_i C^s_i (Eq. 19), whose
 // symmetric part per pair is E_s(U_p) - E_s(U_f) and antisymmetric part
 // E_a(U_f) + E_a(U_p) - a_k; its momentum gives the force of Eq. 21.
-#include <type_traits>
-
 #include "df.cuh"
 #include "psm_internal.cuh"
 
@@ -289,29 +287,31 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   //                     = -omega+/2 s_k + ((9/2 omega+ w) c.U + G_k) c.U + C_c
   //   antisymmetric     = -omega-/2 a_k + 3 omega- w c.U + F_k
   // with C_c = omega+ w base0 + H_c U.f once per class.
-  const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
-  const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
   // the (1 - B) weight is a multiply-add in FP32/FP64; in double-float it is
   // a product of its own, skipped in warps without a covered cell
-  auto relax = [&](auto weighted) {
-    constexpr bool W = decltype(weighted)::value;
-    {
-      const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
-      d[0] += W ? omB * dl : dl;
-    }
+  const bool weighted = !kDF<T> || m != 0u;
+  {
+    const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
+    if (kDF<T> && !weighted) d[0] += dl;
+    else d[0] += omB * dl;
+  }
+  const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
+  const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      T pk[4];
-      ld4(cf->pair[k], pk);
-      const T cu = cdot<T>(k, Ux, Uy, Uz);
-      const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
-      const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
-      d[2 * k + 1] += W ? omB * (ds + da) : ds + da;
-      d[2 * k + 2] += W ? omB * (ds - da) : ds - da;
+  for (int k = 0; k < 9; ++k) {
+    T pk[4];
+    ld4(cf->pair[k], pk);
+    const T cu = cdot<T>(k, Ux, Uy, Uz);
+    const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
+    const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
+    if (kDF<T> && !weighted) {
+      d[2 * k + 1] += ds + da;
+      d[2 * k + 2] += ds - da;
+    } else {
+      d[2 * k + 1] += omB * (ds + da);
+      d[2 * k + 2] += omB * (ds - da);
     }
-  };
-  if (kDF<T> && m == 0u) relax(std::false_type{});
-  else relax(std::true_type{});
+  }
 
   // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
   // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
@@ -1061,7 +1061,7 @@ __global__ void step_const_kernel(MapParams P) {
   }
   fill_coef<double>(sc->d, f, P.omega_p, P.omega_m);
   fill_coef<float>(sc->f, f, P.omega_p, P.omega_m);
-  fill_coef<df>(sc->x, f, P.omega_p, P.omega_m);
+  if (P.dfrec) fill_coef<df>(sc->x, f, P.omega_p, P.omega_m);
 }
 
 int launch_step_const(MapParams P, cudaStream_t s) {

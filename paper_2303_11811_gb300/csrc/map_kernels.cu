@@ -478,7 +478,10 @@ __device__ __forceinline__ int net_class(const Grid& g, const Box& b, const Cell
 // of the n^3 + 1 sampled values when eps is a count), and the particle's
 // surface velocity at the cell centre (Eq. 20); the list entry becomes the
 // slot index (and, for the FP32 path, the float offset from the centre).
-template <int NS>
+// record formats of the slot records the fill pass writes
+enum { REC_FP64 = 0, REC_FP32 = 1, REC_DF = 2 };
+
+template <int NS, int REC>
 __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   __shared__ double s64[16];
   __shared__ float s32[16];
@@ -489,6 +492,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   __shared__ float toff32[3][FILL_AXIS];
   __shared__ df toffd[3][FILL_AXIS];  // double-float records: offsets as pairs
   __shared__ df sud[6];               // and the particle's u, omega
+  __shared__ float suf[6];            // u, omega rounded to FP32 (FP32 records)
   const int p = blockIdx.x;
   if (threadIdx.x == 0) sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
   const double fr = P.p.fr[p];
@@ -504,18 +508,20 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
         const double d = ((double)(b.lo[a] + k) + 0.5) - b.xp[a];
         toff[a][k] = d;
         toff32[a][k] = (float)d;
-        if (P.dfrec) toffd[a][k] = df(d);
+        if (REC == REC_DF) toffd[a][k] = df(d);
       }
     }
   }
-  if (P.dfrec && threadIdx.x < 6)
-    sud[threadIdx.x] = df(threadIdx.x < 3 ? P.p.u[3 * p + threadIdx.x]
-                                          : P.p.om[3 * p + threadIdx.x - 3]);
+  if (threadIdx.x < 6) {
+    const double v = threadIdx.x < 3 ? P.p.u[3 * p + threadIdx.x] : P.p.om[3 * p + threadIdx.x - 3];
+    suf[threadIdx.x] = (float)v;
+    if (REC == REC_DF) sud[threadIdx.x] = df(v);
+  }
   __syncthreads();
   const double u0 = P.p.u[3 * p], u1 = P.p.u[3 * p + 1], u2 = P.p.u[3 * p + 2];
   const double o0 = P.p.om[3 * p], o1 = P.p.om[3 * p + 1], o2 = P.p.om[3 * p + 2];
-  const float uf0 = (float)u0, uf1 = (float)u1, uf2 = (float)u2;
-  const float of0 = (float)o0, of1 = (float)o1, of2 = (float)o2;
+  const float uf0 = suf[0], uf1 = suf[1], uf2 = suf[2];
+  const float of0 = suf[3], of1 = suf[4], of2 = suf[5];
   const float* wtabf = reinterpret_cast<const float*>(wtab + WTAB);  // FP32 copy
   const df* wtabd = reinterpret_cast<const df*>(wtab + WTAB_DF);      // double-float copy
   const float rf = (float)b.r, rinvf = 1.0f / rf, frf = (float)fr;  // surrogate inputs
@@ -547,12 +553,16 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   // 8^3 count is taken by the whole warp), lanes past the list idle
   const int lane = threadIdx.x & 31;
   const double r2 = b.r * b.r;
-  for (int k0 = threadIdx.x & ~31; k0 < cnt; k0 += MAP_THREADS) {
-    const int k = k0 + lane;
-    bool ok = k < cnt;
+  // 8^3 sampling iterates whole warps (its counts are taken by all lanes);
+  // the other modes give each thread its own cells
+  for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += MAP_THREADS) {
+    const int k = NS == 8 ? k0 + lane : k0;
+    bool ok = NS == 8 ? k < cnt : true;
     CellHit h;
-    h.dx = h.dy = h.dz = 0.0;
-    h.dxf = h.dyf = h.dzf = 0.f;
+    if constexpr (NS == 8) {  // lanes past the list still take part in the shuffles
+      h.dx = h.dy = h.dz = 0.0;
+      h.dxf = h.dyf = h.dzf = 0.f;
+    }
     long long cell = 0, e = 0;
     int s = 0;
     if (ok) {
@@ -612,19 +622,21 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       const int cls = net_class(P.g, b, h);
       if (cls == 1) {
         B = 1.0;
+        Bf = 1.f;
       } else if (cls == 2) {
         const int c = supersample_count_n<8>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f,
                                              b.E);
         B = weight((double)c * (1.0 / 512.0), P.tau, P.weighting);
+        Bf = (float)B;
       } else {
         B = -1.0;
+        Bf = -1.f;
         want = true;
       }
-      Bf = (float)B;
     } else if (tab) {
       const int c = NS == 8 ? count8 : cell_count<NS>(P, b, h, s64, s32);
       cidx = c;
-      if (P.fp32) Bf = __ldg(&wtabf[c]);
+      if (REC == REC_FP32) Bf = __ldg(&wtabf[c]);
       else B = __ldg(&wtab[c]);
     } else {
       h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
@@ -633,13 +645,13 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       Bf = (float)B;
     }
     const long long rec = s * P.s.cap + e;  // slot s's record: velocity and B
-    if (P.fp32) {
+    if (REC == REC_FP32) {
       // the FP32 collision takes the surface velocity in FP32
       const float fx = h.dxf, fy = h.dyf, fz = h.dzf;
       static_cast<float4*>(P.s.V)[rec] =
           make_float4(uf0 + (of1 * fz - of2 * fy), uf1 + (of2 * fx - of0 * fz),
                       uf2 + (of0 * fy - of1 * fx), Bf);
-    } else if (P.dfrec) {
+    } else if (REC == REC_DF) {
       // the double-float form: surface velocity (Eq. 20) in double-float from
       // the pairs of the offsets and of u, omega; B from the table's pairs
       df dx, dy, dz;
@@ -748,6 +760,54 @@ __device__ __forceinline__ void rec_store(double* p, const double* o) {
   reinterpret_cast<double2*>(p)[1] = make_double2(o[2], o[3]);
 }
 
+// weights of the slots left pending (B < 0: cells of two particles in
+// surrogate mode, worklist overflow, no network set) by 8^3 sampling, one
+// warp-wide count per pending slot; pend/pend1: lanes with slot 0 / slot 1
+// pending (every lane of the warp calls this together)
+template <typename T>
+struct WeightPair {
+  T b0, b1;
+};
+template <typename T>
+__device__ __noinline__ WeightPair<T> pending_weights(const MapParams& P, int e, int2 pid,
+                                                      unsigned pend, unsigned pend1, T B0, T B1) {
+  const unsigned full = 0xffffffffu;
+  while (pend | pend1) {
+    const bool s1 = pend == 0u;
+    const int L = __ffs(s1 ? pend1 : pend) - 1;
+    if (s1) pend1 &= pend1 - 1u; else pend &= pend - 1u;
+    double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0;
+    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if ((threadIdx.x & 31) == L) {
+      int x, y, z;
+      cell_xyz(P.g, P.s.cell[e], x, y, z);
+      const int p = s1 ? pid.y : pid.x;
+      const double r = P.p.r[p];
+      dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+      dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+      dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+      r2 = r * r;
+      f[0] = (float)dx;
+      f[1] = (float)dy;
+      f[2] = (float)dz;
+      f[3] = (float)r2;
+      f[4] = certified_band(r);
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) f[i] = __shfl_sync(full, f[i], L);
+    const int cnt = warp_count8(f[0], f[1], f[2], f[3], f[4], L, dx, dy, dz, r2);
+    if ((threadIdx.x & 31) == L) {
+      // B of the count: from the context's table when it holds the 8^3 counts
+      const bool tab8 = P.wtab != nullptr && P.eps_n == 8;
+      const T B = tab8 ? (sizeof(T) == 4 ? (T)reinterpret_cast<const float*>(P.wtab + WTAB)[cnt]
+                                         : (T)P.wtab[cnt])
+                       : (T)weight((double)cnt * (1.0 / 512.0), P.tau, P.weighting);
+      if (s1) B1 = B; else B0 = B;
+    }
+  }
+  return WeightPair<T>{B0, B1};
+}
+
 // one slot entry of the finish pass in the storage precision T, taken by a
 // whole warp (lanes with e >= n take part in the sampling only): order the two
 // slots by particle index, sample the slots left pending (B < 0: cells of two
@@ -778,38 +838,14 @@ __device__ double finish_entry(const MapParams& P, int e, int n) {
       }
     }
   }
-  // pending slots, one warp-wide count each
-  const unsigned full = 0xffffffffu;
-  unsigned pend = __ballot_sync(full, live && r0[3] < T(0));          // slot 0 pending
-  unsigned pend1 = __ballot_sync(full, live && two && r1[3] < T(0));  // slot 1 pending
-  while (pend | pend1) {
-    const bool s1 = pend == 0u;
-    const int L = __ffs(s1 ? pend1 : pend) - 1;
-    if (s1) pend1 &= pend1 - 1u; else pend &= pend - 1u;
-    double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0;
-    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if ((threadIdx.x & 31) == L) {
-      int x, y, z;
-      cell_xyz(P.g, P.s.cell[e], x, y, z);
-      const int p = s1 ? pid.y : pid.x;
-      const double r = P.p.r[p];
-      dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-      dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-      dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-      r2 = r * r;
-      f[0] = (float)dx;
-      f[1] = (float)dy;
-      f[2] = (float)dz;
-      f[3] = (float)r2;
-      f[4] = certified_band(r);
-    }
-#pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = __shfl_sync(full, f[i], L);
-    const int cnt = warp_count8(f[0], f[1], f[2], f[3], f[4], L, dx, dy, dz, r2);
-    if ((threadIdx.x & 31) == L) {
-      const T B = (T)weight((double)cnt * (1.0 / 512.0), P.tau, P.weighting);
-      if (s1) r1[3] = B; else r0[3] = B;
-    }
+  // pending slots, one warp-wide count each (out of line: rare, and its
+  // registers should not weigh on the common path)
+  const unsigned pend = __ballot_sync(0xffffffffu, live && r0[3] < T(0));
+  const unsigned pend1 = __ballot_sync(0xffffffffu, live && two && r1[3] < T(0));
+  if (pend | pend1) {
+    const WeightPair<T> w = pending_weights<T>(P, e, pid, pend, pend1, r0[3], r1[3]);
+    r0[3] = w.b0;
+    r1[3] = w.b1;
   }
   if (!live) return 0.0;
   T B = r0[3] + r1[3];
@@ -1172,6 +1208,14 @@ unsigned grid_cap(long long n, int block) {
   return (unsigned)(b > 0 ? b : 1);
 }
 
+template <int REC>
+void launch_fill(const MapParams& P, bool mlp, cudaStream_t s) {
+  if (mlp) fill_kernel<-1, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+  else if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+  else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+  else fill_kernel<0, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+}
+
 int map_common(MapParams P, cudaStream_t s, bool mlp) {
   int launches = 0;
   cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
@@ -1187,10 +1231,10 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
   clear_slots_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P);
   launches += 4;
   if (P.p.n > 0) {
-    if (mlp) fill_kernel<-1><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    else if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    else fill_kernel<0><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+    const int rec = P.fp32 ? REC_FP32 : (P.dfrec ? REC_DF : REC_FP64);
+    if (rec == REC_FP32) launch_fill<REC_FP32>(P, mlp, s);
+    else if (rec == REC_DF) launch_fill<REC_DF>(P, mlp, s);
+    else launch_fill<REC_FP64>(P, mlp, s);
     ++launches;
   }
   return launches;
