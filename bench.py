@@ -488,7 +488,7 @@ def main():
               "class_ms_per_step": {"mapping": t[0] / t[4], "stream_collide": lbm_ms,
                                     "force_reduce": t[2] / t[4], "dem": t[3] / t[4]}}
     if fp64:
-        # FP64 runs at 1/58 of the FP32 rate on this GPU: the FP64 pipe binds
+        # FP64 runs at 1/64 of the FP32 rate on this GPU: the FP64 pipe binds
         sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
         peak = fp64_peak_tflops(sm_max)
         flops = FLOP_PER_CELL * cells + FLOP_PER_SLOT * nslot

@@ -21,7 +21,7 @@
 // with plain IEEE FP64 operations (this file is compiled with -fmad=false),
 // so the sums are bitwise reproducible; then the velocity update and the next
 // sub-step's positions (Eqs. 15-16 with dt/(2m), dt/(2I) formed once per
-// sub-step: equal to the quotients up to rounding).  FP64 runs at 1/58 of the FP32 rate here, so each
+// sub-step: equal to the quotients up to rounding).  FP64 runs at 1/64 of the FP32 rate here, so each
 // FP64 instruction works on 32 particles and the blocks (32 threads) spread
 // over many SMs.
 #include "psm_internal.cuh"

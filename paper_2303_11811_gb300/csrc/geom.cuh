@@ -4,7 +4,7 @@
 // The definition is an FP64 computation: sample offsets
 //   s_a = (a + 1/2)/n - 1/2,  p = d + s,  inside <=> ((p_x^2 + p_y^2) + p_z^2) <= r^2
 // with every operation rounded in FP64 (files including this are compiled with
-// -fmad=false).  FP64 runs at 1/58 of the FP32 rate on this GPU, so the count
+// -fmad=false).  FP64 runs at 1/64 of the FP32 rate on this GPU, so the count
 // is evaluated in FP32 and a sample goes to the FP64 definition only when its
 // FP32 value lies within a certified bound E of r^2:
 //   |S_fp32 - S_fp64| <= 2^-19 (r + 2.5)^2 for |d| <= r + 2 (each of the three

@@ -314,7 +314,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   }
 
   // ---- solid operator of each overlapping particle (Eqs. 19-21).  In FP64
-  // (1/58 of the FP32 rate here) the work is shared out over the lanes of the
+  // (1/64 of the FP32 rate here) the work is shared out over the lanes of the
   // warp; in FP32 each covered lane does its own cell.
   if constexpr (!kFP64<T>) {
   if (cov) {

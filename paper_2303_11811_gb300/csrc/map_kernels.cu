@@ -77,6 +77,23 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
   return b;
 }
 
+// Every particle's box, one thread per particle: the FP64 set-up of the mark
+// and fill passes (on GB300 a serial FP64 sequence in one thread of each
+// block would hold the block at its first barrier)
+__global__ void box_kernel(MapParams P) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P.p.n) static_cast<Box*>(P.boxes)[p] = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
+}
+
+// a particle's box into shared memory, copied by the block's threads
+__device__ __forceinline__ void load_box(const MapParams& P, int p, Box* sb) {
+  static_assert(sizeof(Box) % 4 == 0, "Box is copied as 32-bit words");
+  constexpr int W = (int)(sizeof(Box) / 4);
+  const int* src = reinterpret_cast<const int*>(static_cast<const Box*>(P.boxes) + p);
+  for (int i = threadIdx.x; i < W; i += blockDim.x) reinterpret_cast<int*>(sb)[i] = src[i];
+  __syncthreads();
+}
+
 // nearest image of cell coordinate i relative to xp (integer shifted first)
 __device__ __forceinline__ double image_d(int i, double xp, int n, int periodic) {
   double d = ((double)i + 0.5) - xp;
@@ -193,11 +210,8 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   const long long loff = P.list_off[p];
   const int lcap = (int)(P.list_off[p + 1] - loff);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    running = 0;
-    sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);  // FP64 set-up once per block
-  }
-  __syncthreads();
+  if (threadIdx.x == 0) running = 0;
+  load_box(P, p, &sbox);  // ends with __syncthreads
   const Box b = sbox;
   for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
     const int t = t0 + threadIdx.x;
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   __shared__ df sud[6];               // and the particle's u, omega
   __shared__ float suf[6];            // u, omega rounded to FP32 (FP32 records)
   const int p = blockIdx.x;
-  if (threadIdx.x == 0) sbox = particle_box(P.g, P.p.x + 3 * p, P.p.r[p]);
+  load_box(P, p, &sbox);
   const double fr = P.p.fr[p];
   const bool tab = P.eps_mode == 0 && P.wtab != nullptr;
   const double* wtab = P.wtab;
@@ -768,35 +782,49 @@ template <typename T>
 struct WeightPair {
   T b0, b1;
 };
+// the FP64 set-up of one pending slot's count, in the lane that owns it
+struct PendingPrep {
+  double dx, dy, dz, r2;
+  float f[5];  // FP32 roundings of dx, dy, dz, r^2 and the certified band
+};
+__device__ __forceinline__ PendingPrep pending_prep(const MapParams& P, int cell, int p) {
+  PendingPrep q;
+  int x, y, z;
+  cell_xyz(P.g, cell, x, y, z);
+  const double r = P.p.r[p];
+  q.dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
+  q.dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
+  q.dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
+  q.r2 = r * r;
+  q.f[0] = (float)q.dx;
+  q.f[1] = (float)q.dy;
+  q.f[2] = (float)q.dz;
+  q.f[3] = (float)q.r2;
+  q.f[4] = certified_band(r);
+  return q;
+}
+
 template <typename T>
 __device__ __noinline__ WeightPair<T> pending_weights(const MapParams& P, int e, int2 pid,
                                                       unsigned pend, unsigned pend1, T B0, T B1) {
   const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  // every pending lane forms its FP64 set-up at once (an FP64 instruction
+  // costs a warp the same for one lane as for 32)
+  PendingPrep q0{}, q1{};
+  const int cell = (((pend | pend1) >> lane) & 1u) ? P.s.cell[e] : 0;
+  if ((pend >> lane) & 1u) q0 = pending_prep(P, cell, pid.x);
+  if ((pend1 >> lane) & 1u) q1 = pending_prep(P, cell, pid.y);
   while (pend | pend1) {
     const bool s1 = pend == 0u;
     const int L = __ffs(s1 ? pend1 : pend) - 1;
     if (s1) pend1 &= pend1 - 1u; else pend &= pend - 1u;
-    double dx = 0.0, dy = 0.0, dz = 0.0, r2 = 0.0;
-    float f[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if ((threadIdx.x & 31) == L) {
-      int x, y, z;
-      cell_xyz(P.g, P.s.cell[e], x, y, z);
-      const int p = s1 ? pid.y : pid.x;
-      const double r = P.p.r[p];
-      dx = image_d(x, P.p.x[3 * p], P.g.nx, !P.g.wall[0]);
-      dy = image_d(y, P.p.x[3 * p + 1], P.g.ny, !P.g.wall[1]);
-      dz = image_d(z, P.p.x[3 * p + 2], P.g.nz, !P.g.wall[2]);
-      r2 = r * r;
-      f[0] = (float)dx;
-      f[1] = (float)dy;
-      f[2] = (float)dz;
-      f[3] = (float)r2;
-      f[4] = certified_band(r);
-    }
+    const PendingPrep& q = s1 ? q1 : q0;
+    float f[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) f[i] = __shfl_sync(full, f[i], L);
-    const int cnt = warp_count8(f[0], f[1], f[2], f[3], f[4], L, dx, dy, dz, r2);
-    if ((threadIdx.x & 31) == L) {
+    for (int i = 0; i < 5; ++i) f[i] = __shfl_sync(full, q.f[i], L);
+    const int cnt = warp_count8(f[0], f[1], f[2], f[3], f[4], L, q.dx, q.dy, q.dz, q.r2);
+    if (lane == L) {
       // B of the count: from the context's table when it holds the 8^3 counts
       const bool tab8 = P.wtab != nullptr && P.eps_n == 8;
       const T B = tab8 ? (sizeof(T) == 4 ? (T)reinterpret_cast<const float*>(P.wtab + WTAB)[cnt]
@@ -977,7 +1005,7 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
 // parts); every component is summed with an error-free two-sum (a float pair
 // carrying about 48 bits), across the block by shuffles in a fixed order, and
 // converted to FP64 once.  No FP64 arithmetic per entry: GB300 runs FP64 at
-// 1/58 of the FP32 rate.
+// 1/64 of the FP32 rate.
 struct FloatPair {
   float hi, lo;
   __device__ __forceinline__ void add(float x) {
@@ -1221,8 +1249,9 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
   cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
   if (mlp) cudaMemsetAsync(P.mlp_count, 0, sizeof(int), s);
   if (P.p.n > 0) {
+    box_kernel<<<(P.p.n + 127) / 128, 128, 0, s>>>(P);
     mark_kernel<<<P.p.n, MAP_THREADS, 0, s>>>(P);
-    ++launches;
+    launches += 2;
   }
   const unsigned nb = (unsigned)P.cov.nblocks;
   scan_words_kernel<<<nb, SCAN_THREADS, 0, s>>>(P.cov, P.g.nwords);
@@ -1274,6 +1303,8 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
   }
   return launches + map_finish(P, s);
 }
+
+size_t map_box_bytes() { return sizeof(Box); }
 
 int launch_weight_table(int n, double tau, int weighting, double* out, cudaStream_t s) {
   const int n3 = n * n * n;

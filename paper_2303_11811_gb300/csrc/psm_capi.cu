@@ -73,6 +73,7 @@ struct psm_ctx {
   long long* list_off = nullptr;  // per-particle entry lists (force reduction)
   int* list = nullptr;
   int* list_cnt = nullptr;
+  void* boxes = nullptr;     // per-particle box of cells (mapping set-up)
   bool error_state = false;
   std::string err;
   // graphs: [buffer or parity][with mapping]
@@ -152,6 +153,7 @@ void free_particles(psm_ctx* c) {
   c->dem_nbr = nullptr;
   c->dem_xbuild = nullptr;
   c->list_cnt = nullptr;
+  c->boxes = nullptr;
 }
 
 MapParams map_params(psm_ctx* c) {
@@ -185,6 +187,7 @@ MapParams map_params(psm_ctx* c) {
   P.list_off = c->list_off;
   P.list = c->list;
   P.list_cnt = c->list_cnt;
+  P.boxes = c->boxes;
   return P;
 }
 
@@ -592,6 +595,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->list_off = alloc_n<long long>(c, (size_t)n + 1, c->palloc);
   c->list = alloc_n<int>(c, (size_t)list_total, c->palloc);
   c->list_cnt = alloc_n<int>(c, n1, c->palloc);
+  c->boxes = alloc_n<unsigned char>(c, n1 * map_box_bytes(), c->palloc);
   c->dem_bins = alloc_n<int>(c, 3 * (size_t)c->dem_nbins, c->palloc);
   c->dem_items = alloc_n<int>(c, 3 * n1, c->palloc);
   c->dem_nbr = alloc_n<int>(c, n1 * kDemListCap, c->palloc);

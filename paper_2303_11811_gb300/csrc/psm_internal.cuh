@@ -174,6 +174,7 @@ struct MapParams {
   int* mlp_work;
   int* mlp_count;
   long long mlp_cap;
+  void* boxes;          // per particle: its box of cells and FP64 set-up (map_box_bytes() each)
   // per-particle lists of covered slot entries (box order) for the
   // fixed-order force/torque reduction
   const long long* list_off;   // n+1 offsets
@@ -228,6 +229,7 @@ int launch_sums(const Grid& g, const double* f, double* partials, int nparts, do
 int launch_step_const(MapParams P, cudaStream_t s);
 
 int launch_map(MapParams P, cudaStream_t s);                   // full mapping
+size_t map_box_bytes();                                        // bytes per particle of MapParams::boxes
 int launch_force_reduce(MapParams P, cudaStream_t s);
 // table of B for the n^3 + 1 sampled counts (n^3 < 513); returns launches
 int launch_weight_table(int n, double tau, int weighting, double* out, cudaStream_t s);          // fixed-order F/T
