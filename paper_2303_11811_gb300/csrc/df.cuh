@@ -55,8 +55,13 @@ __device__ __forceinline__ df operator*(df a, df b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return df(p, e);
 }
-// canonical pair: hi the FP32 rounding of hi + lo (valid for any magnitudes)
+// canonical pair: hi the FP32 rounding of hi + lo (exact for any magnitudes)
 __device__ __forceinline__ df renorm(df a) { return two_sum(a.hi, a.lo); }
+// the same by Fast2Sum, for results of a sum or product (|lo| <= a few
+// ulp(hi); after a cancellation where |lo| > |hi| the pair is still put back
+// into canonical form, its value kept to within ulp(lo), the form's own
+// precision)
+__device__ __forceinline__ df renorm_fast(df a) { return fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
 __device__ __forceinline__ bool operator>(df a, df b) {
   a = renorm(a);

@@ -407,7 +407,7 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   if constexpr (kDF<T>) {
     // stored pairs are canonical, so their low parts do not grow over steps
 #pragma unroll
-    for (int q = 0; q < Q; ++q) d[q] = renorm(d[q]);
+    for (int q = 0; q < Q; ++q) d[q] = renorm_fast(d[q]);
   }
 }
 

@@ -3,10 +3,11 @@ oracle cannot step the whole field: sampled cells and budgets.
 
 Sampled cells (tests/subbox.py): the engine's post-collision PDFs of a cell
 after one step must equal the oracle's on a box around the cell: 1e-12
-relative in FP64; in FP32 the one-step bound of tests/test_gpu_fp32.py,
+relative in FP64 and in the double-float form (which is held to the FP64
+bound); in FP32 the one-step bound of tests/test_gpu_fp32.py,
 32 * 2^-24 * max|delta| over the neighbourhood.
 
-Budgets (FP64).  Mass is conserved to rounding; in a periodic box the fluid
+Budgets (FP64 and double-float).  Mass is conserved to rounding; in a periodic box the fluid
 momentum changes per step by V_fluid f - sum_i F_i (Eqs. 1, 8, 17, 21), with
 V_fluid and f the engine's own of that step (with walls, bounce-back passes
 momentum to the walls): sums over all cells, any size.
@@ -54,7 +55,7 @@ def _sampled_step(e, w, cells, precision):
     for c, fb in zip(cells, pre):
         got = e.pdfs_box(*c, 1, 1, 1)[:, 0, 0, 0]
         want = oracle_cell(w, c, fb, fext, xs, R, us, oms, dens)
-        if precision == "fp64":
+        if precision in ("fp64", "df64"):
             err = float(np.max(np.abs(got - want) / np.abs(want)))
             assert err < 1e-12, (c, err)
         else:
@@ -85,7 +86,7 @@ def _budgets(e, steps, periodic):
 
 
 @pytest.mark.parametrize("precision,streaming", [("fp64", "pull"), ("fp32", "pull"),
-                                                 ("fp32", "aa")])
+                                                 ("fp32", "aa"), ("df64", "pull")])
 def test_channel_full_size_sampled(capi, precision, streaming):
     """256x256x512 channel, walls at the x faces, 12,817 fixed spheres r=5,
     4^3 sampling: 24 sampled cells of one step after two warm-up steps; FP64
@@ -95,13 +96,14 @@ def test_channel_full_size_sampled(capi, precision, streaming):
     e = _engine(capi, w, precision, streaming)
     e.step(2)
     _sampled_step(e, w, sample_cells(w, 24, 11), precision)
-    if precision == "fp64":
+    if precision != "fp32":
         _budgets(e, 2, periodic=False)
     e.close()
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("precision,streaming", [("fp64", "pull"), ("fp32", "aa")])
+@pytest.mark.parametrize("precision,streaming", [("fp64", "pull"), ("fp32", "aa"),
+                                                 ("df64", "aa")])
 def test_settle512_full_size_sampled(capi, precision, streaming):
     """512x512x1024 periodic box (268M cells), 94,692 settling spheres r in
     [3, 6] at solid fraction 0.15, gravity, DEM: every step succeeds (no slot
@@ -112,7 +114,7 @@ def test_settle512_full_size_sampled(capi, precision, streaming):
     e = _engine(capi, w, precision, streaming)
     e.step(2)
     _sampled_step(e, w, sample_cells(w, 16, 12), precision)
-    if precision == "fp64":
+    if precision != "fp32":
         _budgets(e, 1, periodic=True)
     e.close()
     torch.cuda.empty_cache()
