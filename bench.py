@@ -147,6 +147,23 @@ def profiled_traffic(kernel_src, name):
     return traffic if (h == want and traffic) else None
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of a per-rank value over all ranks (the whole job's time is
+    that of its slowest replica); the value itself with one rank."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(cells_per_rank, steps, world, ms):
+    """Whole-job throughput: every rank updates its own cells (replicas,
+    weak scaling) in the job's time ms."""
+    return cells_per_rank * steps * world / (ms * 1e-3) / 1e6
+
+
 def make_engine(w, capi, precision="fp64", streaming="pull", eps_mode=None):
     e = capi.Engine(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=w.walls, fbody=w.fbody,
                     weighting=w.weighting, eps_mode=eps_mode or w.eps_mode, eps_n=w.eps_n,
@@ -449,12 +466,9 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     launches = e.last_launch_count()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     cells = w.cells
-    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    value = job_mlups(cells, args.steps, world, ms)
 
     # dominant kernel: per-class CUDA-event timings over a second pass of the
     # same loop (steps launched without graphs, events on the same stream)
@@ -514,6 +528,8 @@ def main():
     hT = torch.zeros((n, 3), dtype=torch.float64).pin_memory()
     ke = max(10, min(args.steps, 100))
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(ke):
         e.update_particles(hx.data_ptr(), hu.data_ptr(), ho.data_ptr())
@@ -522,7 +538,8 @@ def main():
         e.particles_into(hx.data_ptr(), hu.data_ptr(), ho.data_ptr())
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    e2e = {"value": cells * ke * world / te / 1e6, "unit": "MLUPS",
+    te = max_over_ranks(te, dist, "cuda")
+    e2e = {"value": job_mlups(cells, ke, world, te * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": 3 * 3 * n * 8, "d2h_bytes_per_step": (6 + 9) * n * 8,
            "steps": ke}
     e.close()
