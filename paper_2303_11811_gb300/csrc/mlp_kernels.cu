@@ -403,10 +403,32 @@ __global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
   const long long ntiles = (n + INF_M - 1) / INF_M;
   unsigned phase = 0;
   bool in_flight = false;
+  // software pipeline: a tile's inputs (and, in the mapping, its slot item
+  // and linear approximation) are loaded while the previous tile computes
+  auto load_row = [&](long long r, float4& xr, int& it, float& ln) {
+    xr = make_float4(0.f, 0.f, 0.f, 0.f);
+    it = -1;
+    ln = 0.f;
+    if (r < n) {
+      xr = X[r];
+      if (!o.eps) {
+        it = o.work[r];
+        ln = o.lin[r];
+      }
+    }
+  };
+  float4 x;
+  int item;
+  float lin;
+  load_row((long long)blockIdx.x * INF_M + tid, x, item, lin);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long row = tile * INF_M + tid;
     const bool live = row < n;
-    const float4 x = live ? X[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int cnt = item >= 0 ? __ldg(&o.cnt[item >> 1]) : 0;
+    float4 xn;
+    int itemn;
+    float linn;
+    load_row((tile + gridDim.x) * INF_M + tid, xn, itemn, linn);
     // layer 1 (FP32), ReLU, BF16 activations into the A operand
 #pragma unroll
     for (int kc = 0; kc < 4; ++kc) {
@@ -459,16 +481,15 @@ __global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
     if (live) {
       if (o.eps) {
         o.eps[row] = y;
-      } else {
-        const int item = o.work[row];  // -1: an empty item
-        const long long e = item >> 1;
-        if (item >= 0 && __ldg(&o.cnt[e]) == 1) {
-          float eps = o.lin[row] + y;
-          eps = eps < 0.f ? 0.f : (eps > 1.f ? 1.f : eps);
-          apply_weight(o, (item & 1) * o.cap + e, eps);
-        }
+      } else if (item >= 0 && cnt == 1) {  // item -1: an empty item
+        float eps = lin + y;
+        eps = eps < 0.f ? 0.f : (eps > 1.f ? 1.f : eps);
+        apply_weight(o, (item & 1) * o.cap + (item >> 1), eps);
       }
     }
+    x = xn;
+    item = itemn;
+    lin = linn;
     tc_fence_before();
     __syncthreads();  // the A tile and the accumulator are free again
   }
@@ -525,8 +546,9 @@ int launch_mlp_infer(const float* params, long long m, const int* m_dev, long lo
                      const float* X, const InferSink& out, unsigned* status, cudaStream_t s) {
   const long long rows = m >= 0 ? (m < cap ? m : cap) : cap;
   if (rows <= 0) return 0;
+  // up to 12 resident CTAs per SM (12 x 32 of the 512 tensor-memory columns)
   long long blocks = (rows + INF_M - 1) / INF_M;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks > 152 * 12) blocks = 152 * 12;
   infer_tc_kernel<<<(unsigned)blocks, INF_THREADS, 0, s>>>(
       params, m, m_dev, cap, reinterpret_cast<const float4*>(X), out, status);
   return 1;
