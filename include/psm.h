@@ -215,8 +215,10 @@ psm_status psm_train_surrogate(psm_ctx* ctx, long nsamples, unsigned long long s
  * training samples i = first .. first+count-1 of stream seed: network inputs
  * X (count*4) and 8^3 labels eps (count); loss and gradient (PSM_MLP_PARAMS
  * floats) of the mean squared error of params on (X, t); raw network output
- * of the BF16 inference kernel for inputs X (before the linear approximation
- * is added and the result clamped). */
+ * of the inference kernel for inputs X (before the linear approximation is
+ * added and the result clamped): layer 1 in FP32, layer 2 on the tensor cores
+ * (tcgen05.mma, BF16 operands, FP32 accumulation), layer 3 in FP32 — the
+ * kernel the mapping runs in PSM_EPS_MLP mode. */
 psm_status psm_mlp_samples(psm_ctx* ctx, unsigned long long seed, long first, long count,
                            float* X, float* eps);
 psm_status psm_mlp_loss_grad(psm_ctx* ctx, const float* params, long m, const float* X,
