@@ -263,6 +263,26 @@ long psm_last_launch_count(const psm_ctx* ctx);
 psm_status psm_field_sums_noalloc(const double* f, long long ncells, double* sums,
                                   void* stream);
 
+/* Checkpoint and restart of the time stepper (the loop of Sec. 3 and its
+ * Fig. "implementation"; the paper itself describes no checkpoint format).
+ * psm_save writes, to the file at path, everything a later step depends on:
+ * the PDF field in the storage form of ctx (its own values, not canonical
+ * FP64: a resumed run continues bit for bit), the per-particle state (x, u,
+ * omega, r, mass, inertia, volume, f(r), fixed flags, the last hydrodynamic
+ * force and torque, the DEM force history) and the surrogate's parameters
+ * when set.  psm_load reads such a file into ctx, which must have been
+ * created with the same grid, walls, precision, streaming pattern,
+ * relaxation, tau, magic parameter and DEM setting (PSM_ERR_ARG otherwise,
+ * and for a missing, foreign or truncated file, ctx unchanged in that case);
+ * derived state (slots, neighbour lists, step constants) is rebuilt on the
+ * next step, and an error state is cleared.  Both synchronise the stream of
+ * ctx.  The file is in the native byte order (little-endian on x86-64 and
+ * aarch64). */
+psm_status psm_save(psm_ctx* ctx, const char* path);
+psm_status psm_load(psm_ctx* ctx, const char* path);
+/* Number of particles of ctx (after psm_set_particles or psm_load). */
+psm_status psm_get_particle_count(const psm_ctx* ctx, int* n);
+
 /* Human-readable description of the last error of ctx (never NULL). */
 const char* psm_last_error(const psm_ctx* ctx);
 

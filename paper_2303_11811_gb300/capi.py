@@ -36,7 +36,7 @@ EXPORTS = [
     "psm_set_pdfs", "psm_get_slots", "psm_check", "psm_set_mlp", "psm_get_mlp",
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
     "psm_set_timing", "psm_get_timings", "psm_last_launch_count", "psm_last_error",
-    "psm_destroy", "psm_field_sums_noalloc",
+    "psm_destroy", "psm_field_sums_noalloc", "psm_save", "psm_load", "psm_get_particle_count",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -129,6 +129,12 @@ def lib():
     L.psm_destroy.restype = None
     L.psm_field_sums_noalloc.argtypes = [C.c_void_p, C.c_longlong, C.c_void_p, C.c_void_p]
     L.psm_field_sums_noalloc.restype = st
+    L.psm_save.argtypes = [P, C.c_char_p]
+    L.psm_save.restype = st
+    L.psm_load.argtypes = [P, C.c_char_p]
+    L.psm_load.restype = st
+    L.psm_get_particle_count.argtypes = [P, ip]
+    L.psm_get_particle_count.restype = st
     _lib = L
     return L
 
@@ -361,6 +367,17 @@ class Engine:
         P = np.zeros(3)
         self._check(self._L.psm_check(self.h, C.byref(m), _dp(P)))
         return m.value, P
+
+    def save(self, path):
+        """Checkpoint of the stepper state (psm_save)."""
+        self._check(self._L.psm_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """Restart from a checkpoint written by save() (psm_load)."""
+        self._check(self._L.psm_load(self.h, os.fsencode(path)))
+        n = C.c_int()
+        self._check(self._L.psm_get_particle_count(self.h, C.byref(n)))
+        self.np = n.value
 
     def set_mlp(self, params):
         p = _f32(params, PSM_MLP_PARAMS)

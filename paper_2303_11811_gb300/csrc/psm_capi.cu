@@ -349,6 +349,43 @@ psm_status canonical(psm_ctx* c, double** out, const BoxSel* box = nullptr) {
 
 }  // namespace
 
+// ---- checkpoint: the state of the time stepper, exactly.  Layout (native
+// byte order, little-endian on the supported hosts): a header of int64
+// fields, then the PDF storage as stored (the form's own values), the
+// per-particle arrays, the surrogate's parameters when set.
+namespace {
+constexpr char kCkptMagic[8] = {'P', 'S', 'M', 'C', 'K', 'P', 'T', '1'};
+enum {
+  CK_NX, CK_NY, CK_NZ, CK_WX, CK_WY, CK_WZ, CK_PREC, CK_AA, CK_RELAX, CK_PARITY, CK_N,
+  CK_MLP, CK_DEM, CK_FIELDS
+};
+struct CkptHeader {
+  char magic[8];
+  long long v[CK_FIELDS];
+  double tau, omega_m, G[3];
+};
+
+bool write_all(FILE* f, const void* p, size_t bytes) {
+  return bytes == 0 || fwrite(p, 1, bytes, f) == bytes;
+}
+bool read_all(FILE* f, void* p, size_t bytes) {
+  return bytes == 0 || fread(p, 1, bytes, f) == bytes;
+}
+
+// the per-particle device arrays of a checkpoint, in file order, with their
+// element counts (multiples of n) and sizes
+struct CkptArray {
+  void* dev;
+  size_t per, esz;
+};
+std::vector<CkptArray> ckpt_arrays(psm_ctx* c) {
+  Particles& P = c->p;
+  return {{P.x, 3, 8},  {P.u, 3, 8},   {P.om, 3, 8},   {P.r, 1, 8},    {P.m, 1, 8},
+          {P.I, 1, 8},  {P.vol, 1, 8}, {P.fr, 1, 8},   {P.fixed, 1, 1}, {P.Fh, 3, 8},
+          {P.Th, 3, 8}, {P.Fold, 3, 8}, {P.Told, 3, 8}};
+}
+}  // namespace
+
 extern "C" {
 
 void psm_default_options(psm_options* o) {
@@ -1015,6 +1052,128 @@ psm_status psm_update_particles(psm_ctx* c, const double* x, const double* u, co
   CK(cudaMemsetAsync(c->dem_bar + 2, 0, sizeof(unsigned), c->stream));  // new DEM lists
   CK(cudaGetLastError());
   c->need_map = true;
+  return PSM_OK;
+}
+
+
+// checkpoint of the stepper state (layout above)
+psm_status psm_save(psm_ctx* c, const char* path) {
+  if (!c || !path) return PSM_ERR_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  const int n = c->p.n;
+  CkptHeader h{};
+  std::memcpy(h.magic, kCkptMagic, 8);
+  const long long v[CK_FIELDS] = {c->g.nx, c->g.ny, c->g.nz, c->g.wall[0], c->g.wall[1],
+                                  c->g.wall[2], c->prec, c->aa, c->relax,
+                                  c->aa ? c->parity : 0, n, c->have_mlp ? 1 : 0,
+                                  c->opt.dem ? 1 : 0};
+  std::memcpy(h.v, v, sizeof(v));
+  h.tau = c->tau;
+  h.omega_m = c->omega_m;
+  for (int a = 0; a < 3; ++a) h.G[a] = c->G[a];
+  const size_t esz = c->prec == PREC_FP32 ? 4 : 8;
+  const size_t pdf_bytes = esz * Q * (size_t)c->g.ncell;
+  std::vector<unsigned char> host(pdf_bytes);
+  const void* field = c->aa ? c->buf[0] : c->buf[c->cur];
+  CK(cudaMemcpy(host.data(), field, pdf_bytes, cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, PSM_ERR_ARG, std::string("cannot open for writing: ") + path);
+  bool ok = write_all(f, &h, sizeof(h)) && write_all(f, host.data(), pdf_bytes);
+  for (const CkptArray& a : ckpt_arrays(c)) {
+    if (!ok || n == 0) break;
+    const size_t bytes = a.per * a.esz * (size_t)n;
+    std::vector<unsigned char> buf(bytes);
+    if (cudaMemcpy(buf.data(), a.dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      return fail(c, PSM_ERR_CUDA, "reading the particle state");
+    }
+    ok = write_all(f, buf.data(), bytes);
+  }
+  if (ok && c->have_mlp) {
+    std::vector<float> prm(PSM_MLP_PARAMS);
+    if (cudaMemcpy(prm.data(), c->mlp, sizeof(float) * PSM_MLP_PARAMS,
+                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      return fail(c, PSM_ERR_CUDA, "reading the surrogate parameters");
+    }
+    ok = write_all(f, prm.data(), sizeof(float) * PSM_MLP_PARAMS);
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(c, PSM_ERR_ARG, std::string("short write: ") + path);
+  return PSM_OK;
+}
+
+psm_status psm_load(psm_ctx* c, const char* path) {
+  if (!c || !path) return PSM_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, PSM_ERR_ARG, std::string("cannot open: ") + path);
+  auto bad = [&](const std::string& msg) {
+    std::fclose(f);
+    return fail(c, PSM_ERR_ARG, msg);
+  };
+  CkptHeader h{};
+  if (!read_all(f, &h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)
+    return bad("not a checkpoint of this engine");
+  const long long want[CK_N] = {c->g.nx, c->g.ny, c->g.nz, c->g.wall[0], c->g.wall[1],
+                                c->g.wall[2], c->prec, c->aa, c->relax};
+  for (int i = 0; i < CK_PARITY; ++i)
+    if (h.v[i] != want[i]) return bad("checkpoint of another grid, storage form or relaxation");
+  if (h.tau != c->tau || h.omega_m != c->omega_m || (h.v[CK_DEM] != 0) != (c->opt.dem != 0))
+    return bad("checkpoint of another tau, magic parameter or DEM setting");
+  const long long n = h.v[CK_N];
+  if (n < 0 || n > (1LL << 30)) return bad("bad particle count");
+  const size_t esz = c->prec == PREC_FP32 ? 4 : 8;
+  const size_t pdf_bytes = esz * Q * (size_t)c->g.ncell;
+  std::vector<unsigned char> field(pdf_bytes);
+  if (!read_all(f, field.data(), pdf_bytes)) return bad("truncated checkpoint (PDFs)");
+  // particle arrays in file order
+  std::vector<double> x(3 * n), u(3 * n), om(3 * n), r(n), m(n), I(n), vol(n), fr(n);
+  std::vector<unsigned char> fixed(n);
+  std::vector<double> Fh(3 * n), Th(3 * n), Fold(3 * n), Told(3 * n);
+  void* hosts[] = {x.data(),  u.data(),  om.data(),   r.data(),    m.data(),
+                   I.data(),  vol.data(), fr.data(),  fixed.data(), Fh.data(),
+                   Th.data(), Fold.data(), Told.data()};
+  const size_t per[] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 3, 3};
+  const size_t es[] = {8, 8, 8, 8, 8, 8, 8, 8, 1, 8, 8, 8, 8};
+  for (int i = 0; i < 13 && n > 0; ++i)
+    if (!read_all(f, hosts[i], per[i] * es[i] * (size_t)n))
+      return bad("truncated checkpoint (particles)");
+  std::vector<float> prm;
+  if (h.v[CK_MLP]) {
+    prm.resize(PSM_MLP_PARAMS);
+    if (!read_all(f, prm.data(), sizeof(float) * PSM_MLP_PARAMS))
+      return bad("truncated checkpoint (surrogate)");
+  }
+  std::fclose(f);
+  // particles through the regular path (buffers, lists, bins), then their
+  // saved derived values and force history over the recomputed ones
+  std::vector<double> dens(n);
+  for (long long i = 0; i < n; ++i) dens[i] = m[i] / vol[i];
+  psm_status st = psm_set_particles(c, (int)n, x.data(), r.data(), u.data(), om.data(),
+                                    dens.data(), fixed.data());
+  if (st != PSM_OK) return st;
+  const std::vector<CkptArray> arrs = ckpt_arrays(c);
+  for (int i = 4; i < 13 && n > 0; ++i)  // m, I, vol, fr, fixed, Fh, Th, Fold, Told
+    CK(cudaMemcpyAsync(arrs[i].dev, hosts[i], per[i] * es[i] * (size_t)n,
+                       cudaMemcpyHostToDevice, c->stream));
+  for (int a = 0; a < 3; ++a) c->G[a] = h.G[a];
+  if (!prm.empty()) {
+    st = psm_set_mlp(c, prm.data());
+    if (st != PSM_OK) return st;
+  }
+  c->cur = 0;
+  c->parity = c->aa ? (int)h.v[CK_PARITY] : 0;
+  CK(cudaMemcpyAsync(c->buf[0], field.data(), pdf_bytes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->need_map = true;
+  c->error_state = false;
+  return PSM_OK;
+}
+
+psm_status psm_get_particle_count(const psm_ctx* c, int* n) {
+  if (!c || !n) return PSM_ERR_ARG;
+  *n = c->p.n;
   return PSM_OK;
 }
 

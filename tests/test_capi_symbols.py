@@ -54,3 +54,22 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     o.eps_n = 0
     assert L.psm_create(ctypes.byref(g), 0.6, 0, ctypes.byref(o), ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_checkpoint_entries_reject_null_arguments_without_a_gpu():
+    """psm_save / psm_load / psm_get_particle_count check their arguments
+    before touching a context or the GPU."""
+    L = capi.lib()
+    n = ctypes.c_int(-1)
+    assert L.psm_save(None, b"/nonexistent/x.psm") == 1
+    assert L.psm_load(None, b"/nonexistent/x.psm") == 1
+    assert L.psm_get_particle_count(None, ctypes.byref(n)) == 1
+    assert n.value == -1
+    o = capi.PsmOptions()
+    L.psm_default_options(ctypes.byref(o))
+    g = capi.PsmGrid()
+    g.nx, g.ny, g.nz = 8, 8, 8
+    o.precision = capi.PSM_FP64_DF + 1  # not a storage form
+    h = ctypes.c_void_p()
+    assert L.psm_create(ctypes.byref(g), 0.6, 0, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert not h.value
