@@ -280,6 +280,18 @@ psm_status psm_field_sums_noalloc(const double* f, long long ncells, double* sum
  * aarch64). */
 psm_status psm_save(psm_ctx* ctx, const char* path);
 psm_status psm_load(psm_ctx* ctx, const char* path);
+/* Diagnostic of failure detection (the paper has no counterpart): runs each
+ * bounded device wait of the engine (the staged collision kernel's mbarrier
+ * wait, the surrogate inference's wait on the tensor-core commit, the DEM
+ * grid barrier) against a barrier that nothing completes, with a limit of
+ * limit_ns (0..1e9) instead of the production 1 s.  Each must give up and
+ * raise the timeout bit of the device status word; returns PSM_ERR_STATE if
+ * one did not, PSM_OK otherwise, leaving the bit set so that the next
+ * psm_step or psm_get_* reports PSM_ERR_TIMEOUT (and the context enters its
+ * error state until psm_set_pdfs or psm_load).  No wait that can hang is
+ * involved: every one is bounded by the global timer. */
+psm_status psm_selftest_waits(psm_ctx* ctx, long long limit_ns);
+
 /* Number of particles of ctx (after psm_set_particles or psm_load). */
 psm_status psm_get_particle_count(const psm_ctx* ctx, int* n);
 

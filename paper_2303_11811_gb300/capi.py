@@ -37,6 +37,7 @@ EXPORTS = [
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
     "psm_set_timing", "psm_get_timings", "psm_last_launch_count", "psm_last_error",
     "psm_destroy", "psm_field_sums_noalloc", "psm_save", "psm_load", "psm_get_particle_count",
+    "psm_selftest_waits",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -135,6 +136,8 @@ def lib():
     L.psm_load.restype = st
     L.psm_get_particle_count.argtypes = [P, ip]
     L.psm_get_particle_count.restype = st
+    L.psm_selftest_waits.argtypes = [P, C.c_longlong]
+    L.psm_selftest_waits.restype = st
     _lib = L
     return L
 
@@ -378,6 +381,10 @@ class Engine:
         n = C.c_int()
         self._check(self._L.psm_get_particle_count(self.h, C.byref(n)))
         self.np = n.value
+
+    def selftest_waits(self, limit_ns):
+        """Status of psm_selftest_waits (PSM_OK when every bounded wait gave up)."""
+        return self._L.psm_selftest_waits(self.h, int(limit_ns))
 
     def set_mlp(self, params):
         p = _f32(params, PSM_MLP_PARAMS)

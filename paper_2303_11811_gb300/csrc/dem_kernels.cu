@@ -316,7 +316,8 @@ __device__ __forceinline__ unsigned long long dem_ns() {
 
 // sense by generation: the last block to arrive resets the count and bumps
 // the generation the others wait on
-__device__ bool grid_barrier(const DemParams& P, unsigned& gen) {
+__device__ bool grid_barrier(const DemParams& P, unsigned& gen,
+                             unsigned long long limit_ns = kBarrierLimitNs) {
   __syncthreads();
   int ok = 1;
   if (threadIdx.x == 0) {
@@ -329,7 +330,7 @@ __device__ bool grid_barrier(const DemParams& P, unsigned& gen) {
       volatile unsigned* g = &P.bar[1];
       const unsigned long long t0 = dem_ns();
       while (*g == gen) {
-        if (dem_ns() - t0 > kBarrierLimitNs) {
+        if (dem_ns() - t0 > limit_ns) {
           ok = 0;
           atomicOr(P.status, ST_TIMEOUT);
           break;
@@ -420,6 +421,34 @@ int dem_max_blocks() {
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return 0;
   return per_sm * nsm;
+}
+
+// diagnostic: the grid barrier of the DEM step, entered by one block with
+// an arrival count that never completes, gives up after limit_ns and raises
+// ST_TIMEOUT (bar: 4 words of scratch, left zero)
+__global__ void barrier_selftest_kernel(unsigned* bar, unsigned* status,
+                                        unsigned long long limit_ns) {
+  DemParams P{};
+  P.bar = bar;
+  P.status = status;
+  if (threadIdx.x == 0) {
+    bar[0] = 1u;  // one arrival that no block made: the count never completes
+    bar[1] = 0u;
+    __threadfence();
+  }
+  unsigned gen = 0;
+  grid_barrier(P, gen, limit_ns);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bar[0] = 0u;
+    bar[1] = 0u;
+  }
+}
+
+int launch_wait_selftest_dem(unsigned* bar, unsigned* status, unsigned long long limit_ns,
+                             cudaStream_t s) {
+  barrier_selftest_kernel<<<1, DEM_THREADS, 0, s>>>(bar, status, limit_ns);
+  return 1;
 }
 
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s) {

@@ -546,15 +546,28 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned pari
       : "memory");
   return ok != 0;
 }
-// wait until the phase with the given parity has completed, at most kWaitLimitNs
-__device__ __noinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// wait until the phase with the given parity has completed, at most limit_ns
+__device__ __noinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                       unsigned long long limit_ns = kWaitLimitNs) {
   if (mbar_test(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     for (int i = 0; i < 64; ++i)
       if (mbar_test(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
+}
+
+// diagnostic: the staged kernel's bounded wait on an mbarrier that nothing
+// arrives on gives up after limit_ns and raises ST_TIMEOUT
+__global__ void wait_selftest_kernel(unsigned* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit_ns)) atomicOr(status, ST_TIMEOUT);
 }
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
                                               unsigned long long* bar) {
@@ -1062,6 +1075,11 @@ __global__ void step_const_kernel(MapParams P) {
   fill_coef<double>(sc->d, f, P.omega_p, P.omega_m);
   fill_coef<float>(sc->f, f, P.omega_p, P.omega_m);
   if (P.dfrec) fill_coef<df>(sc->x, f, P.omega_p, P.omega_m);
+}
+
+int launch_wait_selftest_lbm(unsigned* status, unsigned long long limit_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(status, limit_ns);
+  return 1;
 }
 
 int launch_step_const(MapParams P, cudaStream_t s) {

@@ -291,7 +291,8 @@ __device__ __forceinline__ bool inf_mbar_test(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-__device__ __noinline__ bool inf_mbar_wait(unsigned long long* bar, unsigned parity) {
+__device__ __noinline__ bool inf_mbar_wait(unsigned long long* bar, unsigned parity,
+                                           unsigned long long limit_ns = kInferWaitNs) {
   if (inf_mbar_test(bar, parity)) return true;
   unsigned long long t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -299,8 +300,20 @@ __device__ __noinline__ bool inf_mbar_wait(unsigned long long* bar, unsigned par
     for (int i = 0; i < 64; ++i)
       if (inf_mbar_test(bar, parity)) return true;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > kInferWaitNs) return false;
+    if (t - t0 > limit_ns) return false;
   }
+}
+
+// diagnostic: the inference kernel's bounded wait on an mbarrier that no
+// commit arrives on gives up after limit_ns and raises ST_TIMEOUT
+__global__ void infer_wait_selftest_kernel(unsigned* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !inf_mbar_wait(&bar, 0u, limit_ns)) atomicOr(status, ST_TIMEOUT);
 }
 __device__ __forceinline__ void tc_mma_bf16(unsigned d_tmem, uint64_t adesc, uint64_t bdesc,
                                             int accumulate) {
@@ -537,6 +550,11 @@ int launch_adam(float* params, const float* grad, float* mstate, float* vstate, 
   const float bc1 = 1.0f - powf(0.9f, (float)step);
   const float bc2 = 1.0f - powf(0.999f, (float)step);
   adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(params, grad, mstate, vstate, bc1, bc2, lr);
+  return 1;
+}
+
+int launch_wait_selftest_mlp(unsigned* status, unsigned long long limit_ns, cudaStream_t s) {
+  infer_wait_selftest_kernel<<<1, 32, 0, s>>>(status, limit_ns);
   return 1;
 }
 

@@ -1171,6 +1171,34 @@ psm_status psm_load(psm_ctx* c, const char* path) {
   return PSM_OK;
 }
 
+psm_status psm_selftest_waits(psm_ctx* c, long long limit_ns) {
+  if (!c || limit_ns < 0 || limit_ns > 1000000000LL) return PSM_ERR_ARG;
+  const unsigned long long ns = (unsigned long long)limit_ns;
+  CK(cudaStreamSynchronize(c->stream));
+  unsigned st = 0;
+  const int which[3] = {0, 1, 2};
+  for (int w : which) {
+    CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+    if (w == 0) launch_wait_selftest_lbm(c->status, ns, c->stream);
+    else if (w == 1) launch_wait_selftest_mlp(c->status, ns, c->stream);
+    else launch_wait_selftest_dem(c->dem_bar, c->status, ns, c->stream);
+    CK(cudaGetLastError());
+    unsigned one = 0;
+    CK(cudaMemcpyAsync(&one, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!(one & ST_TIMEOUT)) {
+      CK(cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      return fail(c, PSM_ERR_STATE, "a bounded wait did not give up");
+    }
+    st |= one;
+  }
+  // the status word keeps ST_TIMEOUT: the next call reports PSM_ERR_TIMEOUT
+  CK(cudaMemsetAsync(c->dem_bar, 0, 4 * sizeof(unsigned), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return PSM_OK;
+}
+
 psm_status psm_get_particle_count(const psm_ctx* c, int* n) {
   if (!c || !n) return PSM_ERR_ARG;
   *n = c->p.n;

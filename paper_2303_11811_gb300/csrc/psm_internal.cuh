@@ -263,6 +263,13 @@ struct DemParams {
   int max_blocks;     // blocks that can be resident at once (cooperative launch)
 };
 int dem_max_blocks();
+// diagnostics of the bounded device waits (each raises ST_TIMEOUT in *status
+// after limit_ns): the staged collision's mbarrier wait, the surrogate
+// inference's mbarrier wait, the DEM grid barrier (bar: 4 words of scratch)
+int launch_wait_selftest_lbm(unsigned* status, unsigned long long limit_ns, cudaStream_t s);
+int launch_wait_selftest_mlp(unsigned* status, unsigned long long limit_ns, cudaStream_t s);
+int launch_wait_selftest_dem(unsigned* bar, unsigned* status, unsigned long long limit_ns,
+                             cudaStream_t s);
 int launch_dem_step(DemParams P, int subcycles, cudaStream_t s);
 
 // MLP
