@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/psm.h"
 #include "psm_internal.cuh"
 
@@ -89,6 +91,15 @@ struct psm_ctx {
 };
 
 namespace {
+
+// NVTX range over a scope of host work (a tracing tool shows the engine's
+// calls and, outside graph replay, the phases each step enqueues)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 psm_status fail(psm_ctx* c, psm_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -208,6 +219,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   MapParams MP = map_params(c);
   if (c->timing) cudaEventRecord(c->ev[0], s);
   if (with_map) {
+    NvtxRange r("psm mapping");
     if (c->opt.eps_mode == PSM_EPS_MLP) n += launch_map_mlp(MP, s);
     else n += launch_map(MP, s);
     n += launch_step_const(MP, s);
@@ -241,11 +253,18 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   L.stages = c->plan.stages;
   L.blocks = c->plan.blocks;
   L.smem = c->plan.smem;
-  n += launch_lbm(L, c->prec, mode, s);
+  {
+    NvtxRange r("psm stream-collide");
+    n += launch_lbm(L, c->prec, mode, s);
+  }
   if (c->timing) cudaEventRecord(c->ev[2], s);
-  if (c->p.n > 0) n += launch_force_reduce(MP, s);
+  if (c->p.n > 0) {
+    NvtxRange r("psm force-reduce");
+    n += launch_force_reduce(MP, s);
+  }
   if (c->timing) cudaEventRecord(c->ev[3], s);
   if (c->any_free) {
+    NvtxRange r("psm dem");
     DemParams D{};
     D.g = c->g;
     D.p = c->p;
@@ -680,6 +699,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
 
 psm_status psm_step(psm_ctx* c, int nsteps) {
   if (!c) return PSM_ERR_ARG;
+  NvtxRange range("psm_step");
   if (nsteps < 0) return fail(c, PSM_ERR_ARG, "negative step count");
   if (c->error_state) return fail(c, PSM_ERR_STATE, "context is in an error state");
   c->launches = 0;
@@ -1059,6 +1079,7 @@ psm_status psm_update_particles(psm_ctx* c, const double* x, const double* u, co
 // checkpoint of the stepper state (layout above)
 psm_status psm_save(psm_ctx* c, const char* path) {
   if (!c || !path) return PSM_ERR_ARG;
+  NvtxRange range("psm_save");
   CK(cudaStreamSynchronize(c->stream));
   const int n = c->p.n;
   CkptHeader h{};
@@ -1105,6 +1126,7 @@ psm_status psm_save(psm_ctx* c, const char* path) {
 
 psm_status psm_load(psm_ctx* c, const char* path) {
   if (!c || !path) return PSM_ERR_ARG;
+  NvtxRange range("psm_load");
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(c, PSM_ERR_ARG, std::string("cannot open: ") + path);
   auto bad = [&](const std::string& msg) {
