@@ -51,6 +51,14 @@ WORKLOADS = {
                 "sequential addition, solid fraction 0.20, seed 20230321), D3Q19 TRT "
                 "(Lambda=3/16) tau=0.55, body force 1e-5 along z, 4^3 sub-division sampling, "
                 "Noble-Torczynski B"),
+    "bed_dilute": ("bed_dilute: stand-in for the paper's dilute fluidized bed, 500x200x800 cells, "
+                   "no-slip walls on the four side faces, periodic vertical axis (the counter "
+                   "force of the buoyant weight drives the flow up through the bed), 627 spheres "
+                   "r=10 (random sequential addition), density ratio 1.1, gravity 2.75e-5, D3Q19 "
+                   "SRT tau=0.55, linear approximation (Eqs. 25-27), B = eps, DEM x10 sub-cycles"),
+    "bed_dense": ("bed_dense: stand-in for the paper's dense fluidized bed, as bed_dilute with "
+                  "8,073 spheres r=10 in hexagonal close-packed layers from the bottom (solid "
+                  "fraction 0.42 over the box)"),
 }
 HBM_FALLBACK_GBS = 6800.0
 SM_COUNT = 152
@@ -395,6 +403,8 @@ def make_workload(name):
     from paper_2303_11811_gb300 import inputs
     if name == "settle256":
         return inputs.settle512(nx=256, ny=256, nz=256)
+    if name.startswith("bed_"):
+        return inputs.bed(name[4:])
     return {"settle128": inputs.settle128, "channel": inputs.channel,
             "settle512": inputs.settle512}[name]()
 

@@ -652,6 +652,26 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
       cidx = c;
       if (REC == REC_FP32) Bf = __ldg(&wtabf[c]);
       else B = __ldg(&wtab[c]);
+    } else if (REC == REC_FP32 && P.eps_mode == 1) {
+      // linear approximation (Eqs. 25-26) for FP32 records: the inside test
+      // as the FP64 definition (certified band), eps and B in FP32 (the
+      // record's own precision; FP64 square roots are slow on this GPU)
+      bool inside = false;
+      if (b.has_in) {
+        if (h.d2f < b.rin2f - b.E) inside = true;
+        else if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
+          inside = true;
+      }
+      float ef = 1.f;
+      if (!inside) {
+        ef = (rf - sqrtf(h.d2f)) + frf;
+        ef = ef < 0.f ? 0.f : (ef > 1.f ? 1.f : ef);
+      }
+      Bf = ef;
+      if (P.weighting && ef != 0.f && ef != 1.f) {
+        const float tm = (float)(P.tau - 0.5);
+        Bf = ef * tm / ((1.f - ef) + tm);
+      }
     } else {
       h.d2 = h.dx * h.dx + h.dy * h.dy + h.dz * h.dz;
       const double eps = cell_eps(P, b, h, fr, s64, s32);

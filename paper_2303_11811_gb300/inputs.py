@@ -183,6 +183,57 @@ def settle512(nx=512, ny=512, nz=1024, phi=0.15, rmin=3.0, rmax=6.0,
     return w
 
 
+def bed(case="dilute", nx=500, ny=200, nz=800, radius=10.0, seed=DEFAULT_SEED) -> Workload:
+    """Stand-in for the paper's fluidized bed (Sec. 4.1): 500 x 200 x 800
+    cells, no-slip walls on the four side faces, spheres of radius 10 (20
+    cells per diameter), particle/fluid density ratio 1.1, ten DEM
+    sub-cycles, SRT, the linear approximation of Eqs. 25-27 with B = eps.
+    The paper's velocity inflow (bottom) and pressure outflow (top) are
+    replaced by a periodic vertical axis: the counter force of the
+    buoyancy-corrected gravity pushes the fluid up through the bed with the
+    bed's buoyant weight.  Gravity 2.75e-5 (Galileo number about 8.9 at
+    tau = 0.55, d = 20).  ``dilute``: 627 spheres by random sequential
+    addition over the whole box; ``dense``: 8,073 spheres in hexagonal
+    close-packed layers from the bottom (surface gap 1), a packed bed."""
+    w = Workload(f"bed_{case}", nx, ny, nz, tau=0.55, relax="srt", walls=(1, 1, 1, 1, 0, 0),
+                 gravity=(0.0, 0.0, -2.75e-5), weighting="eps", eps_mode="linear", eps_n=4,
+                 dem=True, density=1.1, steps=500)
+    if case == "dilute":
+        count = 627
+        r = np.full(count, radius)
+        x = rsa_spheres((nx, ny, nz), w.walls, r, 1.0, seed)
+    else:
+        count = 8073
+        d = 2.0 * radius + 1.0               # centre spacing: surface gap 1
+        dy, dz = d * math.sqrt(3.0) / 2.0, d * math.sqrt(2.0 / 3.0)
+        pts = []
+        layer = 0
+        while len(pts) < count:
+            z = radius + 0.5 + layer * dz
+            if z > nz - radius:
+                raise RuntimeError("packed bed does not fit")
+            sx = 0.5 * d if layer % 3 == 1 else 0.0
+            sy = dy / 3.0 * (layer % 3)
+            j = 0
+            while True:
+                y = radius + 0.5 + sy + j * dy
+                if y > ny - radius - 0.5:
+                    break
+                i = 0
+                while True:
+                    xx = radius + 0.5 + sx + (0.5 * d if j % 2 else 0.0) + i * d
+                    if xx > nx - radius - 0.5:
+                        break
+                    pts.append((xx, y, z))
+                    i += 1
+                j += 1
+            layer += 1
+        x = np.array(pts[:count])
+        r = np.full(count, radius)
+    w.particles = dict(x=x, r=r, density=np.full(count, 1.1), fixed=np.zeros(count, np.uint8))
+    return w
+
+
 def noise(shape, scale, seed):
     """Uniform noise in [-scale, scale) of the given shape."""
     rng = np.random.default_rng(seed)

@@ -91,3 +91,30 @@ def test_fp32_drag_against_fp64_on_fixed_array(capi):
     F32, u32 = res["fp32"]
     assert np.linalg.norm(F32 - F64) / np.linalg.norm(F64) < 5e-3
     assert np.linalg.norm(u32 - u64) / np.linalg.norm(u64) < 1e-3
+
+
+@pytest.mark.parametrize("weighting,tol", [("eps", 2e-5), ("nt", 2e-4)])
+def test_fp32_linear_mapping_against_the_oracle(capi, weighting, tol):
+    """Linear approximation (Eqs. 25-26) with FP32 records: the same slots as
+    the FP64 definition (the inside test is certified), weights within the
+    FP32 evaluation of |d| (|d|^2 rounded to 2^-24 relative, r = 10: about
+    1e-6 in eps; Noble-Torczynski's dB/deps reaches 1/(tau - 1/2) = 20)."""
+    shape = (60, 48, 44)
+    kw = dict(tau=0.55, relax="srt", walls=(1, 1, 1, 1, 0, 0), weighting=weighting,
+              eps_mode="linear", eps_n=4)
+    e = capi.Engine(*shape, precision="fp32", **kw)
+    o = Oracle(*shape, **kw)
+    x = np.array([[14.3, 12.1, 20.7], [36.25, 24.0, 21.0], [47.5, 33.9, 3.2]])
+    r = np.array([10.0, 8.5, 7.25])
+    for s in (e, o):
+        s.set_particles(x, r, fixed=np.ones(3, np.uint8))
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = e.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    Bsum = bo0 + bo1
+    over = Bsum > 1.0
+    bo0 = np.where(over, bo0 / np.where(over, Bsum, 1.0), bo0)
+    bo1 = np.where(over, bo1 / np.where(over, Bsum, 1.0), bo1)
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    assert np.max(np.abs(bg0 - bo0)) < tol and np.max(np.abs(bg1 - bo1)) < tol
+    e.close()
