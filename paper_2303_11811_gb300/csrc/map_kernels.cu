@@ -315,7 +315,7 @@ __global__ void clear_slots_kernel(MapParams P) {
     atomicOr(P.status, ST_SLOT_OVERFLOW);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     P.s.pid[e] = make_int2(-1, -1);
-    P.s.cnt[e] = 0;
+    if ((e & 15) == 0) P.s.cnt[e >> 4] = 0;  // 16 packed counters per word
   }
 }
 
@@ -588,7 +588,11 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
         ok = false;
       } else {
         P.list[loff + k] = (int)e;
-        s = atomicAdd(&P.s.cnt[e], 1);
+        // the cell's particle count: 2-bit fields, 16 per word, so that the
+        // counters of a whole mapping stay in L2 for these atomics
+        const int sh = 2 * (int)(e & 15);
+        s = (int)((atomicAdd(reinterpret_cast<unsigned*>(P.s.cnt) + (e >> 4), 1u << sh) >> sh) &
+                  3u);
         if (s >= 2) {
           atomicOr(P.status, ST_SLOT_OVERFLOW);
           ok = false;

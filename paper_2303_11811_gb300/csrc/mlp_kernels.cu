@@ -437,7 +437,10 @@ __global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long row = tile * INF_M + tid;
     const bool live = row < n;
-    const int cnt = item >= 0 ? __ldg(&o.cnt[item >> 1]) : 0;
+    // particles in reach of the item's cell (2-bit fields, 16 per word)
+    const int cnt = item >= 0 ? (int)((__ldg(&o.cnt[(item >> 1) >> 4]) >>
+                                        (2 * ((item >> 1) & 15))) & 3)
+                              : 0;
     float4 xn;
     int itemn;
     float linn;

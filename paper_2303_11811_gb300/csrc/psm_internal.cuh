@@ -132,7 +132,7 @@ struct Particles {
 struct Slots {
   int* cell;      // padded cell index of each entry
   int2* pid;
-  int* cnt;
+  int* cnt;       // particles in reach of entry e: 2-bit field e % 16 of word e / 16
   void* Fc;       // slot s's force of entry e at T[3 (s cap + e)]
   // slot s's record of entry e at T[4 (s cap + e)]: the particle's surface
   // velocity at the cell centre (Eq. 20) and the slot's normalised weight
