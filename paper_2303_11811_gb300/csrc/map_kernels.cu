@@ -198,14 +198,34 @@ __device__ __forceinline__ void load_offsets(int n, double* s64, float* s32) {
   __syncthreads();
 }
 
+// reach test of box cell (kx, ky, kz) (box coordinates unwrapped), the FP64
+// definition's decision (reach_test)
+__device__ __forceinline__ bool in_reach(const Box& b, int kx, int ky, int kz) {
+  CellHit h;
+  h.kx = kx;
+  h.ky = ky;
+  h.kz = kz;
+  return reach_test(b, h);
+}
+
+// the row-wise mark pass serves boxes of rows long enough to pay for its run
+// search (radius about 7 and more) and of at most MARK_MAX_ROWS rows
+constexpr int MARK_MAX_ROWS = 1024;
+constexpr int MARK_MIN_ROW = 16;
+
 // Cells in reach of one particle (one block per particle): the coverage bits
 // (one atomicOr per distinct word of a warp) and the particle's list of its
 // cells in box order, as box indices t; the fill pass replaces them by slot
-// indices.
+// indices.  Along an x-row of the box the FP64 squared distance is unimodal
+// (IEEE rounding is monotone), so the row's cells in reach form one run: its
+// ends are found with a few certified reach tests around the cell holding
+// the centre, the runs are scanned in row order and written by one warp per
+// row.  Small boxes (short rows) and very large ones test every cell.
 __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   __shared__ int warp_tot[MAP_THREADS / 32];
   __shared__ int running;
   __shared__ Box sbox;
+  __shared__ int row_lo[MARK_MAX_ROWS], row_n[MARK_MAX_ROWS], row_off[MARK_MAX_ROWS];
   const int p = blockIdx.x;
   const long long loff = P.list_off[p];
   const int lcap = (int)(P.list_off[p + 1] - loff);
@@ -213,6 +233,92 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   if (threadIdx.x == 0) running = 0;
   load_box(P, p, &sbox);  // ends with __syncthreads
   const Box b = sbox;
+  const int rows = b.n[1] * b.n[2];
+  if (rows <= MARK_MAX_ROWS && b.n[0] >= MARK_MIN_ROW) {
+    // ---- runs of the rows
+    const int kc = b.ip[0];  // the x cell holding the centre: the row's closest
+    for (int r = threadIdx.x; r < rows; r += MAP_THREADS) {
+      const int kz = b.lo[2] + r / b.n[1];
+      const int ky = b.lo[1] + (r - (r / b.n[1]) * b.n[1]);
+      int lo = 0, cnt = 0;
+      if (b.n[0] > 0 && in_reach(b, kc, ky, kz)) {
+        const float dyf = (float)(ky - b.ip[1]) + (0.5f - b.fpf[1]);
+        const float dzf = (float)(kz - b.ip[2]) + (0.5f - b.fpf[2]);
+        const float rem = b.reach2f - (dyf * dyf + dzf * dzf);
+        const int w = (int)sqrtf(rem > 0.f ? rem : 0.f) + 1;
+        const int x0 = b.lo[0], x1 = b.lo[0] + b.n[0] - 1;
+        int a = kc - w < x0 ? x0 : kc - w;
+        while (a < kc && !in_reach(b, a, ky, kz)) ++a;
+        while (a > x0 && in_reach(b, a - 1, ky, kz)) --a;
+        int e = kc + w > x1 ? x1 : kc + w;
+        while (e > kc && !in_reach(b, e, ky, kz)) --e;
+        while (e < x1 && in_reach(b, e + 1, ky, kz)) ++e;
+        lo = a - x0;
+        cnt = e - a + 1;
+      }
+      row_lo[r] = lo;
+      row_n[r] = cnt;
+    }
+    __syncthreads();
+    // ---- exclusive scan of the run lengths in row order: each thread sums a
+    // contiguous chunk of rows, the chunk totals are scanned across the block
+    const int per = (rows + MAP_THREADS - 1) / MAP_THREADS;
+    const int r0 = threadIdx.x * per;
+    int mine = 0;
+    for (int r = r0; r < r0 + per && r < rows; ++r) mine += row_n[r];
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    int base = 0, total = 0;
+    for (int w = 0; w < MAP_THREADS / 32; ++w) {
+      if (w < wid) base += warp_tot[w];
+      total += warp_tot[w];
+    }
+    int off = base + incl - mine;
+    for (int r = r0; r < r0 + per && r < rows; ++r) {
+      row_off[r] = off;
+      off += row_n[r];
+    }
+    __syncthreads();
+    // ---- one warp per row: list entries and coverage bits
+    for (int r = wid; r < rows; r += MAP_THREADS / 32) {
+      const int n = row_n[r];
+      if (n == 0) continue;
+      const int kz = b.lo[2] + r / b.n[1];
+      const int ky = b.lo[1] + (r - (r / b.n[1]) * b.n[1]);
+      const int iy = wrap1(ky, P.g.ny), iz = wrap1(kz, P.g.nz);
+      for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool in = i < n;
+        const int kxl = row_lo[r] + i;  // box-local x
+        const long long cell =
+            in ? padded_cell(P.g, wrap1(b.lo[0] + kxl, P.g.nx), iy, iz) : 0;
+        if (in) {
+          const int pos = row_off[r] + i;
+          if (pos < lcap) P.list[loff + pos] = kxl + b.n[0] * r;
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, in);
+        while (pend) {
+          const int leader = __ffs(pend) - 1;
+          const long long w0 = __shfl_sync(0xffffffffu, cell >> 5, leader);
+          const bool mine_w = in && (cell >> 5) == w0;
+          const unsigned bits = __reduce_or_sync(0xffffffffu, mine_w ? 1u << (cell & 31) : 0u);
+          if (lane == leader) atomicOr(&P.cov.mask[w0], bits);
+          pend &= ~__ballot_sync(0xffffffffu, mine_w);
+        }
+      }
+    }
+    if (threadIdx.x == 0) {
+      P.list_cnt[p] = total < lcap ? total : lcap;
+      if (total > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
+    }
+    return;
+  }
+  // ---- large boxes: every cell of the box
   for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
     const int t = t0 + threadIdx.x;
     CellHit h;

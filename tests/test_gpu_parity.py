@@ -122,6 +122,32 @@ def test_mapping_slots(capi, eps_mode, eps_n):
     assert (pg1 >= 0).sum() > 0
 
 
+@pytest.mark.parametrize("eps_mode,eps_n", [("supersample", 4), ("linear", 4)])
+def test_mapping_slots_large_spheres(capi, eps_mode, eps_n):
+    """Large spheres (radius 7.5 to 12: the mark pass's row-wise search for
+    the runs of cells in reach), wrapping around the periodic faces and
+    sharing cells: the same slots and weights as the oracle."""
+    shape = (64, 56, 60)
+    e, o = pair(capi, shape, tau=0.6, relax="srt", weighting="nt", eps_mode=eps_mode,
+                eps_n=eps_n)
+    x = np.array([[2.3, 53.9, 30.25], [32.0, 28.0, 30.0], [32.0 + 21.5, 28.4, 30.6],
+                  [20.5, 10.75, 57.1]])
+    r = np.array([12.0, 9.5, 12.25, 7.5])
+    for s_ in (e, o):
+        s_.set_particles(x, r)
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = e.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    Bsum = bo0 + bo1
+    over = Bsum > 1.0
+    bo0 = np.where(over, bo0 / np.where(over, Bsum, 1.0), bo0)
+    bo1 = np.where(over, bo1 / np.where(over, Bsum, 1.0), bo1)
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    assert np.max(np.abs(bg0 - bo0)) < 1e-15 and np.max(np.abs(bg1 - bo1)) < 1e-15
+    assert (pg1 >= 0).sum() > 0
+    e.close()
+
+
 def test_aa_equals_pull_bitwise_fp64(capi):
     """The AA pattern changes where PDFs live, not what is computed: FP64 AA
     and pull give identical bits after an odd and an even number of steps."""
