@@ -82,9 +82,14 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the timed region.
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    The sampler runs every 25 ms from before the region; `start` returns once
+    the first sample is in (at most 3 s), and `stop` keeps the samples whose
+    timestamps fall inside the region marked by `begin`/`end` (all samples if
+    none does, with "in_region": false)."""
+
+    QUERY = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -92,6 +97,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -99,10 +105,30 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        deadline = time.time() + 3.0
+        while time.time() < deadline and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
+    @staticmethod
+    def _stamp(text):
+        try:
+            day, frac = (text.split(".") + ["0"])[:2]
+            return time.mktime(time.strptime(day, "%Y/%m/%d %H:%M:%S")) + float("0." + frac)
+        except Exception:
+            return None
 
     def stop(self):
         if self.proc is None:
@@ -120,6 +146,12 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
+        inside = rows
+        if self.t0 is not None and self.t1 is not None:
+            inside = [r for r in rows
+                      if (ts := self._stamp(r[0])) is not None and self.t0 <= ts <= self.t1]
+        in_region = bool(inside)
+        rows = inside or rows
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -127,7 +159,7 @@ class ClockSampler:
                           and "Not" not in r[5 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(rows), "in_region": in_region}
 
 
 def source_hash(path):
@@ -471,7 +503,9 @@ def main():
     clocks.start()
     if dist:
         dist.barrier()
+    clocks.begin()
     ms = timed_steps(e, torch, args.steps)
+    clocks.end()
     if dist:
         dist.barrier()
     clk = clocks.stop()

@@ -222,32 +222,63 @@ __device__ __forceinline__ void slot_force(const LbmParams& P, int e, int sl, T 
   o[2] = Bi * (duz - f[2]);
 }
 
+// Coverage of one cell and its first slot record (m: coverage word of its
+// warp, eb: slot of the word's first covered cell).  A slot record holds the
+// particle's surface velocity at the cell centre (Eq. 20) and the weight B_i,
+// both written by the mapping; the sign of slot 0's weight tells whether a
+// second particle shares the cell.  Issued ahead of the PDF reads where the
+// kernel can.
+template <typename T>
+struct SlotRec {
+  bool cov;  // covered, and its record exists
+  int e;     // slot index
+  T r0[4];   // slot 0: surface velocity, signed weight
+};
+template <typename T>
+__device__ __forceinline__ void load_slot_rec(const LbmParams& P, uint32_t m, int eb, int lane,
+                                              bool live, SlotRec<T>& R) {
+  R.cov = live && ((m >> lane) & 1u);
+  R.e = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) R.r0[i] = T(0);
+  if (R.cov) {
+    R.e = eb + __popc(m & ((1u << lane) - 1u));
+    if (R.e < P.slot_cap) ld4(static_cast<const T*>(P.slot_V) + 4LL * R.e, R.r0);
+    else R.cov = false;
+  }
+}
+
 // Collision of one cell (Eqs. 3-8 and 17-21) on the PDFs d gathered by the
 // streaming step; the warp's 32 lanes hold the 32 cells of coverage word
 // `word` (padding lanes compute on a copy of a real cell).  FP64 kernels
 // pass the warp's SolidSmem.
-template <typename T>
+// `pre` holds the cell's slot record when the kernel loaded it ahead (PRE),
+// else the record is read here.
+template <typename T, bool PRE>
 __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, int lane, bool live,
-                                            T* d, SolidSmem<T>* solid, uint32_t m, int eb) {
-  // ---- coverage of this cell (m: coverage word, eb: slot of its first
-  // covered cell).  A slot record holds the particle's surface velocity at
-  // the cell centre (Eq. 20) and the weight B_i, both written by the mapping;
-  // the sign of slot 0's weight tells whether a second particle shares the
-  // cell, whose record is read only then.
-  bool cov = live && ((m >> lane) & 1u);
-  bool has1 = false;
+                                            T* d, SolidSmem<T>* solid, uint32_t m, int eb,
+                                            const SlotRec<T>* pre) {
+  // ---- the cell's slots; the second one's record is read only when present
+  bool cov, has1 = false;
   int e = 0;
   T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
-  if (cov) {
-    e = eb + __popc(m & ((1u << lane) - 1u));
-    if (e < P.slot_cap) {
-      ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
-      has1 = neg_flag(r0[3]);
-      r0[3] = magnitude(r0[3]);
-      if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
-    } else {
-      cov = false;
+  if constexpr (PRE) {
+    cov = pre->cov;
+    e = pre->e;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r0[i] = pre->r0[i];
+  } else {
+    cov = live && ((m >> lane) & 1u);
+    if (cov) {
+      e = eb + __popc(m & ((1u << lane) - 1u));
+      if (e < P.slot_cap) ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
+      else cov = false;
     }
+  }
+  if (cov) {
+    has1 = neg_flag(r0[3]);
+    r0[3] = magnitude(r0[3]);
+    if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
   }
   T omB = T(1);  // 1 - B; the FP64 operations only where a lane is covered
   if (cov) {
@@ -490,8 +521,9 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
   }
 
 #undef SRC
-  psm_collide<T>(P, warp, lane, live, d,
-                 reinterpret_cast<SolidSmem<T>*>(lbm_smem) + (threadIdx.x >> 5), m, eb);
+  psm_collide<T, false>(P, warp, lane, live, d,
+                        reinterpret_cast<SolidSmem<T>*>(lbm_smem) + (threadIdx.x >> 5), m, eb,
+                        nullptr);
   if (live) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
 }
 
@@ -650,6 +682,21 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
   SolidSmem<T>* solid = reinterpret_cast<SolidSmem<T>*>(
                             bulk_smem + BULK_BAR_BYTES + S * stage_elems * sizeof(T)) + warp;
 #define SRC(q) static_cast<const T*>(P.srcq[q])
+  // FP32: the coverage word and first slot of a word are loaded one word
+  // ahead (the slot records of the collision depend on them): the word a
+  // warp takes next is w + 8 in the same tile, else its first word in the
+  // block's next tile.  Word index of (tile, w): tile * TR * wpr + w.  FP64
+  // loads them at the word.
+  constexpr bool ahead = !kFP64<T>;
+  const int tile_words = TR * g.wpr;
+  auto words_in = [&](int t) { return min(TR, nrows - t * TR) * g.wpr; };
+  uint32_t m_next = 0u;
+  int eb_next = 0;
+  if (ahead && P.mask && blockIdx.x < P.ntiles && warp < words_in(blockIdx.x)) {
+    const unsigned w0 = (unsigned)(blockIdx.x * tile_words + warp);
+    m_next = __ldg(&P.mask[w0]);
+    eb_next = __ldg(&P.base[w0]);
+  }
   int it = 0;
   for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++it) {
     const int s = it % S;
@@ -659,7 +706,7 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
     }
     const T* st = ring + s * stage_elems;
     const int row0 = tile * TR;
-    const int nw = min(TR, nrows - row0) * g.wpr;  // coverage words of the tile
+    const int nw = words_in(tile);  // coverage words of the tile
     for (int w = warp; w < nw; w += BULK_CONSUMER_WARPS) {
       const int r = (int)g.div_wpr.div((unsigned)w);
       const int wr = w - r * g.wpr;
@@ -668,8 +715,24 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
       const int x = live ? xr : g.nx - 1;
       const int row = row0 + r;
       const unsigned word = (unsigned)(row * g.wpr + wr);
-      const uint32_t m = P.mask ? __ldg(&P.mask[word]) : 0u;
-      const int eb = P.mask ? __ldg(&P.base[word]) : 0;
+      const uint32_t m = ahead ? m_next : (P.mask ? __ldg(&P.mask[word]) : 0u);
+      const int eb = ahead ? eb_next : (P.mask ? __ldg(&P.base[word]) : 0);
+      // FP32: the record loads go out before the PDF reads; FP64 (bound by
+      // its pipe, registers tight) reads them in the collision
+      SlotRec<T> R;
+      if constexpr (ahead) load_slot_rec<T>(P, m, eb, lane, live, R);
+      if (ahead && P.mask) {
+        int t2 = tile, w2 = w + BULK_CONSUMER_WARPS;
+        if (w2 >= nw) {
+          t2 = tile + gridDim.x;
+          w2 = warp;
+        }
+        if (t2 < P.ntiles && w2 < words_in(t2)) {
+          const unsigned wn = (unsigned)(t2 * tile_words + w2);
+          m_next = __ldg(&P.mask[wn]);
+          eb_next = __ldg(&P.base[wn]);
+        }
+      }
       const int z = (int)g.div_ny.div((unsigned)row);
       const int y = row - z * g.ny;
       NbrT<WALLS> nb;
@@ -696,7 +759,7 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
           d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qb) + cell);
         }
       }
-      psm_collide<T>(P, word, lane, live, d, solid, m, eb);
+      psm_collide<T, ahead>(P, word, lane, live, d, solid, m, eb, &R);
       if (live) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
     }
     __syncwarp();

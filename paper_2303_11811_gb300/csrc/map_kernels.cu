@@ -1061,6 +1061,48 @@ __global__ void vfluid_kernel(MapParams P, int nparts) {
 }
 
 // ---- fixed-order force and torque reduction over each particle's list
+//
+// The torque arm of a cell is its nearest-image offset from the centre,
+// (k - i_p) + (1/2 - frac(x_p)) per axis: an integer part that varies per
+// cell plus a fraction that is the same for every cell of the particle.  So
+// T = sum (k - i_p) x F_c + (1/2 - frac) x F, and each entry costs the three
+// force sums and two fused multiply-adds per torque component (FP64 runs at
+// 1/64 of the FP32 rate on GB300).
+
+// Sum of six values over the 32 lanes of a warp in a fixed order, halving the
+// values each lane carries at the first levels: 8 additions per lane instead
+// of 30.  Returns the total of value i in the lanes with (lane & 3) == 0 and
+// lane >> 2 = 4 (i / 3) + (i % 3) (lanes whose index maps to 3 or 7 carry an
+// empty slot).
+__device__ __forceinline__ double warp_sum6(const double (&v)[6], int lane, int& which) {
+  const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
+  double w[4];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {  // lanes 0-15 keep values 0-2, lanes 16-31 values 3-5
+    const double keep = b4 ? v[i + 3] : v[i];
+    const double send = b4 ? v[i] : v[i + 3];
+    w[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  w[3] = 0.0;
+  double u[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {  // then pairs {0,1} / {2,3}
+    const double keep = b3 ? w[i + 2] : w[i];
+    const double send = b3 ? w[i] : w[i + 2];
+    u[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const double keep = b2 ? u[1] : u[0];
+    const double send = b2 ? u[0] : u[1];
+    u[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  u[0] += __shfl_xor_sync(0xffffffffu, u[0], 2);
+  u[0] += __shfl_xor_sync(0xffffffffu, u[0], 1);
+  const int j = 2 * b3 + b2;
+  which = j < 3 ? 3 * b4 + j : -1;
+  return u[0];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) {
   __shared__ double sh[6][RED_THREADS / 32];
@@ -1078,23 +1120,23 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
   }
   __syncthreads();
   const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
+  // F, then sum over cells of (k - i_p) x F_c
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
     const int e = P.list[loff + k];
     const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
-    // torque arm: nearest-image offset of the cell centre, (k - i_p) + (1/2 - frac)
     int c3[3];
     cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
-    double d3[3];
-    for (int a = 0; a < 3; ++a) {
+    double kd[3];
+    for (int a = 0; a < 3; ++a) {  // nearest image of the integer offset
       int k0 = c3[a] - sip[a];
       if (!P.g.wall[a]) {
         if (2 * k0 > dims[a]) k0 -= dims[a];
         else if (2 * k0 < -dims[a]) k0 += dims[a];
       }
-      d3[a] = (double)k0 + sfr[a];
+      kd[a] = (double)k0;
     }
     const long long fo = 3 * (s * P.s.cap + e);
     const double f0 = (double)Fc[fo];
@@ -1103,28 +1145,33 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
     acc[0] += f0;
     acc[1] += f1;
     acc[2] += f2;
-    acc[3] += d3[1] * f2 - d3[2] * f1;
-    acc[4] += d3[2] * f0 - d3[0] * f2;
-    acc[5] += d3[0] * f1 - d3[1] * f0;
+    acc[3] = fma(-kd[2], f1, fma(kd[1], f2, acc[3]));
+    acc[4] = fma(-kd[0], f2, fma(kd[2], f0, acc[4]));
+    acc[5] = fma(-kd[1], f0, fma(kd[0], f1, acc[5]));
   }
   // fixed-order tree: within each warp by shuffles, then over the warps
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int o = 16; o > 0; o >>= 1)
-    for (int i = 0; i < 6; ++i) acc[i] += __shfl_down_sync(0xffffffffu, acc[i], o);
-  if (lane == 0)
-    for (int i = 0; i < 6; ++i) sh[i][wid] = acc[i];
+  int which;
+  const double ws = warp_sum6(acc, lane, which);
+  if ((lane & 3) == 0 && which >= 0) sh[which][wid] = ws;
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int i = threadIdx.x;
+    double t = sh[i][0];
+    for (int w = 1; w < RED_THREADS / 32; ++w) t += sh[i][w];
+    sh[i][0] = t;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tot[6];
-    for (int i = 0; i < 6; ++i) {
-      tot[i] = sh[i][0];
-      for (int w = 1; w < RED_THREADS / 32; ++w) tot[i] += sh[i][w];
-    }
+    const double F[3] = {sh[0][0], sh[1][0], sh[2][0]};
+    const double Tq[3] = {sh[3][0] + (sfr[1] * F[2] - sfr[2] * F[1]),
+                          sh[4][0] + (sfr[2] * F[0] - sfr[0] * F[2]),
+                          sh[5][0] + (sfr[0] * F[1] - sfr[1] * F[0])};
     bool finite = true;
     for (int i = 0; i < 3; ++i) {
-      P.p.Fh[3 * p + i] = tot[i];
-      P.p.Th[3 * p + i] = tot[3 + i];
-      finite = finite && isfinite(tot[i]) && isfinite(tot[3 + i]);
+      P.p.Fh[3 * p + i] = F[i];
+      P.p.Th[3 * p + i] = Tq[i];
+      finite = finite && isfinite(F[i]) && isfinite(Tq[i]);
     }
     if (!finite) atomicOr(P.status, ST_NONFINITE);
   }
