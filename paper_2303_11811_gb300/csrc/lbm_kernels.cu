@@ -470,6 +470,39 @@ __device__ __forceinline__ void store_pdfs(const LbmParams& P, const NbrT<WALLS>
 #undef DST
 }
 
+// components of c_q in the canonical ordering (q = 2k+1: +c_k, q = 2k+2: -c_k)
+__device__ __forceinline__ int qsign(int q) { return (q & 1) ? 1 : -1; }
+
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// L2 prefetch for the one-cell-per-thread kernel: lane q < 19 of the first
+// warp requests the span of source array q that block `bn` will read, the
+// block's 256 consecutive (padded) cells shifted by the streaming offset of
+// that array (pull: back by c_q; AA even: none; AA odd: forward by c_q, the
+// neighbours' swapped slots), widened to 16-byte boundaries and kept inside
+// the array.  Spans across a periodic face point at the neighbouring row
+// instead of the wrapped one: those few are only not prefetched.
+template <typename T, int MODE>
+__device__ __forceinline__ void prefetch_span(const LbmParams& P, unsigned bn, int q) {
+  const Grid& g = P.g;
+  long long off = 0;
+  if (q > 0 && MODE != 1) {
+    const int k = (q - 1) >> 1, sg = MODE == 0 ? qsign(q) : -qsign(q);
+    off = sg * ((long long)ckx(k) + (long long)cky(k) * g.nxp +
+                (long long)ckz(k) * g.nxp * g.ny);
+  }
+  constexpr long long per16 = 16 / sizeof(T);
+  long long c0 = (long long)bn * LBM_THREADS - off;
+  long long c1 = c0 + LBM_THREADS;
+  c0 = c0 < 0 ? 0 : c0 & ~(per16 - 1);
+  c1 = (c1 + per16 - 1) & ~(per16 - 1);
+  if (c1 > g.ncell) c1 = g.ncell & ~(per16 - 1);
+  if (c1 <= c0) return;
+  prefetch_l2(static_cast<const T*>(P.srcq[q]) + c0, (unsigned)((c1 - c0) * sizeof(T)));
+}
+
 // FP32 kernels are bandwidth bound and want resident warps (4 blocks per
 // SM); FP64 kernels are FP64-pipe bound and keep their registers
 template <typename T, int MODE, int WALLS>
@@ -477,6 +510,10 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
     lbm_kernel(LbmParams P) {
   extern __shared__ __align__(16) unsigned char lbm_smem[];
   const Grid& g = P.g;
+  if constexpr (sizeof(T) == 4) {
+    if (P.pf_ahead > 0 && threadIdx.x < Q && blockIdx.x + (unsigned)P.pf_ahead < gridDim.x)
+      prefetch_span<T, MODE>(P, blockIdx.x + (unsigned)P.pf_ahead, (int)threadIdx.x);
+  }
   // the grid has fewer than 2^31 cells: 32-bit indices throughout
   const unsigned warp = blockIdx.x * (LBM_THREADS / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -609,8 +646,6 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// components of c_q in the canonical ordering (q = 2k+1: +c_k, q = 2k+2: -c_k)
-__device__ __forceinline__ int qsign(int q) { return (q & 1) ? 1 : -1; }
 
 template <typename T, int MODE, int WALLS>
 __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
@@ -963,13 +998,41 @@ const void* bulk_fn_w(int w) {
   return w == 0 ? bulk_fn<T, 0>() : (w == 1 ? bulk_fn<T, 1>() : bulk_fn<T, 7>());
 }
 
+template <typename T>
+const void* cell_fn_w(int w) {
+  if (w == 0) return reinterpret_cast<const void*>(lbm_kernel<T, 0, 0>);
+  if (w == 1) return reinterpret_cast<const void*>(lbm_kernel<T, 0, 1>);
+  return reinterpret_cast<const void*>(lbm_kernel<T, 0, 7>);
+}
+
+// Prefetch distance of the one-cell-per-thread kernel: half the number of
+// its blocks resident at once, so the block that many places later starts
+// about half a wave of the grid later.  Measured on GB300 (FP32 pull, channel
+// 256x256x512 and settling box 512x512x1024): half and three quarters of a
+// wave are best (87% of the measured copy bandwidth, from 75-78% without
+// prefetch); a full wave loses 1-2%, two waves 10%.
+template <typename T>
+int cell_prefetch_ahead(const Grid& g, int* ahead) {
+  const int w = g.wall[0] | (g.wall[1] << 1) | (g.wall[2] << 2);
+  int per_sm = 0, dev = 0, nsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cell_fn_w<T>(w), LBM_THREADS,
+                                                    lbm_dyn_smem<T>()) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  *ahead = per_sm * nsm / 2;
+  return 0;
+}
+
 int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan) {
   *plan = LbmPlan{};
   const int fp32 = prec == PREC_FP32;
-  if (fp32 && !aa) return 0;
+  if (fp32 && !aa) return cell_prefetch_ahead<float>(g, &plan->pf_ahead);
   // the double-float form is bound by the FP32 pipes: it takes the
   // one-cell-per-thread kernel (two blocks of eight warps per SM; the staged
   // kernel fits one block of nine warps next to its ring)
+  // (and does not prefetch: on settle128 a prefetch half a wave ahead made
+  // its collision 16% slower)
   if (prec == PREC_DF) return 0;
   const int optin = smem_optin();
   if (optin <= 0) return 1;

@@ -253,6 +253,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
   L.stages = c->plan.stages;
   L.blocks = c->plan.blocks;
   L.smem = c->plan.smem;
+  L.pf_ahead = c->plan.pf_ahead;
   {
     NvtxRange r("psm stream-collide");
     n += launch_lbm(L, c->prec, mode, s);

@@ -201,11 +201,15 @@ struct LbmParams {
   // flight per block, `blocks` persistent blocks with `smem` bytes each
   int tile_rows, ntiles, stages, blocks;
   size_t smem;
+  // one-cell-per-thread FP32 pull kernel: each block prefetches into L2 the
+  // source spans of the block pf_ahead places later (0: no prefetch)
+  int pf_ahead;
 };
 
 struct LbmPlan {
   int tile_rows, ntiles, stages, blocks;
   size_t smem;
+  int pf_ahead;
 };
 
 // ---- launchers (stream-ordered; return the number of kernel launches) ----
