@@ -586,6 +586,22 @@ def main():
     e2e = {"value": job_mlups(cells, ke, world, te * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": 3 * 3 * n * 8, "d2h_bytes_per_step": (6 + 9) * n * 8,
            "steps": ke}
+
+    # the paper's coupling (Sec. 3.2): the same steps with the DEM on the host
+    # cores, hydrodynamic forces copied to the host and the particle state
+    # back every step (psm_step_host_dem), beside the engine's device DEM
+    host_dem = None
+    if w.dem and not bool(np.all(w.particles["fixed"])):
+        kh = max(5, min(args.steps, 50))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        host_ms = e.step_host_dem(kh, threads=0)
+        th = time.perf_counter() - t0
+        th = max_over_ranks(th, dist, "cuda")
+        host_dem = {"mlups": job_mlups(cells, kh, world, th * 1e3), "ms_per_step": th * 1e3 / kh,
+                    "host_phase_ms_per_step": host_ms / kh,
+                    "device_dem_ms_per_step": t[3] / t[4], "threads": os.cpu_count(),
+                    "steps": kh}
     e.close()
 
     forms = None
@@ -613,7 +629,7 @@ def main():
                        "l2": f"working set {ws:.0f} MB of PDFs > 126 MB L2, no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roofline,
-            "cpu_baseline": cpu, "forms": forms,
+            "cpu_baseline": cpu, "host_dem": host_dem, "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -148,6 +148,40 @@ psm_status psm_update_particles(psm_ctx* ctx, const double* x, const double* u,
  * PSM stream-collide, force/torque reduction, DEM sub-cycles. */
 psm_status psm_step(psm_ctx* ctx, int nsteps);
 
+/* Advances nsteps time steps with the particle dynamics on the host cores,
+ * the coupling the paper runs (Sec. 3.2): per step the device maps, collides
+ * and reduces the forces (as psm_step), the hydrodynamic force and torque are
+ * copied to the host, one DEM step (Eqs. 12, 15-16, the context's
+ * sub-cycles) runs on `threads` host threads (<= 0: all hardware threads),
+ * and the particle state (centres, velocities, angular velocities and the
+ * last sub-step's total force and torque) is copied back.  The DEM arithmetic
+ * is the device's, operation for operation, so the state equals psm_step's.
+ * *host_ms (may be NULL) receives the wall-clock milliseconds of the host
+ * phase summed over the steps (force copy, DEM, state copy).  Needs a context
+ * created with the DEM on (PSM_ERR_ARG otherwise); without free particles it
+ * is psm_step.  A particle that moves more than half the partner-list skin
+ * within a step gives PSM_ERR_STATE. */
+psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host_ms);
+
+/* One LBM step of particle dynamics on the host cores for n spheres, without
+ * a context (for a caller that owns its fluid solver): the DEM of
+ * psm_step_host_dem (Eqs. 12, 15-16) with `subcycles` sub-steps of 1/subcycles,
+ * stiffness k_n, restitution in (0, 1], gravity[3], the grid's box and walls
+ * (grid->wall[2a] and wall[2a+1] equal: both faces of an axis are walls or
+ * the axis is periodic).  In/out (host arrays, n*3): x, u, omega and F_old,
+ * T_old (the total force and torque of the last sub-step; a new particle
+ * starts with F_old = (m - V) gravity, T_old = 0).  In: F_hyd, T_hyd (n*3,
+ * held over the sub-steps), r, density (n), fixed (n, may be NULL).  Mass,
+ * volume and inertia follow psm_set_particles (fluid density 1).  threads
+ * <= 0: all hardware threads.  Returns PSM_ERR_ARG for invalid arguments
+ * (nothing changed), PSM_ERR_STATE when a particle moved more than half the
+ * partner-list skin (1 cell) within the step.  Needs no GPU. */
+psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
+                             int subcycles, const double* gravity, int n, double* x, double* u,
+                             double* omega, double* F_old, double* T_old, const double* F_hyd,
+                             const double* T_hyd, const double* r, const double* density,
+                             const unsigned char* fixed, int threads);
+
 /* Hydrodynamic force and torque of Eqs. 21-22 from the last step (n*3 each). */
 psm_status psm_get_force_torque(psm_ctx* ctx, double* F, double* T);
 

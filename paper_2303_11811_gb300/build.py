@@ -1,7 +1,8 @@
 """Builds the engine's shared library ``_build/libpsm.so`` for sm_103a.
 
-Each CUDA translation unit is compiled by nvcc in parallel and linked into one
-shared library that exports the C ABI of ``include/psm.h``.  Files whose
+Each translation unit (CUDA, and the host DEM in C++) is compiled by nvcc in
+parallel and linked into one shared library that exports the C ABI of
+``include/psm.h``.  Files whose
 floating-point decisions must round like the FP64 definition (mapping, DEM,
 training sampler) are compiled with ``-fmad=false``; host code is compiled
 with ``-ffp-contract=off``.
@@ -29,6 +30,7 @@ UNITS = {
     "mlp_kernels.cu": ["-fmad=false"],
     "psm_capi.cu": [],
     "noalloc_sums.cu": [],
+    "host_dem.cpp": [],
 }
 
 
@@ -49,13 +51,13 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile every CUDA unit and link libpsm.so; returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "psm.h"))
     jobs = []
     objs = []
     for unit, flags in UNITS.items():
         src = os.path.join(CSRC, unit)
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(unit)[0] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc(), *ARCH, *COMMON, *flags, *(extra or []), "-c", src, "-o", obj]
@@ -75,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
                 print(out, file=sys.stderr)
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -30,7 +30,7 @@ Q = 19
 
 EXPORTS = [
     "psm_default_options", "psm_create", "psm_set_particles", "psm_update_particles",
-    "psm_step",
+    "psm_step", "psm_step_host_dem", "psm_dem_step_host",
     "psm_get_force_torque", "psm_get_macroscopic", "psm_get_particles", "psm_get_pdfs",
     "psm_get_pdfs_box", "psm_get_fluid_force",
     "psm_set_pdfs", "psm_get_slots", "psm_check", "psm_set_mlp", "psm_get_mlp",
@@ -86,6 +86,13 @@ def lib():
     L.psm_update_particles.restype = st
     L.psm_step.argtypes = [P, C.c_int]
     L.psm_step.restype = st
+    L.psm_step_host_dem.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    L.psm_step_host_dem.restype = st
+    dpp = C.POINTER(C.c_double)
+    L.psm_dem_step_host.argtypes = [C.POINTER(PsmGrid), C.c_double, C.c_double, C.c_int, dpp,
+                                    C.c_int, dpp, dpp, dpp, dpp, dpp, dpp, dpp, dpp, dpp,
+                                    C.POINTER(C.c_ubyte), C.c_int]
+    L.psm_dem_step_host.restype = st
     L.psm_get_pdfs_box.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]
     L.psm_get_pdfs_box.restype = st
     L.psm_get_fluid_force.argtypes = [P, dp, C.POINTER(C.c_double)]
@@ -311,6 +318,13 @@ class Engine:
         """psm_step without raising: returns the status code."""
         return self._L.psm_step(self.h, int(n))
 
+    def step_host_dem(self, n=1, threads=0):
+        """n steps with the particle dynamics on the host cores; returns the
+        milliseconds spent in the host phase (force copy, DEM, state copy)."""
+        ms = C.c_double(0.0)
+        self._check(self._L.psm_step_host_dem(self.h, int(n), int(threads), C.byref(ms)))
+        return ms.value
+
     def force_torque(self):
         F = np.zeros(3 * max(self.np, 1))
         T = np.zeros(3 * max(self.np, 1))
@@ -445,6 +459,34 @@ def field_sums_noalloc(f_dev_ptr: int, ncells: int, sums_dev_ptr: int, stream_pt
     The call allocates no device memory (for callers that cannot)."""
     return lib().psm_field_sums_noalloc(C.c_void_p(f_dev_ptr), int(ncells),
                                         C.c_void_p(sums_dev_ptr), C.c_void_p(stream_ptr))
+
+
+def dem_step_host(shape, walls, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, density,
+                  fixed=None, kn=1e3, restitution=0.9, subcycles=10, gravity=(0.0, 0.0, 0.0),
+                  threads=0):
+    """One LBM step of particle dynamics on the host cores (psm_dem_step_host):
+    x, u, omega, F_old, T_old (float64, n x 3, C-contiguous) are advanced in
+    place.  Raises PsmError on a non-OK status."""
+    n = int(np.asarray(r).size)
+    g = PsmGrid()
+    g.nx, g.ny, g.nz = (int(v) for v in shape)
+    for k in range(6):
+        g.wall[k] = int(walls[k])
+    arrs = [x, u, omega, F_old, T_old]
+    for a in arrs:
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != 3 * n:
+            raise ValueError("state arrays must be C-contiguous float64 of n x 3")
+    Fh, Th = _f64(F_hyd, 3 * n), _f64(T_hyd, 3 * n)
+    rr, dd = _f64(r, n), _f64(density, n)
+    fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
+    gv = _f64(gravity, 3)
+    st = lib().psm_dem_step_host(
+        C.byref(g), float(kn), float(restitution), int(subcycles), _dp(gv), n,
+        _dp(x), _dp(u), _dp(omega), _dp(F_old), _dp(T_old), _dp(Fh), _dp(Th), _dp(rr), _dp(dd),
+        None if fx is None else fx.ctypes.data_as(C.POINTER(C.c_ubyte)), int(threads))
+    if st != 0:
+        raise PsmError(st, "psm_dem_step_host failed")
+    return x, u, omega, F_old, T_old
 
 
 def pack_mlp(params) -> np.ndarray:

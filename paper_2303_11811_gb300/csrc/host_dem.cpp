@@ -1,0 +1,287 @@
+// host_dem.cpp -- particle dynamics of one LBM step on the host cores (see
+// host_dem.h).  Threads own contiguous ranges of particles and meet at a
+// spinning barrier between phases: position update, partner lists, then per
+// sub-step the contacts of the current state (double-buffered positions and
+// velocities) and the Verlet update.
+#include "host_dem.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <thread>
+#include <vector>
+
+namespace psm {
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+
+// damping coefficient of Eq. 12 from the restitution coefficient
+double damping(double meff, double kn, double le) {
+  return -2.0 * le * std::sqrt(meff * kn) / std::sqrt(PI * PI + le * le);
+}
+
+double min_image(double v, double dim, bool periodic) {
+  if (periodic) {
+    if (v > 0.5 * dim) v -= dim;
+    else if (v < -0.5 * dim) v += dim;
+  }
+  return v;
+}
+
+class SpinBarrier {
+ public:
+  explicit SpinBarrier(int n) : n_(n) {}
+  void wait() {
+    if (n_ == 1) return;
+    const int g = gen_.load(std::memory_order_acquire);
+    if (count_.fetch_add(1, std::memory_order_acq_rel) == n_ - 1) {
+      count_.store(0, std::memory_order_relaxed);
+      gen_.fetch_add(1, std::memory_order_acq_rel);
+    } else {
+      while (gen_.load(std::memory_order_acquire) == g) std::this_thread::yield();
+    }
+  }
+
+ private:
+  const int n_;
+  std::atomic<int> count_{0};
+  std::atomic<int> gen_{0};
+};
+
+struct Step {
+  const HostDemParams& P;
+  HostDemState& S;
+  double dims[3];
+  bool periodic[3];
+  std::vector<double> x2, u2;          // second buffers of positions and velocities
+  std::vector<double> xb;              // positions the partner lists were built from
+  std::vector<std::vector<int>> cand;  // partners within contact distance + skin
+  int nc[3] = {1, 1, 1};
+  double h[3] = {1.0, 1.0, 1.0};
+  std::vector<int> bin_start, bin_items;
+  std::atomic<int> moved{0};
+
+  Step(const HostDemParams& p, HostDemState& s) : P(p), S(s) {
+    for (int a = 0; a < 3; ++a) {
+      dims[a] = (double)P.dims[a];
+      periodic[a] = !P.wall[a];
+    }
+    x2.resize(3 * (size_t)S.n);
+    u2.resize(3 * (size_t)S.n);
+    xb.resize(3 * (size_t)S.n);
+    cand.resize(S.n);
+  }
+
+  // positions at the start of the step from the last sub-step's velocity and
+  // force (Eq. 15)
+  void position(int i) {
+    if (S.fixed[i]) return;
+    const double dt = P.dt;
+    const double h2m = dt * dt / (2.0 * S.m[i]);
+    for (int a = 0; a < 3; ++a) {
+      double xn = S.x[3 * i + a] + dt * S.u[3 * i + a] + h2m * S.Fold[3 * i + a];
+      if (periodic[a]) {
+        if (xn >= dims[a]) xn -= dims[a];
+        else if (xn < 0.0) xn += dims[a];
+      }
+      S.x[3 * i + a] = xn;
+    }
+  }
+
+  int bin_of(double v, int a) const {
+    int b = (int)std::floor(v / h[a]);
+    return b < 0 ? 0 : (b >= nc[a] ? nc[a] - 1 : b);
+  }
+
+  // counting sort of the particles into bins of edge >= largest diameter + skin
+  void bins() {
+    double rmax = 0.0;
+    for (int i = 0; i < S.n; ++i) rmax = std::max(rmax, S.r[i]);
+    for (int a = 0; a < 3; ++a) {
+      nc[a] = std::max(1, (int)std::floor(dims[a] / (2.0 * rmax + P.skin)));
+      h[a] = dims[a] / nc[a];
+    }
+    const int nb = nc[0] * nc[1] * nc[2];
+    std::vector<int> pb(S.n);
+    bin_start.assign(nb + 1, 0);
+    for (int i = 0; i < S.n; ++i) {
+      pb[i] = bin_of(S.x[3 * i], 0) +
+              nc[0] * (bin_of(S.x[3 * i + 1], 1) + nc[1] * bin_of(S.x[3 * i + 2], 2));
+      ++bin_start[pb[i] + 1];
+    }
+    for (int b = 0; b < nb; ++b) bin_start[b + 1] += bin_start[b];
+    std::vector<int> cur(bin_start.begin(), bin_start.end() - 1);
+    bin_items.resize(S.n);
+    for (int i = 0; i < S.n; ++i) bin_items[cur[pb[i]]++] = i;
+  }
+
+  int axis_bins(int a, int b, int* out) const {
+    if (nc[a] < 3) {
+      for (int k = 0; k < nc[a]; ++k) out[k] = k;
+      return nc[a];
+    }
+    int m = 0;
+    for (int o = -1; o <= 1; ++o) {
+      int v = b + o;
+      if (v < 0 || v >= nc[a]) {
+        if (!periodic[a]) continue;
+        v = v < 0 ? v + nc[a] : v - nc[a];
+      }
+      out[m++] = v;
+    }
+    return m;
+  }
+
+  void partners(int i) {
+    for (int a = 0; a < 3; ++a) xb[3 * i + a] = S.x[3 * i + a];
+    int bx[3], by[3], bz[3];
+    const int nbx = axis_bins(0, bin_of(S.x[3 * i], 0), bx);
+    const int nby = axis_bins(1, bin_of(S.x[3 * i + 1], 1), by);
+    const int nbz = axis_bins(2, bin_of(S.x[3 * i + 2], 2), bz);
+    std::vector<int>& L = cand[i];
+    L.clear();
+    for (int c = 0; c < nbz; ++c)
+      for (int bb = 0; bb < nby; ++bb)
+        for (int aa = 0; aa < nbx; ++aa) {
+          const int b = bx[aa] + nc[0] * (by[bb] + nc[1] * bz[c]);
+          for (int k = bin_start[b]; k < bin_start[b + 1]; ++k) {
+            const int j = bin_items[k];
+            if (j == i) continue;
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+              const double d = min_image(S.x[3 * i + a] - S.x[3 * j + a], dims[a], periodic[a]);
+              d2 += d * d;
+            }
+            const double reach = S.r[i] + S.r[j] + P.skin;
+            if (d2 < reach * reach) L.push_back(j);
+          }
+        }
+    std::sort(L.begin(), L.end());
+  }
+
+  // exact contact of i with j at the current state (Eq. 12), added to F
+  void pair_contact(const double* X, const double* U, int i, int j, double* F) const {
+    double d[3];
+    for (int a = 0; a < 3; ++a) d[a] = min_image(X[3 * i + a] - X[3 * j + a], dims[a], periodic[a]);
+    const double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double rs = S.r[i] + S.r[j];
+    if (!(dist2 < rs * rs)) return;
+    const double dist = std::sqrt(dist2);
+    const double delta = rs - dist;
+    const double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+    const double vrel[3] = {U[3 * i] - U[3 * j], U[3 * i + 1] - U[3 * j + 1],
+                            U[3 * i + 2] - U[3 * j + 2]};
+    const double vn = vrel[0] * n[0] + vrel[1] * n[1] + vrel[2] * n[2];
+    const double meff = S.m[i] * S.m[j] / (S.m[i] + S.m[j]);
+    const double dn = damping(meff, P.kn, P.log_e);
+    for (int a = 0; a < 3; ++a) F[a] += P.kn * delta * n[a] - dn * vn * n[a];
+  }
+
+  void wall_contacts(const double* X, const double* U, int i, double* F) const {
+    for (int a = 0; a < 3; ++a) {
+      if (periodic[a]) continue;
+      for (int side = 0; side < 2; ++side) {
+        const double delta = side == 0 ? S.r[i] - X[3 * i + a] : X[3 * i + a] + S.r[i] - dims[a];
+        if (!(delta > 0.0)) continue;
+        const double nn = side == 0 ? 1.0 : -1.0;
+        const double vn = U[3 * i + a] * nn;
+        const double dn = damping(S.m[i], P.kn, P.log_e);
+        F[a] += P.kn * delta * nn - dn * vn * nn;
+      }
+    }
+  }
+
+  // one sub-step of particle i: contacts at (Xc, Uc), velocity (Eq. 16) and,
+  // except on the last sub-step, the next positions (Eq. 15) into (Xn, Un)
+  void substep(int i, const double* Xc, const double* Uc, double* Xn, double* Un, bool last) {
+    double F[3] = {0.0, 0.0, 0.0};
+    for (int j : cand[i]) pair_contact(Xc, Uc, i, j, F);
+    wall_contacts(Xc, Uc, i, F);
+    const double dt = P.dt;
+    double u[3], x[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = Uc[3 * i + a];
+      x[a] = Xc[3 * i + a];
+    }
+    if (!S.fixed[i]) {
+      const double hm = dt / (2.0 * S.m[i]), hI = dt / (2.0 * S.I[i]), h2m = dt * hm;
+      for (int a = 0; a < 3; ++a) {
+        const double Fn = S.Fh[3 * i + a] + F[a] + (S.m[i] - S.vol[i]) * P.gravity[a];
+        const double Tn = S.Th[3 * i + a];
+        u[a] += hm * (S.Fold[3 * i + a] + Fn);
+        S.om[3 * i + a] += hI * (S.Told[3 * i + a] + Tn);
+        S.Fold[3 * i + a] = Fn;
+        S.Told[3 * i + a] = Tn;
+      }
+      if (!last) {
+        for (int a = 0; a < 3; ++a) {
+          double xn = x[a] + dt * u[a] + h2m * S.Fold[3 * i + a];
+          if (periodic[a]) {
+            if (xn >= dims[a]) xn -= dims[a];
+            else if (xn < 0.0) xn += dims[a];
+          }
+          x[a] = xn;
+        }
+      }
+      double e2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        const double e = min_image(x[a] - xb[3 * i + a], dims[a], periodic[a]);
+        e2 += e * e;
+      }
+      if (e2 > 0.25 * P.skin * P.skin) moved.store(1, std::memory_order_relaxed);
+    }
+    for (int a = 0; a < 3; ++a) {
+      Un[3 * i + a] = u[a];
+      Xn[3 * i + a] = x[a];
+    }
+  }
+
+  void run(int t, int nt, SpinBarrier& bar) {
+    const int lo = (int)((long long)S.n * t / nt), hi = (int)((long long)S.n * (t + 1) / nt);
+    for (int i = lo; i < hi; ++i) position(i);
+    bar.wait();
+    if (t == 0) bins();
+    bar.wait();
+    for (int i = lo; i < hi; ++i) partners(i);
+    bar.wait();
+    const double* Xc = S.x;
+    const double* Uc = S.u;
+    for (int sc = 0; sc < P.subcycles; ++sc) {
+      double* Xn = (sc % 2 == 0) ? x2.data() : S.x;
+      double* Un = (sc % 2 == 0) ? u2.data() : S.u;
+      for (int i = lo; i < hi; ++i) substep(i, Xc, Uc, Xn, Un, sc + 1 == P.subcycles);
+      bar.wait();
+      Xc = Xn;
+      Uc = Un;
+    }
+    if (Xc != S.x)
+      for (int i = lo; i < hi; ++i)
+        for (int a = 0; a < 3; ++a) {
+          S.x[3 * i + a] = Xc[3 * i + a];
+          S.u[3 * i + a] = Uc[3 * i + a];
+        }
+  }
+};
+
+}  // namespace
+
+int host_dem_step(const HostDemParams& P, HostDemState& S, int threads) {
+  if (S.n <= 0) return 0;
+  int nt = threads < 1 ? 1 : threads;
+  if (nt > S.n) nt = S.n;
+  Step st(P, S);
+  SpinBarrier bar(nt);
+  if (nt == 1) {
+    st.run(0, 1, bar);
+  } else {
+    std::vector<std::thread> pool;
+    pool.reserve(nt - 1);
+    for (int t = 1; t < nt; ++t) pool.emplace_back([&st, &bar, t, nt] { st.run(t, nt, bar); });
+    st.run(0, nt, bar);
+    for (auto& th : pool) th.join();
+  }
+  return st.moved.load() ? 1 : 0;
+}
+
+}  // namespace psm

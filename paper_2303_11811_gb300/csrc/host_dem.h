@@ -1,0 +1,42 @@
+// host_dem.h -- particle dynamics on the host cores: the coupling the paper
+// runs (Sec. 3.2: the DEM on the CPU, with the hydrodynamic forces sent from
+// the GPU and the particle state sent back every LBM step).  The engine's own
+// step keeps the DEM on the device; this form exists to measure that split.
+//
+// The arithmetic is the device DEM's (dem_kernels.cu): velocity Verlet with
+// sub-cycling (Eqs. 15-16), linear spring-dashpot normal contacts between
+// spheres and with the wall faces (Eq. 12), buoyancy-corrected gravity, the
+// hydrodynamic force and torque held over the sub-steps; the same IEEE FP64
+// operations in the same order (partners in ascending index, then the walls),
+// so the two forms agree to the last bit.
+#pragma once
+
+namespace psm {
+
+struct HostDemParams {
+  int dims[3];      // nx, ny, nz
+  int wall[3];      // 1: walls on both faces of the axis, 0: periodic
+  double kn;        // normal spring stiffness
+  double log_e;     // ln(restitution)
+  double dt;        // sub-step, 1 / subcycles
+  double gravity[3];
+  double skin;      // partner lists: contact distance plus this margin
+  int subcycles;
+};
+
+// Particle state in host memory (n particles, vectors as n*3).  x, u, om,
+// Fold and Told are read and advanced by one LBM step; Fh, Th (hydrodynamic
+// force and torque of the step) and the constants are read only.
+struct HostDemState {
+  int n;
+  double *x, *u, *om, *Fold, *Told;
+  const double *Fh, *Th, *r, *m, *I, *vol;
+  const unsigned char* fixed;
+};
+
+// One LBM step of particle dynamics on `threads` host threads (>= 1).
+// Returns 0, or 1 when a particle moved more than half the skin within the
+// step (its partner list may then have missed a contact).
+int host_dem_step(const HostDemParams& P, HostDemState& S, int threads);
+
+}  // namespace psm

@@ -3,16 +3,19 @@
 // handling.  Host arithmetic that feeds the device (particle volume, mass,
 // inertia, f(r) of Eq. 26) is compiled with -ffp-contract=off.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
 
 #include "../../include/psm.h"
 #include "psm_internal.cuh"
+#include "host_dem.h"
 
 namespace psm {
 int launch_map_mlp(MapParams P, cudaStream_t s);
@@ -79,8 +82,9 @@ struct psm_ctx {
   bool error_state = false;
   std::string err;
   // graphs: [buffer or parity][with mapping]
-  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  long graph_launches[2][2] = {{0, 0}, {0, 0}};
+  // [state][with mapping][DEM on the device]
+  cudaGraphExec_t graph[2][2][2] = {};
+  long graph_launches[2][2][2] = {};
   long launches = 0;
   bool timing = false;
   static constexpr int kTimedRing = 64;   // steps whose events are in flight
@@ -142,10 +146,11 @@ T* alloc_n(psm_ctx* c, size_t n, std::vector<void*>& owner) {
 void free_graphs(psm_ctx* c) {
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j)
-      if (c->graph[i][j]) {
-        cudaGraphExecDestroy(c->graph[i][j]);
-        c->graph[i][j] = nullptr;
-      }
+      for (int k = 0; k < 2; ++k)
+        if (c->graph[i][j][k]) {
+          cudaGraphExecDestroy(c->graph[i][j][k]);
+          c->graph[i][j][k] = nullptr;
+        }
 }
 
 void free_particles(psm_ctx* c) {
@@ -213,8 +218,9 @@ double jones_fr(double r) {
 }
 
 // Kernels of one time step, in the order of the paper's Fig. "implementation":
-// mapping (when needed), stream + PSM collide, force/torque reduction, DEM.
-int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
+// mapping (when needed), stream + PSM collide, force/torque reduction, DEM
+// (unless the host runs it: dem = false).
+int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s, bool dem = true) {
   int n = 0;
   MapParams MP = map_params(c);
   if (c->timing) cudaEventRecord(c->ev[0], s);
@@ -264,7 +270,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s) {
     n += launch_force_reduce(MP, s);
   }
   if (c->timing) cudaEventRecord(c->ev[3], s);
-  if (c->any_free) {
+  if (dem && c->any_free) {
     NvtxRange r("psm dem");
     DemParams D{};
     D.g = c->g;
@@ -546,6 +552,14 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   return PSM_OK;
 }
 
+// volume, mass and moment of inertia of a sphere (fluid density 1)
+void sphere_constants(double r, double density, double* vol, double* m, double* I) {
+  const double PI = 3.14159265358979323846;
+  *vol = 4.0 / 3.0 * PI * r * r * r;
+  *m = density * *vol;
+  *I = 0.4 * *m * r * r;
+}
+
 psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r,
                              const double* u, const double* omega, const double* density,
                              const unsigned char* fixed) {
@@ -578,9 +592,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
       }
       hx[3 * i + a] = v;
     }
-    vol[i] = 4.0 / 3.0 * PI * r[i] * r[i] * r[i];
-    m[i] = density[i] * vol[i];
-    I[i] = 0.4 * m[i] * r[i] * r[i];
+    sphere_constants(r[i], density[i], &vol[i], &m[i], &I[i]);
     fr[i] = r[i] * r[i] > 0.5 ? jones_fr(r[i]) : 0.5;
     fx[i] = fixed ? (fixed[i] ? 1 : 0) : 0;
     if (!fx[i] && c->opt.dem) {
@@ -698,47 +710,167 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   return PSM_OK;
 }
 
+// Queues one step (as a captured graph, or launch by launch when timing);
+// dem = false leaves out the DEM kernel.
+psm_status launch_one_step(psm_ctx* c, bool dem) {
+  const bool graphs = c->opt.use_graphs && !c->timing;
+  const bool with_map = c->need_map;
+  const int si = state_index(c), mi = with_map ? 1 : 0, di = dem ? 1 : 0;
+  if (graphs) {
+    cudaGraphExec_t& ge = c->graph[si][mi][di];
+    if (!ge) {
+      cudaGraph_t gr = nullptr;
+      CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+      const int nl = enqueue_step(c, with_map, c->capture, dem);
+      cudaError_t e1 = cudaStreamEndCapture(c->capture, &gr);
+      if (e1 != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e1));
+      cudaError_t e2 = cudaGraphInstantiate(&ge, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e2 != cudaSuccess) {
+        ge = nullptr;
+        return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e2));
+      }
+      c->graph_launches[si][mi][di] = nl;
+    }
+    CK(cudaGraphLaunch(ge, c->stream));
+    c->launches += c->graph_launches[si][mi][di];
+  } else {
+    if (c->timing) {
+      if (c->tpending == psm_ctx::kTimedRing) CK(flush_timing(c));
+      c->ev = &c->tev[5 * c->tpending];
+      ++c->tpending;
+    }
+    c->launches += enqueue_step(c, with_map, c->stream, dem);
+  }
+  CK(cudaGetLastError());
+  if (with_map) c->need_map = c->any_free;
+  advance_state(c);
+  return PSM_OK;
+}
+
 psm_status psm_step(psm_ctx* c, int nsteps) {
   if (!c) return PSM_ERR_ARG;
   NvtxRange range("psm_step");
   if (nsteps < 0) return fail(c, PSM_ERR_ARG, "negative step count");
   if (c->error_state) return fail(c, PSM_ERR_STATE, "context is in an error state");
   c->launches = 0;
-  const bool graphs = c->opt.use_graphs && !c->timing;
   for (int k = 0; k < nsteps; ++k) {
-    const bool with_map = c->need_map;
-    const int si = state_index(c);
-    if (graphs) {
-      cudaGraphExec_t& ge = c->graph[si][with_map ? 1 : 0];
-      if (!ge) {
-        cudaGraph_t gr = nullptr;
-        CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
-        const int nl = enqueue_step(c, with_map, c->capture);
-        cudaError_t e1 = cudaStreamEndCapture(c->capture, &gr);
-        if (e1 != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e1));
-        cudaError_t e2 = cudaGraphInstantiate(&ge, gr, 0);
-        cudaGraphDestroy(gr);
-        if (e2 != cudaSuccess) {
-          ge = nullptr;
-          return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e2));
-        }
-        c->graph_launches[si][with_map ? 1 : 0] = nl;
-      }
-      CK(cudaGraphLaunch(ge, c->stream));
-      c->launches += c->graph_launches[si][with_map ? 1 : 0];
-    } else {
-      if (c->timing) {
-        if (c->tpending == psm_ctx::kTimedRing) CK(flush_timing(c));
-        c->ev = &c->tev[5 * c->tpending];
-        ++c->tpending;
-      }
-      c->launches += enqueue_step(c, with_map, c->stream);
-    }
-    CK(cudaGetLastError());
-    if (with_map) c->need_map = c->any_free;
-    advance_state(c);
+    const psm_status st = launch_one_step(c, true);
+    if (st != PSM_OK) return st;
   }
   return read_status(c);
+}
+
+// The paper's coupling (Sec. 3.2): the LBM part of each step on the device,
+// the particle dynamics on the host cores, the hydrodynamic forces sent to
+// the host and the particle state sent back every step.
+psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_ms) {
+  if (!c) return PSM_ERR_ARG;
+  NvtxRange range("psm_step_host_dem");
+  if (host_ms) *host_ms = 0.0;
+  if (nsteps < 0) return fail(c, PSM_ERR_ARG, "negative step count");
+  if (c->error_state) return fail(c, PSM_ERR_STATE, "context is in an error state");
+  if (!c->opt.dem) return fail(c, PSM_ERR_ARG, "the context was created without the DEM");
+  c->launches = 0;
+  const int n = c->p.n;
+  if (n == 0 || !c->any_free) return psm_step(c, nsteps);
+  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  // host copy of the particle state and constants (the device copy stays the
+  // reference: it is rewritten after every step)
+  const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
+  std::vector<double> x(3 * n), u(3 * n), om(3 * n), Fo(3 * n), To(3 * n), Fh(3 * n),
+      Th(3 * n), r(n), m(n), I(n), vol(n);
+  std::vector<unsigned char> fixed(n);
+  CK(cudaMemcpyAsync(x.data(), c->p.x, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(u.data(), c->p.u, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(om.data(), c->p.om, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(Fo.data(), c->p.Fold, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(To.data(), c->p.Told, b3, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(r.data(), c->p.r, b1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(m.data(), c->p.m, b1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(I.data(), c->p.I, b1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(vol.data(), c->p.vol, b1, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(fixed.data(), c->p.fixed, n, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  HostDemParams HP{};
+  HP.dims[0] = c->g.nx;
+  HP.dims[1] = c->g.ny;
+  HP.dims[2] = c->g.nz;
+  for (int a = 0; a < 3; ++a) {
+    HP.wall[a] = c->g.wall[a];
+    HP.gravity[a] = c->opt.gravity[a];
+  }
+  HP.kn = c->opt.k_n;
+  HP.log_e = c->log_e;
+  HP.dt = 1.0 / c->opt.dem_subcycles;
+  HP.skin = kDemSkin;
+  HP.subcycles = c->opt.dem_subcycles;
+  HostDemState HS{n, x.data(), u.data(), om.data(), Fo.data(), To.data(), Fh.data(),
+                  Th.data(), r.data(), m.data(), I.data(), vol.data(), fixed.data()};
+  for (int k = 0; k < nsteps; ++k) {
+    psm_status st = launch_one_step(c, false);
+    if (st != PSM_OK) return st;
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(cudaMemcpyAsync(Fh.data(), c->p.Fh, b3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(Th.data(), c->p.Th, b3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    const int moved = host_dem_step(HP, HS, threads);
+    CK(cudaMemcpyAsync(c->p.x, x.data(), b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->p.u, u.data(), b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->p.om, om.data(), b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->p.Fold, Fo.data(), b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->p.Told, To.data(), b3, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->dem_bar + 2, 0, sizeof(unsigned), c->stream));  // device lists stale
+    // the host buffers are reused by the next step's copies: wait for these
+    CK(cudaStreamSynchronize(c->stream));
+    const auto t2 = std::chrono::steady_clock::now();
+    if (host_ms) *host_ms += std::chrono::duration<double, std::milli>(t2 - t0).count();
+    c->need_map = true;
+    if (moved) {
+      c->error_state = true;
+      return fail(c, PSM_ERR_STATE,
+                  "a particle moved more than half the DEM neighbour-list skin in one step");
+    }
+  }
+  return read_status(c);
+}
+
+psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
+                             int subcycles, const double* gravity, int n, double* x, double* u,
+                             double* omega, double* F_old, double* T_old, const double* F_hyd,
+                             const double* T_hyd, const double* r, const double* density,
+                             const unsigned char* fixed, int threads) {
+  if (!grid || !gravity || n < 0 || subcycles < 1 || !(k_n > 0.0) || !(restitution > 0.0) ||
+      !(restitution <= 1.0))
+    return PSM_ERR_ARG;
+  if (n == 0) return PSM_OK;
+  if (!x || !u || !omega || !F_old || !T_old || !F_hyd || !T_hyd || !r || !density)
+    return PSM_ERR_ARG;
+  const int dims[3] = {grid->nx, grid->ny, grid->nz};
+  HostDemParams HP{};
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1) return PSM_ERR_ARG;
+    HP.dims[a] = dims[a];
+    if ((grid->wall[2 * a] != 0) != (grid->wall[2 * a + 1] != 0)) return PSM_ERR_ARG;
+    HP.wall[a] = grid->wall[2 * a] ? 1 : 0;
+    HP.gravity[a] = gravity[a];
+  }
+  HP.kn = k_n;
+  HP.log_e = std::log(restitution);
+  HP.dt = 1.0 / subcycles;
+  HP.skin = kDemSkin;
+  HP.subcycles = subcycles;
+  std::vector<double> vol(n), m(n), I(n);
+  std::vector<unsigned char> fx(n);
+  for (int i = 0; i < n; ++i) {
+    if (!(r[i] > 0.0) || !(density[i] > 0.0)) return PSM_ERR_ARG;
+    sphere_constants(r[i], density[i], &vol[i], &m[i], &I[i]);
+    fx[i] = fixed && fixed[i] ? 1 : 0;
+  }
+  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  HostDemState HS{n, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, m.data(), I.data(),
+                  vol.data(), fx.data()};
+  return host_dem_step(HP, HS, threads) ? PSM_ERR_STATE : PSM_OK;
 }
 
 psm_status psm_get_force_torque(psm_ctx* c, double* F, double* T) {
