@@ -600,7 +600,8 @@ def main():
         th = max_over_ranks(th, dist, "cuda")
         host_dem = {"mlups": job_mlups(cells, kh, world, th * 1e3), "ms_per_step": th * 1e3 / kh,
                     "host_phase_ms_per_step": host_ms / kh,
-                    "device_dem_ms_per_step": t[3] / t[4], "threads": os.cpu_count(),
+                    "device_dem_ms_per_step": t[3] / t[4],
+                    "threads": min(os.cpu_count() or 1, max(1, n // 256)),
                     "steps": kh}
     e.close()
 

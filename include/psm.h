@@ -152,12 +152,14 @@ psm_status psm_step(psm_ctx* ctx, int nsteps);
  * the coupling the paper runs (Sec. 3.2): per step the device maps, collides
  * and reduces the forces (as psm_step), the hydrodynamic force and torque are
  * copied to the host, one DEM step (Eqs. 12, 15-16, the context's
- * sub-cycles) runs on `threads` host threads (<= 0: all hardware threads),
+ * sub-cycles) runs on up to `threads` host threads (<= 0: all hardware
+ * threads; at most one thread per 256 particles),
  * and the particle state (centres, velocities, angular velocities and the
  * last sub-step's total force and torque) is copied back.  The DEM arithmetic
  * is the device's, operation for operation, so the state equals psm_step's.
  * *host_ms (may be NULL) receives the wall-clock milliseconds of the host
- * phase summed over the steps (force copy, DEM, state copy).  Needs a context
+ * phase summed over the steps (from the end of the device part: force copy,
+ * DEM, state copy).  Needs a context
  * created with the DEM on (PSM_ERR_ARG otherwise); without free particles it
  * is psm_step.  A particle that moves more than half the partner-list skin
  * within a step gives PSM_ERR_STATE. */

@@ -268,8 +268,11 @@ struct Step {
 
 int host_dem_step(const HostDemParams& P, HostDemState& S, int threads) {
   if (S.n <= 0) return 0;
+  // a thread per 256 particles at most: below that, starting threads and
+  // meeting at the 13 barriers of a step costs more than the work (400
+  // spheres: 0.31 ms per step on one core, 0.79 ms on eight)
   int nt = threads < 1 ? 1 : threads;
-  if (nt > S.n) nt = S.n;
+  nt = std::min(nt, std::max(1, S.n / 256));
   Step st(P, S);
   SpinBarrier bar(nt);
   if (nt == 1) {

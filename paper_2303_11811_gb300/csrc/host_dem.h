@@ -34,7 +34,8 @@ struct HostDemState {
   const unsigned char* fixed;
 };
 
-// One LBM step of particle dynamics on `threads` host threads (>= 1).
+// One LBM step of particle dynamics on up to `threads` host threads (at
+// most one per 256 particles).
 // Returns 0, or 1 when a particle moved more than half the skin within the
 // step (its partner list may then have missed a contact).
 int host_dem_step(const HostDemParams& P, HostDemState& S, int threads);

@@ -810,6 +810,7 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
   for (int k = 0; k < nsteps; ++k) {
     psm_status st = launch_one_step(c, false);
     if (st != PSM_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));  // the device part of the step is done
     const auto t0 = std::chrono::steady_clock::now();
     CK(cudaMemcpyAsync(Fh.data(), c->p.Fh, b3, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(Th.data(), c->p.Th, b3, cudaMemcpyDeviceToHost, c->stream));
