@@ -152,8 +152,9 @@ psm_status psm_step(psm_ctx* ctx, int nsteps);
  * the coupling the paper runs (Sec. 3.2): per step the device maps, collides
  * and reduces the forces (as psm_step), the hydrodynamic force and torque are
  * copied to the host, one DEM step (Eqs. 12, 15-16, the context's
- * sub-cycles) runs on up to `threads` host threads (<= 0: all hardware
- * threads; at most one thread per 256 particles),
+ * sub-cycles) runs on up to `threads` host threads (<= 0 or more than the
+ * hardware threads: all hardware threads; at most one thread per 256
+ * particles),
  * and the particle state (centres, velocities, angular velocities and the
  * last sub-step's total force and torque) is copied back.  The DEM arithmetic
  * is the device's, operation for operation, so the state equals psm_step's.
@@ -175,7 +176,7 @@ psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host
  * starts with F_old = (m - V) gravity, T_old = 0).  In: F_hyd, T_hyd (n*3,
  * held over the sub-steps), r, density (n), fixed (n, may be NULL).  Mass,
  * volume and inertia follow psm_set_particles (fluid density 1).  threads
- * <= 0: all hardware threads.  Returns PSM_ERR_ARG for invalid arguments
+ * as for psm_step_host_dem.  Returns PSM_ERR_ARG for invalid arguments
  * (nothing changed), PSM_ERR_STATE when a particle moved more than half the
  * partner-list skin (1 cell) within the step.  Needs no GPU. */
 psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,

@@ -553,7 +553,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
 }
 
 // volume, mass and moment of inertia of a sphere (fluid density 1)
-void sphere_constants(double r, double density, double* vol, double* m, double* I) {
+static void sphere_constants(double r, double density, double* vol, double* m, double* I) {
   const double PI = 3.14159265358979323846;
   *vol = 4.0 / 3.0 * PI * r * r * r;
   *m = density * *vol;
@@ -712,7 +712,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
 
 // Queues one step (as a captured graph, or launch by launch when timing);
 // dem = false leaves out the DEM kernel.
-psm_status launch_one_step(psm_ctx* c, bool dem) {
+static psm_status launch_one_step(psm_ctx* c, bool dem) {
   const bool graphs = c->opt.use_graphs && !c->timing;
   const bool with_map = c->need_map;
   const int si = state_index(c), mi = with_map ? 1 : 0, di = dem ? 1 : 0;
@@ -761,6 +761,13 @@ psm_status psm_step(psm_ctx* c, int nsteps) {
   return read_status(c);
 }
 
+// host threads for the DEM: the request, at most the hardware threads (all
+// of them for a request <= 0)
+static int host_threads(int requested) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  return requested <= 0 || requested > hw ? hw : requested;
+}
+
 // The paper's coupling (Sec. 3.2): the LBM part of each step on the device,
 // the particle dynamics on the host cores, the hydrodynamic forces sent to
 // the host and the particle state sent back every step.
@@ -774,7 +781,7 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
   c->launches = 0;
   const int n = c->p.n;
   if (n == 0 || !c->any_free) return psm_step(c, nsteps);
-  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  threads = host_threads(threads);
   // host copy of the particle state and constants (the device copy stays the
   // reference: it is rewritten after every step)
   const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
@@ -868,7 +875,7 @@ psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitutio
     sphere_constants(r[i], density[i], &vol[i], &m[i], &I[i]);
     fx[i] = fixed && fixed[i] ? 1 : 0;
   }
-  if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  threads = host_threads(threads);
   HostDemState HS{n, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, m.data(), I.data(),
                   vol.data(), fx.data()};
   return host_dem_step(HP, HS, threads) ? PSM_ERR_STATE : PSM_OK;

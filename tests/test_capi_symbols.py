@@ -73,3 +73,21 @@ def test_checkpoint_entries_reject_null_arguments_without_a_gpu():
     h = ctypes.c_void_p()
     assert L.psm_create(ctypes.byref(g), 0.6, 0, ctypes.byref(o), ctypes.byref(h)) == 1
     assert not h.value
+
+
+def test_no_other_c_symbols_leak():
+    """Every unmangled function the library exports is a psm_ entry point
+    (internal helpers have internal linkage)."""
+    import shutil
+    import subprocess
+
+    import pytest
+    if not shutil.which("nm"):
+        pytest.skip("nm not available")
+    from paper_2303_11811_gb300 import build
+    build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    names = [ln.split()[-1] for ln in out.splitlines() if " T " in ln]
+    leaked = [n for n in names if not n.startswith(("psm_", "_Z", "_init", "_fini"))]
+    assert not leaked, leaked
