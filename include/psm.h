@@ -178,7 +178,8 @@ psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host
  * volume and inertia follow psm_set_particles (fluid density 1).  threads
  * as for psm_step_host_dem.  Returns PSM_ERR_ARG for invalid arguments
  * (nothing changed), PSM_ERR_STATE when a particle moved more than half the
- * partner-list skin (1 cell) within the step.  Needs no GPU. */
+ * partner-list skin (1 cell) within the step (the arrays then hold the
+ * advanced state, which may have missed a contact).  Needs no GPU. */
 psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
                              int subcycles, const double* gravity, int n, double* x, double* u,
                              double* omega, double* F_old, double* T_old, const double* F_hyd,

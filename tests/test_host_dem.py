@@ -124,3 +124,11 @@ def test_arguments_and_skin_are_checked():
     with pytest.raises(capi.PsmError) as e:
         capi.dem_step_host(SHAPE, WALLS, hx, fast, ho, Fo, To, Fh, Th, r, dens, fixed=fixed)
     assert e.value.status == capi.PSM_ERR_STATE
+    # no particles: nothing to do; zero sub-cycles or stiffness: refused
+    e0 = np.zeros((0, 3))
+    capi.dem_step_host(SHAPE, WALLS, e0.copy(), e0.copy(), e0.copy(), e0.copy(), e0.copy(), e0,
+                       e0, np.zeros(0), np.zeros(0))
+    for bad in (dict(subcycles=0), dict(kn=0.0)):
+        with pytest.raises(capi.PsmError) as e:
+            capi.dem_step_host(SHAPE, WALLS, hx, hu, ho, Fo, To, Fh, Th, r, dens, **bad)
+        assert e.value.status == capi.PSM_ERR_ARG
