@@ -204,3 +204,56 @@ def test_moving_sphere_feels_drag_and_rotating_sphere_feels_counter_torque():
     # unbounded-fluid torque on a rotating sphere is -8 pi mu r^3 Omega; the
     # periodic box and the PSM radius error keep this an order-of-magnitude check
     assert 0.5 < T[0, 2] / (-8 * math.pi * nu * 4.0 ** 3 * 1e-3) < 2.0
+
+
+def test_total_momentum_conserved_with_gravity_and_free_particles():
+    """Reading J (Sec. 2.2, Eq. 9; Sec. 2.3, Eq. 17): in a periodic box with
+    gravity, free settling spheres, DEM contacts and a noisy fluid, no net
+    momentum enters the system.  The fluid receives the counter force through
+    the (1-B) forcing term and -F_i from the spheres (Eq. 21); each sphere
+    receives F_i, its buoyancy-corrected weight and equal and opposite contact
+    forces.  The sub-cycled Verlet update (Eq. 16) lags the force by half a
+    sub-step, so the conserved quantity is
+
+        P_fluid + sum_i m_i U_i + (dt_p/2) sum_i F_old,i,
+
+    F_old,i being the last sub-step's total force F_i + F_col,i + (m_i-V_i) g,
+    whose contact part cancels over pairs.  The check forms m_i, V_i and the
+    weights itself from the inputs; it does not read the oracle's counter force."""
+    L, sub = 20, 10
+    g = np.array([0.0, 2e-5, -3e-5])
+    rho_p = np.array([2.5, 2.0, 3.0, 2.5])
+    r = np.array([3.0, 2.6, 2.4, 3.1])
+    # spheres 0 and 1 approach each other and collide within the run
+    x = np.array([[6.0, 6.5, 7.0], [12.0, 6.2, 7.3], [14.5, 15.0, 15.5], [5.5, 14.0, 13.0]])
+    u = np.array([[2e-2, 0, 0], [-2e-2, 0, 0], [0, 1e-3, -2e-3], [1e-3, 0, 2e-3]])
+    om = inputs.random_velocities(4, 1e-3, 17)
+    o = Oracle(L, L, L, 0.55, relax="trt", gravity=tuple(g), weighting="nt",
+               eps_mode="supersample", eps_n=4, kn=1e3, restitution=0.9, subcycles=sub,
+               dem=True)
+    o.set_particles(x, r, u, om, density=rho_p)
+    _noisy_rest(o, 23, 2e-3)
+    V = 4.0 / 3.0 * math.pi * r ** 3
+    m = rho_p * V
+    weight = ((m - V)[:, None] * g[None, :]).sum(axis=0)
+
+    def invariant(F_old_sum):
+        _, up, _ = o.particles()
+        Pp = (m[:, None] * up).sum(axis=0)
+        return o.momentum() + Pp + 0.5 / sub * F_old_sum, np.max(np.abs(Pp))
+
+    I0, scale = invariant(weight)  # F_old starts as the external force (reading L)
+    contact = False
+    for _ in range(25):
+        o.step(1)
+        F, _ = o.force_torque()
+        I1, s = invariant(F.sum(axis=0) + weight)
+        scale = max(scale, s)
+        assert np.max(np.abs(I1 - I0)) < 1e-13 * scale, (I1 - I0, scale)
+        xp, _, _ = o.particles()
+        contact |= np.linalg.norm(xp[0] - xp[1]) < r[0] + r[1]
+    # the run did exercise what the check is about
+    assert contact
+    _, up, _ = o.particles()
+    assert np.max(np.abs(up[2:] - u[2:])) > 1e-4  # settling under gravity and drag
+    assert np.max(np.abs(weight)) * 25 > 1e-3 * scale

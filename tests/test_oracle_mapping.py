@@ -123,6 +123,15 @@ def test_nt_weighting_endpoints_and_order():
         assert np.all(B[1:-1] < e[1:-1])
 
 
+def test_nt_weighting_closed_form_values():
+    """B(eps, tau) = eps (tau - 1/2) / ((1 - eps) + (tau - 1/2)) at points
+    worked by hand: B(1/2, 1) = (1/4)/(1) = 1/4, B(1/4, 0.55) =
+    (1/4)(1/20)/(3/4 + 1/20) = 1/64, B(3/4, 3/2) = (3/4)/(5/4) = 3/5."""
+    assert oracle.nt_weight(0.5, 1.0) == 0.25
+    assert abs(oracle.nt_weight(0.25, 0.55) * 64.0 - 1.0) < 1e-14
+    assert abs(oracle.nt_weight(0.75, 1.5) / 0.6 - 1.0) < 1e-14
+
+
 def test_two_slots_in_index_order_and_overflow():
     """Up to two particles per cell (Sec. 3.1.1): a shared cell lists the
     lower index first; a cell within reach of three particles is an error."""
