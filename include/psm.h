@@ -107,8 +107,11 @@ typedef struct {
   double restitution;    /* normal restitution coefficient, (0, 1] */
   int dem_subcycles;     /* DEM sub-steps per LBM step (default 10) */
   int dem;               /* 1: integrate free particles on the device */
-  int deterministic;     /* 1: fixed-order force/torque reduction (bitwise
-                            reproducible); 0: fused atomic reduction */
+  int deterministic;     /* must be 1: the force/torque reduction sums each
+                            particle's cells in a fixed order (bitwise
+                            reproducible run to run); any other value is
+                            refused with PSM_ERR_ARG (no atomic reduction
+                            is built) */
   int use_graphs;        /* 1: replay captured CUDA graphs for steps */
   void* stream;          /* cudaStream_t to queue all work on */
   void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL */
@@ -163,7 +166,12 @@ psm_status psm_step(psm_ctx* ctx, int nsteps);
  * DEM, state copy).  Needs a context
  * created with the DEM on (PSM_ERR_ARG otherwise); without free particles it
  * is psm_step.  A particle that moves more than half the partner-list skin
- * within a step gives PSM_ERR_STATE. */
+ * within a step gives PSM_ERR_STATE.  The device status word is read with
+ * each step's force copy: an error of the device part (slot overflow,
+ * non-finite force) ends the loop at that step, before the host DEM uses the
+ * forces, and is returned as psm_step would.  PSM_ERR_OOM when host memory
+ * for the particle state runs out.  Every error leaves the context in its
+ * error state. */
 psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host_ms);
 
 /* One LBM step of particle dynamics on the host cores for n spheres, without
@@ -179,7 +187,10 @@ psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host
  * as for psm_step_host_dem.  Returns PSM_ERR_ARG for invalid arguments
  * (nothing changed), PSM_ERR_STATE when a particle moved more than half the
  * partner-list skin (1 cell) within the step (the arrays then hold the
- * advanced state, which may have missed a contact).  Needs no GPU. */
+ * advanced state, which may have missed a contact), PSM_ERR_OOM when host
+ * memory for the step ran out (the arrays may then be partly advanced).  A
+ * worker thread that cannot be started makes the step run on fewer threads
+ * with the same result; nothing is thrown.  Needs no GPU. */
 psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
                              int subcycles, const double* gravity, int n, double* x, double* u,
                              double* omega, double* F_old, double* T_old, const double* F_hyd,
@@ -294,9 +305,12 @@ long psm_last_launch_count(const psm_ctx* ctx);
  * device memory that the library declares at file scope: every GPU that
  * loads the library holds it until the process exits, and all calls on a
  * GPU share it, so calls whose work overlaps on the GPU (unordered streams)
- * race; order them on one stream.  The first call on each device (with that
- * device current) looks up the array's device address; make that first call
- * before any stream capture. */
+ * race; order them on one stream.  The first call in each CUDA context of a
+ * device (with that device current) looks up the array's device address:
+ * the first call on the device, and again the first call after a
+ * cudaDeviceReset or after another context was made current there, since the
+ * library's device code is then loaded anew.  Make such a first call before
+ * any stream capture. */
 #define PSM_NOALLOC_MAX_CELLS (4096LL * 65536LL)
 psm_status psm_field_sums_noalloc(const double* f, long long ncells, double* sums,
                                   void* stream);

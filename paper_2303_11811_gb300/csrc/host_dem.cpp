@@ -29,24 +29,34 @@ double min_image(double v, double dim, bool periodic) {
   return v;
 }
 
+// Spinning barrier that a failing thread can abort: wait() then returns
+// false in every thread (those waiting and those arriving later), so no
+// thread is left spinning for a partner that stopped.
 class SpinBarrier {
  public:
   explicit SpinBarrier(int n) : n_(n) {}
-  void wait() {
-    if (n_ == 1) return;
+  bool wait() {
+    if (n_ == 1) return !aborted();
     const int g = gen_.load(std::memory_order_acquire);
     if (count_.fetch_add(1, std::memory_order_acq_rel) == n_ - 1) {
       count_.store(0, std::memory_order_relaxed);
       gen_.fetch_add(1, std::memory_order_acq_rel);
     } else {
-      while (gen_.load(std::memory_order_acquire) == g) std::this_thread::yield();
+      while (gen_.load(std::memory_order_acquire) == g) {
+        if (aborted()) return false;
+        std::this_thread::yield();
+      }
     }
+    return !aborted();
   }
+  void abort() { abort_.store(true, std::memory_order_release); }
+  bool aborted() const { return abort_.load(std::memory_order_acquire); }
 
  private:
   const int n_;
   std::atomic<int> count_{0};
   std::atomic<int> gen_{0};
+  std::atomic<bool> abort_{false};
 };
 
 struct Step {
@@ -237,21 +247,23 @@ struct Step {
     }
   }
 
-  void run(int t, int nt, SpinBarrier& bar) {
+  // the phases of one step for the particles of thread t; returns early
+  // (leaving the step unfinished) when the barrier was aborted
+  void phases(int t, int nt, SpinBarrier& bar) {
     const int lo = (int)((long long)S.n * t / nt), hi = (int)((long long)S.n * (t + 1) / nt);
     for (int i = lo; i < hi; ++i) position(i);
-    bar.wait();
+    if (!bar.wait()) return;
     if (t == 0) bins();
-    bar.wait();
+    if (!bar.wait()) return;
     for (int i = lo; i < hi; ++i) partners(i);
-    bar.wait();
+    if (!bar.wait()) return;
     const double* Xc = S.x;
     const double* Uc = S.u;
     for (int sc = 0; sc < P.subcycles; ++sc) {
       double* Xn = (sc % 2 == 0) ? x2.data() : S.x;
       double* Un = (sc % 2 == 0) ? u2.data() : S.u;
       for (int i = lo; i < hi; ++i) substep(i, Xc, Uc, Xn, Un, sc + 1 == P.subcycles);
-      bar.wait();
+      if (!bar.wait()) return;
       Xc = Xn;
       Uc = Un;
     }
@@ -262,7 +274,54 @@ struct Step {
           S.u[3 * i + a] = Uc[3 * i + a];
         }
   }
+
+  // a thread's part of the step; an exception (an allocation in the bins or
+  // partner lists) marks the step failed and releases the other threads
+  void run(int t, int nt, SpinBarrier& bar) {
+    try {
+      phases(t, nt, bar);
+    } catch (...) {
+      failed.store(1, std::memory_order_relaxed);
+      bar.abort();
+    }
+  }
+  std::atomic<int> failed{0};
 };
+
+}  // namespace
+
+namespace {
+
+// Starts nt - 1 workers parked on a flag, so that a failure to start one of
+// them (std::system_error) leaves the particle state untouched: the started
+// workers are released with an abort and joined, and the step runs on the
+// calling thread alone.  Returns the number of threads the step ran on.
+int run_threads(Step& st, int nt) {
+  if (nt > 1) {
+    SpinBarrier bar(nt);
+    std::atomic<int> go{0};  // 1: run, -1: give up
+    std::vector<std::thread> pool;
+    bool started = true;
+    try {
+      pool.reserve(nt - 1);
+      for (int t = 1; t < nt; ++t)
+        pool.emplace_back([&st, &bar, &go, t, nt] {
+          int g;
+          while ((g = go.load(std::memory_order_acquire)) == 0) std::this_thread::yield();
+          if (g > 0) st.run(t, nt, bar);
+        });
+    } catch (...) {
+      started = false;
+    }
+    go.store(started ? 1 : -1, std::memory_order_release);
+    if (started) st.run(0, nt, bar);
+    for (auto& th : pool) th.join();
+    if (started) return nt;
+  }
+  SpinBarrier one(1);
+  st.run(0, 1, one);
+  return 1;
+}
 
 }  // namespace
 
@@ -273,18 +332,14 @@ int host_dem_step(const HostDemParams& P, HostDemState& S, int threads) {
   // spheres: 0.31 ms per step on one core, 0.79 ms on eight)
   int nt = threads < 1 ? 1 : threads;
   nt = std::min(nt, std::max(1, S.n / 256));
-  Step st(P, S);
-  SpinBarrier bar(nt);
-  if (nt == 1) {
-    st.run(0, 1, bar);
-  } else {
-    std::vector<std::thread> pool;
-    pool.reserve(nt - 1);
-    for (int t = 1; t < nt; ++t) pool.emplace_back([&st, &bar, t, nt] { st.run(t, nt, bar); });
-    st.run(0, nt, bar);
-    for (auto& th : pool) th.join();
+  try {
+    Step st(P, S);
+    run_threads(st, nt);
+    if (st.failed.load()) return -1;
+    return st.moved.load() ? 1 : 0;
+  } catch (...) {  // the step's own buffers could not be allocated
+    return -1;
   }
-  return st.moved.load() ? 1 : 0;
 }
 
 }  // namespace psm

@@ -36,8 +36,11 @@ struct HostDemState {
 
 // One LBM step of particle dynamics on up to `threads` host threads (at
 // most one per 256 particles).
-// Returns 0, or 1 when a particle moved more than half the skin within the
-// step (its partner list may then have missed a contact).
+// Returns 0, 1 when a particle moved more than half the skin within the
+// step (its partner list may then have missed a contact), or -1 when host
+// memory for the step's buffers ran out (the state is then partly advanced).
+// Throws nothing: a worker thread that cannot be started makes the step run
+// on fewer threads, with the same result.
 int host_dem_step(const HostDemParams& P, HostDemState& S, int threads);
 
 }  // namespace psm

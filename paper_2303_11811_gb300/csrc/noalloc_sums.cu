@@ -16,6 +16,7 @@
 // overlaps on the GPU (different streams, no ordering between them) race on
 // it.  Each call writes every partial it reads before reading it, so nothing
 // has to be cleared between calls.
+#include <cuda.h>  // CUcontext and CUresult types only; the functions come by entry point
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -31,9 +32,52 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 
 static __device__ __align__(256) double g_sum_partials[4 * NOALLOC_MAX_PARTS];
 
-// device address of g_sum_partials per device, looked up once per device
+// Device address of g_sum_partials per device, looked up once per CUDA
+// context: a cudaDeviceReset (or another context made current on the device)
+// loads the module again, possibly at another address, so each cached
+// address is kept with the id of the context it was looked up in (context
+// ids are unique within a process) and looked up again when that changes.
+struct PartialsAddr {
+  unsigned long long ctx_id;
+  double* addr;
+};
 std::mutex g_mutex;
-double* g_partials_addr[NOALLOC_MAX_DEVICES] = {};
+PartialsAddr g_partials[NOALLOC_MAX_DEVICES] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// id of the context current on the calling thread (the runtime makes the
+// device's primary context current if none is); false on failure
+bool current_context_id(unsigned long long* id) {
+  if (!g_ctx_get_current || !g_ctx_get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1)
+      return false;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2)
+      return false;
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return false;
+  if (!ctx) {
+    // no context current on this thread yet: cudaSetDevice initialises the
+    // device's primary context and makes it current (it allocates nothing)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return false;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+  }
+  return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 // velocity components of direction q in the D3Q19 order of include/psm.h
 __device__ __forceinline__ void velocity(int q, int& cx, int& cy, int& cz) {
@@ -113,17 +157,23 @@ extern "C" psm_status psm_field_sums_noalloc(const double* f, long long ncells, 
   }
   double* partials = nullptr;
   {
-    // set-up on the first call on this device (the current one)
+    // set-up on the first call in each context of this device (the current one)
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_partials_addr[dev]) {
+    unsigned long long ctx_id = 0;
+    if (!current_context_id(&ctx_id)) {
+      cudaGetLastError();
+      return PSM_ERR_CUDA;
+    }
+    if (!g_partials[dev].addr || g_partials[dev].ctx_id != ctx_id) {
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_sum_partials) != cudaSuccess || !ptr) {
         cudaGetLastError();
         return PSM_ERR_CUDA;
       }
-      g_partials_addr[dev] = static_cast<double*>(ptr);
+      g_partials[dev].addr = static_cast<double*>(ptr);
+      g_partials[dev].ctx_id = ctx_id;
     }
-    partials = g_partials_addr[dev];
+    partials = g_partials[dev].addr;
   }
   const int nparts = (int)((ncells + NOALLOC_CELLS_PER_PART - 1) / NOALLOC_CELLS_PER_PART);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

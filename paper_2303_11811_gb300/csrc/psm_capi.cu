@@ -444,6 +444,8 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
       opt->precision != PSM_FP64_DF)
     return PSM_ERR_ARG;
   if (opt->streaming != PSM_PULL && opt->streaming != PSM_AA) return PSM_ERR_ARG;
+  // only the fixed-order reduction is built: results are bitwise reproducible
+  if (opt->deterministic != 1) return PSM_ERR_ARG;
   if (opt->eps_mode < 0 || opt->eps_mode > 2) return PSM_ERR_ARG;
   if (opt->eps_n < 1 || opt->eps_n > 16) return PSM_ERR_ARG;
   if (opt->weighting != PSM_W_EPS && opt->weighting != PSM_W_NT) return PSM_ERR_ARG;
@@ -785,9 +787,15 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
   // host copy of the particle state and constants (the device copy stays the
   // reference: it is rewritten after every step)
   const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
-  std::vector<double> x(3 * n), u(3 * n), om(3 * n), Fo(3 * n), To(3 * n), Fh(3 * n),
-      Th(3 * n), r(n), m(n), I(n), vol(n);
-  std::vector<unsigned char> fixed(n);
+  std::vector<double> x, u, om, Fo, To, Fh, Th, r, m, I, vol;
+  std::vector<unsigned char> fixed;
+  try {
+    for (auto* v : {&x, &u, &om, &Fo, &To, &Fh, &Th}) v->resize(3 * (size_t)n);
+    for (auto* v : {&r, &m, &I, &vol}) v->resize((size_t)n);
+    fixed.resize((size_t)n);
+  } catch (...) {
+    return fail(c, PSM_ERR_OOM, "host memory for the particle state");
+  }
   CK(cudaMemcpyAsync(x.data(), c->p.x, b3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(u.data(), c->p.u, b3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(om.data(), c->p.om, b3, cudaMemcpyDeviceToHost, c->stream));
@@ -819,10 +827,20 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
     if (st != PSM_OK) return st;
     CK(cudaStreamSynchronize(c->stream));  // the device part of the step is done
     const auto t0 = std::chrono::steady_clock::now();
+    unsigned dev_status = 0;
     CK(cudaMemcpyAsync(Fh.data(), c->p.Fh, b3, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(Th.data(), c->p.Th, b3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&dev_status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    // an error of the device part (a non-finite force, a slot overflow) stops
+    // the loop before the host DEM integrates with it
+    if (dev_status) return read_status(c);
     const int moved = host_dem_step(HP, HS, threads);
+    if (moved < 0) {
+      c->error_state = true;
+      return fail(c, PSM_ERR_OOM, "host memory for the DEM step");
+    }
     CK(cudaMemcpyAsync(c->p.x, x.data(), b3, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->p.u, u.data(), b3, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->p.om, om.data(), b3, cudaMemcpyHostToDevice, c->stream));
@@ -868,8 +886,16 @@ psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitutio
   HP.dt = 1.0 / subcycles;
   HP.skin = kDemSkin;
   HP.subcycles = subcycles;
-  std::vector<double> vol(n), m(n), I(n);
-  std::vector<unsigned char> fx(n);
+  std::vector<double> vol, m, I;
+  std::vector<unsigned char> fx;
+  try {
+    vol.resize(n);
+    m.resize(n);
+    I.resize(n);
+    fx.resize(n);
+  } catch (...) {
+    return PSM_ERR_OOM;
+  }
   for (int i = 0; i < n; ++i) {
     if (!(r[i] > 0.0) || !(density[i] > 0.0)) return PSM_ERR_ARG;
     sphere_constants(r[i], density[i], &vol[i], &m[i], &I[i]);
@@ -878,7 +904,8 @@ psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitutio
   threads = host_threads(threads);
   HostDemState HS{n, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, m.data(), I.data(),
                   vol.data(), fx.data()};
-  return host_dem_step(HP, HS, threads) ? PSM_ERR_STATE : PSM_OK;
+  const int st = host_dem_step(HP, HS, threads);
+  return st < 0 ? PSM_ERR_OOM : (st ? PSM_ERR_STATE : PSM_OK);
 }
 
 psm_status psm_get_force_torque(psm_ctx* c, double* F, double* T) {

@@ -53,6 +53,9 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     g.wall[0] = 0
     o.eps_n = 0
     assert L.psm_create(ctypes.byref(g), 0.6, 0, ctypes.byref(o), ctypes.byref(h)) == 1
+    o.eps_n = 4
+    o.deterministic = 0  # only the fixed-order reduction exists
+    assert L.psm_create(ctypes.byref(g), 0.6, 0, ctypes.byref(o), ctypes.byref(h)) == 1
     assert not h.value
 
 

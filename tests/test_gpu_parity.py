@@ -2,8 +2,9 @@
 
 FP64 path: PDFs within 1e-12 relative, max over cells and directions of
 |f_gpu - f_oracle| / |f_oracle| (the bound stated for this path); forces and
-torques within 1e-10 relative to the largest component (they are sums of
-thousands of cell contributions accumulated in a different order).
+torques within 1e-12 relative to the largest component (they are sums of
+thousands of cell contributions accumulated in a different order; measured
+errors are near 1e-13, so a reduction that drops or repeats a cell shows).
 Mapping: particle indices exact, B within 1e-15 (same FP64 decisions).
 """
 import numpy as np
@@ -15,6 +16,7 @@ from paper_2303_11811_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 PDF_TOL = 1e-12
+FORCE_TOL = 1e-12
 
 
 @pytest.fixture(scope="module")
@@ -56,8 +58,8 @@ def test_sphere32_fp64_1000_steps(capi):
     assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
     Fg, Tg = e.force_torque()
     Fo, To = o.force_torque()
-    assert force_err(Fg, Fo) < 1e-10
-    assert np.max(np.abs(Tg - To)) < 1e-10 * np.max(np.abs(Fo))
+    assert force_err(Fg, Fo) < FORCE_TOL, force_err(Fg, Fo)
+    assert np.max(np.abs(Tg - To)) < FORCE_TOL * np.max(np.abs(Fo))
 
 
 @pytest.mark.parametrize("streaming", ["pull", "aa"])
@@ -89,7 +91,8 @@ def test_moving_particles_walls_ragged_grid(capi, streaming, relax, eps_mode, we
     assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
     Fg, Tg = e.force_torque()
     Fo, To = o.force_torque()
-    assert force_err(Fg, Fo) < 1e-10 and force_err(Tg, To) < 1e-10
+    assert force_err(Fg, Fo) < FORCE_TOL, force_err(Fg, Fo)
+    assert force_err(Tg, To) < FORCE_TOL, force_err(Tg, To)
     xg, ug, wg = e.particles()
     xo, uo, wo = o.particles()
     assert np.max(np.abs(xg - xo)) < 1e-12
@@ -218,13 +221,13 @@ def test_settle128_full_size_three_steps(capi):
     assert rel_pdf_err(e.pdfs(), o.pdfs()) < PDF_TOL
     Fg, Tg = e.force_torque()
     Fo, To = o.force_torque()
-    assert force_err(Fg, Fo) < 1e-10
+    assert force_err(Fg, Fo) < FORCE_TOL, force_err(Fg, Fo)
     # torques of spheres falling from rest are small next to their natural
     # scale (arm r + 1 times the force), the scale their rounding error
     # follows; many of the 400 spheres straddle a periodic face (nearest-image
     # arms)
     t_scale = (float(np.max(p["r"])) + 1.0) * float(np.max(np.abs(Fo)))
-    assert float(np.max(np.abs(Tg - To))) < 1e-10 * t_scale
+    assert float(np.max(np.abs(Tg - To))) < FORCE_TOL * t_scale
     xg, _, _ = e.particles()
     xo, _, _ = o.particles()
     assert np.max(np.abs(xg - xo)) < 1e-12
