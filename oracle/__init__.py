@@ -33,8 +33,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_SO) >= os.path.getmtime(src)):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared",
-                           "-ffp-contract=off", "-o", tmp, src, "-lm"])
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, src]
+    try:  # OpenMP for the threaded loops; without it the oracle runs on one thread
+        subprocess.check_call(base + ["-fopenmp", "-lm"], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -66,6 +69,7 @@ def lib():
             L.or_map.argtypes = [P]
             L.or_get_slots.argtypes = [P, ip, dp, ip, dp]
             L.or_step.argtypes = [P, C.c_int]
+            L.or_set_threads.argtypes = [P, C.c_int]
             L.or_dem_only.argtypes = [P, C.c_int]
             L.or_get_force_torque.argtypes = [P, dp, dp]
             L.or_set_hydro.argtypes = [P, dp, dp]
@@ -196,6 +200,10 @@ class Oracle:
                              p1.ctypes.data_as(ip), _dp(b1))
         return (p0.reshape(self.shape), b0.reshape(self.shape),
                 p1.reshape(self.shape), b1.reshape(self.shape))
+
+    def set_threads(self, n):
+        """Host threads of the step's loops; results do not depend on it."""
+        self._L.or_set_threads(self.h, int(n))
 
     def step(self, n=1):
         st = self._L.or_step(self.h, n)

@@ -54,6 +54,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define Q 19
 
@@ -96,6 +99,14 @@ struct or_ctx {
   /* last step */
   double fext_last[3];
   double vfluid_last;
+  /* host threads of the loops (or_set_threads) */
+  int threads;
+  /* per covered cell and slot, the force and torque contributions of the
+   * last collision in cell order (z, y, x, slot), summed per particle after
+   * the cell loop */
+  long* plane_off;   /* first covered cell of each z-plane */
+  double* contrib;   /* 12 values per covered cell: F, T of slot 0, then slot 1 */
+  long contrib_cap;
 };
 
 or_ctx* or_create(const or_config* cfg) {
@@ -121,8 +132,12 @@ or_ctx* or_create(const or_config* cfg) {
   }
   c->vfluid_last = (double)c->N;
   for (int a = 0; a < 3; ++a) c->fext_last[a] = cfg->fbody[a];
+  c->threads = 1;
+  c->plane_off = (long*)malloc(sizeof(long) * ((size_t)cfg->nz + 1));
   return c;
 }
+
+void or_set_threads(or_ctx* c, int threads) { c->threads = threads < 1 ? 1 : threads; }
 
 static void free_particles(or_ctx* c) {
   free(c->x); free(c->r); free(c->u); free(c->om); free(c->m); free(c->I);
@@ -136,6 +151,7 @@ static void free_particles(or_ctx* c) {
 void or_destroy(or_ctx* c) {
   if (!c) return;
   free(c->f); free(c->fnew); free(c->pid0); free(c->pid1); free(c->B0); free(c->B1);
+  free(c->plane_off); free(c->contrib);
   free_particles(c);
   free(c);
 }
@@ -308,67 +324,112 @@ static int nearest_image(int i, double xp, int n, int periodic) {
   return i;
 }
 
+/* The cells within reach of particle p (reading S), in the order of its box
+ * of cells (z, y, x): their indices and nearest-image offsets d = x_cell - x_p
+ * (3 per cell).  Returns -1 when the box is wider than a periodic axis. */
+static int reach_list(const or_ctx* c, int p, const int dims[3], const int per[3],
+                      long** cells_out, double** offs_out, int* count_out) {
+  double r = c->r[p];
+  int lo[3], hi[3];
+  long box = 1;
+  *cells_out = NULL; *offs_out = NULL; *count_out = 0;
+  for (int a = 0; a < 3; ++a) {
+    double xp = c->x[3 * p + a];
+    lo[a] = (int)floor(xp - r - 1.0);
+    hi[a] = (int)floor(xp + r + 1.0);
+    if (per[a] && hi[a] - lo[a] + 1 > dims[a]) return -1;
+    if (!per[a]) {
+      if (lo[a] < 0) lo[a] = 0;
+      if (hi[a] > dims[a] - 1) hi[a] = dims[a] - 1;
+    }
+    box *= (hi[a] >= lo[a]) ? (long)(hi[a] - lo[a] + 1) : 0;
+  }
+  long* cells = (long*)malloc(sizeof(long) * (size_t)(box > 0 ? box : 1));
+  double* offs = (double*)malloc(sizeof(double) * 3 * (size_t)(box > 0 ? box : 1));
+  int n = 0;
+  double reach = r + HALF_SQRT3;
+  for (int kz = lo[2]; kz <= hi[2]; ++kz)
+    for (int ky = lo[1]; ky <= hi[1]; ++ky)
+      for (int kx = lo[0]; kx <= hi[0]; ++kx) {
+        int ix = ((kx % dims[0]) + dims[0]) % dims[0];
+        int iy = ((ky % dims[1]) + dims[1]) % dims[1];
+        int iz = ((kz % dims[2]) + dims[2]) % dims[2];
+        int ux = nearest_image(ix, c->x[3 * p + 0], dims[0], per[0]);
+        int uy = nearest_image(iy, c->x[3 * p + 1], dims[1], per[1]);
+        int uz = nearest_image(iz, c->x[3 * p + 2], dims[2], per[2]);
+        double dx = (ux + 0.5) - c->x[3 * p + 0];
+        double dy = (uy + 0.5) - c->x[3 * p + 1];
+        double dz = (uz + 0.5) - c->x[3 * p + 2];
+        double d2 = dx * dx + dy * dy + dz * dz;
+        if (!(d2 < reach * reach)) continue;
+        cells[n] = cell_index(c, ix, iy, iz);
+        offs[3 * n + 0] = dx; offs[3 * n + 1] = dy; offs[3 * n + 2] = dz;
+        ++n;
+      }
+  *cells_out = cells; *offs_out = offs; *count_out = n;
+  return 0;
+}
+
 int or_map(or_ctx* c) {
   const or_config* g = &c->cfg;
   int dims[3] = {g->nx, g->ny, g->nz};
   int per[3] = {!g->wall[0], !g->wall[2], !g->wall[4]};
-  int status = 0;
-  int* nreach = (int*)calloc((size_t)c->N, sizeof(int));
+  int np = c->np;
+  int status = 0, bad = 0;
   for (long i = 0; i < c->N; ++i) {
     c->pid0[i] = -1; c->pid1[i] = -1; c->B0[i] = 0.0; c->B1[i] = 0.0;
   }
-  /* pass 1: how many particles reach each cell (for the MLP fallback rule) */
-  for (int pass = 0; pass < 2; ++pass) {
-    for (int p = 0; p < c->np; ++p) {
-      double r = c->r[p];
-      int lo[3], hi[3];
-      for (int a = 0; a < 3; ++a) {
-        double xp = c->x[3 * p + a];
-        lo[a] = (int)floor(xp - r - 1.0);
-        hi[a] = (int)floor(xp + r + 1.0);
-        if (per[a] && hi[a] - lo[a] + 1 > dims[a]) { free(nreach); return -1; }
-        if (!per[a]) {
-          if (lo[a] < 0) lo[a] = 0;
-          if (hi[a] > dims[a] - 1) hi[a] = dims[a] - 1;
-        }
-      }
-      for (int kz = lo[2]; kz <= hi[2]; ++kz)
-        for (int ky = lo[1]; ky <= hi[1]; ++ky)
-          for (int kx = lo[0]; kx <= hi[0]; ++kx) {
-            int ix = ((kx % dims[0]) + dims[0]) % dims[0];
-            int iy = ((ky % dims[1]) + dims[1]) % dims[1];
-            int iz = ((kz % dims[2]) + dims[2]) % dims[2];
-            int ux = nearest_image(ix, c->x[3 * p + 0], dims[0], per[0]);
-            int uy = nearest_image(iy, c->x[3 * p + 1], dims[1], per[1]);
-            int uz = nearest_image(iz, c->x[3 * p + 2], dims[2], per[2]);
-            double dx = (ux + 0.5) - c->x[3 * p + 0];
-            double dy = (uy + 0.5) - c->x[3 * p + 1];
-            double dz = (uz + 0.5) - c->x[3 * p + 2];
-            double d2 = dx * dx + dy * dy + dz * dz;
-            double reach = r + HALF_SQRT3;
-            if (!(d2 < reach * reach)) continue;
-            long cell = cell_index(c, ix, iy, iz);
-            if (pass == 0) {
-              nreach[cell] += 1;
-              continue;
-            }
-            int next_to_wall = (g->wall[0] && (ix == 0 || ix == dims[0] - 1)) ||
-                               (g->wall[2] && (iy == 0 || iy == dims[1] - 1)) ||
-                               (g->wall[4] && (iz == 0 || iz == dims[2] - 1));
-            double eps = cell_eps(c, dx, dy, dz, r, nreach[cell] == 1, next_to_wall);
-            double B = (g->weighting == 1) ? or_nt_weight(eps, g->tau) : eps;
-            if (c->pid0[cell] < 0) {
-              c->pid0[cell] = p; c->B0[cell] = B;
-            } else if (c->pid1[cell] < 0) {
-              c->pid1[cell] = p; c->B1[cell] = B;
-            } else {
-              status = -2;
-            }
-          }
+  int* nreach = (int*)calloc((size_t)c->N, sizeof(int));
+  long** cells = (long**)calloc((size_t)(np > 0 ? np : 1), sizeof(long*));
+  double** offs = (double**)calloc((size_t)(np > 0 ? np : 1), sizeof(double*));
+  double** Bs = (double**)calloc((size_t)(np > 0 ? np : 1), sizeof(double*));
+  int* cnt = (int*)calloc((size_t)(np > 0 ? np : 1), sizeof(int));
+  /* pass 1: the cells each particle reaches, and how many particles reach
+   * each cell (for the MLP fallback rule; integer counts, so the order of
+   * the increments does not matter) */
+#pragma omp parallel for schedule(dynamic, 4) num_threads(c->threads) reduction(| : bad)
+  for (int p = 0; p < np; ++p) {
+    bad |= reach_list(c, p, dims, per, &cells[p], &offs[p], &cnt[p]) != 0;
+    for (int k = 0; k < cnt[p]; ++k) {
+#pragma omp atomic
+      nreach[cells[p][k]] += 1;
     }
   }
-  free(nreach);
-  return status;
+  if (!bad) {
+    /* pass 2: overlap fraction and weight of every (particle, cell) pair
+     * (Sec. 2.3.2; reading B) */
+#pragma omp parallel for schedule(dynamic, 4) num_threads(c->threads)
+    for (int p = 0; p < np; ++p) {
+      Bs[p] = (double*)malloc(sizeof(double) * (size_t)(cnt[p] > 0 ? cnt[p] : 1));
+      for (int k = 0; k < cnt[p]; ++k) {
+        long cell = cells[p][k];
+        int ix = (int)(cell % g->nx);
+        int iy = (int)((cell / g->nx) % g->ny);
+        int iz = (int)(cell / ((long)g->nx * g->ny));
+        int next_to_wall = (g->wall[0] && (ix == 0 || ix == dims[0] - 1)) ||
+                           (g->wall[2] && (iy == 0 || iy == dims[1] - 1)) ||
+                           (g->wall[4] && (iz == 0 || iz == dims[2] - 1));
+        const double* d = &offs[p][3 * k];
+        double eps = cell_eps(c, d[0], d[1], d[2], c->r[p], nreach[cell] == 1, next_to_wall);
+        Bs[p][k] = (g->weighting == 1) ? or_nt_weight(eps, g->tau) : eps;
+      }
+    }
+    /* slots filled in particle-index order (reading S) */
+    for (int p = 0; p < np; ++p)
+      for (int k = 0; k < cnt[p]; ++k) {
+        long cell = cells[p][k];
+        if (c->pid0[cell] < 0) {
+          c->pid0[cell] = p; c->B0[cell] = Bs[p][k];
+        } else if (c->pid1[cell] < 0) {
+          c->pid1[cell] = p; c->B1[cell] = Bs[p][k];
+        } else {
+          status = -2;
+        }
+      }
+  }
+  for (int p = 0; p < np; ++p) { free(cells[p]); free(offs[p]); free(Bs[p]); }
+  free(cells); free(offs); free(Bs); free(cnt); free(nreach);
+  return bad ? -1 : status;
 }
 
 void or_get_slots(const or_ctx* c, int* pid0, double* B0, int* pid1, double* B1) {
@@ -450,8 +511,25 @@ static void psm_collide_stream(or_ctx* c) {
   for (int a = 0; a < 3; ++a) c->fext_last[a] = fe[a];
   for (int p = 0; p < c->np; ++p)
     for (int a = 0; a < 3; ++a) { c->Fh[3 * p + a] = 0.0; c->Th[3 * p + a] = 0.0; }
+  /* a place for the force and torque contributions of every covered cell,
+   * numbered in cell order from the first covered cell of its z-plane */
+  long ncov = 0;
+  for (int z = 0; z < g->nz; ++z) {
+    c->plane_off[z] = ncov;
+    for (long i = (long)z * g->nx * g->ny; i < (long)(z + 1) * g->nx * g->ny; ++i)
+      if (c->pid0[i] >= 0) ++ncov;
+  }
+  c->plane_off[g->nz] = ncov;
+  if (ncov > c->contrib_cap) {
+    free(c->contrib);
+    c->contrib = (double*)malloc(sizeof(double) * 12 * (size_t)ncov);
+    c->contrib_cap = ncov;
+  }
 
-  for (int z = 0; z < g->nz; ++z)
+  /* the cells of one z-plane are visited in order by one thread */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(c->threads)
+  for (int z = 0; z < g->nz; ++z) {
+    long icov = c->plane_off[z];
     for (int y = 0; y < g->ny; ++y)
       for (int x = 0; x < g->nx; ++x) {
         long cell = cell_index(c, x, y, z);
@@ -520,10 +598,9 @@ static void psm_collide_stream(or_ctx* c) {
             if (pid[s] >= 0) sol += Bi[s] * Cs[s][q];
           c->fnew[q * c->N + cell] = f[q] + (1.0 - B) * Cf[q] + sol + (1.0 - B) * Fq[q];
         }
-        /* Eqs. 21-22 with dx = dt = 1 */
+        /* Eqs. 21-22 with dx = dt = 1: this cell's contribution per slot */
         for (int s = 0; s < 2; ++s) {
           if (pid[s] < 0) continue;
-          int p = pid[s];
           double S[3] = {0.0, 0.0, 0.0};
           for (int q = 0; q < Q; ++q) {
             int qb = opposite(q);
@@ -532,15 +609,32 @@ static void psm_collide_stream(or_ctx* c) {
             S[2] += Cs[s][q] * CZ[qb];
           }
           double* d = dvec[s];
-          double Fc[3] = {Bi[s] * S[0], Bi[s] * S[1], Bi[s] * S[2]};
-          c->Fh[3 * p + 0] += Fc[0];
-          c->Fh[3 * p + 1] += Fc[1];
-          c->Fh[3 * p + 2] += Fc[2];
-          c->Th[3 * p + 0] += d[1] * Fc[2] - d[2] * Fc[1];
-          c->Th[3 * p + 1] += d[2] * Fc[0] - d[0] * Fc[2];
-          c->Th[3 * p + 2] += d[0] * Fc[1] - d[1] * Fc[0];
+          double* o = &c->contrib[12 * icov + 6 * s];
+          o[0] = Bi[s] * S[0];
+          o[1] = Bi[s] * S[1];
+          o[2] = Bi[s] * S[2];
+          o[3] = d[1] * o[2] - d[2] * o[1];
+          o[4] = d[2] * o[0] - d[0] * o[2];
+          o[5] = d[0] * o[1] - d[1] * o[0];
         }
+        if (pid[0] >= 0) ++icov;
       }
+  }
+  /* per-particle sums in cell order (z, y, x), slot 0 before slot 1 */
+  long icov = 0;
+  for (long cell = 0; cell < c->N; ++cell) {
+    if (c->pid0[cell] < 0) continue;
+    int pid[2] = {c->pid0[cell], c->pid1[cell]};
+    for (int s = 0; s < 2; ++s) {
+      if (pid[s] < 0) continue;
+      const double* o = &c->contrib[12 * icov + 6 * s];
+      for (int a = 0; a < 3; ++a) {
+        c->Fh[3 * pid[s] + a] += o[a];
+        c->Th[3 * pid[s] + a] += o[3 + a];
+      }
+    }
+    ++icov;
+  }
   double* t = c->f;
   c->f = c->fnew;
   c->fnew = t;
@@ -563,6 +657,7 @@ static void dem_substeps(or_ctx* c) {
   double* Fc = (double*)malloc(sizeof(double) * 3 * np);
   for (int sc = 0; sc < g->subcycles; ++sc) {
     /* Eq. 15: position update with the old force */
+#pragma omp parallel for num_threads(c->threads)
     for (int i = 0; i < np; ++i) {
       if (c->fixed[i]) continue;
       for (int a = 0; a < 3; ++a) {
@@ -576,6 +671,7 @@ static void dem_substeps(or_ctx* c) {
       }
     }
     /* Eq. 12: normal spring-dashpot contacts, pairs in ascending j, then walls */
+#pragma omp parallel for schedule(dynamic, 16) num_threads(c->threads)
     for (int i = 0; i < np; ++i) {
       double F[3] = {0.0, 0.0, 0.0};
       for (int jj = 0; jj < np; ++jj) {
@@ -617,6 +713,7 @@ static void dem_substeps(or_ctx* c) {
       for (int a = 0; a < 3; ++a) Fc[3 * i + a] = F[a];
     }
     /* total force (Eq. 9 without lubrication) and Eq. 16 */
+#pragma omp parallel for num_threads(c->threads)
     for (int i = 0; i < np; ++i) {
       if (c->fixed[i]) continue;
       for (int a = 0; a < 3; ++a) {

@@ -74,6 +74,12 @@ void or_get_pdfs(const or_ctx* c, double* f);
 int or_map(or_ctx* c);
 /* Per-cell slots of the last mapping: pid = -1 for an empty slot. */
 void or_get_slots(const or_ctx* c, int* pid0, double* B0, int* pid1, double* B1);
+/* Host threads of the step's loops (default 1).  The mapping's overlap
+ * fractions, the cells of the collision and the particles of the DEM are
+ * split over the threads; every sum keeps the single-thread order (slots in
+ * particle-index order, forces in cell order), so the results do not depend
+ * on the thread count.  Without OpenMP the oracle runs on one thread. */
+void or_set_threads(or_ctx* c, int threads);
 /* n full time steps: mapping, PSM stream-collide, force/torque, DEM. */
 int or_step(or_ctx* c, int n);
 /* Only the DEM sub-cycles of n time steps, hydrodynamic force held fixed. */
