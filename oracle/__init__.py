@@ -48,7 +48,8 @@ class _Config(C.Structure):
                 ("magic", C.c_double), ("fbody", C.c_double * 3),
                 ("weighting", C.c_int), ("eps_mode", C.c_int), ("eps_n", C.c_int),
                 ("gravity", C.c_double * 3), ("kn", C.c_double),
-                ("restitution", C.c_double), ("subcycles", C.c_int), ("dem", C.c_int)]
+                ("restitution", C.c_double), ("subcycles", C.c_int), ("dem", C.c_int),
+                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double)]
 
 
 def lib():
@@ -114,7 +115,9 @@ class Oracle:
     """One oracle simulation (wraps ``or_ctx``).
 
     Arguments mirror the engine's configuration: grid ``(nx, ny, nz)``, ``walls``
-    as six 0/1 flags for faces -x,+x,-y,+y,-z,+z, relaxation time ``tau``,
+    as six face types for faces -x,+x,-y,+y,-z,+z (0 periodic, 1 wall, 2
+    velocity inflow at ``bc_velocity``, 3 pressure outflow at ``bc_density``;
+    2 and 3 on the z faces only), relaxation time ``tau``,
     ``relax`` ("srt"/"trt"), TRT ``magic``, fluid body force ``fbody``,
     ``weighting`` ("eps"/"nt"), ``eps_mode`` ("supersample"/"linear"/"mlp")
     with ``eps_n`` samples per axis, and the DEM parameters.
@@ -123,7 +126,8 @@ class Oracle:
     def __init__(self, nx, ny, nz, tau, relax="srt", magic=3.0 / 16.0,
                  walls=(0, 0, 0, 0, 0, 0), fbody=(0.0, 0.0, 0.0), weighting="eps",
                  eps_mode="supersample", eps_n=4, gravity=(0.0, 0.0, 0.0), kn=1e3,
-                 restitution=0.9, subcycles=10, dem=False):
+                 restitution=0.9, subcycles=10, dem=False, bc_velocity=(0.0, 0.0, 0.0),
+                 bc_density=1.0):
         L = lib()
         cfg = _Config()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
@@ -142,6 +146,9 @@ class Oracle:
         cfg.restitution = restitution
         cfg.subcycles = subcycles
         cfg.dem = int(bool(dem))
+        for i in range(3):
+            cfg.bc_velocity[i] = bc_velocity[i]
+        cfg.bc_density = bc_density
         self._L = L
         self.h = L.or_create(C.byref(cfg))
         if not self.h:

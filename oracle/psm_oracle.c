@@ -24,6 +24,18 @@
  *  G  n^3 sampling uses sub-cell centres (a+1/2)/n - 1/2, a = 0..n-1.
  *  H  Walls sit on the domain faces; all cells are fluid cells; halfway
  *     bounce-back f_q(x) = f~_qbar(x) for a link that leaves the domain.
+ *  V  Open faces of the fluidized bed (Sec. 4.1 names a velocity inflow at
+ *     the bottom and a pressure outflow at the top, without formulas), on the
+ *     z faces: an inflow face is a wall moving with the inflow velocity U_b,
+ *     f_q(x) = f~_qbar(x) + 6 w_q (c_q . U_b) (bounce-back of a moving wall,
+ *     rho_0 = 1), which lets exactly U_b,z cross each face cell per step; an
+ *     outflow face holds the density rho_b by anti-bounce-back,
+ *     f_q(x) = -f~_qbar(x) + 2 w_q (rho_b + 9/2 (c_q . u_b)^2 - 3/2 u_b . u_b),
+ *     with u_b = sum_p f~_p(x) c_p the cell's own velocity after the last
+ *     collision.  A link that also crosses a side wall is bounced back.  For
+ *     particles the open faces are walls (Sec. 4.1: planes keep the particles
+ *     in the box), and the counter force of reading J is not applied: the
+ *     fluid is not a closed periodic system.
  *  I  MLP mode: the network is used for a partial cell within reach of one
  *     particle and not next to a wall face; every other partial cell uses
  *     8^3 sampling.  The network predicts the correction to the linear
@@ -112,8 +124,12 @@ struct or_ctx {
 or_ctx* or_create(const or_config* cfg) {
   init_weights();
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return NULL;
+  for (int f = 0; f < 6; ++f) {
+    if (cfg->wall[f] < 0 || cfg->wall[f] > 3) return NULL;
+    if (cfg->wall[f] >= 2 && f < 4) return NULL; /* open faces on z only */
+  }
   for (int a = 0; a < 3; ++a)
-    if (cfg->wall[2 * a] != cfg->wall[2 * a + 1]) return NULL;
+    if ((cfg->wall[2 * a] != 0) != (cfg->wall[2 * a + 1] != 0)) return NULL;
   if (!(cfg->tau > 0.5)) return NULL;
   or_ctx* c = (or_ctx*)calloc(1, sizeof(or_ctx));
   c->cfg = *cfg;
@@ -469,16 +485,35 @@ static void cell_offset(const or_ctx* c, int p, int x, int y, int z, double d[3]
 }
 
 /* pull streaming of direction q into cell (x,y,z): Eq. 2 read backwards, with
- * periodic wrap and halfway bounce-back (reading H) */
+ * periodic wrap, halfway bounce-back (reading H) and the open faces of
+ * reading V */
 static double pull(const or_ctx* c, const double* src, int q, int x, int y, int z) {
   const or_config* g = &c->cfg;
   int sx = x - CX[q], sy = y - CY[q], sz = z - CZ[q];
-  int out = 0;
-  if (sx < 0 || sx >= g->nx) { if (g->wall[0]) out = 1; else sx = (sx + g->nx) % g->nx; }
-  if (sy < 0 || sy >= g->ny) { if (g->wall[2]) out = 1; else sy = (sy + g->ny) % g->ny; }
-  if (sz < 0 || sz >= g->nz) { if (g->wall[4]) out = 1; else sz = (sz + g->nz) % g->nz; }
-  if (out) return src[opposite(q) * c->N + cell_index(c, x, y, z)];
-  return src[q * c->N + cell_index(c, sx, sy, sz)];
+  int side = 0; /* face type the link leaves through: 1 wall, 2 inflow, 3 outflow */
+  if (sx < 0 || sx >= g->nx) { if (g->wall[0]) side = 1; else sx = (sx + g->nx) % g->nx; }
+  if (sy < 0 || sy >= g->ny) { if (g->wall[2]) side = 1; else sy = (sy + g->ny) % g->ny; }
+  if (sz < 0 || sz >= g->nz) {
+    int t = g->wall[sz < 0 ? 4 : 5];
+    if (!t) sz = (sz + g->nz) % g->nz;
+    else if (side != 1) side = t;
+  }
+  long cell = cell_index(c, x, y, z);
+  int qb = opposite(q);
+  if (side == 0) return src[q * c->N + cell_index(c, sx, sy, sz)];
+  if (side == 1) return src[qb * c->N + cell];
+  if (side == 2) {
+    const double* U = g->bc_velocity;
+    return src[qb * c->N + cell] + 6.0 * W[q] * (CX[q] * U[0] + CY[q] * U[1] + CZ[q] * U[2]);
+  }
+  double ub[3] = {0.0, 0.0, 0.0};
+  for (int p = 0; p < Q; ++p) {
+    double fp = src[p * c->N + cell];
+    ub[0] += fp * CX[p]; ub[1] += fp * CY[p]; ub[2] += fp * CZ[p];
+  }
+  double cu = CX[q] * ub[0] + CY[q] * ub[1] + CZ[q] * ub[2];
+  double uu = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+  return -src[qb * c->N + cell] + 2.0 * W[q] * (g->bc_density + 4.5 * cu * cu - 1.5 * uu);
 }
 
 static void fluid_force_density(or_ctx* c, double fe[3]) {
@@ -491,7 +526,9 @@ static void fluid_force_density(or_ctx* c, double fe[3]) {
     vfluid += 1.0 - B;
   }
   double G[3] = {0.0, 0.0, 0.0};
-  if (c->cfg.dem) {
+  int open = 0;
+  for (int f = 0; f < 6; ++f) open |= c->cfg.wall[f] >= 2;
+  if (c->cfg.dem && !open) {
     for (int p = 0; p < c->np; ++p) {
       if (c->fixed[p]) continue;
       for (int a = 0; a < 3; ++a) G[a] += (c->m[p] - c->vol[p]) * c->cfg.gravity[a];

@@ -38,9 +38,11 @@ extern "C" {
 
 typedef struct {
   int nx, ny, nz;
-  int wall[6];        /* faces -x,+x,-y,+y,-z,+z: 1 = stationary halfway
-                         bounce-back wall at that face, 0 = periodic.  Both
-                         faces of one axis must agree. */
+  int wall[6];        /* faces -x,+x,-y,+y,-z,+z: 0 = periodic, 1 =
+                         stationary halfway bounce-back wall, 2 = velocity
+                         inflow (bc_velocity), 3 = pressure outflow
+                         (bc_density); 2 and 3 on the z faces only.  Both
+                         faces of one axis are periodic or neither is. */
   double tau;         /* relaxation time (tau_plus for TRT) */
   int relax;          /* 0 = SRT (Eq. 3), 1 = TRT */
   double magic;       /* TRT magic parameter Lambda */
@@ -54,6 +56,8 @@ typedef struct {
   double restitution; /* normal coefficient of restitution */
   int subcycles;      /* DEM sub-steps per LBM step */
   int dem;            /* 1: integrate free particles; 0: particles never move */
+  double bc_velocity[3]; /* fluid velocity of an inflow face */
+  double bc_density;     /* fluid density of an outflow face */
 } or_config;
 
 typedef struct or_ctx or_ctx;
