@@ -234,6 +234,29 @@ def bed(case="dilute", nx=500, ny=200, nz=800, radius=10.0, seed=DEFAULT_SEED) -
     return w
 
 
+def slab(w: Workload, z0: int, nz: int) -> Workload:
+    """The cells z0 .. z0+nz-1 of a workload that is periodic in z, as a
+    periodic box of its own: the spheres whose centres lie at least r + 1/2
+    inside the slab's faces, shifted down by z0 (an integer, so every
+    cell-centre offset is the same number as in the full box).  Two spheres
+    next to opposite faces then keep the placement gap of 1 across the new
+    periodic wrap.  A bounded sample of a workload too large for a quick CPU
+    run."""
+    assert not w.walls[4] and 0 <= z0 and z0 + nz <= w.nz
+    x, r = w.particles["x"], w.particles["r"]
+    zr = x[:, 2] - z0
+    keep = (zr >= r + 0.5) & (zr <= nz - r - 0.5)
+    out = Workload(f"{w.name}_slab{nz}", w.nx, w.ny, nz, tau=w.tau, relax=w.relax,
+                   walls=w.walls, fbody=w.fbody, gravity=w.gravity, weighting=w.weighting,
+                   eps_mode=w.eps_mode, eps_n=w.eps_n, kn=w.kn, restitution=w.restitution,
+                   subcycles=w.subcycles, dem=w.dem, density=w.density, steps=w.steps)
+    xs = x[keep].copy()
+    xs[:, 2] -= z0
+    out.particles = {k: (xs if k == "x" else np.asarray(v)[keep].copy())
+                     for k, v in w.particles.items()}
+    return out
+
+
 def noise(shape, scale, seed):
     """Uniform noise in [-scale, scale) of the given shape."""
     rng = np.random.default_rng(seed)
