@@ -57,10 +57,11 @@ WORKLOADS = {
                 "(Lambda=3/16) tau=0.55, body force 1e-5 along z, 4^3 sub-division sampling, "
                 "Noble-Torczynski B"),
     "bed_dilute": ("bed_dilute: stand-in for the paper's dilute fluidized bed, 500x200x800 cells, "
-                   "no-slip walls on the four side faces, periodic vertical axis (the counter "
-                   "force of the buoyant weight drives the flow up through the bed), 627 spheres "
-                   "r=10 (random sequential addition), density ratio 1.1, gravity 2.75e-5, D3Q19 "
-                   "SRT tau=0.55, linear approximation (Eqs. 25-27), B = eps, DEM x10 sub-cycles"),
+                   "no-slip walls on the four side faces, velocity inflow at the bottom (8.33e-4, "
+                   "particle Reynolds number 1) and pressure outflow (density 1) at the top, 627 "
+                   "spheres r=10 (random sequential addition), density ratio 1.1, gravity "
+                   "2.75e-5, D3Q19 SRT tau=0.55, linear approximation (Eqs. 25-27), B = eps, DEM "
+                   "x10 sub-cycles"),
     "bed_dense": ("bed_dense: stand-in for the paper's dense fluidized bed, as bed_dilute with "
                   "8,073 spheres r=10 in hexagonal close-packed layers from the bottom (solid "
                   "fraction 0.42 over the box)"),
@@ -221,7 +222,7 @@ def make_engine(w, capi, precision="fp64", streaming="pull", eps_mode=None):
                     weighting=w.weighting, eps_mode=eps_mode or w.eps_mode, eps_n=w.eps_n,
                     gravity=w.gravity, kn=w.kn, restitution=w.restitution,
                     subcycles=w.subcycles, dem=w.dem, precision=precision,
-                    streaming=streaming)
+                    streaming=streaming, bc_velocity=w.bc_velocity, bc_density=w.bc_density)
     p = w.particles
     e.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])
     return e
@@ -269,7 +270,8 @@ def oracle_rate(w, seconds, max_steps, threads, warmup=0):
     from oracle import Oracle
     o = Oracle(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=w.walls, fbody=w.fbody,
                weighting=w.weighting, eps_mode=w.eps_mode, eps_n=w.eps_n, gravity=w.gravity,
-               kn=w.kn, restitution=w.restitution, subcycles=w.subcycles, dem=w.dem)
+               kn=w.kn, restitution=w.restitution, subcycles=w.subcycles, dem=w.dem,
+               bc_velocity=w.bc_velocity, bc_density=w.bc_density)
     o.set_threads(threads)
     p = w.particles
     o.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])

@@ -62,10 +62,22 @@ typedef enum {
   PSM_ERR_STATE = 7          /* call not allowed in the current state */
 } psm_status;
 
-/* Domain: nx, ny, nz cells.  wall[f] = 1 puts a stationary halfway
- * bounce-back wall on face f (order -x,+x,-y,+y,-z,+z; the walls sit on the
- * domain faces, all cells are fluid cells); 0 makes that axis periodic.  Both
- * faces of an axis must agree. */
+/* Domain: nx, ny, nz cells.  wall[f] sets the type of face f (order
+ * -x,+x,-y,+y,-z,+z; boundaries sit on the domain faces, all cells are fluid
+ * cells): PSM_FACE_PERIODIC, PSM_FACE_WALL (stationary halfway bounce-back),
+ * and on the z faces only the open faces of the fluidized bed (Sec. 4.1: a
+ * velocity inflow at the bottom, a pressure outflow at the top):
+ * PSM_FACE_INFLOW, bounce-back of a wall moving with
+ * psm_options.bc_velocity, f_q = f~_qbar + 6 w_q c_q.U_b, which lets exactly
+ * U_b,z of mass through each face cell per step; PSM_FACE_OUTFLOW,
+ * anti-bounce-back to psm_options.bc_density,
+ * f_q = -f~_qbar + 2 w_q (rho_b + 9/2 (c_q.u_b)^2 - 3/2 u_b.u_b), u_b the
+ * cell's own velocity after the last collision.  A link that also crosses a
+ * side wall is bounced back.  Both faces of an axis are periodic or neither
+ * is.  Particles see every non-periodic face as a wall plane; with an open
+ * face the fluid gets no counter force for the particles' weight.  Open faces
+ * need pull streaming (PSM_AA gives PSM_ERR_ARG). */
+enum { PSM_FACE_PERIODIC = 0, PSM_FACE_WALL = 1, PSM_FACE_INFLOW = 2, PSM_FACE_OUTFLOW = 3 };
 typedef struct {
   int nx, ny, nz;
   int wall[6];
@@ -117,6 +129,8 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL */
   void (*free)(void* ptr, void* user);      /* matching release or NULL */
   void* alloc_user;                         /* passed to alloc/free */
+  double bc_velocity[3]; /* fluid velocity of a PSM_FACE_INFLOW face */
+  double bc_density;     /* fluid density of a PSM_FACE_OUTFLOW face (default 1) */
 } psm_options;
 
 /* Fills *o with the defaults: Lambda = 3/16, FP64, pull, 4^3 sampling, NT

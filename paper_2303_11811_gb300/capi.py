@@ -55,7 +55,8 @@ class PsmOptions(C.Structure):
                 ("k_n", C.c_double), ("restitution", C.c_double),
                 ("dem_subcycles", C.c_int), ("dem", C.c_int), ("deterministic", C.c_int),
                 ("use_graphs", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_user", C.c_void_p)]
+                ("free", FREE_FN), ("alloc_user", C.c_void_p),
+                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double)]
 
 
 _lib = None
@@ -205,7 +206,9 @@ class TorchAllocator:
 
 class Engine:
     """One engine context.  Arguments mirror the oracle's configuration:
-    grid (nx, ny, nz), ``walls`` six 0/1 flags (-x,+x,-y,+y,-z,+z), ``tau``,
+    grid (nx, ny, nz), ``walls`` six face types (-x,+x,-y,+y,-z,+z: 0 periodic,
+    1 wall, 2 velocity inflow at ``bc_velocity`` and 3 pressure outflow at
+    ``bc_density``, the last two on the z faces only), ``tau``,
     ``relax`` "srt"/"trt", ``magic``, ``fbody``, ``weighting`` "eps"/"nt",
     ``eps_mode`` "supersample"/"linear"/"mlp", ``eps_n``, DEM parameters,
     ``precision`` "fp64"/"fp32"/"df64" (FP64, FP32 deviations, double-float
@@ -216,7 +219,7 @@ class Engine:
                  eps_mode="supersample", eps_n=4, gravity=(0.0, 0.0, 0.0), kn=1e3,
                  restitution=0.9, subcycles=10, dem=False, precision="fp64",
                  streaming="pull", deterministic=True, use_graphs=True, torch_alloc=True,
-                 stream=None):
+                 stream=None, bc_velocity=(0.0, 0.0, 0.0), bc_density=1.0):
         L = lib()
         self._L = L
         opt = PsmOptions()
@@ -236,6 +239,9 @@ class Engine:
         opt.dem = int(bool(dem))
         opt.deterministic = int(bool(deterministic))
         opt.use_graphs = int(bool(use_graphs))
+        for i in range(3):
+            opt.bc_velocity[i] = bc_velocity[i]
+        opt.bc_density = bc_density
         self._alloc = None
         if torch_alloc:
             import torch

@@ -442,6 +442,58 @@ __device__ __forceinline__ void psm_collide(const LbmParams& P, unsigned word, i
   }
 }
 
+// ---- open z faces (the velocity inflow and pressure outflow of the
+// fluidized bed, Sec. 4.1): type of the open face a pulled link with source
+// offset (ox, oy, oz) leaves through, or 0 (a link that also leaves through a
+// side wall is bounced back)
+template <int WALLS>
+__device__ __forceinline__ int open_face(const Grid& g, const NbrT<WALLS>& nb, int ox, int oy,
+                                         int oz) {
+  if constexpr (!(WALLS & 4)) {
+    return 0;
+  } else {
+    if (oz == 0 || nb.ok(0, 0, oz) || !nb.ok(ox, 0, 0) || !nb.ok(0, oy, 0)) return 0;
+    const int t = g.zface[oz < 0 ? 0 : 1];
+    return t >= FACE_INFLOW ? t : 0;
+  }
+}
+
+// deviation of direction q pulled across an open face, from the bounced-back
+// deviation bb: an inflow adds 6 w_q c_q.U_b (bounce-back of a moving wall);
+// an outflow reverses it and adds 2 w_q (rho_b - 1 + 9/2 (c_q.u_b)^2 -
+// 3/2 u_b.u_b) (anti-bounce-back), u_b the cell's own velocity after the last
+// collision
+template <typename T>
+__device__ __forceinline__ T open_value(const OpenBC& bc, int type, int q, T bb, const T* ub) {
+  if (type == FACE_INFLOW) return bb + from_double<T>(bc.in[q]);
+  const int k = (q - 1) >> 1;
+  const T cu = cdot<T>(k, ub[0], ub[1], ub[2]);
+  const T uu = (ub[0] * ub[0] + ub[1] * ub[1]) + ub[2] * ub[2];
+  const T e = (from_double<T>(bc.rho1) + from_double<T>(4.5) * (cu * cu)) -
+              from_double<T>(1.5) * uu;
+  return from_double<T>(2.0 * wq(q)) * e - bb;
+}
+
+// the cell's own velocity after the last collision, sum_q delta~_q c_q, from
+// the source buffer of pull streaming
+template <typename T>
+__device__ __forceinline__ void own_velocity(const LbmParams& P, int cell, T* ub) {
+  T a[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    a[k] = ld(static_cast<const T*>(P.srcq[2 * k + 1]) + cell) -
+           ld(static_cast<const T*>(P.srcq[2 * k + 2]) + cell);
+  ub[0] = ((a[0] + a[3]) + (a[4] + a[5])) + a[6];
+  ub[1] = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
+  ub[2] = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
+}
+
+// whether the layer z of a pull step needs its cells' own velocity (an
+// outflow face on its side)
+__device__ __forceinline__ bool outflow_layer(const Grid& g, int z) {
+  return (z == 0 && g.zface[0] == FACE_OUTFLOW) || (z == g.nz - 1 && g.zface[1] == FACE_OUTFLOW);
+}
+
 // store of the collided PDFs (pull: own cell of the other buffer; AA even:
 // swapped slots of the own cell; AA odd: the neighbours' slots, or the own
 // cell's opposite slot across a wall)
@@ -538,7 +590,12 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
   // the same array: every thread reads its whole set of locations before it
   // writes the same set.
 #define SRC(q) static_cast<const T*>(P.srcq[q])
-  // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls)
+  // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls, the
+  // open faces' values across open z faces)
+  T ub[3] = {T(0), T(0), T(0)};
+  if constexpr (MODE == 0 && (WALLS & 4) != 0) {
+    if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
+  }
   T d[Q];
   d[0] = ld(SRC(0) + cell);
 #pragma unroll
@@ -546,8 +603,20 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
     const int cx = ckx(k), cy = cky(k), cz = ckz(k);
     const int qa = 2 * k + 1, qb = 2 * k + 2;
     if (MODE == 0) {         // pull from the other buffer
-      d[qa] = nb.ok(-cx, -cy, -cz) ? ld(SRC(qa) + nb.idx(-cx, -cy, -cz)) : ld(SRC(qb) + cell);
-      d[qb] = nb.ok(cx, cy, cz) ? ld(SRC(qb) + nb.idx(cx, cy, cz)) : ld(SRC(qa) + cell);
+      if (nb.ok(-cx, -cy, -cz)) {
+        d[qa] = ld(SRC(qa) + nb.idx(-cx, -cy, -cz));
+      } else {
+        const T bb = ld(SRC(qb) + cell);
+        const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
+        d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
+      }
+      if (nb.ok(cx, cy, cz)) {
+        d[qb] = ld(SRC(qb) + nb.idx(cx, cy, cz));
+      } else {
+        const T bb = ld(SRC(qa) + cell);
+        const int t = open_face<WALLS>(g, nb, cx, cy, cz);
+        d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
+      }
     } else if (MODE == 1) {  // AA even: own cell
       d[qa] = ld(SRC(qa) + cell);
       d[qb] = ld(SRC(qb) + cell);
@@ -775,6 +844,10 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
       const int cell = nb.idx(0, 0, 0);
       const int xm = x == 0 ? g.nx - 1 : x - 1, xq = x == g.nx - 1 ? 0 : x + 1;
       const T* sr = st + (size_t)r * nxp;  // direction q of this row at sr[q * C]
+      T ub[3] = {T(0), T(0), T(0)};
+      if constexpr (MODE == 0 && (WALLS & 4) != 0) {
+        if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
+      }
       T d[Q];
       d[0] = sr[x];
 #pragma unroll
@@ -784,8 +857,20 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
         const int xa = cx > 0 ? xm : (cx < 0 ? xq : x);  // x - c_x
         const int xb = cx > 0 ? xq : (cx < 0 ? xm : x);  // x + c_x
         if (MODE == 0) {
-          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qb) + cell);
-          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qa) + cell);
+          if (nb.ok(-cx, -cy, -cz)) {
+            d[qa] = sr[qa * C + xa];
+          } else {
+            const T bb = ld(SRC(qb) + cell);
+            const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
+            d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
+          }
+          if (nb.ok(cx, cy, cz)) {
+            d[qb] = sr[qb * C + xb];
+          } else {
+            const T bb = ld(SRC(qa) + cell);
+            const int t = open_face<WALLS>(g, nb, cx, cy, cz);
+            d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
+          }
         } else if (MODE == 1) {
           d[qa] = sr[qa * C + x];
           d[qb] = sr[qb * C + x];
@@ -873,7 +958,7 @@ __global__ void from_canonical_kernel(Grid g, const double* __restrict__ in, int
 
 // rho and U of the streamed canonical field (Eqs. 6-7)
 __global__ void macroscopic_kernel(Grid g, const double* __restrict__ f, const StepConst* sc,
-                                   double* __restrict__ rho, double* __restrict__ u) {
+                                   OpenBC bc, double* __restrict__ rho, double* __restrict__ u) {
   const long long N = (long long)g.nx * g.ny * g.nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
        c += (long long)gridDim.x * blockDim.x) {
@@ -882,12 +967,28 @@ __global__ void macroscopic_kernel(Grid g, const double* __restrict__ f, const S
     const int z = (int)(c / ((long long)g.nx * g.ny));
     Nbr nc;
     nc.init(x, y, z, g.nx, g.ny, g.nz, g.nx, g.wall);
+    // the open faces' values, in deviations from the lattice weights
+    double ub[3] = {0.0, 0.0, 0.0};
+    if (outflow_layer(g, z)) {
+      for (int k = 0; k < 9; ++k) {
+        const double ak = f[(2 * k + 1) * N + c] - f[(2 * k + 2) * N + c];
+        ub[0] += ak * ckx(k);
+        ub[1] += ak * cky(k);
+        ub[2] += ak * ckz(k);
+      }
+    }
+    auto pulled = [&](int q, int qr, int ox, int oy, int oz) {
+      if (nc.ok(ox, oy, oz)) return f[q * N + nc.idx(ox, oy, oz)];
+      const double bb = f[qr * N + c];
+      const int t = open_face<7>(g, nc, ox, oy, oz);
+      return t ? wq(q) + open_value<double>(bc, t, q, bb - wq(qr), ub) : bb;
+    };
     double r = f[c], jx = 0.0, jy = 0.0, jz = 0.0;
     for (int k = 0; k < 9; ++k) {
       const int cx = ckx(k), cy = cky(k), cz = ckz(k);
       const int qa = 2 * k + 1, qb = 2 * k + 2;
-      const double va = nc.ok(-cx, -cy, -cz) ? f[qa * N + nc.idx(-cx, -cy, -cz)] : f[qb * N + c];
-      const double vb = nc.ok(cx, cy, cz) ? f[qb * N + nc.idx(cx, cy, cz)] : f[qa * N + c];
+      const double va = pulled(qa, qb, -cx, -cy, -cz);
+      const double vb = pulled(qb, qa, cx, cy, cz);
       r += va + vb;
       jx += (va - vb) * cx;
       jy += (va - vb) * cy;
@@ -1145,10 +1246,10 @@ int launch_from_canonical(const Grid& g, const double* in, void* buf, int prec, 
   return 1;
 }
 
-int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,
-                       double* u, cudaStream_t s) {
+int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, const OpenBC& bc,
+                       double* rho, double* u, cudaStream_t s) {
   const long long N = (long long)g.nx * g.ny * g.nz;
-  macroscopic_kernel<<<grid_for(N, 256), 256, 0, s>>>(g, f, sc, rho, u);
+  macroscopic_kernel<<<grid_for(N, 256), 256, 0, s>>>(g, f, sc, bc, rho, u);
   return 1;
 }
 

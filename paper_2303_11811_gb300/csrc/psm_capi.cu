@@ -35,6 +35,8 @@ constexpr int kDemListCap = 64;
 struct psm_ctx {
   psm_options opt{};
   Grid g{};
+  OpenBC bc{};         // constants of the open z faces
+  bool open = false;   // an inflow or outflow face exists
   double tau = 0.6, omega_p = 0, omega_m = 0;
   int relax = 0, fp32 = 0, aa = 0;
   int prec = PREC_FP64;  // PDF storage and collision arithmetic (PREC_*)
@@ -187,7 +189,8 @@ MapParams map_params(psm_ctx* c) {
   P.status = c->status;
   P.sc = c->sc;
   for (int a = 0; a < 3; ++a) {
-    P.G[a] = c->G[a];
+    // no counter force for the particles' weight when the fluid has open faces
+    P.G[a] = c->open ? 0.0 : c->G[a];
     P.fbody[a] = c->opt.body_force[a];
   }
   P.omega_p = c->omega_p;
@@ -253,6 +256,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s, bool dem = true) {
   L.sc = c->sc;
   L.omega_p = c->omega_p;
   L.omega_m = c->omega_m;
+  L.bc = c->bc;
   L.status = c->status;
   L.tile_rows = c->plan.tile_rows;
   L.ntiles = c->plan.ntiles;
@@ -385,6 +389,13 @@ enum {
   CK_NX, CK_NY, CK_NZ, CK_WX, CK_WY, CK_WZ, CK_PREC, CK_AA, CK_RELAX, CK_PARITY, CK_N,
   CK_MLP, CK_DEM, CK_FIELDS
 };
+// the z faces in the header: 0 periodic, 1 walls, and with an open face
+// 1 + 4 * type(-z) + 16 * type(+z)
+long long z_code(const Grid& g) {
+  if (!g.wall[2]) return 0;
+  if (g.zface[0] < FACE_INFLOW && g.zface[1] < FACE_INFLOW) return 1;
+  return 1 + 4LL * g.zface[0] + 16LL * g.zface[1];
+}
 struct CkptHeader {
   char magic[8];
   long long v[CK_FIELDS];
@@ -436,8 +447,23 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   *out = nullptr;
   if (!grid || !opt) return PSM_ERR_ARG;
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return PSM_ERR_ARG;
+  static_assert(FACE_INFLOW == PSM_FACE_INFLOW && FACE_OUTFLOW == PSM_FACE_OUTFLOW &&
+                    FACE_WALL == PSM_FACE_WALL && FACE_PERIODIC == PSM_FACE_PERIODIC,
+                "face types");
+  bool open = false;
+  for (int f = 0; f < 6; ++f) {
+    if (grid->wall[f] < PSM_FACE_PERIODIC || grid->wall[f] > PSM_FACE_OUTFLOW) return PSM_ERR_ARG;
+    if (grid->wall[f] >= PSM_FACE_INFLOW) {
+      if (f < 4) return PSM_ERR_ARG;  // open faces on the z faces only
+      open = true;
+    }
+  }
   for (int a = 0; a < 3; ++a)
-    if (grid->wall[2 * a] != grid->wall[2 * a + 1]) return PSM_ERR_ARG;
+    if ((grid->wall[2 * a] != 0) != (grid->wall[2 * a + 1] != 0)) return PSM_ERR_ARG;
+  if (open && opt->streaming != PSM_PULL) return PSM_ERR_ARG;
+  if (open && !(opt->bc_density > 0.0 && std::isfinite(opt->bc_density))) return PSM_ERR_ARG;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(opt->bc_velocity[a])) return PSM_ERR_ARG;
   if (!(tau > 0.5) || !std::isfinite(tau)) return PSM_ERR_ARG;
   if (relax != PSM_SRT && relax != PSM_TRT) return PSM_ERR_ARG;
   if (opt->precision != PSM_FP64 && opt->precision != PSM_FP32_DEV &&
@@ -476,6 +502,22 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   g.nz = grid->nz;
   g.nxp = (int)nxp;
   for (int a = 0; a < 3; ++a) g.wall[a] = grid->wall[2 * a] ? 1 : 0;
+  g.zface[0] = grid->wall[4];
+  g.zface[1] = grid->wall[5];
+  c->open = open;
+  {
+    // open faces: 6 w_q c_q.U_b per direction (inflow), rho_b - 1 (outflow)
+    static const int cq[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                  {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                                  {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                                  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    for (int q = 0; q < Q; ++q) {
+      const double w = q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+      const double* U = opt->bc_velocity;
+      c->bc.in[q] = 6.0 * w * (cq[q][0] * U[0] + cq[q][1] * U[1] + cq[q][2] * U[2]);
+    }
+    c->bc.rho1 = opt->bc_density - 1.0;
+  }
   g.wpr = (int)(nxp / 32);
   g.ncell = ncell;
   g.nwords = ncell / 32;
@@ -1003,7 +1045,7 @@ psm_status psm_get_macroscopic(psm_ctx* c, double* rho, double* u) {
     dfree(c, f);
     return fail(c, PSM_ERR_OOM, "allocator returned NULL");
   }
-  launch_macroscopic(c->g, f, c->sc, ru, ru + N, c->stream);
+  launch_macroscopic(c->g, f, c->sc, c->bc, ru, ru + N, c->stream);
   cudaError_t e = cudaMemcpyAsync(rho, ru, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(u, ru + N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, c->stream);
@@ -1253,7 +1295,7 @@ psm_status psm_save(psm_ctx* c, const char* path) {
   CkptHeader h{};
   std::memcpy(h.magic, kCkptMagic, 8);
   const long long v[CK_FIELDS] = {c->g.nx, c->g.ny, c->g.nz, c->g.wall[0], c->g.wall[1],
-                                  c->g.wall[2], c->prec, c->aa, c->relax,
+                                  z_code(c->g), c->prec, c->aa, c->relax,
                                   c->aa ? c->parity : 0, n, c->have_mlp ? 1 : 0,
                                   c->opt.dem ? 1 : 0};
   std::memcpy(h.v, v, sizeof(v));
@@ -1305,7 +1347,7 @@ psm_status psm_load(psm_ctx* c, const char* path) {
   if (!read_all(f, &h, sizeof(h)) || std::memcmp(h.magic, kCkptMagic, 8) != 0)
     return bad("not a checkpoint of this engine");
   const long long want[CK_N] = {c->g.nx, c->g.ny, c->g.nz, c->g.wall[0], c->g.wall[1],
-                                c->g.wall[2], c->prec, c->aa, c->relax};
+                                z_code(c->g), c->prec, c->aa, c->relax};
   for (int i = 0; i < CK_PARITY; ++i)
     if (h.v[i] != want[i]) return bad("checkpoint of another grid, storage form or relaxation");
   if (h.tau != c->tau || h.omega_m != c->omega_m || (h.v[CK_DEM] != 0) != (c->opt.dem != 0))

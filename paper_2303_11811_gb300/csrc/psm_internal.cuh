@@ -62,9 +62,20 @@ __host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
   return f;
 }
 
+// face types (the values of PSM_FACE_* in include/psm.h)
+enum { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_INFLOW = 2, FACE_OUTFLOW = 3 };
+
+// constants of the open z faces: per direction 6 w_q c_q.U_b of a velocity
+// inflow, and rho_b - 1 of a pressure outflow
+struct OpenBC {
+  double in[19];
+  double rho1;
+};
+
 struct Grid {
   int nx, ny, nz, nxp;
-  int wall[3];          // 1 = walls on both faces of that axis
+  int wall[3];          // 1 = both faces of that axis are not periodic
+  int zface[2];         // face types of -z and +z (PSM_FACE_*; open faces on z only)
   int wpr;              // warps (coverage words) per x-row = nxp / 32
   long long ncell;      // nxp * ny * nz (< 2^31)
   long long nwords;     // ncell / 32
@@ -196,6 +207,7 @@ struct LbmParams {
   long long slot_cap;   // entries allocated
   const StepConst* sc;
   double omega_p, omega_m;
+  OpenBC bc;            // open z faces
   unsigned* status;     // device status word (ST_* bits)
   // staged kernel (stages > 0): tiles of tile_rows x-rows, `stages` tiles in
   // flight per block, `blocks` persistent blocks with `smem` bytes each
@@ -226,7 +238,8 @@ int launch_to_canonical(const Grid& g, const void* buf, int prec, int aa_parity,
                         const BoxSel& B, double* out, cudaStream_t s);
 int launch_from_canonical(const Grid& g, const double* in, void* buf, int prec, int aa,
                           cudaStream_t s);
-int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, double* rho,
+int launch_macroscopic(const Grid& g, const double* f, const StepConst* sc, const OpenBC& bc,
+                       double* rho,
                        double* u, cudaStream_t s);
 int launch_sums(const Grid& g, const double* f, double* partials, int nparts, double* out4,
                 cudaStream_t s);

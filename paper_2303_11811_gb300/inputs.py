@@ -49,6 +49,8 @@ class Workload:
     dem: bool = False
     density: float = 2.5
     steps: int = 1000
+    bc_velocity: tuple = (0.0, 0.0, 0.0)  # fluid velocity of an inflow face
+    bc_density: float = 1.0               # fluid density of an outflow face
     particles: dict = field(default_factory=dict)
 
     @property
@@ -188,16 +190,20 @@ def bed(case="dilute", nx=500, ny=200, nz=800, radius=10.0, seed=DEFAULT_SEED) -
     cells, no-slip walls on the four side faces, spheres of radius 10 (20
     cells per diameter), particle/fluid density ratio 1.1, ten DEM
     sub-cycles, SRT, the linear approximation of Eqs. 25-27 with B = eps.
-    The paper's velocity inflow (bottom) and pressure outflow (top) are
-    replaced by a periodic vertical axis: the counter force of the
-    buoyancy-corrected gravity pushes the fluid up through the bed with the
-    bed's buoyant weight.  Gravity 2.75e-5 (Galileo number about 8.9 at
-    tau = 0.55, d = 20).  ``dilute``: 627 spheres by random sequential
-    addition over the whole box; ``dense``: 8,073 spheres in hexagonal
-    close-packed layers from the bottom (surface gap 1), a packed bed."""
-    w = Workload(f"bed_{case}", nx, ny, nz, tau=0.55, relax="srt", walls=(1, 1, 1, 1, 0, 0),
+    A velocity inflow at the bottom face and a pressure outflow (density 1)
+    at the top, as in the paper; the inflow velocity 8.33e-4 gives the
+    paper's particle Reynolds number 1.0 (U d / nu, nu = (tau - 1/2)/3 at
+    tau = 0.55, d = 20).  Gravity 2.75e-5 (Galileo number about 8.9).  The
+    faces are walls for the particles.  ``dilute``: 627 spheres by random
+    sequential addition over the whole box; ``dense``: 8,073 spheres in
+    hexagonal close-packed layers from the bottom (surface gap 1), a packed
+    bed."""
+    tau, d = 0.55, 2.0 * radius
+    u_in = ((tau - 0.5) / 3.0) / d  # particle Reynolds number 1
+    w = Workload(f"bed_{case}", nx, ny, nz, tau=tau, relax="srt", walls=(1, 1, 1, 1, 2, 3),
                  gravity=(0.0, 0.0, -2.75e-5), weighting="eps", eps_mode="linear", eps_n=4,
-                 dem=True, density=1.1, steps=500)
+                 dem=True, density=1.1, steps=500, bc_velocity=(0.0, 0.0, u_in),
+                 bc_density=1.0)
     if case == "dilute":
         count = 627
         r = np.full(count, radius)

@@ -2,7 +2,8 @@
 (shared by the full-size GPU tests and the CPU test of the method).
 
 For a cell c the oracle runs one step on a box around c (16 cells along a
-periodic axis, the whole extent along an axis with walls), filled with the
+periodic axis or along z with open faces, the whole extent along an axis
+with walls), filled with the
 post-collision PDFs of that box and holding the spheres within reach of c,
 shifted by an integer so that every cell-centre offset is the same FP64
 number as in the full field.  Its body force is the full field's fluid force
@@ -11,6 +12,7 @@ the same inputs.  The box wraps periodically at its own faces, which changes
 cells next to those faces only; c sits 8 cells from them.
 """
 import math
+import os
 
 import numpy as np
 
@@ -41,12 +43,40 @@ def sample_cells(w, count, seed):
     return cells
 
 
+def _open_z(w):
+    return max(w.walls[4], w.walls[5]) >= 2 and w.nz > BOX
+
+
 def box(w, c):
+    """Origin and extent of the box around cell c: 16 cells along a periodic
+    axis; along the z axis with open faces 16 cells clamped to the domain
+    (c at least 7 cells from an end of the box that is not a domain face);
+    the whole extent along any other axis with walls."""
     dims = (w.nx, w.ny, w.nz)
     walls = (w.walls[0], w.walls[2], w.walls[4])
-    o = tuple(0 if walls[a] else c[a] - BOX // 2 for a in range(3))
-    ext = tuple(dims[a] if walls[a] else BOX for a in range(3))
-    return o, ext
+    o, ext = [], []
+    for a in range(3):
+        if not walls[a]:
+            o.append(c[a] - BOX // 2)
+            ext.append(BOX)
+        elif a == 2 and _open_z(w):
+            o.append(min(max(c[2] - BOX // 2, 0), dims[2] - BOX))
+            ext.append(BOX)
+        else:
+            o.append(0)
+            ext.append(dims[a])
+    return tuple(o), tuple(ext)
+
+
+def box_faces(w, o):
+    """Face types of the box: the domain's, with a wall where the box ends
+    inside the domain along z (c is far enough from it for one step)."""
+    if not _open_z(w):
+        return tuple(int(w.walls[2 * a]) for a in range(3) for _ in range(2))
+    zlo = w.walls[4] if o[2] == 0 else 1
+    zhi = w.walls[5] if o[2] + BOX == w.nz else 1
+    return (int(w.walls[0]), int(w.walls[1]), int(w.walls[2]), int(w.walls[3]), int(zlo),
+            int(zhi))
 
 
 def oracle_cell(w, c, pre, fext, X, R, U, OM, dens):
@@ -64,10 +94,11 @@ def oracle_cell(w, c, pre, fext, X, R, U, OM, dens):
     for a in range(3):
         if not walls[a]:
             xs[:, a] -= dims[a] * np.round((xs[:, a] - BOX / 2) / dims[a])
-    box_walls = tuple(int(walls[a]) for a in range(3) for _ in range(2))
-    orc = Oracle(ext[0], ext[1], ext[2], w.tau, relax=w.relax, walls=box_walls,
+    orc = Oracle(ext[0], ext[1], ext[2], w.tau, relax=w.relax, walls=box_faces(w, o),
                  fbody=tuple(float(v) for v in fext), weighting=w.weighting,
-                 eps_mode=w.eps_mode, eps_n=w.eps_n)
+                 eps_mode=w.eps_mode, eps_n=w.eps_n, bc_velocity=w.bc_velocity,
+                 bc_density=w.bc_density)
+    orc.set_threads(os.cpu_count() or 1)  # results do not depend on the thread count
     orc.set_pdfs(pre.ravel())
     if sel.size:
         orc.set_particles(xs, R[sel], u=U[sel], omega=OM[sel], density=dens[sel],

@@ -34,7 +34,8 @@ def _engine(capi, w, precision, streaming):
     e = capi.Engine(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=w.walls, fbody=w.fbody,
                     weighting=w.weighting, eps_mode=w.eps_mode, eps_n=w.eps_n,
                     gravity=w.gravity, kn=w.kn, restitution=w.restitution,
-                    subcycles=w.subcycles, dem=w.dem, precision=precision, streaming=streaming)
+                    subcycles=w.subcycles, dem=w.dem, precision=precision, streaming=streaming,
+                    bc_velocity=w.bc_velocity, bc_density=w.bc_density)
     p = w.particles
     e.set_particles(p["x"], p["r"], density=p["density"], fixed=p["fixed"])
     return e
@@ -116,5 +117,25 @@ def test_settle512_full_size_sampled(capi, precision, streaming):
     _sampled_step(e, w, sample_cells(w, 16, 12), precision)
     if precision != "fp32":
         _budgets(e, 1, periodic=True)
+    e.close()
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("case,precision", [("dilute", "fp64"), ("dense", "fp64"),
+                                            ("dilute", "fp32"), ("dense", "df64")])
+def test_bed_full_size_sampled(capi, case, precision):
+    """The fluidized-bed stand-ins at full size (500x200x800, side walls,
+    velocity inflow at the bottom, pressure outflow at the top, spheres r=10,
+    the linear approximation): 20 sampled cells of one step after two warm-up
+    steps, among them cells on the inflow and outflow layers, at the side
+    walls and in the packed bed, match the oracle on boxes with the same
+    faces."""
+    import torch
+    w = inputs.bed(case)
+    e = _engine(capi, w, precision, "pull")
+    e.step(2)
+    faces = [(250, 100, 0), (0, 0, 0), (499, 199, 0), (123, 57, 1), (250, 100, 799),
+             (0, 199, 799), (331, 17, 798), (7, 150, 400)]
+    _sampled_step(e, w, faces + sample_cells(w, 12, 13), precision)
     e.close()
     torch.cuda.empty_cache()

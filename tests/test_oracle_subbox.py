@@ -15,7 +15,8 @@ from tests.subbox import box, oracle_cell, sample_cells
 def _field(walls):
     w = inputs.Workload("t", 24, 20, 22, tau=0.57, relax="trt", walls=walls,
                         fbody=(1e-6, 0.0, 0.0), gravity=(0.0, 0.0, -2e-5), weighting="nt",
-                        eps_mode="supersample", eps_n=4)
+                        eps_mode="supersample", eps_n=4, bc_velocity=(1e-4, 0.0, 2e-3),
+                        bc_density=1.003)
     x = np.array([[7.3, 9.1, 10.6], [15.2, 9.7, 11.4], [12.0, 2.0, 20.5]])
     r = np.array([4.6, 3.9, 3.2])
     u = inputs.random_velocities(3, 2e-3, 21)
@@ -24,14 +25,15 @@ def _field(walls):
     w.particles = dict(x=x, r=r, density=dens, fixed=np.zeros(3, np.uint8))
     o = Oracle(w.nx, w.ny, w.nz, w.tau, relax=w.relax, walls=walls, fbody=w.fbody,
                weighting=w.weighting, eps_mode=w.eps_mode, eps_n=w.eps_n, gravity=w.gravity,
-               dem=True)
+               dem=True, bc_velocity=w.bc_velocity, bc_density=w.bc_density)
     f0 = o.pdfs()
     o.set_pdfs((f0 * (1.0 + inputs.noise(f0.shape, 1e-3, 23))).ravel())
     o.set_particles(x, r, u=u, omega=om, density=dens)
     return w, o, u, om, dens
 
 
-@pytest.mark.parametrize("walls", [(0, 0, 0, 0, 0, 0), (1, 1, 0, 0, 0, 0)])
+@pytest.mark.parametrize("walls", [(0, 0, 0, 0, 0, 0), (1, 1, 0, 0, 0, 0),
+                                   (1, 1, 1, 1, 2, 3)])
 def test_box_step_equals_field_step(walls):
     w, o, u, om, dens = _field(walls)
     o.step(2)
@@ -40,8 +42,10 @@ def test_box_step_equals_field_step(walls):
     o.step(1)
     post = o.pdfs()
     fext = o.last_fext()
-    assert np.max(np.abs(fext - np.array(w.fbody))) > 0  # gravity's counter force acts
-    cells = sample_cells(w, 24, 5) + [(0, 3, 4), (w.nx - 1, 10, 21)]
+    # gravity's counter force acts, but not with open faces
+    assert (np.max(np.abs(fext - np.array(w.fbody))) > 0) == (max(walls) < 2)
+    cells = sample_cells(w, 24, 5) + [(0, 3, 4), (w.nx - 1, 10, 21), (5, 5, 0), (9, 12, 1),
+                                      (w.nx - 1, 0, w.nz - 1), (7, 9, w.nz - 2)]
     for c in cells:
         orig, ext = box(w, c)
         idx = [np.arange(orig[a], orig[a] + ext[a]) % (w.nx, w.ny, w.nz)[a] for a in range(3)]
