@@ -131,6 +131,11 @@ typedef struct {
   void* alloc_user;                         /* passed to alloc/free */
   double bc_velocity[3]; /* fluid velocity of a PSM_FACE_INFLOW face */
   double bc_density;     /* fluid density of a PSM_FACE_OUTFLOW face (default 1) */
+  double kt_ratio;       /* tangential contact between spheres (Eqs. 13-14):
+                            k_t = kt_ratio k_n, d_t = kt_ratio d_n, with the
+                            accumulated tangential displacement kept per pair
+                            while in contact; 0 = normal contacts only
+                            (default 2/7) */
 } psm_options;
 
 /* Fills *o with the defaults: Lambda = 3/16, FP64, pull, 4^3 sampling, NT
@@ -190,26 +195,33 @@ psm_status psm_step_host_dem(psm_ctx* ctx, int nsteps, int threads, double* host
 
 /* One LBM step of particle dynamics on the host cores for n spheres, without
  * a context (for a caller that owns its fluid solver): the DEM of
- * psm_step_host_dem (Eqs. 12, 15-16) with `subcycles` sub-steps of 1/subcycles,
- * stiffness k_n, restitution in (0, 1], gravity[3], the grid's box and walls
- * (grid->wall[2a] and wall[2a+1] equal: both faces of an axis are walls or
- * the axis is periodic).  In/out (host arrays, n*3): x, u, omega and F_old,
+ * psm_step_host_dem (Eqs. 12-16) with `subcycles` sub-steps of 1/subcycles,
+ * stiffness k_n, restitution in (0, 1], tangential ratio kt_ratio (>= 0, see
+ * psm_options), gravity[3], the grid's box (an axis whose faces are not
+ * periodic has wall planes; both faces of an axis are periodic or neither
+ * is).  In/out (host arrays, n*3): x, u, omega and F_old,
  * T_old (the total force and torque of the last sub-step; a new particle
- * starts with F_old = (m - V) gravity, T_old = 0).  In: F_hyd, T_hyd (n*3,
+ * starts with F_old = (m - V) gravity, T_old = 0), and the tangential
+ * contact history: hist_count (n), hist_partner (n*64, each particle's
+ * partners in contact in ascending order) and hist_delta (n*64*3, their
+ * accumulated tangential displacement); a new particle starts with
+ * hist_count = 0.  In: F_hyd, T_hyd (n*3,
  * held over the sub-steps), r, density (n), fixed (n, may be NULL).  Mass,
  * volume and inertia follow psm_set_particles (fluid density 1).  threads
  * as for psm_step_host_dem.  Returns PSM_ERR_ARG for invalid arguments
  * (nothing changed), PSM_ERR_STATE when a particle moved more than half the
  * partner-list skin (1 cell) within the step (the arrays then hold the
- * advanced state, which may have missed a contact), PSM_ERR_OOM when host
+ * advanced state, which may have missed a contact) or when a particle
+ * touched more than 64 partners, PSM_ERR_OOM when host
  * memory for the step ran out (the arrays may then be partly advanced).  A
  * worker thread that cannot be started makes the step run on fewer threads
  * with the same result; nothing is thrown.  Needs no GPU. */
 psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
-                             int subcycles, const double* gravity, int n, double* x, double* u,
-                             double* omega, double* F_old, double* T_old, const double* F_hyd,
-                             const double* T_hyd, const double* r, const double* density,
-                             const unsigned char* fixed, int threads);
+                             double kt_ratio, int subcycles, const double* gravity, int n,
+                             double* x, double* u, double* omega, double* F_old, double* T_old,
+                             int* hist_count, int* hist_partner, double* hist_delta,
+                             const double* F_hyd, const double* T_hyd, const double* r,
+                             const double* density, const unsigned char* fixed, int threads);
 
 /* Hydrodynamic force and torque of Eqs. 21-22 from the last step (n*3 each). */
 psm_status psm_get_force_torque(psm_ctx* ctx, double* F, double* T);

@@ -49,7 +49,8 @@ class _Config(C.Structure):
                 ("weighting", C.c_int), ("eps_mode", C.c_int), ("eps_n", C.c_int),
                 ("gravity", C.c_double * 3), ("kn", C.c_double),
                 ("restitution", C.c_double), ("subcycles", C.c_int), ("dem", C.c_int),
-                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double)]
+                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double),
+                ("kt_ratio", C.c_double)]
 
 
 def lib():
@@ -74,6 +75,7 @@ def lib():
             L.or_dem_only.argtypes = [P, C.c_int]
             L.or_get_force_torque.argtypes = [P, dp, dp]
             L.or_set_hydro.argtypes = [P, dp, dp]
+            L.or_get_contact.argtypes = [P, dp, dp]
             L.or_get_particles.argtypes = [P, dp, dp, dp]
             L.or_macroscopic.argtypes = [P, dp, dp]
             L.or_mass.argtypes = [P]
@@ -127,7 +129,7 @@ class Oracle:
                  walls=(0, 0, 0, 0, 0, 0), fbody=(0.0, 0.0, 0.0), weighting="eps",
                  eps_mode="supersample", eps_n=4, gravity=(0.0, 0.0, 0.0), kn=1e3,
                  restitution=0.9, subcycles=10, dem=False, bc_velocity=(0.0, 0.0, 0.0),
-                 bc_density=1.0):
+                 bc_density=1.0, kt_ratio=2.0 / 7.0):
         L = lib()
         cfg = _Config()
         cfg.nx, cfg.ny, cfg.nz = nx, ny, nz
@@ -149,6 +151,7 @@ class Oracle:
         for i in range(3):
             cfg.bc_velocity[i] = bc_velocity[i]
         cfg.bc_density = bc_density
+        cfg.kt_ratio = kt_ratio
         self._L = L
         self.h = L.or_create(C.byref(cfg))
         if not self.h:
@@ -224,6 +227,13 @@ class Oracle:
         F = np.empty(3 * max(self.np, 1))
         T = np.empty(3 * max(self.np, 1))
         self._L.or_get_force_torque(self.h, _dp(F), _dp(T))
+        return F[: 3 * self.np].reshape(-1, 3), T[: 3 * self.np].reshape(-1, 3)
+
+    def contact(self):
+        """Contact force and torque of every particle at the last DEM sub-step."""
+        n = max(self.np, 1)
+        F, T = np.empty(3 * n), np.empty(3 * n)
+        self._L.or_get_contact(self.h, _dp(F), _dp(T))
         return F[: 3 * self.np].reshape(-1, 3), T[: 3 * self.np].reshape(-1, 3)
 
     def set_hydro(self, F, T):

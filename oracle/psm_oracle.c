@@ -47,10 +47,22 @@
  *     The fluid gets the uniform counter force density
  *     -sum_free (m_i - V_i) g / V_fluid, V_fluid = sum_x (1 - B(x)), applied
  *     through the (1-B) F_q term, so no net momentum enters a periodic box.
- *  K  Contacts are normal spring-dashpot only (Eq. 12); n_ij points from j to
- *     i and the spring term is written to be repulsive.  Damping from the
- *     restitution coefficient: d_n = -2 ln(e) sqrt(m_eff k_n)/sqrt(pi^2+ln^2 e)
- *     with m_eff = m_i m_j/(m_i+m_j) (m_i for a wall).
+ *  K  Normal contact (Eq. 12): n_ij points from j to i and the spring term
+ *     is written to be repulsive.  Damping from the restitution coefficient:
+ *     d_n = -2 ln(e) sqrt(m_eff k_n)/sqrt(pi^2+ln^2 e) with
+ *     m_eff = m_i m_j/(m_i+m_j) (m_i for a wall).
+ *  W  Tangential contact between particles (Eqs. 13-14; the paper gives no
+ *     coefficients): k_t = kt_ratio k_n and d_t = kt_ratio d_n.  With
+ *     kt_ratio = 2/7 the tangential oscillator of two solid spheres (its
+ *     effective mass is 2/7 m_eff) has the normal one's frequency and damping
+ *     ratio.  The contact point is x_cp = x_i - (r_i - delta_n/2) n_ij; U^cp is
+ *     the relative velocity of the two surfaces there, U_t its tangential
+ *     part.  The history delta_t of a pair (Eq. 14) is kept while the pair is
+ *     in contact: each sub-step it is projected onto the current tangent
+ *     plane and advanced by dt_p U_t; it is dropped when the contact ends.
+ *     F_t = -k_t delta_t - d_t U_t acts on i, -F_t on j, with the torques
+ *     (x_cp - x_p) x F_t (Eq. 11).  No Coulomb limit (none is printed).
+ *     Wall contacts stay normal only (Eqs. 11-13 sum over particle pairs).
  *  L  DEM sub-cycles use dt_p = 1/subcycles; the hydrodynamic force and torque
  *     of the LBM step are held constant over them; F_old starts as the
  *     external force when particles are set.
@@ -113,6 +125,13 @@ struct or_ctx {
   double vfluid_last;
   /* host threads of the loops (or_set_threads) */
   int threads;
+  /* tangential contact history (reading W): per particle the partners in
+   * contact at the last sub-step, ascending, with their delta_t */
+  int* hcnt;
+  int* hcap;
+  int** hj;
+  double** hd;
+  double *Fcol, *Tcol;  /* contact force and torque of the last sub-step */
   /* per covered cell and slot, the force and torque contributions of the
    * last collision in cell order (z, y, x, slot), summed per particle after
    * the cell loop */
@@ -156,6 +175,12 @@ or_ctx* or_create(const or_config* cfg) {
 void or_set_threads(or_ctx* c, int threads) { c->threads = threads < 1 ? 1 : threads; }
 
 static void free_particles(or_ctx* c) {
+  for (int i = 0; i < c->np; ++i) {
+    if (c->hj) free(c->hj[i]);
+    if (c->hd) free(c->hd[i]);
+  }
+  free(c->hcnt); free(c->hcap); free(c->hj); free(c->hd); free(c->Fcol); free(c->Tcol);
+  c->hcnt = c->hcap = NULL; c->hj = NULL; c->hd = NULL; c->Fcol = c->Tcol = NULL;
   free(c->x); free(c->r); free(c->u); free(c->om); free(c->m); free(c->I);
   free(c->vol); free(c->fixed); free(c->Fh); free(c->Th); free(c->Fold); free(c->Told);
   c->x = c->r = c->u = c->om = c->m = c->I = c->vol = NULL;
@@ -188,6 +213,13 @@ int or_set_particles(or_ctx* c, int n, const double* x, const double* r,
   c->r = (double*)malloc(s1); c->m = (double*)malloc(s1); c->I = (double*)malloc(s1);
   c->vol = (double*)malloc(s1);
   c->fixed = (unsigned char*)calloc(1, (size_t)(n > 0 ? n : 1));
+  size_t n1 = (size_t)(n > 0 ? n : 1);
+  c->hcnt = (int*)calloc(n1, sizeof(int));
+  c->hcap = (int*)calloc(n1, sizeof(int));
+  c->hj = (int**)calloc(n1, sizeof(int*));
+  c->hd = (double**)calloc(n1, sizeof(double*));
+  c->Fcol = (double*)calloc(1, s3);
+  c->Tcol = (double*)calloc(1, s3);
   for (int i = 0; i < n; ++i) {
     if (!(r[i] > 0.0) || !(rho_p[i] > 0.0)) return -1;
     for (int a = 0; a < 3; ++a) {
@@ -691,7 +723,6 @@ static void dem_substeps(or_ctx* c) {
   double dims[3] = {g->nx, g->ny, g->nz};
   int per[3] = {!g->wall[0], !g->wall[2], !g->wall[4]};
   double dt = 1.0 / g->subcycles;
-  double* Fc = (double*)malloc(sizeof(double) * 3 * np);
   for (int sc = 0; sc < g->subcycles; ++sc) {
     /* Eq. 15: position update with the old force */
 #pragma omp parallel for num_threads(c->threads)
@@ -707,10 +738,14 @@ static void dem_substeps(or_ctx* c) {
         c->x[3 * i + a] = xn;
       }
     }
-    /* Eq. 12: normal spring-dashpot contacts, pairs in ascending j, then walls */
+    /* Eq. 12 (and Eqs. 13-14, reading W): spring-dashpot contacts, pairs in
+     * ascending j, then walls */
 #pragma omp parallel for schedule(dynamic, 16) num_threads(c->threads)
     for (int i = 0; i < np; ++i) {
-      double F[3] = {0.0, 0.0, 0.0};
+      double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+      int nold = c->hcnt[i], po = 0, nnew = 0, cap = nold + 8;
+      int* nj = (int*)malloc(sizeof(int) * (size_t)cap);
+      double* nd = (double*)malloc(sizeof(double) * 3 * (size_t)cap);
       for (int jj = 0; jj < np; ++jj) {
         if (jj == i) continue;
         double d[3];
@@ -734,7 +769,49 @@ static void dem_substeps(or_ctx* c) {
         double meff = c->m[i] * c->m[jj] / (c->m[i] + c->m[jj]);
         double dn = damping(meff, g->kn, g->restitution);
         for (int a = 0; a < 3; ++a) F[a] += g->kn * delta * n[a] - dn * vn * n[a];
+        if (!(g->kt_ratio > 0.0)) continue;
+        /* Eq. 13 at the contact point: arms from the centres, relative
+         * velocity of the surfaces, its tangential part */
+        double ai = -(c->r[i] - 0.5 * delta), aj = c->r[jj] - 0.5 * delta;
+        double Ai[3] = {ai * n[0], ai * n[1], ai * n[2]};
+        double Aj[3] = {aj * n[0], aj * n[1], aj * n[2]};
+        const double* wi = &c->om[3 * i];
+        const double* wj = &c->om[3 * jj];
+        double Ucp[3] = {
+            (c->u[3 * i + 0] + (wi[1] * Ai[2] - wi[2] * Ai[1])) -
+                (c->u[3 * jj + 0] + (wj[1] * Aj[2] - wj[2] * Aj[1])),
+            (c->u[3 * i + 1] + (wi[2] * Ai[0] - wi[0] * Ai[2])) -
+                (c->u[3 * jj + 1] + (wj[2] * Aj[0] - wj[0] * Aj[2])),
+            (c->u[3 * i + 2] + (wi[0] * Ai[1] - wi[1] * Ai[0])) -
+                (c->u[3 * jj + 2] + (wj[0] * Aj[1] - wj[1] * Aj[0]))};
+        double un = Ucp[0] * n[0] + Ucp[1] * n[1] + Ucp[2] * n[2];
+        double Ut[3] = {Ucp[0] - un * n[0], Ucp[1] - un * n[1], Ucp[2] - un * n[2]};
+        /* Eq. 14: the pair's history, projected onto the current tangent
+         * plane and advanced by this sub-step */
+        double h[3] = {0.0, 0.0, 0.0};
+        while (po < nold && c->hj[i][po] < jj) ++po;
+        if (po < nold && c->hj[i][po] == jj)
+          for (int a = 0; a < 3; ++a) h[a] = c->hd[i][3 * po + a];
+        double hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+        for (int a = 0; a < 3; ++a) h[a] = (h[a] - hn * n[a]) + dt * Ut[a];
+        double kt = g->kt_ratio * g->kn, dtg = g->kt_ratio * dn;
+        double Ft[3] = {-kt * h[0] - dtg * Ut[0], -kt * h[1] - dtg * Ut[1],
+                        -kt * h[2] - dtg * Ut[2]};
+        for (int a = 0; a < 3; ++a) F[a] += Ft[a];
+        T[0] += Ai[1] * Ft[2] - Ai[2] * Ft[1];
+        T[1] += Ai[2] * Ft[0] - Ai[0] * Ft[2];
+        T[2] += Ai[0] * Ft[1] - Ai[1] * Ft[0];
+        if (nnew == cap) {
+          cap *= 2;
+          nj = (int*)realloc(nj, sizeof(int) * (size_t)cap);
+          nd = (double*)realloc(nd, sizeof(double) * 3 * (size_t)cap);
+        }
+        nj[nnew] = jj;
+        for (int a = 0; a < 3; ++a) nd[3 * nnew + a] = h[a];
+        ++nnew;
       }
+      free(c->hj[i]); free(c->hd[i]);
+      c->hj[i] = nj; c->hd[i] = nd; c->hcnt[i] = nnew; c->hcap[i] = cap;
       for (int a = 0; a < 3; ++a) {
         if (per[a]) continue;
         for (int side = 0; side < 2; ++side) {
@@ -747,15 +824,18 @@ static void dem_substeps(or_ctx* c) {
           F[a] += g->kn * delta * nn - dn * vn * nn;
         }
       }
-      for (int a = 0; a < 3; ++a) Fc[3 * i + a] = F[a];
+      for (int a = 0; a < 3; ++a) {
+        c->Fcol[3 * i + a] = F[a];
+        c->Tcol[3 * i + a] = T[a];
+      }
     }
     /* total force (Eq. 9 without lubrication) and Eq. 16 */
 #pragma omp parallel for num_threads(c->threads)
     for (int i = 0; i < np; ++i) {
       if (c->fixed[i]) continue;
       for (int a = 0; a < 3; ++a) {
-        double Fn = c->Fh[3 * i + a] + Fc[3 * i + a] + (c->m[i] - c->vol[i]) * g->gravity[a];
-        double Tn = c->Th[3 * i + a];
+        double Fn = c->Fh[3 * i + a] + c->Fcol[3 * i + a] + (c->m[i] - c->vol[i]) * g->gravity[a];
+        double Tn = c->Th[3 * i + a] + c->Tcol[3 * i + a];
         c->u[3 * i + a] += dt * (c->Fold[3 * i + a] + Fn) / (2.0 * c->m[i]);
         c->om[3 * i + a] += dt * (c->Told[3 * i + a] + Tn) / (2.0 * c->I[i]);
         c->Fold[3 * i + a] = Fn;
@@ -763,7 +843,6 @@ static void dem_substeps(or_ctx* c) {
       }
     }
   }
-  free(Fc);
 }
 
 int or_step(or_ctx* c, int n) {
@@ -784,6 +863,11 @@ int or_dem_only(or_ctx* c, int n) {
 void or_get_force_torque(const or_ctx* c, double* F, double* T) {
   memcpy(F, c->Fh, sizeof(double) * 3 * c->np);
   memcpy(T, c->Th, sizeof(double) * 3 * c->np);
+}
+
+void or_get_contact(const or_ctx* c, double* F, double* T) {
+  memcpy(F, c->Fcol, sizeof(double) * 3 * c->np);
+  memcpy(T, c->Tcol, sizeof(double) * 3 * c->np);
 }
 
 void or_set_hydro(or_ctx* c, const double* F, const double* T) {

@@ -58,6 +58,8 @@ typedef struct {
   int dem;            /* 1: integrate free particles; 0: particles never move */
   double bc_velocity[3]; /* fluid velocity of an inflow face */
   double bc_density;     /* fluid density of an outflow face */
+  double kt_ratio;       /* tangential contact (Eqs. 13-14): k_t = kt_ratio k_n,
+                            d_t = kt_ratio d_n; 0 = normal contacts only */
 } or_config;
 
 typedef struct or_ctx or_ctx;
@@ -91,6 +93,9 @@ int or_dem_only(or_ctx* c, int n);
 void or_get_force_torque(const or_ctx* c, double* F, double* T);
 void or_set_hydro(or_ctx* c, const double* F, const double* T);
 void or_get_particles(const or_ctx* c, double* x, double* u, double* om);
+/* contact force and torque on every particle (fixed ones included) at the
+ * last DEM sub-step */
+void or_get_contact(const or_ctx* c, double* F, double* T);
 /* rho and U (component-major, 3*N) of the streamed field, Eqs. 6-7 */
 void or_macroscopic(const or_ctx* c, double* rho, double* u);
 /* sums over the stored field: mass and momentum */

@@ -56,7 +56,8 @@ class PsmOptions(C.Structure):
                 ("dem_subcycles", C.c_int), ("dem", C.c_int), ("deterministic", C.c_int),
                 ("use_graphs", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", C.c_void_p),
-                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double)]
+                ("bc_velocity", C.c_double * 3), ("bc_density", C.c_double),
+                ("kt_ratio", C.c_double)]
 
 
 _lib = None
@@ -90,9 +91,10 @@ def lib():
     L.psm_step_host_dem.argtypes = [P, C.c_int, C.c_int, C.POINTER(C.c_double)]
     L.psm_step_host_dem.restype = st
     dpp = C.POINTER(C.c_double)
-    L.psm_dem_step_host.argtypes = [C.POINTER(PsmGrid), C.c_double, C.c_double, C.c_int, dpp,
-                                    C.c_int, dpp, dpp, dpp, dpp, dpp, dpp, dpp, dpp, dpp,
-                                    C.POINTER(C.c_ubyte), C.c_int]
+    ipp = C.POINTER(C.c_int)
+    L.psm_dem_step_host.argtypes = [C.POINTER(PsmGrid), C.c_double, C.c_double, C.c_double,
+                                    C.c_int, dpp, C.c_int, dpp, dpp, dpp, dpp, dpp, ipp, ipp,
+                                    dpp, dpp, dpp, dpp, dpp, C.POINTER(C.c_ubyte), C.c_int]
     L.psm_dem_step_host.restype = st
     L.psm_get_pdfs_box.argtypes = [P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]
     L.psm_get_pdfs_box.restype = st
@@ -219,7 +221,8 @@ class Engine:
                  eps_mode="supersample", eps_n=4, gravity=(0.0, 0.0, 0.0), kn=1e3,
                  restitution=0.9, subcycles=10, dem=False, precision="fp64",
                  streaming="pull", deterministic=True, use_graphs=True, torch_alloc=True,
-                 stream=None, bc_velocity=(0.0, 0.0, 0.0), bc_density=1.0):
+                 stream=None, bc_velocity=(0.0, 0.0, 0.0), bc_density=1.0,
+                 kt_ratio=2.0 / 7.0):
         L = lib()
         self._L = L
         opt = PsmOptions()
@@ -242,6 +245,7 @@ class Engine:
         for i in range(3):
             opt.bc_velocity[i] = bc_velocity[i]
         opt.bc_density = bc_density
+        opt.kt_ratio = kt_ratio
         self._alloc = None
         if torch_alloc:
             import torch
@@ -467,13 +471,31 @@ def field_sums_noalloc(f_dev_ptr: int, ncells: int, sums_dev_ptr: int, stream_pt
                                         C.c_void_p(sums_dev_ptr), C.c_void_p(stream_ptr))
 
 
+DEM_HIST_CAP = 64  # partners per particle in the tangential contact history
+
+
+def dem_history(n):
+    """An empty tangential contact history for n particles: counts (n),
+    partners (n x 64) and accumulated tangential displacements (n x 64 x 3)."""
+    return (np.zeros(n, np.int32), np.zeros((n, DEM_HIST_CAP), np.int32),
+            np.zeros((n, DEM_HIST_CAP, 3), np.float64))
+
+
 def dem_step_host(shape, walls, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, density,
                   fixed=None, kn=1e3, restitution=0.9, subcycles=10, gravity=(0.0, 0.0, 0.0),
-                  threads=0):
+                  threads=0, kt_ratio=2.0 / 7.0, history=None):
     """One LBM step of particle dynamics on the host cores (psm_dem_step_host):
-    x, u, omega, F_old, T_old (float64, n x 3, C-contiguous) are advanced in
+    x, u, omega, F_old, T_old (float64, n x 3, C-contiguous) and the contact
+    ``history`` (from dem_history; a fresh one when None) are advanced in
     place.  Raises PsmError on a non-OK status."""
     n = int(np.asarray(r).size)
+    if history is None:
+        history = dem_history(n)
+    hc, hj, hd = history
+    if (hc.dtype != np.int32 or hj.dtype != np.int32 or hd.dtype != np.float64 or
+            hc.size != n or hj.size != n * DEM_HIST_CAP or hd.size != 3 * n * DEM_HIST_CAP or
+            not (hc.flags.c_contiguous and hj.flags.c_contiguous and hd.flags.c_contiguous)):
+        raise ValueError("history arrays must come from dem_history(n)")
     g = PsmGrid()
     g.nx, g.ny, g.nz = (int(v) for v in shape)
     for k in range(6):
@@ -486,9 +508,11 @@ def dem_step_host(shape, walls, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, dens
     rr, dd = _f64(r, n), _f64(density, n)
     fx = None if fixed is None else np.ascontiguousarray(fixed, dtype=np.uint8)
     gv = _f64(gravity, 3)
+    ip = C.POINTER(C.c_int)
     st = lib().psm_dem_step_host(
-        C.byref(g), float(kn), float(restitution), int(subcycles), _dp(gv), n,
-        _dp(x), _dp(u), _dp(omega), _dp(F_old), _dp(T_old), _dp(Fh), _dp(Th), _dp(rr), _dp(dd),
+        C.byref(g), float(kn), float(restitution), float(kt_ratio), int(subcycles), _dp(gv), n,
+        _dp(x), _dp(u), _dp(omega), _dp(F_old), _dp(T_old), hc.ctypes.data_as(ip),
+        hj.ctypes.data_as(ip), _dp(hd), _dp(Fh), _dp(Th), _dp(rr), _dp(dd),
         None if fx is None else fx.ctypes.data_as(C.POINTER(C.c_ubyte)), int(threads))
     if st != 0:
         raise PsmError(st, "psm_dem_step_host failed")

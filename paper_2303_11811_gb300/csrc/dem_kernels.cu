@@ -1,6 +1,9 @@
 // dem_kernels.cu -- particle dynamics on the device (paper Sec. 2.2, Sec. 3.2):
 // velocity Verlet (Eqs. 15-16) with sub-cycling, linear spring-dashpot normal
-// contacts between spheres and with wall faces (Eq. 12), buoyancy-corrected
+// contacts between spheres and with wall faces (Eq. 12), tangential
+// spring-dashpot contacts with history between spheres (Eqs. 13-14), and
+// positions, velocities and angular velocities double-buffered over the
+// sub-steps; buoyancy-corrected
 // gravity and the hydrodynamic force/torque of the last LBM step held fixed
 // over the sub-steps.
 //
@@ -53,10 +56,27 @@ __device__ void dem_position(const DemParams& P, int i) {
   P.p.xf[4 * i + 3] = (float)P.p.r[i];
 }
 
-// exact FP64 contact of i with j (j != i); adds to F when in contact.
-// X and U are the positions and velocities of the current sub-step.
+// Tangential history of particle i: its entries in buffer b (partners in
+// ascending order), read by a moving cursor while the new entries of the
+// sub-step are written to buffer 1 - b.
+struct HistCursor {
+  const int* oj;
+  const double* od;
+  int nold, po;
+  int* nj;
+  double* nd;
+  int nnew;
+};
+
+// exact FP64 contact of i with j (j != i); adds to F (and, with the
+// tangential model, the tangential force to F and its torque to T) when in
+// contact.  X, U, W are the positions, velocities and angular velocities of
+// the current sub-step.  Eqs. 12-14 with the readings of the oracle: contact
+// point x_i - (r_i - delta/2) n, history projected onto the current tangent
+// plane and advanced by dt U_t, F_t = -k_t delta_t - d_t U_t.
 __device__ __noinline__ void pair_contact(const DemParams& P, const double* X,
-                                             const double* U, int i, int j, double* F) {
+                                             const double* U, const double* W, int i, int j,
+                                             double* F, double* T, HistCursor& H) {
   const double dims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
   double d[3];
   for (int a = 0; a < 3; ++a) {
@@ -79,6 +99,38 @@ __device__ __noinline__ void pair_contact(const DemParams& P, const double* X,
   const double meff = P.p.m[i] * P.p.m[j] / (P.p.m[i] + P.p.m[j]);
   const double dn = damping(meff, P.kn, P.log_e);
   for (int a = 0; a < 3; ++a) F[a] += P.kn * delta * n[a] - dn * vn * n[a];
+  if (!(P.kt_ratio > 0.0)) return;
+  const double ai = -(P.p.r[i] - 0.5 * delta), aj = P.p.r[j] - 0.5 * delta;
+  const double Ai[3] = {ai * n[0], ai * n[1], ai * n[2]};
+  const double Aj[3] = {aj * n[0], aj * n[1], aj * n[2]};
+  const double* wi = W + 3 * i;
+  const double* wj = W + 3 * j;
+  const double Ucp[3] = {
+      (U[3 * i + 0] + (wi[1] * Ai[2] - wi[2] * Ai[1])) -
+          (U[3 * j + 0] + (wj[1] * Aj[2] - wj[2] * Aj[1])),
+      (U[3 * i + 1] + (wi[2] * Ai[0] - wi[0] * Ai[2])) -
+          (U[3 * j + 1] + (wj[2] * Aj[0] - wj[0] * Aj[2])),
+      (U[3 * i + 2] + (wi[0] * Ai[1] - wi[1] * Ai[0])) -
+          (U[3 * j + 2] + (wj[0] * Aj[1] - wj[1] * Aj[0]))};
+  const double un = Ucp[0] * n[0] + Ucp[1] * n[1] + Ucp[2] * n[2];
+  const double Ut[3] = {Ucp[0] - un * n[0], Ucp[1] - un * n[1], Ucp[2] - un * n[2]};
+  double h[3] = {0.0, 0.0, 0.0};
+  while (H.po < H.nold && H.oj[H.po] < j) ++H.po;
+  if (H.po < H.nold && H.oj[H.po] == j)
+    for (int a = 0; a < 3; ++a) h[a] = H.od[3 * H.po + a];
+  const double hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+  for (int a = 0; a < 3; ++a) h[a] = (h[a] - hn * n[a]) + P.dt * Ut[a];
+  const double kt = P.kt_ratio * P.kn, dtg = P.kt_ratio * dn;
+  const double Ft[3] = {-kt * h[0] - dtg * Ut[0], -kt * h[1] - dtg * Ut[1],
+                        -kt * h[2] - dtg * Ut[2]};
+  for (int a = 0; a < 3; ++a) F[a] += Ft[a];
+  T[0] += Ai[1] * Ft[2] - Ai[2] * Ft[1];
+  T[1] += Ai[2] * Ft[0] - Ai[0] * Ft[2];
+  T[2] += Ai[0] * Ft[1] - Ai[1] * Ft[0];
+  // the list of partners holds every particle in contact: at most K entries
+  H.nj[H.nnew] = j;
+  for (int a = 0; a < 3; ++a) H.nd[3 * H.nnew + a] = h[a];
+  ++H.nnew;
 }
 
 __device__ __forceinline__ void wall_contacts(const DemParams& P, const double* X,
@@ -221,14 +273,23 @@ __device__ void dem_nbr(const DemParams& P, int i) {
 // positions are carried over.
 constexpr int DEM_BATCH = 8;
 __device__ void dem_substep(const DemParams& P, int i, const double* __restrict__ Xc,
-                            const double* __restrict__ Uc, const float4* __restrict__ XFc,
-                            double* __restrict__ Xn, double* __restrict__ Un,
-                            float4* __restrict__ XFn, int last) {
+                            const double* __restrict__ Uc, const double* __restrict__ Wc,
+                            const float4* __restrict__ XFc, double* __restrict__ Xn,
+                            double* __restrict__ Un, double* __restrict__ Wn,
+                            float4* __restrict__ XFn, int hb, int last) {
   const float dims[3] = {(float)P.g.nx, (float)P.g.ny, (float)P.g.nz};
   const float4 xi = XFc[i];
-  double F[3] = {0.0, 0.0, 0.0};
+  double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
   const int cnt = P.nbr_cnt[i];
   const int* L = P.nbr + (size_t)i * P.K;
+  HistCursor H;
+  H.oj = P.p.hj[hb] + (size_t)i * P.K;
+  H.od = P.p.hd[hb] + (size_t)i * P.K * 3;
+  H.nold = P.kt_ratio > 0.0 ? P.p.hcnt[hb][i] : 0;
+  H.po = 0;
+  H.nj = P.p.hj[1 - hb] + (size_t)i * P.K;
+  H.nd = P.p.hd[1 - hb] + (size_t)i * P.K * 3;
+  H.nnew = 0;
   for (int k0 = 0; k0 < cnt; k0 += DEM_BATCH) {
     // the batch's partners and positions are loaded before any is used
     int jj[DEM_BATCH];
@@ -244,16 +305,18 @@ __device__ void dem_substep(const DemParams& P, int i, const double* __restrict_
       const float dy = min_image(xi.y - xj[u].y, dims[1], !P.g.wall[1]);
       const float dz = min_image(xi.z - xj[u].z, dims[2], !P.g.wall[2]);
       const float rs = xi.w + xj[u].w + 1e-2f;
-      if (dx * dx + dy * dy + dz * dz < rs * rs) pair_contact(P, Xc, Uc, i, jj[u], F);
+      if (dx * dx + dy * dy + dz * dz < rs * rs) pair_contact(P, Xc, Uc, Wc, i, jj[u], F, T, H);
     }
   }
+  P.p.hcnt[1 - hb][i] = H.nnew;
   wall_contacts(P, Xc, Uc, i, F);
   const double dt = P.dt;
   const double ddims[3] = {(double)P.g.nx, (double)P.g.ny, (double)P.g.nz};
-  double u[3], x[3];
+  double u[3], x[3], w[3];
   for (int a = 0; a < 3; ++a) {
     u[a] = Uc[3 * i + a];
     x[a] = Xc[3 * i + a];
+    w[a] = Wc[3 * i + a];
   }
   if (!P.p.fixed[i]) {
     // FP64 division is a long instruction sequence here: the three
@@ -261,9 +324,9 @@ __device__ void dem_substep(const DemParams& P, int i, const double* __restrict_
     const double hm = dt / (2.0 * P.p.m[i]), hI = dt / (2.0 * P.p.I[i]), h2m = dt * hm;
     for (int a = 0; a < 3; ++a) {
       const double Fn = P.p.Fh[3 * i + a] + F[a] + (P.p.m[i] - P.p.vol[i]) * P.gravity[a];
-      const double Tn = P.p.Th[3 * i + a];
+      const double Tn = P.p.Th[3 * i + a] + T[a];
       u[a] += hm * (P.p.Fold[3 * i + a] + Fn);
-      P.p.om[3 * i + a] += hI * (P.p.Told[3 * i + a] + Tn);
+      w[a] += hI * (P.p.Told[3 * i + a] + Tn);
       P.p.Fold[3 * i + a] = Fn;
       P.p.Told[3 * i + a] = Tn;
     }
@@ -289,17 +352,29 @@ __device__ void dem_substep(const DemParams& P, int i, const double* __restrict_
   for (int a = 0; a < 3; ++a) {
     Un[3 * i + a] = u[a];
     Xn[3 * i + a] = x[a];
+    Wn[3 * i + a] = w[a];
   }
   XFn[i] = make_float4((float)x[0], (float)x[1], (float)x[2], xi.w);
 }
 
+// after an odd number of sub-steps the state is in the second buffers: back
+// to the first ones (history included)
 __device__ void dem_copy_back(const DemParams& P, int i, const double* __restrict__ X,
-                              const double* __restrict__ U, const float4* __restrict__ XF) {
+                              const double* __restrict__ U, const double* __restrict__ W,
+                              const float4* __restrict__ XF) {
   for (int a = 0; a < 3; ++a) {
     P.p.x[3 * i + a] = X[3 * i + a];
     P.p.u[3 * i + a] = U[3 * i + a];
+    P.p.om[3 * i + a] = W[3 * i + a];
   }
   reinterpret_cast<float4*>(P.p.xf)[i] = XF[i];
+  const int c = P.p.hcnt[1][i];
+  P.p.hcnt[0][i] = c;
+  for (int k = 0; k < c; ++k) {
+    P.p.hj[0][(size_t)i * P.K + k] = P.p.hj[1][(size_t)i * P.K + k];
+    for (int a = 0; a < 3; ++a)
+      P.p.hd[0][((size_t)i * P.K + k) * 3 + a] = P.p.hd[1][((size_t)i * P.K + k) * 3 + a];
+  }
 }
 
 // ---- one DEM step in one launch: the phases above separated by a grid
@@ -369,6 +444,7 @@ __global__ void __launch_bounds__(DEM_THREADS) dem_step_kernel(DemParams P, int 
   if (!grid_barrier(P, gen)) return;
   const double* X0 = P.p.x;
   const double* U0 = P.p.u;
+  const double* W0 = P.p.om;
   const float4* XF0 = reinterpret_cast<const float4*>(P.p.xf);
   if (*(volatile unsigned*)&P.bar[3] == 0u) {
     // no particle has a partner within contact distance plus the skin: no
@@ -377,38 +453,44 @@ __global__ void __launch_bounds__(DEM_THREADS) dem_step_kernel(DemParams P, int 
     for (int i = i0; i < n; i += stride) {
       const double* Xc = X0;
       const double* Uc = U0;
+      const double* Wc = W0;
       const float4* XFc = XF0;
       for (int sc = 0; sc < subcycles; ++sc) {
         const bool to2 = (sc % 2) == 0;
         double* Xn = to2 ? P.p.x2 : P.p.x;
         double* Un = to2 ? P.p.u2 : P.p.u;
+        double* Wn = to2 ? P.p.om2 : P.p.om;
         float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
-        dem_substep(P, i, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+        dem_substep(P, i, Xc, Uc, Wc, XFc, Xn, Un, Wn, XFn, sc & 1, sc + 1 == subcycles);
         Xc = Xn;
         Uc = Un;
+        Wc = Wn;
         XFc = XFn;
       }
-      if (subcycles % 2 == 1) dem_copy_back(P, i, Xc, Uc, XFc);
+      if (subcycles % 2 == 1) dem_copy_back(P, i, Xc, Uc, Wc, XFc);
     }
     return;
   }
   const double* Xc = X0;
   const double* Uc = U0;
+  const double* Wc = W0;
   const float4* XFc = XF0;
   for (int sc = 0; sc < subcycles; ++sc) {
     const bool to2 = (sc % 2) == 0;
     double* Xn = to2 ? P.p.x2 : P.p.x;
     double* Un = to2 ? P.p.u2 : P.p.u;
+    double* Wn = to2 ? P.p.om2 : P.p.om;
     float4* XFn = reinterpret_cast<float4*>(to2 ? P.p.xf2 : P.p.xf);
     for (int i = i0; i < n; i += stride)
-      dem_substep(P, i, Xc, Uc, XFc, Xn, Un, XFn, sc + 1 == subcycles);
+      dem_substep(P, i, Xc, Uc, Wc, XFc, Xn, Un, Wn, XFn, sc & 1, sc + 1 == subcycles);
     if (!grid_barrier(P, gen)) return;
     Xc = Xn;
     Uc = Un;
+    Wc = Wn;
     XFc = XFn;
   }
   if (subcycles % 2 == 1)
-    for (int i = i0; i < n; i += stride) dem_copy_back(P, i, Xc, Uc, XFc);
+    for (int i = i0; i < n; i += stride) dem_copy_back(P, i, Xc, Uc, Wc, XFc);
 }
 
 }  // namespace

@@ -64,13 +64,16 @@ struct Step {
   HostDemState& S;
   double dims[3];
   bool periodic[3];
-  std::vector<double> x2, u2;          // second buffers of positions and velocities
+  std::vector<double> x2, u2, om2;     // second buffers of positions and velocities
+  std::vector<int> hcnt2, hj2;         // second buffer of the contact history
+  std::vector<double> hd2;
   std::vector<double> xb;              // positions the partner lists were built from
   std::vector<std::vector<int>> cand;  // partners within contact distance + skin
   int nc[3] = {1, 1, 1};
   double h[3] = {1.0, 1.0, 1.0};
   std::vector<int> bin_start, bin_items;
   std::atomic<int> moved{0};
+  mutable std::atomic<int> overflow{0};  // a particle in contact with more than kHostDemHistCap others
 
   Step(const HostDemParams& p, HostDemState& s) : P(p), S(s) {
     for (int a = 0; a < 3; ++a) {
@@ -79,6 +82,10 @@ struct Step {
     }
     x2.resize(3 * (size_t)S.n);
     u2.resize(3 * (size_t)S.n);
+    om2.resize(3 * (size_t)S.n);
+    hcnt2.resize((size_t)S.n);
+    hj2.resize((size_t)S.n * kHostDemHistCap);
+    hd2.resize((size_t)S.n * kHostDemHistCap * 3);
     xb.resize(3 * (size_t)S.n);
     cand.resize(S.n);
   }
@@ -170,8 +177,26 @@ struct Step {
     std::sort(L.begin(), L.end());
   }
 
-  // exact contact of i with j at the current state (Eq. 12), added to F
-  void pair_contact(const double* X, const double* U, int i, int j, double* F) const {
+  // history buffer b of particle i: counts, partners, delta_t
+  int* hc(int b) { return b ? hcnt2.data() : S.hcnt; }
+  int* hjb(int b, int i) { return (b ? hj2.data() : S.hj) + (size_t)i * kHostDemHistCap; }
+  double* hdb(int b, int i) {
+    return (b ? hd2.data() : S.hd) + (size_t)i * kHostDemHistCap * 3;
+  }
+
+  struct Cursor {
+    const int* oj;
+    const double* od;
+    int nold, po;
+    int* nj;
+    double* nd;
+    int nnew;
+  };
+
+  // exact contact of i with j at the current state (Eq. 12, and Eqs. 13-14
+  // with the device DEM's readings), added to F and T
+  void pair_contact(const double* X, const double* U, const double* W, int i, int j, double* F,
+                    double* T, Cursor& H) const {
     double d[3];
     for (int a = 0; a < 3; ++a) d[a] = min_image(X[3 * i + a] - X[3 * j + a], dims[a], periodic[a]);
     const double dist2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
@@ -186,6 +211,41 @@ struct Step {
     const double meff = S.m[i] * S.m[j] / (S.m[i] + S.m[j]);
     const double dn = damping(meff, P.kn, P.log_e);
     for (int a = 0; a < 3; ++a) F[a] += P.kn * delta * n[a] - dn * vn * n[a];
+    if (!(P.kt_ratio > 0.0)) return;
+    const double ai = -(S.r[i] - 0.5 * delta), aj = S.r[j] - 0.5 * delta;
+    const double Ai[3] = {ai * n[0], ai * n[1], ai * n[2]};
+    const double Aj[3] = {aj * n[0], aj * n[1], aj * n[2]};
+    const double* wi = W + 3 * i;
+    const double* wj = W + 3 * j;
+    const double Ucp[3] = {
+        (U[3 * i + 0] + (wi[1] * Ai[2] - wi[2] * Ai[1])) -
+            (U[3 * j + 0] + (wj[1] * Aj[2] - wj[2] * Aj[1])),
+        (U[3 * i + 1] + (wi[2] * Ai[0] - wi[0] * Ai[2])) -
+            (U[3 * j + 1] + (wj[2] * Aj[0] - wj[0] * Aj[2])),
+        (U[3 * i + 2] + (wi[0] * Ai[1] - wi[1] * Ai[0])) -
+            (U[3 * j + 2] + (wj[0] * Aj[1] - wj[1] * Aj[0]))};
+    const double un = Ucp[0] * n[0] + Ucp[1] * n[1] + Ucp[2] * n[2];
+    const double Ut[3] = {Ucp[0] - un * n[0], Ucp[1] - un * n[1], Ucp[2] - un * n[2]};
+    double h[3] = {0.0, 0.0, 0.0};
+    while (H.po < H.nold && H.oj[H.po] < j) ++H.po;
+    if (H.po < H.nold && H.oj[H.po] == j)
+      for (int a = 0; a < 3; ++a) h[a] = H.od[3 * H.po + a];
+    const double hn = h[0] * n[0] + h[1] * n[1] + h[2] * n[2];
+    for (int a = 0; a < 3; ++a) h[a] = (h[a] - hn * n[a]) + P.dt * Ut[a];
+    const double kt = P.kt_ratio * P.kn, dtg = P.kt_ratio * dn;
+    const double Ft[3] = {-kt * h[0] - dtg * Ut[0], -kt * h[1] - dtg * Ut[1],
+                          -kt * h[2] - dtg * Ut[2]};
+    for (int a = 0; a < 3; ++a) F[a] += Ft[a];
+    T[0] += Ai[1] * Ft[2] - Ai[2] * Ft[1];
+    T[1] += Ai[2] * Ft[0] - Ai[0] * Ft[2];
+    T[2] += Ai[0] * Ft[1] - Ai[1] * Ft[0];
+    if (H.nnew < kHostDemHistCap) {
+      H.nj[H.nnew] = j;
+      for (int a = 0; a < 3; ++a) H.nd[3 * H.nnew + a] = h[a];
+      ++H.nnew;
+    } else {
+      overflow.store(1, std::memory_order_relaxed);
+    }
   }
 
   void wall_contacts(const double* X, const double* U, int i, double* F) const {
@@ -202,25 +262,32 @@ struct Step {
     }
   }
 
-  // one sub-step of particle i: contacts at (Xc, Uc), velocity (Eq. 16) and,
-  // except on the last sub-step, the next positions (Eq. 15) into (Xn, Un)
-  void substep(int i, const double* Xc, const double* Uc, double* Xn, double* Un, bool last) {
-    double F[3] = {0.0, 0.0, 0.0};
-    for (int j : cand[i]) pair_contact(Xc, Uc, i, j, F);
+  // one sub-step of particle i: contacts at (Xc, Uc, Wc) with the history of
+  // buffer hb, velocity and angular velocity (Eq. 16) and, except on the
+  // last sub-step, the next positions (Eq. 15) into (Xn, Un, Wn), the
+  // history into buffer 1 - hb
+  void substep(int i, const double* Xc, const double* Uc, const double* Wc, double* Xn,
+               double* Un, double* Wn, int hb, bool last) {
+    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    Cursor H{hjb(hb, i), hdb(hb, i), P.kt_ratio > 0.0 ? hc(hb)[i] : 0, 0, hjb(1 - hb, i),
+             hdb(1 - hb, i), 0};
+    for (int j : cand[i]) pair_contact(Xc, Uc, Wc, i, j, F, T, H);
+    hc(1 - hb)[i] = H.nnew;
     wall_contacts(Xc, Uc, i, F);
     const double dt = P.dt;
-    double u[3], x[3];
+    double u[3], x[3], w[3];
     for (int a = 0; a < 3; ++a) {
       u[a] = Uc[3 * i + a];
       x[a] = Xc[3 * i + a];
+      w[a] = Wc[3 * i + a];
     }
     if (!S.fixed[i]) {
       const double hm = dt / (2.0 * S.m[i]), hI = dt / (2.0 * S.I[i]), h2m = dt * hm;
       for (int a = 0; a < 3; ++a) {
         const double Fn = S.Fh[3 * i + a] + F[a] + (S.m[i] - S.vol[i]) * P.gravity[a];
-        const double Tn = S.Th[3 * i + a];
+        const double Tn = S.Th[3 * i + a] + T[a];
         u[a] += hm * (S.Fold[3 * i + a] + Fn);
-        S.om[3 * i + a] += hI * (S.Told[3 * i + a] + Tn);
+        w[a] += hI * (S.Told[3 * i + a] + Tn);
         S.Fold[3 * i + a] = Fn;
         S.Told[3 * i + a] = Tn;
       }
@@ -244,6 +311,7 @@ struct Step {
     for (int a = 0; a < 3; ++a) {
       Un[3 * i + a] = u[a];
       Xn[3 * i + a] = x[a];
+      Wn[3 * i + a] = w[a];
     }
   }
 
@@ -259,20 +327,34 @@ struct Step {
     if (!bar.wait()) return;
     const double* Xc = S.x;
     const double* Uc = S.u;
+    const double* Wc = S.om;
     for (int sc = 0; sc < P.subcycles; ++sc) {
       double* Xn = (sc % 2 == 0) ? x2.data() : S.x;
       double* Un = (sc % 2 == 0) ? u2.data() : S.u;
-      for (int i = lo; i < hi; ++i) substep(i, Xc, Uc, Xn, Un, sc + 1 == P.subcycles);
+      double* Wn = (sc % 2 == 0) ? om2.data() : S.om;
+      for (int i = lo; i < hi; ++i)
+        substep(i, Xc, Uc, Wc, Xn, Un, Wn, sc & 1, sc + 1 == P.subcycles);
       if (!bar.wait()) return;
       Xc = Xn;
       Uc = Un;
+      Wc = Wn;
     }
     if (Xc != S.x)
-      for (int i = lo; i < hi; ++i)
+      for (int i = lo; i < hi; ++i) {
         for (int a = 0; a < 3; ++a) {
           S.x[3 * i + a] = Xc[3 * i + a];
           S.u[3 * i + a] = Uc[3 * i + a];
+          S.om[3 * i + a] = Wc[3 * i + a];
         }
+        const int c = hcnt2[i];
+        S.hcnt[i] = c;
+        for (int k = 0; k < c; ++k) {
+          S.hj[(size_t)i * kHostDemHistCap + k] = hj2[(size_t)i * kHostDemHistCap + k];
+          for (int a = 0; a < 3; ++a)
+            S.hd[((size_t)i * kHostDemHistCap + k) * 3 + a] =
+                hd2[((size_t)i * kHostDemHistCap + k) * 3 + a];
+        }
+      }
   }
 
   // a thread's part of the step; an exception (an allocation in the bins or
@@ -336,7 +418,7 @@ int host_dem_step(const HostDemParams& P, HostDemState& S, int threads) {
     Step st(P, S);
     run_threads(st, nt);
     if (st.failed.load()) return -1;
-    return st.moved.load() ? 1 : 0;
+    return (st.moved.load() || st.overflow.load()) ? 1 : 0;
   } catch (...) {  // the step's own buffers could not be allocated
     return -1;
   }

@@ -5,7 +5,8 @@
 //
 // The arithmetic is the device DEM's (dem_kernels.cu): velocity Verlet with
 // sub-cycling (Eqs. 15-16), linear spring-dashpot normal contacts between
-// spheres and with the wall faces (Eq. 12), buoyancy-corrected gravity, the
+// spheres and with the wall faces (Eq. 12), tangential contacts with history
+// between spheres (Eqs. 13-14), buoyancy-corrected gravity, the
 // hydrodynamic force and torque held over the sub-steps; the same IEEE FP64
 // operations in the same order (partners in ascending index, then the walls),
 // so the two forms agree to the last bit.
@@ -13,10 +14,15 @@
 
 namespace psm {
 
+// partners per particle in the tangential contact history (the device DEM's
+// neighbour-list capacity)
+constexpr int kHostDemHistCap = 64;
+
 struct HostDemParams {
   int dims[3];      // nx, ny, nz
   int wall[3];      // 1: walls on both faces of the axis, 0: periodic
   double kn;        // normal spring stiffness
+  double kt_ratio;  // tangential contact: k_t = kt_ratio k_n, d_t = kt_ratio d_n (0: off)
   double log_e;     // ln(restitution)
   double dt;        // sub-step, 1 / subcycles
   double gravity[3];
@@ -32,6 +38,11 @@ struct HostDemState {
   double *x, *u, *om, *Fold, *Told;
   const double *Fh, *Th, *r, *m, *I, *vol;
   const unsigned char* fixed;
+  // tangential contact history, read and advanced: per particle the count,
+  // the partners (ascending, kHostDemHistCap per particle) and delta_t (3 each)
+  int* hcnt;
+  int* hj;
+  double* hd;
 };
 
 // One LBM step of particle dynamics on up to `threads` host threads (at

@@ -888,6 +888,347 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
 #undef SRC
 }
 
+// ---- FP64 collision on compacted warps.  FP64 runs at 1/64 of the FP32
+// rate on GB300, so the FP64 kernel is bound by its count of FP64
+// instructions.  Two things cost instructions on warps of 32 consecutive
+// cells: a warp with a covered cell weights every lane's fluid change by
+// (1 - B), and the solid operator of a few covered lanes keeps the whole warp
+// busy.  So each tile's cells are listed with the uncovered cells first and
+// the covered ones after, and warps take 32 list entries at a time: a warp of
+// uncovered cells runs the particle-free form below, a warp of covered cells
+// does every lane's own solid operators; at most one warp per tile is mixed.
+
+// FP64 collision of one cell (Eqs. 3-8 and 17-21).  UNIFORM: all lanes of
+// the warp are uncovered (B = 0); a pair's update is then written as
+// d_q' = S_k + A_k, d_qbar' = S_k - A_k with S_k = (1 - omega+)/2 s_k + X_k,
+// A_k = (1 - omega-)/2 a_k + Y_k, X_k = (9/2 omega+ w c.U + G_k) c.U + C_c,
+// Y_k = 3 omega- w c.U + F_k: seven FP64 operations per pair instead of
+// nine.  Otherwise a covered lane (cov, slot index e) reads its slot
+// records, weights the fluid change by 1 - B and adds the solid operator of
+// each of its slots (Eq. 19) and writes the slots' forces (Eq. 21).
+template <bool UNIFORM>
+__device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool cov, int e) {
+  using T = double;
+  const CollideCoef<T>* cf = &P.sc->d;
+  T a[9], sk[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    sk[k] = d[2 * k + 1] + d[2 * k + 2];
+    a[k] = d[2 * k + 1] - d[2 * k + 2];
+  }
+  const T drho = ((d[0] + (sk[0] + sk[1])) + ((sk[2] + sk[3]) + (sk[4] + sk[5]))) +
+                 ((sk[6] + sk[7]) + sk[8]);
+  const T jx = ((a[0] + a[3]) + (a[4] + a[5])) + a[6];
+  const T jy = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
+  const T jz = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
+  T h[16];
+  ld4(cf->head, h);
+  ld4(cf->head + 4, h + 4);
+  ld4(cf->head + 8, h + 8);
+  ld4(cf->head + 12, h + 12);
+  const T Ux = jx + h[CC_HF];
+  const T Uy = jy + h[CC_HF + 1];
+  const T Uz = jz + h[CC_HF + 2];
+  const T uu = Ux * Ux + Uy * Uy + Uz * Uz;
+  const T Uf = Ux * h[CC_F] + Uy * h[CC_F + 1] + Uz * h[CC_F + 2];
+  const T base0 = drho - T(1.5) * uu;
+  const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
+  const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
+
+  if constexpr (UNIFORM) {
+    T tl[4];
+    ld4(cf->tail, tl);
+    d[0] = fma(tl[0], d[0], h[CC_WPW0] * base0 + h[CC_H] * Uf);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      T pk[4];
+      ld4(cf->pair[k], pk);
+      const T cu = cdot<T>(k, Ux, Uy, Uz);
+      const T X = (pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1);
+      const T Y = pk[3] * cu + pk[1];
+      const T Sk = tl[1] * sk[k] + X;
+      const T Ak = tl[2] * a[k] + Y;
+      d[2 * k + 1] = Sk + Ak;
+      d[2 * k + 2] = Sk - Ak;
+    }
+  } else {
+    // the cell's slots; the second one's record is read only when present
+    T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
+    bool has1 = false;
+    T omB = T(1);
+    if (cov) {
+      ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
+      has1 = neg_flag(r0[3]);
+      r0[3] = magnitude(r0[3]);
+      if (has1) ld4(static_cast<const T*>(P.slot_V) + 4LL * (P.slot_cap + e), r1);
+      T B = r0[3] + r1[3];
+      if (B > T(1)) B = T(1);
+      omB = T(1) - B;
+    }
+    {
+      const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
+      d[0] += omB * dl;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      T pk[4];
+      ld4(cf->pair[k], pk);
+      const T cu = cdot<T>(k, Ux, Uy, Uz);
+      const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
+      const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
+      d[2 * k + 1] += omB * (ds + da);
+      d[2 * k + 2] += omB * (ds - da);
+    }
+    if (cov) {
+      // solid operator of each slot: symmetric part B_i w_k (9/2 (cv^2 - cu^2)
+      // - 3/2 dU2), antisymmetric part B_i (3 w_k (cu + cv) - a_k)
+#pragma unroll 1
+      for (int sl = 0; sl < 2; ++sl) {
+        if (sl && !has1) continue;
+        const T Vx = sl ? r1[0] : r0[0], Vy = sl ? r1[1] : r0[1], Vz = sl ? r1[2] : r0[2];
+        const T Bi = sl ? r1[3] : r0[3];
+        const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+        const T BdU = Bi * dU2;
+        d[0] += (T(-1.5) * w0<T>()) * BdU;
+        const T c45[2] = {(T(4.5) * wk<T>(0)) * Bi, (T(4.5) * wk<T>(3)) * Bi};
+        const T c3[2] = {(T(3) * wk<T>(0)) * Bi, (T(3) * wk<T>(3)) * Bi};
+        const T cd[2] = {(T(-1.5) * wk<T>(0)) * BdU, (T(-1.5) * wk<T>(3)) * BdU};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const int cl = k < 3 ? 0 : 1;
+          const T cu = cdot<T>(k, Ux, Uy, Uz);
+          const T cv = cdot<T>(k, Vx, Vy, Vz);
+          const T Sv = cv + cu;
+          const T BdS = c45[cl] * ((cv - cu) * Sv) + cd[cl];
+          const T BA = c3[cl] * Sv - Bi * a[k];
+          d[2 * k + 1] += BdS + BA;
+          d[2 * k + 2] += BdS - BA;
+        }
+        slot_force<T>(P, e, sl, Bi, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
+      }
+    }
+  }
+}
+
+// The producer warp lists the cells of a tile into the tile's stage: the
+// live cells' positions (r << 16 | x), uncovered cells first and covered
+// cells after, each group in cell order, with each covered cell's slot index
+// (-1 for an uncovered cell); hdr[0] = number of uncovered cells, hdr[1] =
+// number of live cells.  A warp-wide pass over the tile's coverage words:
+// counts, a scan over the words, then the entries.
+__device__ __forceinline__ void fp64_list_tile(const LbmParams& P, int tile, int nw,
+                                               int* lst_cell, int* lst_slot, int* hdr,
+                                               int lane) {
+  const Grid& g = P.g;
+  const int tile_words = P.tile_rows * g.wpr;
+  const unsigned below = (1u << lane) - 1u;
+  // counts per word: lane w of each round of 32 words
+  int tot_u = 0, tot_c = 0;
+  for (int w0 = 0; w0 < nw; w0 += 32) {
+    int cu = 0, cc = 0;
+    for (int k = 0; k < 32 && w0 + k < nw; ++k) {
+      const int w = w0 + k;
+      const int r = (int)g.div_wpr.div((unsigned)w);
+      const int xr = (w - r * g.wpr) * 32 + lane;
+      const bool live = xr < g.nx;
+      const uint32_t m = P.mask ? __ldg(&P.mask[(size_t)tile * tile_words + w]) : 0u;
+      const bool cv = live && ((m >> lane) & 1u);
+      const int nu = __popc(__ballot_sync(0xffffffffu, live && !cv));
+      const int nc = __popc(__ballot_sync(0xffffffffu, cv));
+      if (lane == k) {
+        cu = nu;
+        cc = nc;
+      }
+    }
+    tot_u += __reduce_add_sync(0xffffffffu, (unsigned)cu);
+    tot_c += __reduce_add_sync(0xffffffffu, (unsigned)cc);
+  }
+  // entries: per word, the running positions of its first uncovered and
+  // first covered cell
+  int pu = 0, pc = tot_u;
+  for (int w = 0; w < nw; ++w) {
+    const int r = (int)g.div_wpr.div((unsigned)w);
+    const int xr = (w - r * g.wpr) * 32 + lane;
+    const bool live = xr < g.nx;
+    const size_t word = (size_t)tile * tile_words + w;
+    const uint32_t m = P.mask ? __ldg(&P.mask[word]) : 0u;
+    const bool cv = live && ((m >> lane) & 1u);
+    const unsigned bu = __ballot_sync(0xffffffffu, live && !cv);
+    const unsigned bc = __ballot_sync(0xffffffffu, cv);
+    if (live) {
+      const int pos = cv ? pc + __popc(bc & below) : pu + __popc(bu & below);
+      lst_cell[pos] = (r << 16) | xr;
+      int e = -1;
+      if (cv) {
+        e = __ldg(&P.base[word]) + __popc(m & below);
+        if (e >= P.slot_cap) e = -1;  // never the case: the mapping sized the slots
+      }
+      lst_slot[pos] = e;
+    }
+    pu += __popc(bu);
+    pc += __popc(bc);
+  }
+  if (lane == 0) {
+    hdr[0] = tot_u;
+    hdr[1] = tot_u + tot_c;
+  }
+}
+
+// Staged FP64 kernel with compacted warps: the producer warp and the ring of
+// staged rows are those of lbm_bulk_kernel, and the producer also lists each
+// tile's cells into the tile's stage (fp64_list_tile) before it arrives on
+// the stage's full barrier (count 2: its expect-tx arrival and this one), so
+// the consumers find the list with the data.  Consumer warps take 32 list
+// entries at a time and need no barrier among themselves.
+template <int MODE, int WALLS>
+__global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) {
+  using T = double;
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  const Grid& g = P.g;
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bulk_smem);
+  unsigned long long* empty = full + BULK_MAX_STAGES;
+  const int S = P.stages, TR = P.tile_rows, nxp = g.nxp;
+  const int C = TR * nxp;  // elements per direction in a tile
+  const size_t stage_elems = (size_t)Q * C;
+  T* ring = reinterpret_cast<T*>(bulk_smem + BULK_BAR_BYTES);
+  // per stage: header (2 ints, padded to 4), cells, slot indices
+  int* lists = reinterpret_cast<int*>(ring + S * stage_elems);
+  const size_t list_ints = 4 + 2 * (size_t)C;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nrows = g.ny * g.nz;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 2);
+      mbar_init(&empty[s], BULK_CONSUMER_WARPS);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == BULK_CONSUMER_WARPS) {
+    // ---- producer
+    int issued = 0;
+    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+      const int s = issued % S;
+      const unsigned ph = (unsigned)(issued / S) & 1u;
+      if (issued >= S && !mbar_wait(&empty[s], ph ^ 1u)) {
+        if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+        break;
+      }
+      const int row0 = tile * TR;
+      const int nr = min(TR, nrows - row0);
+      if (lane == 0) mbar_expect_tx(&full[s], (unsigned)(Q * nr * nxp * sizeof(T)));
+      __syncwarp();
+      T* st = ring + s * stage_elems;
+      for (int j = lane; j < Q * nr; j += 32) {
+        const int q = j / nr, r = j - q * nr;
+        const int row = row0 + r;
+        const int z = (int)g.div_ny.div((unsigned)row);
+        const int y = row - z * g.ny;
+        int sy = y, sz = z, sq = q;
+        if (MODE != 1 && q > 0) {
+          const int k = (q - 1) >> 1, sg = qsign(q);
+          sy -= sg * cky(k);
+          sz -= sg * ckz(k);
+          sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+          sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
+          if (MODE == 2) sq = q + sg;  // AA odd: the opposite direction's array
+        }
+        const T* src = static_cast<const T*>(P.src) + (size_t)sq * g.ncell +
+                       ((size_t)sz * g.ny + sy) * nxp;
+        bulk_copy_g2s(st + ((size_t)q * TR + r) * nxp, src, (unsigned)(nxp * sizeof(T)),
+                      &full[s]);
+      }
+      int* ls = lists + s * list_ints;
+      fp64_list_tile(P, tile, nr * g.wpr, ls + 4, ls + 4 + C, ls, lane);
+      __threadfence_block();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);  // release: the list is visible with the data
+      ++issued;
+    }
+    // no copy may land after the block has exited
+    for (int j = issued - S < 0 ? 0 : issued - S; j < issued; ++j)
+      if (!mbar_wait(&full[j % S], (unsigned)(j / S) & 1u)) {
+        if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+      }
+    return;
+  }
+
+  // ---- consumers
+#define SRC(q) static_cast<const T*>(P.srcq[q])
+  int it = 0;
+  for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++it) {
+    const int s = it % S;
+    if (!mbar_wait(&full[s], (unsigned)(it / S) & 1u)) {
+      if (lane == 0) atomicOr(P.status, ST_TIMEOUT);
+      break;
+    }
+    const T* st = ring + s * stage_elems;
+    const int* ls = lists + s * list_ints;
+    const int tot_u = ls[0], L = ls[1];
+    const int* lst_cell = ls + 4;
+    const int* lst_slot = ls + 4 + C;
+    const int row0 = tile * TR;
+    const int nch = (L + 31) / 32;
+    for (int ch = warp; ch < nch; ch += BULK_CONSUMER_WARPS) {
+      const int i = ch * 32 + lane;
+      const bool active = i < L;
+      const int ent = lst_cell[active ? i : L - 1];
+      const int e = active ? lst_slot[i] : -1;
+      const int r = ent >> 16, x = ent & 0xffff;
+      const int row = row0 + r;
+      const int z = (int)g.div_ny.div((unsigned)row);
+      const int y = row - z * g.ny;
+      NbrT<WALLS> nb;
+      nb.init(x, y, z, g.nx, g.ny, g.nz, g.nxp, g.wall);
+      const int cell = nb.idx(0, 0, 0);
+      const int xm = x == 0 ? g.nx - 1 : x - 1, xq = x == g.nx - 1 ? 0 : x + 1;
+      const T* sr = st + (size_t)r * nxp;  // direction q of this row at sr[q * C]
+      T ub[3] = {T(0), T(0), T(0)};
+      if constexpr (MODE == 0 && (WALLS & 4) != 0) {
+        if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
+      }
+      T d[Q];
+      d[0] = sr[x];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+        const int qa = 2 * k + 1, qb = 2 * k + 2;
+        const int xa = cx > 0 ? xm : (cx < 0 ? xq : x);  // x - c_x
+        const int xb = cx > 0 ? xq : (cx < 0 ? xm : x);  // x + c_x
+        if (MODE == 0) {
+          if (nb.ok(-cx, -cy, -cz)) {
+            d[qa] = sr[qa * C + xa];
+          } else {
+            const T bb = ld(SRC(qb) + cell);
+            const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
+            d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
+          }
+          if (nb.ok(cx, cy, cz)) {
+            d[qb] = sr[qb * C + xb];
+          } else {
+            const T bb = ld(SRC(qa) + cell);
+            const int t = open_face<WALLS>(g, nb, cx, cy, cz);
+            d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
+          }
+        } else if (MODE == 1) {
+          d[qa] = sr[qa * C + x];
+          d[qb] = sr[qb * C + x];
+        } else {
+          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qa) + cell);
+          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qb) + cell);
+        }
+      }
+      if (ch * 32 + 32 <= tot_u) fp64_collide<true>(P, d, false, -1);
+      else fp64_collide<false>(P, d, e >= 0, e);
+      if (active) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+#undef SRC
+}
+
 // canonical FP64 f~ (unpadded, full f = w + delta) from the storage layout
 template <typename T>
 __global__ void to_canonical_kernel(Grid g, const T* __restrict__ buf, int aa, int parity,
@@ -1059,9 +1400,15 @@ int configure_walls(int optin) {
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 0, W>, a, sm) != cudaSuccess;
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 1, W>, a, sm) != cudaSuccess;
   bad |= cudaFuncSetAttribute(lbm_kernel<T, 2, W>, a, sm) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 0, W>, a, optin) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 1, W>, a, optin) != cudaSuccess;
-  bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 2, W>, a, optin) != cudaSuccess;
+  if constexpr (!kFP64<T>) {  // FP64 stages through lbm_fp64_kernel
+    bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 0, W>, a, optin) != cudaSuccess;
+    bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 1, W>, a, optin) != cudaSuccess;
+    bad |= cudaFuncSetAttribute(lbm_bulk_kernel<T, 2, W>, a, optin) != cudaSuccess;
+  } else {
+    bad |= cudaFuncSetAttribute(lbm_fp64_kernel<0, W>, a, optin) != cudaSuccess;
+    bad |= cudaFuncSetAttribute(lbm_fp64_kernel<1, W>, a, optin) != cudaSuccess;
+    bad |= cudaFuncSetAttribute(lbm_fp64_kernel<2, W>, a, optin) != cudaSuccess;
+  }
   return bad;
 }
 
@@ -1092,7 +1439,8 @@ int lbm_configure() {
 // the one-cell-per-thread kernel is to be used.
 template <typename T, int W>
 const void* bulk_fn() {
-  return (const void*)lbm_bulk_kernel<T, 0, W>;
+  if constexpr (kFP64<T>) return (const void*)lbm_fp64_kernel<0, W>;
+  else return (const void*)lbm_bulk_kernel<T, 0, W>;
 }
 template <typename T>
 const void* bulk_fn_w(int w) {
@@ -1140,18 +1488,19 @@ int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan) {
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
   const int TR = (g.nxp <= 256 && 256 % g.nxp == 0) ? 256 / g.nxp : 1;
   const size_t stage = (size_t)Q * TR * g.nxp * esz;
-  const size_t extra = BULK_BAR_BYTES + (prec == PREC_FP64 ? BULK_CONSUMER_WARPS *
-                                                                 sizeof(SolidSmem<double>)
-                                                           : 0);
+  // FP64 (compacted warps): per stage the tile's cell list and slot indices
+  // with a 16-byte header
+  const size_t list_stage = prec == PREC_FP64 ? (size_t)8 * TR * g.nxp + 16 : 0;
+  const size_t extra = BULK_BAR_BYTES;
   const size_t budget = prec == PREC_FP64 ? (size_t)optin : (size_t)100 * 1024;
   if (budget <= extra) return 0;
-  size_t S = (budget - extra) / stage;
+  size_t S = (budget - extra) / (stage + list_stage);
   if (S > BULK_MAX_STAGES) S = BULK_MAX_STAGES;
   if (S < 2) {
-    if (extra + 2 * stage > (size_t)optin) return 0;
+    if (extra + 2 * (stage + list_stage) > (size_t)optin) return 0;
     S = 2;
   }
-  const size_t smem = extra + S * stage;
+  const size_t smem = extra + S * (stage + list_stage);
   const int w = g.wall[0] | (g.wall[1] << 1) | (g.wall[2] << 2);
   const void* fn = prec == PREC_FP32 ? bulk_fn_w<float>(w)
                    : prec == PREC_DF ? bulk_fn_w<df>(w)
@@ -1175,12 +1524,21 @@ int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan) {
 
 template <typename T, int W>
 void launch_lbm_t(const LbmParams& P, int mode, unsigned grid, cudaStream_t s) {
-  if (P.stages > 0) {
+  if (P.stages > 0 && kFP64<T>) {
     const size_t sm = P.smem;
-    if (mode == 0) lbm_bulk_kernel<T, 0, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
-    else if (mode == 1) lbm_bulk_kernel<T, 1, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
-    else lbm_bulk_kernel<T, 2, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    if (mode == 0) lbm_fp64_kernel<0, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    else if (mode == 1) lbm_fp64_kernel<1, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+    else lbm_fp64_kernel<2, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
     return;
+  }
+  if constexpr (!kFP64<T>) {
+    if (P.stages > 0) {
+      const size_t sm = P.smem;
+      if (mode == 0) lbm_bulk_kernel<T, 0, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+      else if (mode == 1) lbm_bulk_kernel<T, 1, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+      else lbm_bulk_kernel<T, 2, W><<<P.blocks, BULK_THREADS, sm, s>>>(P);
+      return;
+    }
   }
   const size_t sm = lbm_dyn_smem<T>();
   if (mode == 0) lbm_kernel<T, 0, W><<<grid, LBM_THREADS, sm, s>>>(P);
@@ -1280,6 +1638,10 @@ __device__ void fill_coef(CollideCoef<T>& c, const double* f, double wp, double 
   c.head[CC_WPW + 1] = (T)(wp * (1.0 / 36.0));
   c.head[CC_MHWM] = (T)(-0.5 * wm);
   c.head[15] = (T)0;
+  c.tail[0] = (T)(1.0 - wp);
+  c.tail[1] = (T)(0.5 * (1.0 - wp));
+  c.tail[2] = (T)(0.5 * (1.0 - wm));
+  c.tail[3] = (T)0;
   for (int k = 0; k < 9; ++k) {
     const double cfk = ckx(k) * f[0] + cky(k) * f[1] + ckz(k) * f[2];
     const double w = wk<double>(k);

@@ -1492,7 +1492,8 @@ int launch_weight_table(int n, double tau, int weighting, double* out, cudaStrea
 
 int launch_force_reduce(MapParams P, cudaStream_t s) {
   if (P.p.n == 0) return 0;
-  if (P.fp32) force_reduce_f32_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
+  // FP32 form: the FP32 slot forces are summed in FP64 like the FP64 form's
+  if (P.fp32) force_reduce_kernel<float><<<P.p.n, RED_THREADS, 0, s>>>(P);
   else if (P.dfrec) force_reduce_df_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
   else force_reduce_kernel<double><<<P.p.n, RED_THREADS, 0, s>>>(P);
   return 1;

@@ -280,6 +280,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s, bool dem = true) {
     D.g = c->g;
     D.p = c->p;
     D.kn = c->opt.k_n;
+    D.kt_ratio = c->opt.kt_ratio;
     D.log_e = c->log_e;
     D.dt = 1.0 / c->opt.dem_subcycles;
     for (int a = 0; a < 3; ++a) {
@@ -384,7 +385,7 @@ psm_status canonical(psm_ctx* c, double** out, const BoxSel* box = nullptr) {
 // fields, then the PDF storage as stored (the form's own values), the
 // per-particle arrays, the surrogate's parameters when set.
 namespace {
-constexpr char kCkptMagic[8] = {'P', 'S', 'M', 'C', 'K', 'P', 'T', '1'};
+constexpr char kCkptMagic[8] = {'P', 'S', 'M', 'C', 'K', 'P', 'T', '2'};
 enum {
   CK_NX, CK_NY, CK_NZ, CK_WX, CK_WY, CK_WZ, CK_PREC, CK_AA, CK_RELAX, CK_PARITY, CK_N,
   CK_MLP, CK_DEM, CK_FIELDS
@@ -419,7 +420,8 @@ std::vector<CkptArray> ckpt_arrays(psm_ctx* c) {
   Particles& P = c->p;
   return {{P.x, 3, 8},  {P.u, 3, 8},   {P.om, 3, 8},   {P.r, 1, 8},    {P.m, 1, 8},
           {P.I, 1, 8},  {P.vol, 1, 8}, {P.fr, 1, 8},   {P.fixed, 1, 1}, {P.Fh, 3, 8},
-          {P.Th, 3, 8}, {P.Fold, 3, 8}, {P.Told, 3, 8}};
+          {P.Th, 3, 8}, {P.Fold, 3, 8}, {P.Told, 3, 8}, {P.hcnt[0], 1, 4},
+          {P.hj[0], kDemListCap, 4}, {P.hd[0], 3 * kDemListCap, 8}};
 }
 }  // namespace
 
@@ -439,6 +441,8 @@ void psm_default_options(psm_options* o) {
   o->dem = 1;
   o->deterministic = 1;
   o->use_graphs = 1;
+  o->bc_density = 1.0;
+  o->kt_ratio = 2.0 / 7.0;
 }
 
 psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const psm_options* opt,
@@ -477,7 +481,8 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   if (opt->weighting != PSM_W_EPS && opt->weighting != PSM_W_NT) return PSM_ERR_ARG;
   if (relax == PSM_TRT && !(opt->magic > 0.0)) return PSM_ERR_ARG;
   if (opt->dem && (opt->dem_subcycles < 1 || !(opt->k_n > 0) || !(opt->restitution > 0) ||
-                   opt->restitution > 1.0))
+                   opt->restitution > 1.0 || !(opt->kt_ratio >= 0.0) ||
+                   !std::isfinite(opt->kt_ratio)))
     return PSM_ERR_ARG;
   const long long nxp = ((grid->nx + 31) / 32) * 32LL;
   const long long ncell = nxp * grid->ny * grid->nz;
@@ -697,6 +702,12 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   P.x2 = alloc_n<double>(c, n3, c->palloc);
   P.u2 = alloc_n<double>(c, n3, c->palloc);
   P.xf2 = alloc_n<float>(c, n4, c->palloc);
+  P.om2 = alloc_n<double>(c, n3, c->palloc);
+  for (int b = 0; b < 2; ++b) {
+    P.hcnt[b] = alloc_n<int>(c, n1, c->palloc);
+    P.hj[b] = alloc_n<int>(c, n1 * kDemListCap, c->palloc);
+    P.hd[b] = alloc_n<double>(c, n1 * kDemListCap * 3, c->palloc);
+  }
   Slots& S = c->slots;
   const size_t cp = cap > 0 ? (size_t)cap : 1;
   S.cap = (long long)cp;
@@ -741,6 +752,9 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
     CK(cudaMemsetAsync(P.Fh, 0, b3, s));
     CK(cudaMemsetAsync(P.Th, 0, b3, s));
     CK(cudaMemsetAsync(P.Fc, 0, b3, s));
+    // new particles: no tangential contact history
+    CK(cudaMemsetAsync(P.hcnt[0], 0, sizeof(int) * n, s));
+    CK(cudaMemsetAsync(P.hcnt[1], 0, sizeof(int) * n, s));
   }
   CK(cudaMemcpyAsync(c->list_off, loff.data(), sizeof(long long) * (n + 1),
                      cudaMemcpyHostToDevice, s));
@@ -829,15 +843,20 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
   // host copy of the particle state and constants (the device copy stays the
   // reference: it is rewritten after every step)
   const size_t b3 = sizeof(double) * 3 * n, b1 = sizeof(double) * n;
-  std::vector<double> x, u, om, Fo, To, Fh, Th, r, m, I, vol;
+  std::vector<double> x, u, om, Fo, To, Fh, Th, r, m, I, vol, hd;
   std::vector<unsigned char> fixed;
+  std::vector<int> hc, hj;
   try {
     for (auto* v : {&x, &u, &om, &Fo, &To, &Fh, &Th}) v->resize(3 * (size_t)n);
     for (auto* v : {&r, &m, &I, &vol}) v->resize((size_t)n);
     fixed.resize((size_t)n);
+    hc.resize((size_t)n);
+    hj.resize((size_t)n * kDemListCap);
+    hd.resize((size_t)n * kDemListCap * 3);
   } catch (...) {
     return fail(c, PSM_ERR_OOM, "host memory for the particle state");
   }
+  static_assert(kDemListCap == kHostDemHistCap, "history layout");
   CK(cudaMemcpyAsync(x.data(), c->p.x, b3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(u.data(), c->p.u, b3, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(om.data(), c->p.om, b3, cudaMemcpyDeviceToHost, c->stream));
@@ -848,6 +867,13 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
   CK(cudaMemcpyAsync(I.data(), c->p.I, b1, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(vol.data(), c->p.vol, b1, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(fixed.data(), c->p.fixed, n, cudaMemcpyDeviceToHost, c->stream));
+  // the tangential contact history continues on the host (and comes back at
+  // the end, for a later device step)
+  const size_t bh = sizeof(int) * (size_t)n * kDemListCap;
+  CK(cudaMemcpyAsync(hc.data(), c->p.hcnt[0], sizeof(int) * n, cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(hj.data(), c->p.hj[0], bh, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hd.data(), c->p.hd[0], 6 * bh, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   HostDemParams HP{};
   HP.dims[0] = c->g.nx;
@@ -858,12 +884,14 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
     HP.gravity[a] = c->opt.gravity[a];
   }
   HP.kn = c->opt.k_n;
+  HP.kt_ratio = c->opt.kt_ratio;
   HP.log_e = c->log_e;
   HP.dt = 1.0 / c->opt.dem_subcycles;
   HP.skin = kDemSkin;
   HP.subcycles = c->opt.dem_subcycles;
-  HostDemState HS{n, x.data(), u.data(), om.data(), Fo.data(), To.data(), Fh.data(),
-                  Th.data(), r.data(), m.data(), I.data(), vol.data(), fixed.data()};
+  HostDemState HS{n,         x.data(),   u.data(),  om.data(),   Fo.data(),
+                  To.data(), Fh.data(),  Th.data(), r.data(),    m.data(),
+                  I.data(),  vol.data(), fixed.data(), hc.data(), hj.data(), hd.data()};
   for (int k = 0; k < nsteps; ++k) {
     psm_status st = launch_one_step(c, false);
     if (st != PSM_OK) return st;
@@ -897,23 +925,31 @@ psm_status psm_step_host_dem(psm_ctx* c, int nsteps, int threads, double* host_m
     if (moved) {
       c->error_state = true;
       return fail(c, PSM_ERR_STATE,
-                  "a particle moved more than half the DEM neighbour-list skin in one step");
+                  "a particle moved more than half the DEM neighbour-list skin in one step, "
+                  "or touched more partners than the contact history holds");
     }
   }
+  CK(cudaMemcpyAsync(c->p.hcnt[0], hc.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                     c->stream));
+  CK(cudaMemcpyAsync(c->p.hj[0], hj.data(), bh, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->p.hd[0], hd.data(), 6 * bh, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return read_status(c);
 }
 
 psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitution,
-                             int subcycles, const double* gravity, int n, double* x, double* u,
-                             double* omega, double* F_old, double* T_old, const double* F_hyd,
-                             const double* T_hyd, const double* r, const double* density,
-                             const unsigned char* fixed, int threads) {
+                             double kt_ratio, int subcycles, const double* gravity, int n,
+                             double* x, double* u, double* omega, double* F_old, double* T_old,
+                             int* hist_count, int* hist_partner, double* hist_delta,
+                             const double* F_hyd, const double* T_hyd, const double* r,
+                             const double* density, const unsigned char* fixed, int threads) {
   if (!grid || !gravity || n < 0 || subcycles < 1 || !(k_n > 0.0) || !(restitution > 0.0) ||
-      !(restitution <= 1.0))
+      !(restitution <= 1.0) || !(kt_ratio >= 0.0) || !std::isfinite(kt_ratio))
     return PSM_ERR_ARG;
   if (n == 0) return PSM_OK;
   if (!x || !u || !omega || !F_old || !T_old || !F_hyd || !T_hyd || !r || !density)
     return PSM_ERR_ARG;
+  if (!hist_count || !hist_partner || !hist_delta) return PSM_ERR_ARG;
   const int dims[3] = {grid->nx, grid->ny, grid->nz};
   HostDemParams HP{};
   for (int a = 0; a < 3; ++a) {
@@ -924,6 +960,7 @@ psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitutio
     HP.gravity[a] = gravity[a];
   }
   HP.kn = k_n;
+  HP.kt_ratio = kt_ratio;
   HP.log_e = std::log(restitution);
   HP.dt = 1.0 / subcycles;
   HP.skin = kDemSkin;
@@ -944,8 +981,9 @@ psm_status psm_dem_step_host(const psm_grid* grid, double k_n, double restitutio
     fx[i] = fixed && fixed[i] ? 1 : 0;
   }
   threads = host_threads(threads);
-  HostDemState HS{n, x, u, omega, F_old, T_old, F_hyd, T_hyd, r, m.data(), I.data(),
-                  vol.data(), fx.data()};
+  HostDemState HS{n,      x,      u,        omega,    F_old,     T_old,
+                  F_hyd,  T_hyd,  r,        m.data(), I.data(),  vol.data(),
+                  fx.data(), hist_count, hist_partner, hist_delta};
   const int st = host_dem_step(HP, HS, threads);
   return st < 0 ? PSM_ERR_OOM : (st ? PSM_ERR_STATE : PSM_OK);
 }
@@ -1362,12 +1400,15 @@ psm_status psm_load(psm_ctx* c, const char* path) {
   std::vector<double> x(3 * n), u(3 * n), om(3 * n), r(n), m(n), I(n), vol(n), fr(n);
   std::vector<unsigned char> fixed(n);
   std::vector<double> Fh(3 * n), Th(3 * n), Fold(3 * n), Told(3 * n);
-  void* hosts[] = {x.data(),  u.data(),  om.data(),   r.data(),    m.data(),
-                   I.data(),  vol.data(), fr.data(),  fixed.data(), Fh.data(),
-                   Th.data(), Fold.data(), Told.data()};
-  const size_t per[] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 3, 3};
-  const size_t es[] = {8, 8, 8, 8, 8, 8, 8, 8, 1, 8, 8, 8, 8};
-  for (int i = 0; i < 13 && n > 0; ++i)
+  std::vector<int> hc(n), hj(n * kDemListCap);
+  std::vector<double> hd(n * kDemListCap * 3);
+  void* hosts[] = {x.data(),  u.data(),    om.data(),   r.data(),    m.data(),  I.data(),
+                   vol.data(), fr.data(),  fixed.data(), Fh.data(),  Th.data(), Fold.data(),
+                   Told.data(), hc.data(), hj.data(),   hd.data()};
+  const size_t per[] = {3, 3, 3, 1, 1, 1, 1, 1, 1, 3, 3, 3, 3, 1, kDemListCap, 3 * kDemListCap};
+  const size_t es[] = {8, 8, 8, 8, 8, 8, 8, 8, 1, 8, 8, 8, 8, 4, 4, 8};
+  constexpr int kArrays = 16;
+  for (int i = 0; i < kArrays && n > 0; ++i)
     if (!read_all(f, hosts[i], per[i] * es[i] * (size_t)n))
       return bad("truncated checkpoint (particles)");
   std::vector<float> prm;
@@ -1385,7 +1426,8 @@ psm_status psm_load(psm_ctx* c, const char* path) {
                                     dens.data(), fixed.data());
   if (st != PSM_OK) return st;
   const std::vector<CkptArray> arrs = ckpt_arrays(c);
-  for (int i = 4; i < 13 && n > 0; ++i)  // m, I, vol, fr, fixed, Fh, Th, Fold, Told
+  // m, I, vol, fr, fixed, Fh, Th, Fold, Told, contact history
+  for (int i = 4; i < kArrays && n > 0; ++i)
     CK(cudaMemcpyAsync(arrs[i].dev, hosts[i], per[i] * es[i] * (size_t)n,
                        cudaMemcpyHostToDevice, c->stream));
   for (int a = 0; a < 3; ++a) c->G[a] = h.G[a];

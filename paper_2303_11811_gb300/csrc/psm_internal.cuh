@@ -104,6 +104,9 @@ struct alignas(16) CollideCoef {
   // per pair k: symmetric forcing / (c_k . U), antisymmetric forcing,
   // 9/2 omega+ w_c, 3 omega- w_c
   T pair[9][4];
+  // for cells without particles, where a pair's update is written as
+  // d_q' = S_k + A_k: 1 - omega+, (1 - omega+)/2, (1 - omega-)/2, 0
+  T tail[4];
 };
 
 struct StepConst {
@@ -138,6 +141,13 @@ struct Particles {
   double* x2;     // second buffers of the DEM sub-steps
   double* u2;
   float* xf2;
+  double* om2;
+  // tangential contact history (Eqs. 13-14), two buffers: per particle the
+  // partners in contact at the last sub-step (ascending, at most DEM list
+  // capacity K) and their accumulated tangential displacement delta_t
+  int* hcnt[2];   // n
+  int* hj[2];     // n*K
+  double* hd[2];  // n*K*3
 };
 
 struct Slots {
@@ -260,6 +270,7 @@ struct DemParams {
   Grid g;
   Particles p;
   double kn, log_e, dt;
+  double kt_ratio;    // tangential contact: k_t = kt_ratio k_n, d_t = kt_ratio d_n (0: off)
   double gravity[3];
   unsigned* status;
   int nc[3];          // bins per axis (edge >= largest diameter + skin)

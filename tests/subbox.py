@@ -3,12 +3,13 @@
 
 For a cell c the oracle runs one step on a box around c (16 cells along a
 periodic axis or along z with open faces, the whole extent along an axis
-with walls), filled with the
-post-collision PDFs of that box and holding the spheres within reach of c,
-shifted by an integer so that every cell-centre offset is the same FP64
-number as in the full field.  Its body force is the full field's fluid force
-density of that step, with no gravity and no DEM, so the collision of c sees
-the same inputs.  The box wraps periodically at its own faces, which changes
+with walls), filled with the post-collision PDFs of that box and holding the
+spheres within reach of c, shifted by an integer, so that every cell-centre
+offset is the same number as in the full field up to the rounding of the
+shifted centre (the shift is exact unless it moves a centre across a power
+of two).  Its body force is the full field's fluid force density of that
+step, with no gravity and no DEM, so the collision of c sees the same
+inputs.  The box wraps periodically at its own faces, which changes
 cells next to those faces only; c sits 8 cells from them.
 """
 import math
@@ -90,7 +91,7 @@ def oracle_cell(w, c, pre, fext, X, R, U, OM, dens):
             d[:, a] -= dims[a] * np.round(d[:, a] / dims[a])
     sel = np.nonzero((d * d).sum(axis=1) < (R + math.sqrt(3.0) / 2) ** 2)[0]
     assert sel.size <= 2
-    xs = X[sel] - np.array(o, dtype=float)  # exact: integer shifts
+    xs = X[sel] - np.array(o, dtype=float)  # integer shifts
     for a in range(3):
         if not walls[a]:
             xs[:, a] -= dims[a] * np.round((xs[:, a] - BOX / 2) / dims[a])

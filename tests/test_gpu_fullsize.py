@@ -66,7 +66,8 @@ def _sampled_step(e, w, cells, precision):
                     max(loc[0] - 1, 0):loc[0] + 2]
             delta = np.max(np.abs(nb - REST[:, None, None, None]))
             err = float(np.max(np.abs(got - want)))
-            assert err <= 32 * 2.0 ** -24 * delta, (c, err, delta)
+            # plus the FP64 rounding of w_q + delta in the canonical values
+            assert err <= 32 * 2.0 ** -24 * delta + 2.0 ** -50, (c, err, delta)
         worst = max(worst, err)
     return worst
 

@@ -1,5 +1,6 @@
 """The host-core DEM of the hybrid coupling (psm_dem_step_host, the DEM of
-psm_step_host_dem) against the oracle's DEM (Sec. 2.2, Eqs. 12, 15-16) with
+psm_step_host_dem) against the oracle's DEM (Sec. 2.2, Eqs. 12-16, with the
+tangential contact history carried over the steps) with
 the same hydrodynamic forces: contacts between spheres and with walls, a
 sphere wrapping around periodic faces, a fixed sphere; thread-count
 independence; argument and skin errors.  No GPU: the library's host code runs
@@ -58,12 +59,17 @@ def test_host_dem_matches_the_oracle_dem():
     o.set_particles(x, r, u=u, omega=om, density=dens, fixed=fixed)
     hx, hu, ho, Fo, To = host_state(x, r, u, om, dens, fixed)
     n = r.size
+    hist = capi.dem_history(n)  # the tangential contact history, carried over the steps
+    most = 0
     for k in range(30):
         Fh, Th = hydro(n, k)
         o.set_hydro(Fh.ravel(), Th.ravel())
         o.dem_only(1)
         capi.dem_step_host(SHAPE, WALLS, hx, hu, ho, Fo, To, Fh, Th, r, dens, fixed=fixed,
-                           kn=KN, restitution=E, subcycles=SUB, gravity=G, threads=2)
+                           kn=KN, restitution=E, subcycles=SUB, gravity=G, threads=2,
+                           history=hist)
+        most = max(most, int(hist[0].sum()))
+    assert most > 0  # contacts with tangential history were carried over steps
     xo, uo, wo = o.particles()
     # nearest image: sphere 2 crosses the periodic z faces
     d = hx - xo
@@ -82,11 +88,13 @@ def test_thread_count_does_not_change_the_result():
     runs = []
     for threads in (1, 3, 4):
         hx, hu, ho, Fo, To = host_state(x, r, u, om, dens, fixed)
+        hist = capi.dem_history(r.size)
         for k in range(5):
             Fh, Th = hydro(r.size, k)
             capi.dem_step_host(SHAPE, WALLS, hx, hu, ho, Fo, To, Fh, Th, r, dens, fixed=fixed,
-                               kn=KN, restitution=E, subcycles=SUB, gravity=G, threads=threads)
-        runs.append(np.concatenate([hx, hu, ho, Fo, To]))
+                               kn=KN, restitution=E, subcycles=SUB, gravity=G, threads=threads,
+                               history=hist)
+        runs.append(np.concatenate([hx, hu, ho, Fo, To, hist[2].reshape(-1, 3)]))
     assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
 
 

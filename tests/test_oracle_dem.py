@@ -89,3 +89,92 @@ def test_wall_bounce():
     x, u, _ = o.particles()
     assert abs(u[0, 0] / 0.02 - e) < 0.02 * e
     assert x[0, 0] > r
+
+
+def _damping(meff, kn, e):
+    le = math.log(e)
+    return -2.0 * le * math.sqrt(meff * kn) / math.sqrt(math.pi ** 2 + le * le)
+
+
+def test_tangential_history_of_a_spinning_contact():
+    """Eqs. 13-14 (reading W) at a contact whose surfaces slide at a constant
+    rate: two fixed, overlapping spheres, sphere 0 spinning.  The relative
+    surface velocity at the contact point is U_t = omega_0 x a_0 with the arm
+    a_0 = -(r_0 - delta/2) n, constant, so after S sub-steps the history is
+    S dt_p U_t and the contact force on sphere 0 is k_n delta n - k_t S dt_p U_t
+    - d_t U_t, with k_t = 2/7 k_n, d_t = 2/7 d_n; its torque is a_0 x F_t;
+    sphere 1 gets -F and the torque a_1 x (-F_t), a_1 = (r_1 - delta/2) n."""
+    kn, e, sub = 1e3, 0.9, 10
+    o = _dem(e=e, sub=sub)
+    x = np.array([[20.0, 21.0, 22.0], [26.7, 23.1, 21.4]])
+    r = np.array([3.5, 3.6])
+    rho = np.array([2.5, 1.8])
+    om = np.array([[1e-3, -2e-3, 3e-3], [0.0, 0.0, 0.0]])
+    o.set_particles(x, r, omega=om, density=rho, fixed=np.ones(2, np.uint8))
+    steps = 3
+    o.dem_only(steps)
+    F, T = o.contact()
+    d = x[0] - x[1]
+    dist = np.linalg.norm(d)
+    n = d / dist
+    delta = r.sum() - dist
+    assert delta > 0
+    m = rho * 4.0 / 3.0 * math.pi * r ** 3
+    dn = _damping(m[0] * m[1] / m.sum(), kn, e)
+    a0 = -(r[0] - delta / 2) * n
+    a1 = (r[1] - delta / 2) * n
+    Ut = np.cross(om[0], a0)
+    S = steps * sub
+    Ft = -(2.0 / 7.0) * kn * (S / sub) * Ut - (2.0 / 7.0) * dn * Ut
+    F0 = kn * delta * n + Ft
+    assert np.max(np.abs(F[0] - F0)) < 1e-12 * np.max(np.abs(F0))
+    assert np.max(np.abs(F[1] + F0)) < 1e-12 * np.max(np.abs(F0))
+    assert np.max(np.abs(T[0] - np.cross(a0, Ft))) < 1e-12 * np.max(np.abs(np.cross(a0, Ft)))
+    assert np.max(np.abs(T[1] - np.cross(a1, -Ft))) < 1e-12 * np.max(np.abs(np.cross(a1, Ft)))
+    # the spring part grows with the slid distance: twice the steps, about
+    # twice the history term
+    o.dem_only(steps)
+    F2, _ = o.contact()
+    Ft2 = F2[0] - kn * delta * n
+    assert np.allclose(Ft2, -(2.0 / 7.0) * kn * 2 * steps * Ut - (2.0 / 7.0) * dn * Ut,
+                       rtol=1e-12, atol=0)
+
+
+def test_tangential_contact_needs_sliding_and_balances_torques():
+    """A head-on collision without spin has no tangential motion: the model
+    with Eqs. 13-14 gives the normal-only result bit for bit.  In an oblique
+    collision with spin the contact forces and torques of a pair balance about
+    any point (the arms meet at the contact point): sum_i (x_i x F_i + T_i) = 0
+    at each sub-step, and the linear momentum is conserved."""
+    res = []
+    for kt in (0.0, 2.0 / 7.0):
+        o = Oracle(64, 64, 64, 0.6, kn=1e3, restitution=0.8, subcycles=10, dem=True,
+                   kt_ratio=kt)
+        o.set_particles(np.array([[20.0, 30.0, 30.0], [27.2, 30.0, 30.0]]), np.array([3.5, 3.5]),
+                        u=np.array([[2e-2, 0, 0], [-2e-2, 0, 0]]), density=np.array([2.5, 2.5]))
+        o.dem_only(6)
+        res.append(o.particles())
+    for a, b in zip(*res):
+        assert np.array_equal(a, b)
+    o = Oracle(64, 64, 64, 0.6, kn=1e3, restitution=0.8, subcycles=10, dem=True)
+    x = np.array([[20.0, 30.0, 30.0], [26.5, 32.1, 29.0]])
+    r = np.array([3.5, 3.2])
+    u = np.array([[2e-2, 4e-3, -1e-3], [-2e-2, -3e-3, 2e-3]])
+    om = np.array([[1e-3, -4e-3, 2e-3], [3e-3, 1e-3, -2e-3]])
+    rho = np.array([2.5, 2.0])
+    m = rho * 4.0 / 3.0 * math.pi * r ** 3
+    o.set_particles(x, r, u=u, omega=om, density=rho)
+    P0 = (m[:, None] * u).sum(axis=0)
+    touched = 0
+    for _ in range(12):
+        o.dem_only(1)
+        F, T = o.contact()
+        xp, up, wp = o.particles()
+        if np.max(np.abs(F)) > 0:
+            touched += 1
+            tot = np.cross(xp, F).sum(axis=0) + T.sum(axis=0)
+            scale = np.max(np.abs(np.cross(xp, F)))
+            assert np.max(np.abs(tot)) < 1e-12 * scale
+            assert np.max(np.abs(T)) > 1e-6 * np.max(np.abs(F))  # friction torques act
+    assert touched >= 1
+    assert np.max(np.abs((m[:, None] * up).sum(axis=0) - P0)) < 1e-14 * np.abs(m[:, None] * u).sum()
