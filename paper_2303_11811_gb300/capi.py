@@ -37,7 +37,7 @@ EXPORTS = [
     "psm_train_surrogate", "psm_mlp_samples", "psm_mlp_loss_grad", "psm_mlp_infer",
     "psm_set_timing", "psm_get_timings", "psm_last_launch_count", "psm_last_error",
     "psm_destroy", "psm_field_sums_noalloc", "psm_save", "psm_load", "psm_get_particle_count",
-    "psm_selftest_waits",
+    "psm_selftest_waits", "psm_get_slot_forces",
 ]
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -146,6 +146,8 @@ def lib():
     L.psm_load.restype = st
     L.psm_get_particle_count.argtypes = [P, ip]
     L.psm_get_particle_count.restype = st
+    L.psm_get_slot_forces.argtypes = [P, dp, dp]
+    L.psm_get_slot_forces.restype = st
     L.psm_selftest_waits.argtypes = [P, C.c_longlong]
     L.psm_selftest_waits.restype = st
     _lib = L
@@ -388,6 +390,14 @@ class Engine:
                                           p1.ctypes.data_as(ip), _dp(b1)))
         return (p0.reshape(self.shape), b0.reshape(self.shape), p1.reshape(self.shape),
                 b1.reshape(self.shape))
+
+    def slot_forces(self):
+        """Per-slot forces of the last step as dense (nz, ny, nx, 3) arrays
+        for slot 0 and slot 1 (psm_get_slot_forces)."""
+        F0 = np.empty(3 * self.N)
+        F1 = np.empty(3 * self.N)
+        self._check(self._L.psm_get_slot_forces(self.h, _dp(F0), _dp(F1)))
+        return F0.reshape(self.shape + (3,)), F1.reshape(self.shape + (3,))
 
     def check(self):
         m = C.c_double()

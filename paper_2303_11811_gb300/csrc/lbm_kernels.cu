@@ -1014,63 +1014,61 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
 // live cells' positions (r << 16 | x), uncovered cells first and covered
 // cells after, each group in cell order, with each covered cell's slot index
 // (-1 for an uncovered cell); hdr[0] = number of uncovered cells, hdr[1] =
-// number of live cells.  A warp-wide pass over the tile's coverage words:
-// counts, a scan over the words, then the entries.
+// number of live cells.  Two warp-wide passes over the tile's coverage words
+// (the number of uncovered cells, then the entries); the lanes load the words
+// 32 at a time and the rounds take them by shuffles.
 __device__ __forceinline__ void fp64_list_tile(const LbmParams& P, int tile, int nw,
                                                int* lst_cell, int* lst_slot, int* hdr,
                                                int lane) {
   const Grid& g = P.g;
-  const int tile_words = P.tile_rows * g.wpr;
+  const size_t word0 = (size_t)tile * P.tile_rows * g.wpr;
   const unsigned below = (1u << lane) - 1u;
-  // counts per word: lane w of each round of 32 words
-  int tot_u = 0, tot_c = 0;
-  for (int w0 = 0; w0 < nw; w0 += 32) {
-    int cu = 0, cc = 0;
-    for (int k = 0; k < 32 && w0 + k < nw; ++k) {
-      const int w = w0 + k;
-      const int r = (int)g.div_wpr.div((unsigned)w);
-      const int xr = (w - r * g.wpr) * 32 + lane;
-      const bool live = xr < g.nx;
-      const uint32_t m = P.mask ? __ldg(&P.mask[(size_t)tile * tile_words + w]) : 0u;
-      const bool cv = live && ((m >> lane) & 1u);
-      const int nu = __popc(__ballot_sync(0xffffffffu, live && !cv));
-      const int nc = __popc(__ballot_sync(0xffffffffu, cv));
-      if (lane == k) {
-        cu = nu;
-        cc = nc;
+  int pu = 0, pc = 0, tot_u = 0;
+  // two passes over the words (counts, then entries), 32 words at a time:
+  // lane k loads word w0 + k and the rounds take them by shuffles, so each
+  // round issues its loads together
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      pc = tot_u;  // the covered cells follow all uncovered ones
+      pu = 0;
+    }
+    for (int w0 = 0; w0 < nw; w0 += 32) {
+      const int kmax = min(32, nw - w0);
+      const uint32_t m_l = (P.mask && lane < kmax) ? __ldg(&P.mask[word0 + w0 + lane]) : 0u;
+      const int b_l = (P.mask && pass == 1 && lane < kmax) ? __ldg(&P.base[word0 + w0 + lane]) : 0;
+      for (int k = 0; k < kmax; ++k) {
+        const int w = w0 + k;
+        const int r = (int)g.div_wpr.div((unsigned)w);
+        const int xr = (w - r * g.wpr) * 32 + lane;
+        const bool live = xr < g.nx;
+        const uint32_t m = __shfl_sync(0xffffffffu, m_l, k);
+        const bool cv = live && ((m >> lane) & 1u);
+        const unsigned bu = __ballot_sync(0xffffffffu, live && !cv);
+        const unsigned bc = __ballot_sync(0xffffffffu, cv);
+        if (pass == 0) {
+          pu += __popc(bu);
+          continue;
+        }
+        const int base = __shfl_sync(0xffffffffu, b_l, k);
+        if (live) {
+          const int pos = cv ? pc + __popc(bc & below) : pu + __popc(bu & below);
+          lst_cell[pos] = (r << 16) | xr;
+          int e = -1;
+          if (cv) {
+            e = base + __popc(m & below);
+            if (e >= P.slot_cap) e = -1;  // never the case: the mapping sized the slots
+          }
+          lst_slot[pos] = e;
+        }
+        pu += __popc(bu);
+        pc += __popc(bc);
       }
     }
-    tot_u += __reduce_add_sync(0xffffffffu, (unsigned)cu);
-    tot_c += __reduce_add_sync(0xffffffffu, (unsigned)cc);
-  }
-  // entries: per word, the running positions of its first uncovered and
-  // first covered cell
-  int pu = 0, pc = tot_u;
-  for (int w = 0; w < nw; ++w) {
-    const int r = (int)g.div_wpr.div((unsigned)w);
-    const int xr = (w - r * g.wpr) * 32 + lane;
-    const bool live = xr < g.nx;
-    const size_t word = (size_t)tile * tile_words + w;
-    const uint32_t m = P.mask ? __ldg(&P.mask[word]) : 0u;
-    const bool cv = live && ((m >> lane) & 1u);
-    const unsigned bu = __ballot_sync(0xffffffffu, live && !cv);
-    const unsigned bc = __ballot_sync(0xffffffffu, cv);
-    if (live) {
-      const int pos = cv ? pc + __popc(bc & below) : pu + __popc(bu & below);
-      lst_cell[pos] = (r << 16) | xr;
-      int e = -1;
-      if (cv) {
-        e = __ldg(&P.base[word]) + __popc(m & below);
-        if (e >= P.slot_cap) e = -1;  // never the case: the mapping sized the slots
-      }
-      lst_slot[pos] = e;
-    }
-    pu += __popc(bu);
-    pc += __popc(bc);
+    if (pass == 0) tot_u = pu;
   }
   if (lane == 0) {
     hdr[0] = tot_u;
-    hdr[1] = tot_u + tot_c;
+    hdr[1] = pc;  // after the second pass: tot_u + covered cells
   }
 }
 

@@ -1407,6 +1407,28 @@ __global__ void dense_scatter_kernel(MapParams P, int* pid0, double* B0, int* pi
   }
 }
 
+// per-slot forces of the last collision (Eq. 21), in FP64, into dense
+// per-cell arrays (3 per cell; zero where the slot is empty)
+__global__ void dense_forces_kernel(MapParams P, double* F0, double* F1) {
+  const int n = slot_count(P);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_xyz(P.g, P.s.cell[e], x, y, z);
+    const long long c = (long long)x + (long long)P.g.nx * ((long long)y + (long long)P.g.ny * z);
+    const int2 pid = P.s.pid[e];
+    for (int sl = 0; sl < 2; ++sl) {
+      if ((sl ? pid.y : pid.x) < 0) continue;
+      const long long fo = 3 * ((long long)sl * P.s.cap + e);
+      double* out = (sl ? F1 : F0) + 3 * c;
+      for (int a = 0; a < 3; ++a) {
+        if (P.fp32) out[a] = (double)static_cast<const float*>(P.s.Fc)[fo + a];
+        else if (P.dfrec) out[a] = to_double(static_cast<const df*>(P.s.Fc)[fo + a]);
+        else out[a] = static_cast<const double*>(P.s.Fc)[fo + a];
+      }
+    }
+  }
+}
+
 unsigned grid_cap(long long n, int block) {
   long long b = (n + block - 1) / block;
   if (b > MAP_PARTIALS) b = MAP_PARTIALS;
@@ -1492,8 +1514,7 @@ int launch_weight_table(int n, double tau, int weighting, double* out, cudaStrea
 
 int launch_force_reduce(MapParams P, cudaStream_t s) {
   if (P.p.n == 0) return 0;
-  // FP32 form: the FP32 slot forces are summed in FP64 like the FP64 form's
-  if (P.fp32) force_reduce_kernel<float><<<P.p.n, RED_THREADS, 0, s>>>(P);
+  if (P.fp32) force_reduce_f32_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
   else if (P.dfrec) force_reduce_df_kernel<<<P.p.n, RED_THREADS, 0, s>>>(P);
   else force_reduce_kernel<double><<<P.p.n, RED_THREADS, 0, s>>>(P);
   return 1;
@@ -1508,6 +1529,14 @@ int launch_pack_particles(Particles p, cudaStream_t s) {
 int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s) {
   if (p.n == 0) return 0;
   wrap_particles_kernel<<<(p.n + 127) / 128, 128, 0, s>>>(g, p);
+  return 1;
+}
+
+int launch_slot_forces_to_dense(MapParams P, double* F0, double* F1, cudaStream_t s) {
+  const long long N = (long long)P.g.nx * P.g.ny * P.g.nz;
+  cudaMemsetAsync(F0, 0, sizeof(double) * 3 * N, s);
+  cudaMemsetAsync(F1, 0, sizeof(double) * 3 * N, s);
+  dense_forces_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P, F0, F1);
   return 1;
 }
 
