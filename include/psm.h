@@ -261,13 +261,15 @@ psm_status psm_set_pdfs(psm_ctx* ctx, const double* f);
 psm_status psm_get_slots(psm_ctx* ctx, int* pid0, double* B0, int* pid1, double* B1);
 
 /* Per-slot hydrodynamic forces of the last step (Eq. 21: B_i times the
- * momentum the solid operator of slot i takes from the cell), as dense
- * per-cell arrays in the slot order of psm_get_slots: F0, F1 (3*N each,
- * component-minor: F0[3 c + a]), converted to FP64 from the form's precision,
- * zero for an empty slot.  The per-particle sums of these (with the torque
- * arms of Eq. 22) are what psm_get_force_torque returns; the call lets a
- * caller check that reduction. */
-psm_status psm_get_slot_forces(psm_ctx* ctx, double* F0, double* F1);
+ * momentum the solid operator of slot i takes from the cell), with the
+ * mapping they belong to (the last step's, not remapped for particles moved
+ * since), as dense per-cell arrays: pid0, pid1 (N each, -1 for an empty
+ * slot) and F0, F1 (3*N each, component-minor: F0[3 c + a]), converted to
+ * FP64 from the form's precision, zero for an empty slot.  The per-particle
+ * sums of these, with the torque arms of Eq. 22 taken from the particle
+ * positions the mapping used, are what psm_get_force_torque returns; the
+ * call lets a caller check that reduction. */
+psm_status psm_get_slot_forces(psm_ctx* ctx, int* pid0, int* pid1, double* F0, double* F1);
 
 /* FP64 sums over the stored PDFs: mass sum_x sum_q f_q and momentum
  * sum_x sum_q f_q c_q (3 values); fixed summation order. */

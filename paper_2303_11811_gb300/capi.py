@@ -146,7 +146,7 @@ def lib():
     L.psm_load.restype = st
     L.psm_get_particle_count.argtypes = [P, ip]
     L.psm_get_particle_count.restype = st
-    L.psm_get_slot_forces.argtypes = [P, dp, dp]
+    L.psm_get_slot_forces.argtypes = [P, ip, ip, dp, dp]
     L.psm_get_slot_forces.restype = st
     L.psm_selftest_waits.argtypes = [P, C.c_longlong]
     L.psm_selftest_waits.restype = st
@@ -392,12 +392,18 @@ class Engine:
                 b1.reshape(self.shape))
 
     def slot_forces(self):
-        """Per-slot forces of the last step as dense (nz, ny, nx, 3) arrays
-        for slot 0 and slot 1 (psm_get_slot_forces)."""
+        """Per-slot forces of the last step with the mapping they belong to
+        (psm_get_slot_forces): pid0, pid1 (nz, ny, nx) and F0, F1
+        (nz, ny, nx, 3)."""
+        p0 = np.empty(self.N, np.int32)
+        p1 = np.empty(self.N, np.int32)
         F0 = np.empty(3 * self.N)
         F1 = np.empty(3 * self.N)
-        self._check(self._L.psm_get_slot_forces(self.h, _dp(F0), _dp(F1)))
-        return F0.reshape(self.shape + (3,)), F1.reshape(self.shape + (3,))
+        ipp = C.POINTER(C.c_int)
+        self._check(self._L.psm_get_slot_forces(self.h, p0.ctypes.data_as(ipp),
+                                                p1.ctypes.data_as(ipp), _dp(F0), _dp(F1)))
+        return (p0.reshape(self.shape), p1.reshape(self.shape),
+                F0.reshape(self.shape + (3,)), F1.reshape(self.shape + (3,)))
 
     def check(self):
         m = C.c_double()

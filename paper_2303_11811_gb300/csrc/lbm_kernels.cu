@@ -965,47 +965,62 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
       if (B > T(1)) B = T(1);
       omB = T(1) - B;
     }
+    // slot 0 (zero weight on an uncovered lane) joins the fluid update of each
+    // pair: with the fluid change omB (ds +- da) and the solid operator's
+    // symmetric part BdS = B_0 w (9/2 (cv^2 - cu^2) - 3/2 dU2) and
+    // antisymmetric part B_0 (3 w (cu + cv) - a_k), a pair changes by
+    // SYM +- ANT with SYM = omB hp s_k + (omB X_k + BdS) and
+    // ANT = (omB hm - B_0) a_k + (omB Y_k + 3 w B_0 (cu + cv))
+    const T Vx = r0[0], Vy = r0[1], Vz = r0[2], B0 = r0[3];
+    const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+    const T BdU = B0 * dU2;
     {
       const T dl = h[CC_NWP] * d[0] + (h[CC_WPW0] * base0 + h[CC_H] * Uf);
-      d[0] += omB * dl;
+      d[0] = (d[0] + omB * dl) + (T(-1.5) * w0<T>()) * BdU;
     }
+    const T c45[2] = {(T(4.5) * wk<T>(0)) * B0, (T(4.5) * wk<T>(3)) * B0};
+    const T c3[2] = {(T(3) * wk<T>(0)) * B0, (T(3) * wk<T>(3)) * B0};
+    const T cd[2] = {(T(-1.5) * wk<T>(0)) * BdU, (T(-1.5) * wk<T>(3)) * BdU};
+    const T as = omB * h[CC_MHWP];
+    const T aa = omB * h[CC_MHWM] - B0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       T pk[4];
       ld4(cf->pair[k], pk);
+      const int cl = k < 3 ? 0 : 1;
       const T cu = cdot<T>(k, Ux, Uy, Uz);
-      const T ds = h[CC_MHWP] * sk[k] + ((pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1));
-      const T da = h[CC_MHWM] * a[k] + (pk[3] * cu + pk[1]);
-      d[2 * k + 1] += omB * (ds + da);
-      d[2 * k + 2] += omB * (ds - da);
+      const T cv = cdot<T>(k, Vx, Vy, Vz);
+      const T Sv = cv + cu;
+      const T BdS = c45[cl] * ((cv - cu) * Sv) + cd[cl];
+      const T X = (pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1);
+      const T Y = pk[3] * cu + pk[1];
+      const T SYM = as * sk[k] + (omB * X + BdS);
+      const T ANT = aa * a[k] + (omB * Y + c3[cl] * Sv);
+      d[2 * k + 1] += SYM + ANT;
+      d[2 * k + 2] += SYM - ANT;
     }
-    if (cov) {
-      // solid operator of each slot: symmetric part B_i w_k (9/2 (cv^2 - cu^2)
-      // - 3/2 dU2), antisymmetric part B_i (3 w_k (cu + cv) - a_k)
-#pragma unroll 1
-      for (int sl = 0; sl < 2; ++sl) {
-        if (sl && !has1) continue;
-        const T Vx = sl ? r1[0] : r0[0], Vy = sl ? r1[1] : r0[1], Vz = sl ? r1[2] : r0[2];
-        const T Bi = sl ? r1[3] : r0[3];
-        const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
-        const T BdU = Bi * dU2;
-        d[0] += (T(-1.5) * w0<T>()) * BdU;
-        const T c45[2] = {(T(4.5) * wk<T>(0)) * Bi, (T(4.5) * wk<T>(3)) * Bi};
-        const T c3[2] = {(T(3) * wk<T>(0)) * Bi, (T(3) * wk<T>(3)) * Bi};
-        const T cd[2] = {(T(-1.5) * wk<T>(0)) * BdU, (T(-1.5) * wk<T>(3)) * BdU};
+    if (cov) slot_force<T>(P, e, 0, B0, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
+    // slot 1 (a cell shared by two particles: rare), on its own
+    if (__any_sync(0xffffffffu, has1) && has1) {
+      const T Wx = r1[0], Wy = r1[1], Wz = r1[2], B1 = r1[3];
+      const T eU2 = (Wx * Wx + Wy * Wy + Wz * Wz) - uu;
+      const T BeU = B1 * eU2;
+      d[0] += (T(-1.5) * w0<T>()) * BeU;
+      const T e45[2] = {(T(4.5) * wk<T>(0)) * B1, (T(4.5) * wk<T>(3)) * B1};
+      const T e3[2] = {(T(3) * wk<T>(0)) * B1, (T(3) * wk<T>(3)) * B1};
+      const T ed[2] = {(T(-1.5) * wk<T>(0)) * BeU, (T(-1.5) * wk<T>(3)) * BeU};
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const int cl = k < 3 ? 0 : 1;
-          const T cu = cdot<T>(k, Ux, Uy, Uz);
-          const T cv = cdot<T>(k, Vx, Vy, Vz);
-          const T Sv = cv + cu;
-          const T BdS = c45[cl] * ((cv - cu) * Sv) + cd[cl];
-          const T BA = c3[cl] * Sv - Bi * a[k];
-          d[2 * k + 1] += BdS + BA;
-          d[2 * k + 2] += BdS - BA;
-        }
-        slot_force<T>(P, e, sl, Bi, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
+      for (int k = 0; k < 9; ++k) {
+        const int cl = k < 3 ? 0 : 1;
+        const T cu = cdot<T>(k, Ux, Uy, Uz);
+        const T cv = cdot<T>(k, Wx, Wy, Wz);
+        const T Sv = cv + cu;
+        const T BdS = e45[cl] * ((cv - cu) * Sv) + ed[cl];
+        const T BA = e3[cl] * Sv - B1 * a[k];
+        d[2 * k + 1] += BdS + BA;
+        d[2 * k + 2] += BdS - BA;
       }
+      slot_force<T>(P, e, 1, B1, Ux - Wx, Uy - Wy, Uz - Wz, h + CC_F);
     }
   }
 }
@@ -1168,7 +1183,11 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
     const int* lst_slot = ls + 4 + C;
     const int row0 = tile * TR;
     const int nch = (L + 31) / 32;
-    for (int ch = warp; ch < nch; ch += BULK_CONSUMER_WARPS) {
+    // the covered chunks come last in every tile: the chunk a warp starts
+    // with turns by 3 from tile to tile (3 and 8 are coprime), so every
+    // warp takes its share of them and none runs ahead of the ring
+    const int ch0 = (warp + 3 * it) % BULK_CONSUMER_WARPS;
+    for (int ch = ch0; ch < nch; ch += BULK_CONSUMER_WARPS) {
       const int i = ch * 32 + lane;
       const bool active = i < L;
       const int ent = lst_cell[active ? i : L - 1];

@@ -1409,13 +1409,15 @@ __global__ void dense_scatter_kernel(MapParams P, int* pid0, double* B0, int* pi
 
 // per-slot forces of the last collision (Eq. 21), in FP64, into dense
 // per-cell arrays (3 per cell; zero where the slot is empty)
-__global__ void dense_forces_kernel(MapParams P, double* F0, double* F1) {
+__global__ void dense_forces_kernel(MapParams P, int* pid0, int* pid1, double* F0, double* F1) {
   const int n = slot_count(P);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     int x, y, z;
     cell_xyz(P.g, P.s.cell[e], x, y, z);
     const long long c = (long long)x + (long long)P.g.nx * ((long long)y + (long long)P.g.ny * z);
     const int2 pid = P.s.pid[e];
+    pid0[c] = pid.x;
+    pid1[c] = pid.y;
     for (int sl = 0; sl < 2; ++sl) {
       if ((sl ? pid.y : pid.x) < 0) continue;
       const long long fo = 3 * ((long long)sl * P.s.cap + e);
@@ -1532,11 +1534,14 @@ int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s) {
   return 1;
 }
 
-int launch_slot_forces_to_dense(MapParams P, double* F0, double* F1, cudaStream_t s) {
+int launch_slot_forces_to_dense(MapParams P, int* pid0, int* pid1, double* F0, double* F1,
+                                cudaStream_t s) {
   const long long N = (long long)P.g.nx * P.g.ny * P.g.nz;
+  cudaMemsetAsync(pid0, 0xff, sizeof(int) * N, s);  // -1
+  cudaMemsetAsync(pid1, 0xff, sizeof(int) * N, s);
   cudaMemsetAsync(F0, 0, sizeof(double) * 3 * N, s);
   cudaMemsetAsync(F1, 0, sizeof(double) * 3 * N, s);
-  dense_forces_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P, F0, F1);
+  dense_forces_kernel<<<grid_cap(P.s.cap, 256), 256, 0, s>>>(P, pid0, pid1, F0, F1);
   return 1;
 }
 

@@ -1094,24 +1094,29 @@ psm_status psm_get_macroscopic(psm_ctx* c, double* rho, double* u) {
   return PSM_OK;
 }
 
-psm_status psm_get_slot_forces(psm_ctx* c, double* F0, double* F1) {
-  if (!c || !F0 || !F1) return PSM_ERR_ARG;
+psm_status psm_get_slot_forces(psm_ctx* c, int* pid0, int* pid1, double* F0, double* F1) {
+  if (!c || !pid0 || !pid1 || !F0 || !F1) return PSM_ERR_ARG;
   const size_t N = (size_t)c->g.nx * c->g.ny * c->g.nz;
   if (c->p.n == 0) {
+    for (size_t i = 0; i < N; ++i) pid0[i] = pid1[i] = -1;
     std::memset(F0, 0, sizeof(double) * 3 * N);
     std::memset(F1, 0, sizeof(double) * 3 * N);
     return PSM_OK;
   }
   psm_status st = read_status(c);
   if (st != PSM_OK) return st;
-  double* d = static_cast<double*>(dalloc(c, sizeof(double) * 6 * N));
+  double* d = static_cast<double*>(dalloc(c, sizeof(double) * 7 * N));
   if (!d) return fail(c, PSM_ERR_OOM, "allocator returned NULL");
-  launch_slot_forces_to_dense(map_params(c), d, d + 3 * N, c->stream);
+  int* dp0 = reinterpret_cast<int*>(d + 6 * N);
+  int* dp1 = dp0 + N;
+  launch_slot_forces_to_dense(map_params(c), dp0, dp1, d, d + 3 * N, c->stream);
   cudaError_t e = cudaMemcpyAsync(F0, d, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost,
                                   c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(F1, d + 3 * N, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost,
                         c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pid0, dp0, 4 * N, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(pid1, dp1, 4 * N, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   dfree(c, d);
   if (e != cudaSuccess) return fail(c, PSM_ERR_CUDA, cudaGetErrorString(e));

@@ -263,7 +263,8 @@ int launch_weight_table(int n, double tau, int weighting, double* out, cudaStrea
 int launch_force_reduce_atomic_finish(MapParams P, cudaStream_t s);
 int launch_pack_particles(Particles p, cudaStream_t s);
 int launch_wrap_particles(const Grid& g, Particles p, cudaStream_t s);
-int launch_slot_forces_to_dense(MapParams P, double* F0, double* F1, cudaStream_t s);
+int launch_slot_forces_to_dense(MapParams P, int* pid0, int* pid1, double* F0, double* F1,
+                                cudaStream_t s);
 int launch_slots_to_dense(MapParams P, int* pid0, double* B0, int* pid1, double* B1,
                           cudaStream_t s);
 
