@@ -626,13 +626,17 @@ def main():
     bytes_psm = bytes_lbm + ncov * (24 if esz == 8 else 16)
     hbm, peak_kind = peaks()
     hbm_achieved = bytes_psm / (lbm_ms * 1e-3) / 1e9
-    staged = fp64 or (args.precision == "fp32" and args.streaming == "aa")
-    kname = ("lbm_bulk_kernel" if staged else "lbm_kernel") + \
-        f"<{ {'fp64': 'double', 'fp32': 'float', 'df64': 'df'}[args.precision] },{args.streaming}>"
+    # the collision kernel of the form: FP64 on compacted warps, FP32 AA
+    # staged, FP32 pull and double-float one cell per thread
+    if fp64:
+        kbase, kname = "lbm_fp64_kernel", f"lbm_fp64_kernel<{args.streaming}>"
+    else:
+        kbase = "lbm_bulk_kernel" if args.streaming == "aa" and args.precision == "fp32" \
+            else "lbm_kernel"
+        kname = kbase + f"<{ {'fp32': 'float', 'df64': 'df'}[args.precision] },{args.streaming}>"
     traffic = profiled_traffic(os.path.join(ROOT, "paper_2303_11811_gb300", "csrc",
                                             "lbm_kernels.cu"),
-                               f"{'lbm_bulk_kernel' if staged else 'lbm_kernel'}_"
-                               f"{args.precision}{args.streaming}_{args.workload}", cells)
+                               f"{kbase}_{args.precision}{args.streaming}_{args.workload}", cells)
     hbm_part = {"achieved": hbm_achieved, "peak": hbm, "unit": "GB/s",
                 "frac": hbm_achieved / hbm, "peak_source": peak_kind,
                 "bytes_per_launch": bytes_psm, "lbm_only_bytes_per_launch": bytes_lbm}

@@ -24,6 +24,9 @@ namespace {
 
 constexpr double HALF_SQRT3 = kHalfSqrt3;
 constexpr int MAP_THREADS = 256;
+// threads of a fill block (one block per particle) and blocks per SM
+constexpr int FILL_THREADS = 256;
+constexpr int FILL_MIN_BLOCKS = 3;
 constexpr int RED_THREADS = 128;
 constexpr int SCAN_THREADS = 1024;
 
@@ -602,7 +605,7 @@ __device__ __forceinline__ int net_class(const Grid& g, const Box& b, const Cell
 enum { REC_FP64 = 0, REC_FP32 = 1, REC_DF = 2 };
 
 template <int NS, int REC>
-__global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
+__global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(MapParams P) {
   __shared__ double s64[16];
   __shared__ float s32[16];
   __shared__ Box sbox;
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   const Box b = sbox;
   const bool tables = b.n[0] <= FILL_AXIS && b.n[1] <= FILL_AXIS && b.n[2] <= FILL_AXIS;
   if (tables) {
-    for (int t = threadIdx.x; t < 3 * FILL_AXIS; t += MAP_THREADS) {
+    for (int t = threadIdx.x; t < 3 * FILL_AXIS; t += FILL_THREADS) {
       const int a = t / FILL_AXIS, k = t - a * FILL_AXIS;
       if (k < b.n[a]) {
         const double d = ((double)(b.lo[a] + k) + 0.5) - b.xp[a];
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     if (threadIdx.x == 0) net_cnt = 0;
     __syncthreads();
     int mine = 0;
-    for (int k = threadIdx.x; k < cnt; k += MAP_THREADS) {
+    for (int k = threadIdx.x; k < cnt; k += FILL_THREADS) {
       CellHit h;
       cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
       mine += net_class(P.g, b, h) == 0;
@@ -675,7 +678,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
   const double r2 = b.r * b.r;
   // 8^3 sampling iterates whole warps (its counts are taken by all lanes);
   // the other modes give each thread its own cells
-  for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += MAP_THREADS) {
+  for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += FILL_THREADS) {
     const int k = NS == 8 ? k0 + lane : k0;
     bool ok = NS == 8 ? k < cnt : true;
     CellHit h;
@@ -856,7 +859,7 @@ __global__ void __launch_bounds__(MAP_THREADS, 3) fill_kernel(MapParams P) {
     // cells counted but not listed (slot overflow) leave empty items
     __syncthreads();
     const long long end = (long long)net_base + net_cnt;
-    for (long long k = net_next + threadIdx.x; k < end && k < P.mlp_cap; k += MAP_THREADS) {
+    for (long long k = net_next + threadIdx.x; k < end && k < P.mlp_cap; k += FILL_THREADS) {
       reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       P.mlp_lin[k] = 0.f;
       P.mlp_work[k] = -1;
@@ -1439,10 +1442,10 @@ unsigned grid_cap(long long n, int block) {
 
 template <int REC>
 void launch_fill(const MapParams& P, bool mlp, cudaStream_t s) {
-  if (mlp) fill_kernel<-1, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-  else if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-  else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
-  else fill_kernel<0, REC><<<P.p.n, MAP_THREADS, 0, s>>>(P);
+  if (mlp) fill_kernel<-1, REC><<<P.p.n, FILL_THREADS, 0, s>>>(P);
+  else if (P.eps_mode == 0 && P.eps_n == 4) fill_kernel<4, REC><<<P.p.n, FILL_THREADS, 0, s>>>(P);
+  else if (P.eps_mode == 0 && P.eps_n == 8) fill_kernel<8, REC><<<P.p.n, FILL_THREADS, 0, s>>>(P);
+  else fill_kernel<0, REC><<<P.p.n, FILL_THREADS, 0, s>>>(P);
 }
 
 int map_common(MapParams P, cudaStream_t s, bool mlp) {
