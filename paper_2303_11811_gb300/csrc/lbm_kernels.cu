@@ -494,6 +494,37 @@ __device__ __forceinline__ bool outflow_layer(const Grid& g, int z) {
   return (z == 0 && g.zface[0] == FACE_OUTFLOW) || (z == g.nz - 1 && g.zface[1] == FACE_OUTFLOW);
 }
 
+// pull streaming across open z faces: the links of a cell in the first or
+// last layer that leave through an open face take the face's value, from the
+// bounced-back deviation the pull loaded for them (d[q] of a link whose
+// source is outside the grid).  Applied after all loads of the cell, so that
+// the loads of every other cell stay unconditional selects.
+template <typename T, int WALLS>
+__device__ __forceinline__ void apply_open_faces(const LbmParams& P, const NbrT<WALLS>& nb, int z,
+                                                 int cell, T* d) {
+  if constexpr ((WALLS & 4) != 0) {
+    const Grid& g = P.g;
+    if (!((z == 0 && g.zface[0] >= FACE_INFLOW) || (z == g.nz - 1 && g.zface[1] >= FACE_INFLOW)))
+      return;
+    T ub[3] = {T(0), T(0), T(0)};
+    if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int cx = ckx(k), cy = cky(k), cz = ckz(k);
+      if (cz == 0) continue;
+      const int qa = 2 * k + 1, qb = 2 * k + 2;
+      if (!nb.ok(-cx, -cy, -cz)) {
+        const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
+        if (t) d[qa] = open_value<T>(P.bc, t, qa, d[qa], ub);
+      }
+      if (!nb.ok(cx, cy, cz)) {
+        const int t = open_face<WALLS>(g, nb, cx, cy, cz);
+        if (t) d[qb] = open_value<T>(P.bc, t, qb, d[qb], ub);
+      }
+    }
+  }
+}
+
 // store of the collided PDFs (pull: own cell of the other buffer; AA even:
 // swapped slots of the own cell; AA odd: the neighbours' slots, or the own
 // cell's opposite slot across a wall)
@@ -592,10 +623,6 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
 #define SRC(q) static_cast<const T*>(P.srcq[q])
   // ---- streaming (Eq. 2 read backwards; halfway bounce-back at walls, the
   // open faces' values across open z faces)
-  T ub[3] = {T(0), T(0), T(0)};
-  if constexpr (MODE == 0 && (WALLS & 4) != 0) {
-    if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
-  }
   T d[Q];
   d[0] = ld(SRC(0) + cell);
 #pragma unroll
@@ -603,20 +630,8 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
     const int cx = ckx(k), cy = cky(k), cz = ckz(k);
     const int qa = 2 * k + 1, qb = 2 * k + 2;
     if (MODE == 0) {         // pull from the other buffer
-      if (nb.ok(-cx, -cy, -cz)) {
-        d[qa] = ld(SRC(qa) + nb.idx(-cx, -cy, -cz));
-      } else {
-        const T bb = ld(SRC(qb) + cell);
-        const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
-        d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
-      }
-      if (nb.ok(cx, cy, cz)) {
-        d[qb] = ld(SRC(qb) + nb.idx(cx, cy, cz));
-      } else {
-        const T bb = ld(SRC(qa) + cell);
-        const int t = open_face<WALLS>(g, nb, cx, cy, cz);
-        d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
-      }
+      d[qa] = nb.ok(-cx, -cy, -cz) ? ld(SRC(qa) + nb.idx(-cx, -cy, -cz)) : ld(SRC(qb) + cell);
+      d[qb] = nb.ok(cx, cy, cz) ? ld(SRC(qb) + nb.idx(cx, cy, cz)) : ld(SRC(qa) + cell);
     } else if (MODE == 1) {  // AA even: own cell
       d[qa] = ld(SRC(qa) + cell);
       d[qb] = ld(SRC(qb) + cell);
@@ -626,6 +641,7 @@ __global__ void __launch_bounds__(LBM_THREADS, kFP64<T> ? 1 : (sizeof(T) == 4 ? 
     }
   }
 
+  if constexpr (MODE == 0) apply_open_faces<T, WALLS>(P, nb, z, cell, d);
 #undef SRC
   psm_collide<T, false>(P, warp, lane, live, d,
                         reinterpret_cast<SolidSmem<T>*>(lbm_smem) + (threadIdx.x >> 5), m, eb,
@@ -844,10 +860,6 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
       const int cell = nb.idx(0, 0, 0);
       const int xm = x == 0 ? g.nx - 1 : x - 1, xq = x == g.nx - 1 ? 0 : x + 1;
       const T* sr = st + (size_t)r * nxp;  // direction q of this row at sr[q * C]
-      T ub[3] = {T(0), T(0), T(0)};
-      if constexpr (MODE == 0 && (WALLS & 4) != 0) {
-        if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
-      }
       T d[Q];
       d[0] = sr[x];
 #pragma unroll
@@ -857,20 +869,8 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
         const int xa = cx > 0 ? xm : (cx < 0 ? xq : x);  // x - c_x
         const int xb = cx > 0 ? xq : (cx < 0 ? xm : x);  // x + c_x
         if (MODE == 0) {
-          if (nb.ok(-cx, -cy, -cz)) {
-            d[qa] = sr[qa * C + xa];
-          } else {
-            const T bb = ld(SRC(qb) + cell);
-            const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
-            d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
-          }
-          if (nb.ok(cx, cy, cz)) {
-            d[qb] = sr[qb * C + xb];
-          } else {
-            const T bb = ld(SRC(qa) + cell);
-            const int t = open_face<WALLS>(g, nb, cx, cy, cz);
-            d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
-          }
+          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qb) + cell);
+          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qa) + cell);
         } else if (MODE == 1) {
           d[qa] = sr[qa * C + x];
           d[qb] = sr[qb * C + x];
@@ -879,6 +879,7 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
           d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qb) + cell);
         }
       }
+      if constexpr (MODE == 0) apply_open_faces<T, WALLS>(P, nb, z, cell, d);
       psm_collide<T, ahead>(P, word, lane, live, d, solid, m, eb, &R);
       if (live) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
     }
@@ -893,20 +894,31 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
 // instructions.  Two things cost instructions on warps of 32 consecutive
 // cells: a warp with a covered cell weights every lane's fluid change by
 // (1 - B), and the solid operator of a few covered lanes keeps the whole warp
-// busy.  So each tile's cells are listed with the uncovered cells first and
-// the covered ones after, and warps take 32 list entries at a time: a warp of
-// uncovered cells runs the particle-free form below, a warp of covered cells
-// does every lane's own solid operators; at most one warp per tile is mixed.
+// busy.  So each tile's cells are listed in three groups (uncovered cells,
+// covered cells, covered cells of one particle with B = 1) and warps take 32
+// list entries at a time: a warp of uncovered cells runs the particle-free
+// form, a warp of full cells the solid operator alone, any other warp every
+// lane's own fluid change and solid operators; at most two warps per tile
+// are mixed.
+enum { CK_UNCOVERED = 0, CK_MIXED = 1, CK_FULL = 2 };
 
-// FP64 collision of one cell (Eqs. 3-8 and 17-21).  UNIFORM: all lanes of
-// the warp are uncovered (B = 0); a pair's update is then written as
-// d_q' = S_k + A_k, d_qbar' = S_k - A_k with S_k = (1 - omega+)/2 s_k + X_k,
-// A_k = (1 - omega-)/2 a_k + Y_k, X_k = (9/2 omega+ w c.U + G_k) c.U + C_c,
-// Y_k = 3 omega- w c.U + F_k: seven FP64 operations per pair instead of
-// nine.  Otherwise a covered lane (cov, slot index e) reads its slot
-// records, weights the fluid change by 1 - B and adds the solid operator of
-// each of its slots (Eq. 19) and writes the slots' forces (Eq. 21).
-template <bool UNIFORM>
+// FP64 collision of one cell (Eqs. 3-8 and 17-21).
+// CK_UNCOVERED: all lanes of the warp are uncovered (B = 0); a pair's update
+// is written as d_q' = S_k + A_k, d_qbar' = S_k - A_k with
+// S_k = (1 - omega+)/2 s_k + X_k, A_k = (1 - omega-)/2 a_k + Y_k,
+// X_k = (9/2 omega+ w c.U + G_k) c.U + C_c, Y_k = 3 omega- w c.U + F_k: seven
+// FP64 operations per pair instead of nine.
+// CK_FULL: every lane is a covered cell of one particle with B = 1; the fluid
+// change vanishes and the solid operator (Eq. 19) swaps the pair and adds the
+// difference of the equilibria: d_q' = d_qbar + (BdS + 3 w (cu + cv)),
+// d_qbar' = d_q + (BdS - 3 w (cu + cv)), BdS = w (9/2 (cv^2 - cu^2) -
+// 3/2 (V^2 - U^2)).
+// CK_MIXED: a covered lane (cov, slot index e) reads its slot records,
+// weights the fluid change by 1 - B and adds the solid operator of each of
+// its slots (Eq. 19); an uncovered lane has B = 0.
+// Covered lanes write their slots' forces (Eq. 21).
+
+template <int KIND>
 __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool cov, int e) {
   using T = double;
   const CollideCoef<T>* cf = &P.sc->d;
@@ -935,7 +947,7 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
   const T C0 = h[CC_WPW] * base0 + h[CC_H + 1] * Uf;
   const T C1 = h[CC_WPW + 1] * base0 + h[CC_H + 2] * Uf;
 
-  if constexpr (UNIFORM) {
+  if constexpr (KIND == CK_UNCOVERED) {
     T tl[4];
     ld4(cf->tail, tl);
     d[0] = fma(tl[0], d[0], h[CC_WPW0] * base0 + h[CC_H] * Uf);
@@ -951,6 +963,26 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
       d[2 * k + 1] = Sk + Ak;
       d[2 * k + 2] = Sk - Ak;
     }
+  } else if constexpr (KIND == CK_FULL) {
+    T r0[4] = {T(0), T(0), T(0), T(0)};
+    if (cov) ld4(static_cast<const T*>(P.slot_V) + 4LL * e, r0);
+    const T Vx = r0[0], Vy = r0[1], Vz = r0[2];
+    const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
+    d[0] += (T(-1.5) * w0<T>()) * dU2;
+    const T cd[2] = {(T(-1.5) * wk<T>(0)) * dU2, (T(-1.5) * wk<T>(3)) * dU2};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int cl = k < 3 ? 0 : 1;
+      const T cu = cdot<T>(k, Ux, Uy, Uz);
+      const T cv = cdot<T>(k, Vx, Vy, Vz);
+      const T Sv = cv + cu;
+      const T BdS = (T(4.5) * wk<T>(cl == 0 ? 0 : 3)) * ((cv - cu) * Sv) + cd[cl];
+      const T t = (T(3) * wk<T>(cl == 0 ? 0 : 3)) * Sv;
+      const T dq = d[2 * k + 1];
+      d[2 * k + 1] = d[2 * k + 2] + (BdS + t);
+      d[2 * k + 2] = dq + (BdS - t);
+    }
+    if (cov) slot_force<T>(P, e, 0, T(1), Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
   } else {
     // the cell's slots; the second one's record is read only when present
     T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
@@ -968,9 +1000,10 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
     // slot 0 (zero weight on an uncovered lane) joins the fluid update of each
     // pair: with the fluid change omB (ds +- da) and the solid operator's
     // symmetric part BdS = B_0 w (9/2 (cv^2 - cu^2) - 3/2 dU2) and
-    // antisymmetric part B_0 (3 w (cu + cv) - a_k), a pair changes by
-    // SYM +- ANT with SYM = omB hp s_k + (omB X_k + BdS) and
-    // ANT = (omB hm - B_0) a_k + (omB Y_k + 3 w B_0 (cu + cv))
+    // antisymmetric part B_0 (3 w (cu + cv) - a_k), the pair becomes
+    // d_q' = SYM + ANT, d_qbar' = SYM - ANT with
+    // SYM = (1/2 + omB hp) s_k + (omB X_k + BdS) and
+    // ANT = (1/2 + omB hm - B_0) a_k + (omB Y_k + 3 w B_0 (cu + cv))
     const T Vx = r0[0], Vy = r0[1], Vz = r0[2], B0 = r0[3];
     const T dU2 = (Vx * Vx + Vy * Vy + Vz * Vz) - uu;
     const T BdU = B0 * dU2;
@@ -981,8 +1014,8 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
     const T c45[2] = {(T(4.5) * wk<T>(0)) * B0, (T(4.5) * wk<T>(3)) * B0};
     const T c3[2] = {(T(3) * wk<T>(0)) * B0, (T(3) * wk<T>(3)) * B0};
     const T cd[2] = {(T(-1.5) * wk<T>(0)) * BdU, (T(-1.5) * wk<T>(3)) * BdU};
-    const T as = omB * h[CC_MHWP];
-    const T aa = omB * h[CC_MHWM] - B0;
+    const T as = omB * h[CC_MHWP] + T(0.5);
+    const T aa = omB * h[CC_MHWM] + (T(0.5) - B0);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       T pk[4];
@@ -996,8 +1029,8 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
       const T Y = pk[3] * cu + pk[1];
       const T SYM = as * sk[k] + (omB * X + BdS);
       const T ANT = aa * a[k] + (omB * Y + c3[cl] * Sv);
-      d[2 * k + 1] += SYM + ANT;
-      d[2 * k + 2] += SYM - ANT;
+      d[2 * k + 1] = SYM + ANT;
+      d[2 * k + 2] = SYM - ANT;
     }
     if (cov) slot_force<T>(P, e, 0, B0, Ux - Vx, Uy - Vy, Uz - Vz, h + CC_F);
     // slot 1 (a cell shared by two particles: rare), on its own
@@ -1026,47 +1059,58 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
 }
 
 // The producer warp lists the cells of a tile into the tile's stage: the
-// live cells' positions (r << 16 | x), uncovered cells first and covered
-// cells after, each group in cell order, with each covered cell's slot index
-// (-1 for an uncovered cell); hdr[0] = number of uncovered cells, hdr[1] =
-// number of live cells.  Two warp-wide passes over the tile's coverage words
-// (the number of uncovered cells, then the entries); the lanes load the words
-// 32 at a time and the rounds take them by shuffles.
+// live cells' positions (r << 16 | x) in three groups, each in cell order:
+// uncovered cells, covered cells, and covered cells of one particle with
+// B = 1 (the full mask), with each covered cell's slot index (-1 for an
+// uncovered cell); hdr[0] = number of uncovered cells, hdr[1] = number of
+// live cells, hdr[2] = index of the first cell of the third group.  Two
+// warp-wide passes over the tile's coverage words (the group sizes, then the
+// entries); the lanes load the words 32 at a time and the rounds take them by
+// shuffles.
 __device__ __forceinline__ void fp64_list_tile(const LbmParams& P, int tile, int nw,
                                                int* lst_cell, int* lst_slot, int* hdr,
                                                int lane) {
   const Grid& g = P.g;
   const size_t word0 = (size_t)tile * P.tile_rows * g.wpr;
   const unsigned below = (1u << lane) - 1u;
-  int pu = 0, pc = 0, tot_u = 0;
+  int pu = 0, pc = 0, pf = 0, tot_u = 0, tot_c = 0;
   // two passes over the words (counts, then entries), 32 words at a time:
   // lane k loads word w0 + k and the rounds take them by shuffles, so each
   // round issues its loads together
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
       pc = tot_u;  // the covered cells follow all uncovered ones
+      pf = tot_u + tot_c;  // and the full ones follow them
       pu = 0;
     }
     for (int w0 = 0; w0 < nw; w0 += 32) {
       const int kmax = min(32, nw - w0);
-      const uint32_t m_l = (P.mask && lane < kmax) ? __ldg(&P.mask[word0 + w0 + lane]) : 0u;
-      const int b_l = (P.mask && pass == 1 && lane < kmax) ? __ldg(&P.base[word0 + w0 + lane]) : 0;
+      const bool own = P.mask && lane < kmax;
+      const uint32_t m_l = own ? __ldg(&P.mask[word0 + w0 + lane]) : 0u;
+      const uint32_t f_l = (own && P.full) ? __ldg(&P.full[word0 + w0 + lane]) : 0u;
+      const int b_l = (own && pass == 1) ? __ldg(&P.base[word0 + w0 + lane]) : 0;
       for (int k = 0; k < kmax; ++k) {
         const int w = w0 + k;
         const int r = (int)g.div_wpr.div((unsigned)w);
         const int xr = (w - r * g.wpr) * 32 + lane;
         const bool live = xr < g.nx;
         const uint32_t m = __shfl_sync(0xffffffffu, m_l, k);
+        const uint32_t fm = __shfl_sync(0xffffffffu, f_l, k) & m;
         const bool cv = live && ((m >> lane) & 1u);
+        const bool fl = live && ((fm >> lane) & 1u);
         const unsigned bu = __ballot_sync(0xffffffffu, live && !cv);
-        const unsigned bc = __ballot_sync(0xffffffffu, cv);
+        const unsigned bc = __ballot_sync(0xffffffffu, cv && !fl);
+        const unsigned bf = __ballot_sync(0xffffffffu, fl);
         if (pass == 0) {
           pu += __popc(bu);
+          pc += __popc(bc);
           continue;
         }
         const int base = __shfl_sync(0xffffffffu, b_l, k);
         if (live) {
-          const int pos = cv ? pc + __popc(bc & below) : pu + __popc(bu & below);
+          const int pos = fl   ? pf + __popc(bf & below)
+                          : cv ? pc + __popc(bc & below)
+                               : pu + __popc(bu & below);
           lst_cell[pos] = (r << 16) | xr;
           int e = -1;
           if (cv) {
@@ -1077,13 +1121,18 @@ __device__ __forceinline__ void fp64_list_tile(const LbmParams& P, int tile, int
         }
         pu += __popc(bu);
         pc += __popc(bc);
+        pf += __popc(bf);
       }
     }
-    if (pass == 0) tot_u = pu;
+    if (pass == 0) {
+      tot_u = pu;
+      tot_c = pc;
+    }
   }
   if (lane == 0) {
     hdr[0] = tot_u;
-    hdr[1] = pc;  // after the second pass: tot_u + covered cells
+    hdr[1] = pf;  // after the second pass: every live cell
+    hdr[2] = tot_u + tot_c;
   }
 }
 
@@ -1178,7 +1227,7 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
     }
     const T* st = ring + s * stage_elems;
     const int* ls = lists + s * list_ints;
-    const int tot_u = ls[0], L = ls[1];
+    const int tot_u = ls[0], L = ls[1], full0 = ls[2];
     const int* lst_cell = ls + 4;
     const int* lst_slot = ls + 4 + C;
     const int row0 = tile * TR;
@@ -1201,10 +1250,6 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
       const int cell = nb.idx(0, 0, 0);
       const int xm = x == 0 ? g.nx - 1 : x - 1, xq = x == g.nx - 1 ? 0 : x + 1;
       const T* sr = st + (size_t)r * nxp;  // direction q of this row at sr[q * C]
-      T ub[3] = {T(0), T(0), T(0)};
-      if constexpr (MODE == 0 && (WALLS & 4) != 0) {
-        if (outflow_layer(g, z)) own_velocity<T>(P, cell, ub);
-      }
       T d[Q];
       d[0] = sr[x];
 #pragma unroll
@@ -1214,20 +1259,8 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
         const int xa = cx > 0 ? xm : (cx < 0 ? xq : x);  // x - c_x
         const int xb = cx > 0 ? xq : (cx < 0 ? xm : x);  // x + c_x
         if (MODE == 0) {
-          if (nb.ok(-cx, -cy, -cz)) {
-            d[qa] = sr[qa * C + xa];
-          } else {
-            const T bb = ld(SRC(qb) + cell);
-            const int t = open_face<WALLS>(g, nb, -cx, -cy, -cz);
-            d[qa] = t ? open_value<T>(P.bc, t, qa, bb, ub) : bb;
-          }
-          if (nb.ok(cx, cy, cz)) {
-            d[qb] = sr[qb * C + xb];
-          } else {
-            const T bb = ld(SRC(qa) + cell);
-            const int t = open_face<WALLS>(g, nb, cx, cy, cz);
-            d[qb] = t ? open_value<T>(P.bc, t, qb, bb, ub) : bb;
-          }
+          d[qa] = nb.ok(-cx, -cy, -cz) ? sr[qa * C + xa] : ld(SRC(qb) + cell);
+          d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qa) + cell);
         } else if (MODE == 1) {
           d[qa] = sr[qa * C + x];
           d[qb] = sr[qb * C + x];
@@ -1236,8 +1269,10 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
           d[qb] = nb.ok(cx, cy, cz) ? sr[qb * C + xb] : ld(SRC(qb) + cell);
         }
       }
-      if (ch * 32 + 32 <= tot_u) fp64_collide<true>(P, d, false, -1);
-      else fp64_collide<false>(P, d, e >= 0, e);
+      if constexpr (MODE == 0) apply_open_faces<T, WALLS>(P, nb, z, cell, d);
+      if (ch * 32 + 32 <= tot_u) fp64_collide<CK_UNCOVERED>(P, d, false, -1);
+      else if (ch * 32 >= full0) fp64_collide<CK_FULL>(P, d, e >= 0, e);
+      else fp64_collide<CK_MIXED>(P, d, e >= 0, e);
       if (active) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
     }
     __syncwarp();

@@ -1022,6 +1022,11 @@ __device__ double finish_entry(const MapParams& P, int e, int n) {
   if (two) {
     P.s.pid[e] = pid;
     rec_store(V + 4 * e1, r1);
+  } else if (P.cov.full && r0[3] == T(1)) {
+    // one particle and B = 1: the FP64 collision takes these cells in warps
+    // of their own (the fluid change vanishes)
+    const int cell = P.s.cell[e];
+    atomicOr(P.cov.full + (cell >> 5), 1u << (cell & 31));
   }
   return (double)B;
 }
@@ -1453,6 +1458,7 @@ void launch_fill(const MapParams& P, bool mlp, cudaStream_t s) {
 int map_common(MapParams P, cudaStream_t s, bool mlp) {
   int launches = 0;
   cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
+  if (P.cov.full) cudaMemsetAsync(P.cov.full, 0, sizeof(uint32_t) * P.g.nwords, s);
   if (mlp) cudaMemsetAsync(P.mlp_count, 0, sizeof(int), s);
   if (P.p.n > 0) {
     box_kernel<<<(P.p.n + 127) / 128, 128, 0, s>>>(P);

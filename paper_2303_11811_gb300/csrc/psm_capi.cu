@@ -249,6 +249,7 @@ int enqueue_step(psm_ctx* c, bool with_map, cudaStream_t s, bool dem = true) {
   if (c->p.n > 0) {
     L.mask = c->cov.mask;
     L.base = c->cov.base;
+    L.full = c->cov.full;
     L.slot_Fc = c->slots.Fc;
     L.slot_V = c->slots.V;
     L.slot_cap = c->slots.cap;
@@ -543,6 +544,10 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   }
   c->cov.mask = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
   c->cov.base = alloc_n<int>(c, (size_t)g.nwords, c->allocs);
+  if (c->prec == PREC_FP64) {
+    c->cov.full = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
+    if (!c->cov.full) return bail(PSM_ERR_OOM, "allocator returned NULL");
+  }
   c->cov.nblocks = (g.nwords + 1023) / 1024;
   c->cov.blocksum = alloc_n<int>(c, (size_t)c->cov.nblocks, c->allocs);
   c->cov.ncov = alloc_n<int>(c, 1, c->allocs);
@@ -562,6 +567,8 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   for (int b = 0; b < nbuf; ++b)
     ok = ok && cudaMemsetAsync(c->buf[b], 0, esz * Q * (size_t)ncell, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.mask, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
+  if (c->cov.full)
+    ok = ok && cudaMemsetAsync(c->cov.full, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->dem_bar, 0, 4 * sizeof(unsigned), s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.ncov, 0, sizeof(int), s) == cudaSuccess;

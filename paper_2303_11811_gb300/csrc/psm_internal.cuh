@@ -165,6 +165,9 @@ struct Slots {
 struct Coverage {
   uint32_t* mask;
   int* base;
+  // FP64 records only (else nullptr): bit = covered cell with one particle
+  // and B = 1 (every sample inside), written by the finish pass
+  uint32_t* full;
   int* blocksum;
   int* ncov;      // device scalar
   long long nblocks;
@@ -212,6 +215,7 @@ struct LbmParams {
   void* dstq[19];
   const uint32_t* mask; // nullptr when there are no particles
   const int* base;
+  const uint32_t* full; // Coverage::full (FP64 records), or nullptr
   void* slot_Fc;        // Slots::Fc
   const void* slot_V;   // Slots::V
   long long slot_cap;   // entries allocated
