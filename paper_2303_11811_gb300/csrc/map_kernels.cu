@@ -45,6 +45,10 @@ struct Box {
   float reach2f, E;   // its FP32 value and the certified band of geom.cuh
   float r2f;          // (float)(r * r)
   bool has_in;        // rin2 >= 0: cells can lie inside by the margin
+  // the n^3 = 8^3 samples lie within 7 sqrt(3)/16 < 0.76 of the cell centre:
+  // (r -+ 0.76)^2 in FP32 (in8f < 0 when r <= 0.76), for counts of 512 and 0
+  // taken without sampling
+  float in8f, out8f;
   FastDiv div_n0, div_nxy;  // box index t -> (kx, ky, kz)
 };
 
@@ -79,6 +83,8 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
   b.rin2 = rin > 0.0 ? rin * rin : -1.0;
   b.has_in = rin > 0.0;
   b.rin2f = (float)b.rin2;
+  b.in8f = r > 0.76 ? (float)((r - 0.76) * (r - 0.76)) : -1.0f;
+  b.out8f = (float)((r + 0.76) * (r + 0.76));
   return b;
 }
 
@@ -555,6 +561,68 @@ __device__ int warp_count8(float dxf, float dyf, float dzf, float r2f, float E, 
   return __reduce_add_sync(0xffffffffu, in);
 }
 
+// 8^3 sampled counts of up to four cells at once, eight lanes per cell: lane
+// a = lane & 7 of group g = lane >> 3 takes the sample plane x = a (64
+// samples) of the group's cell, with the FP32 roundings of its offset d (dxf,
+// dyf, dzf), of r^2 (r2f) and the certified band E of geom.cuh.  Each sample's
+// D = ((px^2 - r2f) + py^2) + pz^2 in FP32 lies within E of the FP64
+// definition's S - r^2 (three squares off by at most 2^-21 (r + 2.5)^2 each,
+// three sums by 2^-24 (r + 2.5)^2 each, r2f by 2^-24 r^2), so D < -E is
+// inside and D > E outside; a lane with a sample at |D| <= E recounts its
+// plane with the FP64 definition there (fp64(dx, dy, dz, r2) gives the
+// group's FP64 offset and r^2; called by every lane of the warp together).
+// Returns the group's count in every lane of the group: the FP64
+// definition's count.
+template <class Fp64>
+__device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, float r2f, float E,
+                                            Fp64 fp64) {
+  const unsigned all = 0xffffffffu;
+  const int a = threadIdx.x & 7;
+  const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
+  const float Xr = px * px - r2f;
+  float Z[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+    Z[c] = pz * pz;
+  }
+  int in = 0;
+  float mn = 3.0e38f;
+#pragma unroll
+  for (int bb = 0; bb < 8; ++bb) {
+    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+    const float XY = Xr + py * py;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const float D = XY + Z[c];
+      in += D < -E;
+      mn = fminf(mn, fabsf(D));
+    }
+  }
+  if (__any_sync(all, mn <= E)) {
+    double dx, dy, dz, r2;
+    fp64(dx, dy, dz, r2);
+    if (mn <= E) {
+      in = 0;
+      for (int bb = 0; bb < 8; ++bb) {
+        const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+        const float XY = Xr + py * py;
+        for (int c = 0; c < 8; ++c) {
+          const float D = XY + Z[c];
+          if (D < -E) ++in;
+          else if (D <= E && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
+                                                 sample_offset(bb, 8), sample_offset(c, 8), r2))
+            ++in;
+        }
+      }
+    }
+  }
+  in += __shfl_xor_sync(all, in, 4);
+  in += __shfl_xor_sync(all, in, 2);
+  in += __shfl_xor_sync(all, in, 1);
+  return in;
+}
+
 // a cell of a particle's box (box index t): coordinates, FP64 offsets from
 // the centre and their FP32 roundings (from the per-block tables when the
 // box fits them), FP32 squared distance
@@ -654,6 +722,12 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   const int cnt = P.list_cnt[p];
   // surrogate mode: the block's network cells, its worklist range and next free index
   __shared__ int net_cnt, net_base, net_next;
+  // 8^3 sampling: next free item of the particle's worklist
+  __shared__ int wl_next;
+  if constexpr (NS == 8) {
+    if (threadIdx.x == 0) wl_next = 0;
+    __syncthreads();
+  }
   if constexpr (NS < 0) {
     // count the block's network cells first and reserve their worklist
     // range with one atomic (a counter shared by every block would serialise)
@@ -674,17 +748,15 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     }
     __syncthreads();
   }
-  // warp-uniform loop: every lane of a warp runs the same iterations (the
-  // 8^3 count is taken by the whole warp), lanes past the list idle
+  // 8^3 sampling iterates whole warps (the worklist is appended to warp by
+  // warp; lanes past the list idle); the other modes give each thread its
+  // own cells
   const int lane = threadIdx.x & 31;
-  const double r2 = b.r * b.r;
-  // 8^3 sampling iterates whole warps (its counts are taken by all lanes);
-  // the other modes give each thread its own cells
   for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += FILL_THREADS) {
     const int k = NS == 8 ? k0 + lane : k0;
     bool ok = NS == 8 ? k < cnt : true;
     CellHit h;
-    if constexpr (NS == 8) {  // lanes past the list still take part in the shuffles
+    if constexpr (NS == 8) {  // lanes past the list still take part in the ballot
       h.dx = h.dy = h.dz = 0.0;
       h.dxf = h.dyf = h.dzf = 0.f;
     }
@@ -713,30 +785,33 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
         }
       }
     }
-    // 8^3 sampling: a cell inside by the margin counts 512 without
-    // sampling; the partial cells of the warp are counted one after the
-    // other by all 32 lanes
+    // 8^3 sampling: a cell whose samples all lie inside (centre closer than
+    // r - 0.76) counts 512 and one whose samples all lie outside (farther
+    // than r + 0.76) counts 0 without sampling, both certified in FP32; the
+    // other cells go to the particle's worklist (B stays -1 until the count
+    // pass writes it; without a worklist the finish pass samples them)
     int count8 = 512;
+    bool pending = false;
     if constexpr (NS == 8) {
-      bool partial = false;
       if (ok && tab) {
-        partial = true;
-        if (b.has_in) {
-          if (h.d2f < b.rin2f - b.E) partial = false;
-          else if (h.d2f <= b.rin2f + b.E &&
-                   h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2)
-            partial = false;
+        pending = true;
+        if (h.d2f < b.in8f - b.E) {
+          pending = false;
+        } else if (h.d2f > b.out8f + b.E) {
+          pending = false;
+          count8 = 0;
         }
       }
-      unsigned need = __ballot_sync(0xffffffffu, partial);
-      while (need) {
-        const int L = __ffs(need) - 1;
-        need &= need - 1u;
-        const float dxf = __shfl_sync(0xffffffffu, h.dxf, L);
-        const float dyf = __shfl_sync(0xffffffffu, h.dyf, L);
-        const float dzf = __shfl_sync(0xffffffffu, h.dzf, L);
-        const int c = warp_count8(dxf, dyf, dzf, b.r2f, b.E, L, h.dx, h.dy, h.dz, r2);
-        if (lane == L) count8 = c;
+      const unsigned pm = __ballot_sync(0xffffffffu, pending);
+      if (pm && P.wl_X) {
+        int first = 0;
+        if (lane == 0) first = atomicAdd(&wl_next, __popc(pm));
+        first = __shfl_sync(0xffffffffu, first, 0);
+        if (pending) {
+          const long long k2 = loff + first + __popc(pm & ((1u << lane) - 1u));
+          P.wl_X[k2] = make_float4(h.dxf, h.dyf, h.dzf, __int_as_float(p));
+          P.wl_work[k2] = (int)(unsigned)(2 * e + s);
+        }
       }
     }
     if (!ok) continue;
@@ -762,6 +837,9 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
         Bf = -1.f;
         want = true;
       }
+    } else if (NS == 8 && pending) {
+      B = -1.0;
+      Bf = -1.f;
     } else if (tab) {
       const int c = NS == 8 ? count8 : cell_count<NS>(P, b, h, s64, s32);
       cidx = c;
@@ -857,6 +935,10 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       }
     }
   }
+  if constexpr (NS == 8) {
+    __syncthreads();
+    if (threadIdx.x == 0 && P.wl_cnt) P.wl_cnt[p] = wl_next;
+  }
   if constexpr (NS < 0) {
     // cells counted but not listed (slot overflow) leave empty items
     __syncthreads();
@@ -865,6 +947,64 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       reinterpret_cast<float4*>(P.mlp_X)[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       P.mlp_lin[k] = 0.f;
       P.mlp_work[k] = -1;
+    }
+  }
+}
+
+// 8^3 counts of the cells the fill pass listed (one block per particle, four
+// cells per warp and round, eight lanes per cell): B of each count from the
+// table into the slot record's weight.  A lane group with a sample in the
+// certified band forms the cell's FP64 offset as the fill pass did (box
+// coordinates unwrapped around the centre, ((double)k + 1/2) - x_p).
+constexpr int COUNT_THREADS = 128;
+template <int REC>
+__global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
+  __shared__ Box sbox;
+  const int p = blockIdx.x;
+  const int n = P.wl_cnt[p];
+  if (n == 0) return;  // the whole block
+  load_box(P, p, &sbox);
+  const long long base = P.list_off[p];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 3;
+  const float r2f = sbox.r2f, E = sbox.E;
+  for (int i0 = 4 * warp; i0 < n; i0 += 4 * (COUNT_THREADS / 32)) {  // warp-uniform
+    const int i = i0 + g;
+    const bool valid = i < n;
+    const long long it = base + (valid ? i : i0);
+    const float4 X = P.wl_X[it];
+    const unsigned wk = (unsigned)P.wl_work[it];
+    const unsigned e = wk >> 1, sl = wk & 1u;
+    auto fp64 = [&](double& dx, double& dy, double& dz, double& r2) {
+      int c3[3];
+      cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+      const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
+      double d[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        int k = c3[a];
+        if (k < sbox.lo[a]) k += dims[a];
+        else if (k >= sbox.lo[a] + sbox.n[a]) k -= dims[a];
+        d[a] = ((double)k + 0.5) - sbox.xp[a];
+      }
+      dx = d[0];
+      dy = d[1];
+      dz = d[2];
+      r2 = sbox.r * sbox.r;
+    };
+    const int c = group_count8(X.x, X.y, X.z, r2f, E, fp64);
+    if (valid && (lane & 7) == 0) {
+      const long long rec = (long long)sl * P.s.cap + e;
+      if (REC == REC_FP32) {
+        reinterpret_cast<float*>(P.s.V)[4 * rec + 3] =
+            __ldg(reinterpret_cast<const float*>(P.wtab + WTAB) + c);
+      } else if (REC == REC_DF) {
+        const df w = reinterpret_cast<const df*>(P.wtab + WTAB_DF)[c];
+        float* R = reinterpret_cast<float*>(P.s.V) + 8 * rec;
+        R[6] = w.hi;
+        R[7] = w.lo;
+      } else {
+        reinterpret_cast<double*>(P.s.V)[4 * rec + 3] = __ldg(P.wtab + c);
+      }
     }
   }
 }
@@ -978,7 +1118,7 @@ __device__ __noinline__ WeightPair<T> pending_weights(const MapParams& P, int e,
 // normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
 // weight; returns min(B, 1) (0 for lanes without an entry)
 template <typename T, typename S>  // arithmetic in T, records stored as S
-__device__ double finish_entry(const MapParams& P, int e, int n) {
+__device__ double finish_entry(const MapParams& P, int e, int n, bool* full) {
   const bool live = e < n;
   int2 pid = make_int2(-1, -1);
   T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
@@ -1022,13 +1162,30 @@ __device__ double finish_entry(const MapParams& P, int e, int n) {
   if (two) {
     P.s.pid[e] = pid;
     rec_store(V + 4 * e1, r1);
-  } else if (P.cov.full && r0[3] == T(1)) {
-    // one particle and B = 1: the FP64 collision takes these cells in warps
-    // of their own (the fluid change vanishes)
-    const int cell = P.s.cell[e];
-    atomicOr(P.cov.full + (cell >> 5), 1u << (cell & 31));
   }
+  *full = !two && r0[3] == T(1);
   return (double)B;
+}
+
+// the full-cell mask (one particle, B = 1: the FP64 collision takes these
+// cells in warps of their own, where the fluid change vanishes): the warp's
+// entries are consecutive slots, hence cells in increasing order; a
+// segmented OR over lanes of the same mask word leaves one atomicOr per run
+__device__ __forceinline__ void mark_full(const MapParams& P, int e, bool fl) {
+  const unsigned all = 0xffffffffu;
+  if (!__any_sync(all, fl)) return;
+  const int lane = threadIdx.x & 31;
+  const int cell = fl ? P.s.cell[e] : 0;
+  const int w = fl ? cell >> 5 : -1;
+  unsigned v = fl ? 1u << (cell & 31) : 0u;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned vu = __shfl_up_sync(all, v, off);
+    const int wu = __shfl_up_sync(all, w, off);
+    if (lane >= off && wu == w) v |= vu;
+  }
+  const int wn = __shfl_down_sync(all, w, 1);
+  if (fl && (lane == 31 || wn != w)) atomicOr(P.cov.full + w, v);
 }
 
 __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
@@ -1039,9 +1196,11 @@ __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   const int stride = gridDim.x * blockDim.x;
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
-    accB += P.fp32    ? finish_entry<float, float>(P, e, n)
-            : P.dfrec ? finish_entry<double, df>(P, e, n)
-                      : finish_entry<double, double>(P, e, n);
+    bool fl = false;
+    accB += P.fp32    ? finish_entry<float, float>(P, e, n, &fl)
+            : P.dfrec ? finish_entry<double, df>(P, e, n, &fl)
+                      : finish_entry<double, double>(P, e, n, &fl);
+    if (P.cov.full) mark_full(P, e, fl);
   }
   red[threadIdx.x] = accB;
   __syncthreads();
@@ -1477,6 +1636,12 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
     else if (rec == REC_DF) launch_fill<REC_DF>(P, mlp, s);
     else launch_fill<REC_FP64>(P, mlp, s);
     ++launches;
+    if (!mlp && P.eps_mode == 0 && P.eps_n == 8 && P.wtab && P.wl_X) {
+      if (rec == REC_FP32) count8_kernel<REC_FP32><<<P.p.n, COUNT_THREADS, 0, s>>>(P);
+      else if (rec == REC_DF) count8_kernel<REC_DF><<<P.p.n, COUNT_THREADS, 0, s>>>(P);
+      else count8_kernel<REC_FP64><<<P.p.n, COUNT_THREADS, 0, s>>>(P);
+      ++launches;
+    }
   }
   return launches;
 }

@@ -72,6 +72,9 @@ struct psm_ctx {
   int dem_blocks = 0;            // resident blocks of the DEM step kernel
   float* mlp = nullptr;   // FP32 parameters on the device
   bool have_mlp = false;
+  float4* wl_X = nullptr;  // 8^3 sampling worklist (per list entry)
+  int* wl_work = nullptr;
+  int* wl_cnt = nullptr;     // its length per particle
   float* mlp_X = nullptr; // MLP worklist inputs (float4 per slot)
   float* mlp_lin = nullptr;  // linear approximation per worklist item
   int* mlp_work = nullptr;   // entry index per worklist item
@@ -160,6 +163,9 @@ void free_particles(psm_ctx* c) {
   c->palloc.clear();
   c->p = Particles{};
   c->slots = Slots{};
+  c->wl_X = nullptr;
+  c->wl_work = nullptr;
+  c->wl_cnt = nullptr;
   c->mlp_X = nullptr;
   c->mlp_lin = nullptr;
   c->mlp_work = nullptr;
@@ -198,6 +204,9 @@ MapParams map_params(psm_ctx* c) {
   P.mlp = c->have_mlp ? c->mlp : nullptr;
   P.wtab = c->have_wtab ? c->wtab : nullptr;
   P.partials = c->partials;
+  P.wl_X = c->wl_X;
+  P.wl_work = c->wl_work;
+  P.wl_cnt = c->wl_cnt;
   P.mlp_X = c->mlp_X;
   P.mlp_lin = c->mlp_lin;
   P.mlp_cap = c->mlp_cap;
@@ -731,6 +740,11 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->dem_items = alloc_n<int>(c, 3 * n1, c->palloc);
   c->dem_nbr = alloc_n<int>(c, n1 * kDemListCap, c->palloc);
   c->dem_xbuild = alloc_n<float4>(c, n1, c->palloc);
+  if (c->opt.eps_mode == PSM_EPS_SUPERSAMPLE && c->opt.eps_n == 8) {
+    c->wl_X = alloc_n<float4>(c, (size_t)list_total, c->palloc);
+    c->wl_work = alloc_n<int>(c, (size_t)list_total, c->palloc);
+    c->wl_cnt = alloc_n<int>(c, n1, c->palloc);
+  }
   if (c->opt.eps_mode == PSM_EPS_MLP) {
     c->mlp_cap = (long long)cp;
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);

@@ -193,6 +193,13 @@ struct MapParams {
   double* partials;     // >= MAP_PARTIALS doubles of scratch
   // surrogate worklist (eps mode 2): network inputs, linear approximation,
   // 2 * slot entry + slot, item count (at most mlp_cap items)
+  // 8^3 sampling: each particle's cells that need sampling, listed by the
+  // fill pass at the particle's list range (FP32 offset of the cell centre
+  // and the particle index; 2 * slot entry + slot, as unsigned) and their
+  // number per particle; counted by a pass of their own
+  float4* wl_X;
+  int* wl_work;
+  int* wl_cnt;
   float* mlp_X;
   float* mlp_lin;
   int* mlp_work;
