@@ -9,13 +9,16 @@
 //             cell its slot-table index, in cell order;
 //   3. fill   each (particle, covered cell) pair claims one of the cell's two
 //             slots, stores B_i = W(eps_i) and appends the entry to the
-//             particle's list (box order, deterministic);
+//             particle's list (box order, deterministic); with 8^3 sampling
+//             the cells that need samples go to a per-particle worklist,
+//             3b. count8 counts them, four cells per warp;
 //   4. finish slots are ordered by particle index, MLP-mode and fallback cells
 //             get their eps, and B > 1 is normalised (every B_i divided by
-//             the sum).
+//             the sum); FP64 records: the mask of cells with one particle and
+//             B = 1.
 // Reach tests and sub-cell sampling take the FP64 definition's decisions: FP32
 // with a certified band and FP64 inside the band (geom.cuh); this file is
-// compiled with -fmad=false.
+// compiled with -fmad=false (fused multiply-adds only where written out).
 #include "geom.cuh"
 #include "psm_internal.cuh"
 
@@ -569,23 +572,48 @@ __device__ int warp_count8(float dxf, float dyf, float dzf, float r2f, float E, 
 // definition's S - r^2 (three squares off by at most 2^-21 (r + 2.5)^2 each,
 // three sums by 2^-24 (r + 2.5)^2 each, r2f by 2^-24 r^2), so D < -E is
 // inside and D > E outside; a lane with a sample at |D| <= E recounts its
-// plane with the FP64 definition there (fp64(dx, dy, dz, r2) gives the
-// group's FP64 offset and r^2; called by every lane of the warp together).
-// Returns the group's count in every lane of the group: the FP64
-// definition's count.
-template <class Fp64>
+// plane with the FP64 definition there (plane_recount8).  Returns the group's
+// count in every lane of the group: the FP64 definition's count.
+__device__ __forceinline__ float sample_z8(float dzf, int c) {
+  const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+  return pz * pz;
+}
+
+// one lane's plane of 64 samples again, with the FP64 definition for the
+// samples in the band: the cell's FP64 offset from its box coordinates
+// (kx, ky, kz), unwrapped around the centre as the fill pass forms it.  Out
+// of line, so that its FP64 set-up stays off the common path.
+__device__ __noinline__ int plane_recount8(float dyf, float dzf, float Xr, float E, int a, int kx,
+                                           int ky, int kz, const Box* b) {
+  const double dx = ((double)kx + 0.5) - b->xp[0];
+  const double dy = ((double)ky + 0.5) - b->xp[1];
+  const double dz = ((double)kz + 0.5) - b->xp[2];
+  const double r2 = b->r * b->r;
+  int in = 0;
+  for (int bb = 0; bb < 8; ++bb) {
+    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+    const float XY = Xr + py * py;
+    for (int c = 0; c < 8; ++c) {
+      const float D = XY + sample_z8(dzf, c);
+      if (D < -E) ++in;
+      else if (D <= E && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
+                                             sample_offset(bb, 8), sample_offset(c, 8), r2))
+        ++in;
+    }
+  }
+  return in;
+}
+
+// b: the particle's box (shared memory); t: the cell's box index
 __device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, float r2f, float E,
-                                            Fp64 fp64) {
+                                            const Box* b, int t) {
   const unsigned all = 0xffffffffu;
   const int a = threadIdx.x & 7;
   const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
   const float Xr = px * px - r2f;
   float Z[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
-    Z[c] = pz * pz;
-  }
+  for (int c = 0; c < 8; ++c) Z[c] = sample_z8(dzf, c);
   int in = 0;
   float mn = 3.0e38f;
 #pragma unroll
@@ -599,23 +627,13 @@ __device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, flo
       mn = fminf(mn, fabsf(D));
     }
   }
-  if (__any_sync(all, mn <= E)) {
-    double dx, dy, dz, r2;
-    fp64(dx, dy, dz, r2);
-    if (mn <= E) {
-      in = 0;
-      for (int bb = 0; bb < 8; ++bb) {
-        const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
-        const float XY = Xr + py * py;
-        for (int c = 0; c < 8; ++c) {
-          const float D = XY + Z[c];
-          if (D < -E) ++in;
-          else if (D <= E && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
-                                                 sample_offset(bb, 8), sample_offset(c, 8), r2))
-            ++in;
-        }
-      }
-    }
+  if (__any_sync(all, mn <= E) && mn <= E) {
+    const int nxy = b->n[0] * b->n[1];
+    const int kz = (int)b->div_nxy.div((unsigned)t);
+    const int rem = t - kz * nxy;
+    const int ky = (int)b->div_n0.div((unsigned)rem);
+    in = plane_recount8(dyf, dzf, Xr, E, a, b->lo[0] + (rem - ky * b->n[0]), b->lo[1] + ky,
+                        b->lo[2] + kz, b);
   }
   in += __shfl_xor_sync(all, in, 4);
   in += __shfl_xor_sync(all, in, 2);
@@ -762,8 +780,10 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     }
     long long cell = 0, e = 0;
     int s = 0;
+    int tb = 0;  // box index of the cell (the list entry before the fill)
     if (ok) {
-      cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
+      tb = P.list[loff + k];
+      cell_hit(P.g, b, tb, tables, toff, toff32, h);
       cell = padded_cell(P.g, h.ix, h.iy, h.iz);
       e = slot_index(P.cov, cell);
       if (e >= P.s.cap) {
@@ -809,7 +829,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
         first = __shfl_sync(0xffffffffu, first, 0);
         if (pending) {
           const long long k2 = loff + first + __popc(pm & ((1u << lane) - 1u));
-          P.wl_X[k2] = make_float4(h.dxf, h.dyf, h.dzf, __int_as_float(p));
+          P.wl_X[k2] = make_float4(h.dxf, h.dyf, h.dzf, __int_as_float(tb));
           P.wl_work[k2] = (int)(unsigned)(2 * e + s);
         }
       }
@@ -899,9 +919,11 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       R[0] = make_float4(v0.hi, v0.lo, v1.hi, v1.lo);
       R[1] = make_float4(v2.hi, v2.lo, w.hi, w.lo);
     } else {
-      const double v0 = u0 + (o1 * h.dz - o2 * h.dy);
-      const double v1 = u1 + (o2 * h.dx - o0 * h.dz);
-      const double v2 = u2 + (o0 * h.dy - o1 * h.dx);
+      // Eq. 20 with one fused multiply-add per component (FP64 runs at 1/64
+      // of the FP32 rate)
+      const double v0 = u0 + __fma_rn(o1, h.dz, -(o2 * h.dy));
+      const double v1 = u1 + __fma_rn(o2, h.dx, -(o0 * h.dz));
+      const double v2 = u2 + __fma_rn(o0, h.dy, -(o1 * h.dx));
       double2* R = static_cast<double2*>(P.s.V) + 2 * rec;
       R[0] = make_double2(v0, v1);
       R[1] = make_double2(v2, B);
@@ -953,9 +975,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
 
 // 8^3 counts of the cells the fill pass listed (one block per particle, four
 // cells per warp and round, eight lanes per cell): B of each count from the
-// table into the slot record's weight.  A lane group with a sample in the
-// certified band forms the cell's FP64 offset as the fill pass did (box
-// coordinates unwrapped around the centre, ((double)k + 1/2) - x_p).
+// table into the slot record's weight.
 constexpr int COUNT_THREADS = 128;
 template <int REC>
 __global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
@@ -974,24 +994,7 @@ __global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
     const float4 X = P.wl_X[it];
     const unsigned wk = (unsigned)P.wl_work[it];
     const unsigned e = wk >> 1, sl = wk & 1u;
-    auto fp64 = [&](double& dx, double& dy, double& dz, double& r2) {
-      int c3[3];
-      cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
-      const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
-      double d[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        int k = c3[a];
-        if (k < sbox.lo[a]) k += dims[a];
-        else if (k >= sbox.lo[a] + sbox.n[a]) k -= dims[a];
-        d[a] = ((double)k + 0.5) - sbox.xp[a];
-      }
-      dx = d[0];
-      dy = d[1];
-      dz = d[2];
-      r2 = sbox.r * sbox.r;
-    };
-    const int c = group_count8(X.x, X.y, X.z, r2f, E, fp64);
+    const int c = group_count8(X.x, X.y, X.z, r2f, E, &sbox, __float_as_int(X.w));
     if (valid && (lane & 7) == 0) {
       const long long rec = (long long)sl * P.s.cap + e;
       if (REC == REC_FP32) {

@@ -195,7 +195,7 @@ struct MapParams {
   // 2 * slot entry + slot, item count (at most mlp_cap items)
   // 8^3 sampling: each particle's cells that need sampling, listed by the
   // fill pass at the particle's list range (FP32 offset of the cell centre
-  // and the particle index; 2 * slot entry + slot, as unsigned) and their
+  // and the cell's box index; 2 * slot entry + slot, as unsigned) and their
   // number per particle; counted by a pass of their own
   float4* wl_X;
   int* wl_work;
