@@ -902,6 +902,17 @@ __global__ void __launch_bounds__(BULK_THREADS, sizeof(T) == 4 ? 2 : 1)
 // are mixed.
 enum { CK_UNCOVERED = 0, CK_MIXED = 1, CK_FULL = 2 };
 
+// the step's FP64 collision coefficients sit in shared memory (copied once
+// per block): the same four values for every lane, read as two 16-byte
+// broadcasts, which keeps them off the L1/texture path of the slot records
+constexpr int F64_COEF_BYTES = 512;
+static_assert(sizeof(CollideCoef<double>) <= F64_COEF_BYTES, "coefficient area");
+__device__ __forceinline__ void lds4(const double* p, double* o) {
+  const double2 u = reinterpret_cast<const double2*>(p)[0];
+  const double2 v = reinterpret_cast<const double2*>(p)[1];
+  o[0] = u.x; o[1] = u.y; o[2] = v.x; o[3] = v.y;
+}
+
 // FP64 collision of one cell (Eqs. 3-8 and 17-21).
 // CK_UNCOVERED: all lanes of the warp are uncovered (B = 0); a pair's update
 // is written as d_q' = S_k + A_k, d_qbar' = S_k - A_k with
@@ -919,9 +930,9 @@ enum { CK_UNCOVERED = 0, CK_MIXED = 1, CK_FULL = 2 };
 // Covered lanes write their slots' forces (Eq. 21).
 
 template <int KIND>
-__device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool cov, int e) {
+__device__ __forceinline__ void fp64_collide(const LbmParams& P, const CollideCoef<double>* cf,
+                                             double* d, bool cov, int e) {
   using T = double;
-  const CollideCoef<T>* cf = &P.sc->d;
   T a[9], sk[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -934,10 +945,10 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
   const T jy = ((a[1] + a[3]) - (a[4] - a[7])) + a[8];
   const T jz = ((a[2] + a[5]) - (a[6] - a[7])) - a[8];
   T h[16];
-  ld4(cf->head, h);
-  ld4(cf->head + 4, h + 4);
-  ld4(cf->head + 8, h + 8);
-  ld4(cf->head + 12, h + 12);
+  lds4(cf->head, h);
+  lds4(cf->head + 4, h + 4);
+  lds4(cf->head + 8, h + 8);
+  lds4(cf->head + 12, h + 12);
   const T Ux = jx + h[CC_HF];
   const T Uy = jy + h[CC_HF + 1];
   const T Uz = jz + h[CC_HF + 2];
@@ -949,12 +960,12 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
 
   if constexpr (KIND == CK_UNCOVERED) {
     T tl[4];
-    ld4(cf->tail, tl);
+    lds4(cf->tail, tl);
     d[0] = fma(tl[0], d[0], h[CC_WPW0] * base0 + h[CC_H] * Uf);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       T pk[4];
-      ld4(cf->pair[k], pk);
+      lds4(cf->pair[k], pk);
       const T cu = cdot<T>(k, Ux, Uy, Uz);
       const T X = (pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1);
       const T Y = pk[3] * cu + pk[1];
@@ -1016,19 +1027,29 @@ __device__ __forceinline__ void fp64_collide(const LbmParams& P, double* d, bool
     const T cd[2] = {(T(-1.5) * wk<T>(0)) * BdU, (T(-1.5) * wk<T>(3)) * BdU};
     const T as = omB * h[CC_MHWP] + T(0.5);
     const T aa = omB * h[CC_MHWM] + (T(0.5) - B0);
+    // per class, with X_k = (9/2 omega+ w c.U + G_k) c.U + C_c and
+    // Y_k = 3 omega- w c.U + F_k: SYM = as s_k + ((al cu + omB G_k) cu + ga
+    // + c45 cv^2) with al = omB 9/2 omega+ w - c45, ga = omB C_c + cd, and
+    // ANT = aa a_k + (de cu + (c3 cv + omB F_k)) with de = omB 3 omega- w + c3
+    T al[2], ga[2], de[2];
+#pragma unroll
+    for (int cl = 0; cl < 2; ++cl) {
+      T pc[4];
+      lds4(cf->pair[cl == 0 ? 0 : 3], pc);
+      al[cl] = omB * pc[2] - c45[cl];
+      ga[cl] = omB * (cl == 0 ? C0 : C1) + cd[cl];
+      de[cl] = omB * pc[3] + c3[cl];
+    }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       T pk[4];
-      ld4(cf->pair[k], pk);
+      lds4(cf->pair[k], pk);
       const int cl = k < 3 ? 0 : 1;
       const T cu = cdot<T>(k, Ux, Uy, Uz);
       const T cv = cdot<T>(k, Vx, Vy, Vz);
-      const T Sv = cv + cu;
-      const T BdS = c45[cl] * ((cv - cu) * Sv) + cd[cl];
-      const T X = (pk[2] * cu + pk[0]) * cu + (k < 3 ? C0 : C1);
-      const T Y = pk[3] * cu + pk[1];
-      const T SYM = as * sk[k] + (omB * X + BdS);
-      const T ANT = aa * a[k] + (omB * Y + c3[cl] * Sv);
+      const T sy = (al[cl] * cu + omB * pk[0]) * cu + ga[cl];
+      const T SYM = as * sk[k] + ((c45[cl] * cv) * cv + sy);
+      const T ANT = aa * a[k] + (de[cl] * cu + (c3[cl] * cv + omB * pk[1]));
       d[2 * k + 1] = SYM + ANT;
       d[2 * k + 2] = SYM - ANT;
     }
@@ -1152,12 +1173,19 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
   const int S = P.stages, TR = P.tile_rows, nxp = g.nxp;
   const int C = TR * nxp;  // elements per direction in a tile
   const size_t stage_elems = (size_t)Q * C;
-  T* ring = reinterpret_cast<T*>(bulk_smem + BULK_BAR_BYTES);
+  // the barriers, the step's collision coefficients, the ring
+  CollideCoef<double>* coef = reinterpret_cast<CollideCoef<double>*>(bulk_smem + BULK_BAR_BYTES);
+  T* ring = reinterpret_cast<T*>(bulk_smem + BULK_BAR_BYTES + F64_COEF_BYTES);
   // per stage: header (2 ints, padded to 4), cells, slot indices
   int* lists = reinterpret_cast<int*>(ring + S * stage_elems);
   const size_t list_ints = 4 + 2 * (size_t)C;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nrows = g.ny * g.nz;
+  {
+    constexpr int NV = (int)(sizeof(CollideCoef<double>) / sizeof(double2));
+    const double2* src = reinterpret_cast<const double2*>(&P.sc->d);
+    for (int i = threadIdx.x; i < NV; i += blockDim.x) reinterpret_cast<double2*>(coef)[i] = src[i];
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 2);
@@ -1270,9 +1298,9 @@ __global__ void __launch_bounds__(BULK_THREADS, 1) lbm_fp64_kernel(LbmParams P) 
         }
       }
       if constexpr (MODE == 0) apply_open_faces<T, WALLS>(P, nb, z, cell, d);
-      if (ch * 32 + 32 <= tot_u) fp64_collide<CK_UNCOVERED>(P, d, false, -1);
-      else if (ch * 32 >= full0) fp64_collide<CK_FULL>(P, d, e >= 0, e);
-      else fp64_collide<CK_MIXED>(P, d, e >= 0, e);
+      if (ch * 32 + 32 <= tot_u) fp64_collide<CK_UNCOVERED>(P, coef, d, false, -1);
+      else if (ch * 32 >= full0) fp64_collide<CK_FULL>(P, coef, d, e >= 0, e);
+      else fp64_collide<CK_MIXED>(P, coef, d, e >= 0, e);
       if (active) store_pdfs<T, MODE, WALLS>(P, nb, cell, d);
     }
     __syncwarp();
@@ -1543,7 +1571,7 @@ int lbm_plan(const Grid& g, int prec, int aa, LbmPlan* plan) {
   // FP64 (compacted warps): per stage the tile's cell list and slot indices
   // with a 16-byte header
   const size_t list_stage = prec == PREC_FP64 ? (size_t)8 * TR * g.nxp + 16 : 0;
-  const size_t extra = BULK_BAR_BYTES;
+  const size_t extra = BULK_BAR_BYTES + (prec == PREC_FP64 ? F64_COEF_BYTES : 0);
   const size_t budget = prec == PREC_FP64 ? (size_t)optin : (size_t)100 * 1024;
   if (budget <= extra) return 0;
   size_t S = (budget - extra) / (stage + list_stage);

@@ -987,12 +987,26 @@ __global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
   const long long base = P.list_off[p];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 3;
   const float r2f = sbox.r2f, E = sbox.E;
-  for (int i0 = 4 * warp; i0 < n; i0 += 4 * (COUNT_THREADS / 32)) {  // warp-uniform
+  // each round's items are loaded one round ahead
+  constexpr int STEP = 4 * (COUNT_THREADS / 32);
+  float4 Xn = make_float4(0.f, 0.f, 0.f, 0.f);
+  unsigned wkn = 0u;
+  if (4 * warp < n) {
+    const long long it = base + (4 * warp + g < n ? 4 * warp + g : 4 * warp);
+    Xn = P.wl_X[it];
+    wkn = (unsigned)P.wl_work[it];
+  }
+  for (int i0 = 4 * warp; i0 < n; i0 += STEP) {  // warp-uniform
     const int i = i0 + g;
     const bool valid = i < n;
-    const long long it = base + (valid ? i : i0);
-    const float4 X = P.wl_X[it];
-    const unsigned wk = (unsigned)P.wl_work[it];
+    const float4 X = Xn;
+    const unsigned wk = wkn;
+    if (i0 + STEP < n) {
+      const int i2 = i0 + STEP + g;
+      const long long it = base + (i2 < n ? i2 : i0 + STEP);
+      Xn = P.wl_X[it];
+      wkn = (unsigned)P.wl_work[it];
+    }
     const unsigned e = wk >> 1, sl = wk & 1u;
     const int c = group_count8(X.x, X.y, X.z, r2f, E, &sbox, __float_as_int(X.w));
     if (valid && (lane & 7) == 0) {

@@ -125,6 +125,31 @@ def test_mapping_slots(capi, eps_mode, eps_n):
     assert (pg1 >= 0).sum() > 0
 
 
+@pytest.mark.parametrize("eps_n,num", [(8, (2043, 4299, 6747)), (4, (507, 1091, 1731))])
+def test_mapping_samples_on_the_surface(capi, eps_n, num):
+    """Sample points exactly on the sphere surface.  With the centres at cell
+    centres the sample points are (odd / 2n)-multiples away from them, and a
+    radius of sqrt(N) / 2n with N = 3 mod 8 (a sum of three odd squares) puts
+    whole families of samples at distance r, up to the rounding of r * r: the
+    certified FP32 test cannot decide them, and the FP64 definition must
+    (the count pass's out-of-line recount for 8^3, the fill pass's for 4^3)."""
+    shape = (48, 40, 36)
+    e, o = pair(capi, shape, tau=0.6, relax="srt", weighting="nt", eps_mode="supersample",
+                eps_n=eps_n)
+    x = np.array([[10.5, 10.5, 10.5], [30.5, 20.5, 18.5], [16.5, 30.5, 26.5]])
+    r = np.sqrt(np.array(num, dtype=np.float64)) / (2 * eps_n)
+    assert all(v % 8 == 3 for v in num)
+    for s_ in (e, o):
+        s_.set_particles(x, r)
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = e.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    assert np.max(np.abs(bg0 - bo0)) < 1e-15 and np.max(np.abs(bg1 - bo1)) < 1e-15
+    # some cells are cut by the surface: neither empty nor full
+    assert np.any((bo0 > 0.0) & (bo0 < 1.0))
+
+
 @pytest.mark.parametrize("eps_mode,eps_n", [("supersample", 4), ("linear", 4)])
 def test_mapping_slots_large_spheres(capi, eps_mode, eps_n):
     """Large spheres (radius 7.5 to 12: the mark pass's row-wise search for
