@@ -571,49 +571,22 @@ __device__ int warp_count8(float dxf, float dyf, float dzf, float r2f, float E, 
 // D = ((px^2 - r2f) + py^2) + pz^2 in FP32 lies within E of the FP64
 // definition's S - r^2 (three squares off by at most 2^-21 (r + 2.5)^2 each,
 // three sums by 2^-24 (r + 2.5)^2 each, r2f by 2^-24 r^2), so D < -E is
-// inside and D > E outside; a lane with a sample at |D| <= E recounts its
-// plane with the FP64 definition there (plane_recount8).  Returns the group's
-// count in every lane of the group: the FP64 definition's count.
-__device__ __forceinline__ float sample_z8(float dzf, int c) {
-  const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
-  return pz * pz;
-}
-
-// one lane's plane of 64 samples again, with the FP64 definition for the
-// samples in the band: the cell's FP64 offset from its box coordinates
-// (kx, ky, kz), unwrapped around the centre as the fill pass forms it.  Out
-// of line, so that its FP64 set-up stays off the common path.
-__device__ __noinline__ int plane_recount8(float dyf, float dzf, float Xr, float E, int a, int kx,
-                                           int ky, int kz, const Box* b) {
-  const double dx = ((double)kx + 0.5) - b->xp[0];
-  const double dy = ((double)ky + 0.5) - b->xp[1];
-  const double dz = ((double)kz + 0.5) - b->xp[2];
-  const double r2 = b->r * b->r;
-  int in = 0;
-  for (int bb = 0; bb < 8; ++bb) {
-    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
-    const float XY = Xr + py * py;
-    for (int c = 0; c < 8; ++c) {
-      const float D = XY + sample_z8(dzf, c);
-      if (D < -E) ++in;
-      else if (D <= E && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
-                                             sample_offset(bb, 8), sample_offset(c, 8), r2))
-        ++in;
-    }
-  }
-  return in;
-}
-
-// b: the particle's box (shared memory); t: the cell's box index
+// inside and D > E outside.  Returns the group's count in every lane of the
+// group (the samples certainly inside), whether this lane's plane has a
+// sample in the band (|D| <= E) and whether any lane of the group has one;
+// such samples are decided afterwards by plane_band8.
 __device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, float r2f, float E,
-                                            const Box* b, int t) {
+                                            bool* lane_band, bool* band) {
   const unsigned all = 0xffffffffu;
   const int a = threadIdx.x & 7;
   const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
   const float Xr = px * px - r2f;
   float Z[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) Z[c] = sample_z8(dzf, c);
+  for (int c = 0; c < 8; ++c) {
+    const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+    Z[c] = pz * pz;
+  }
   int in = 0;
   float mn = 3.0e38f;
 #pragma unroll
@@ -627,14 +600,9 @@ __device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, flo
       mn = fminf(mn, fabsf(D));
     }
   }
-  if (__any_sync(all, mn <= E) && mn <= E) {
-    const int nxy = b->n[0] * b->n[1];
-    const int kz = (int)b->div_nxy.div((unsigned)t);
-    const int rem = t - kz * nxy;
-    const int ky = (int)b->div_n0.div((unsigned)rem);
-    in = plane_recount8(dyf, dzf, Xr, E, a, b->lo[0] + (rem - ky * b->n[0]), b->lo[1] + ky,
-                        b->lo[2] + kz, b);
-  }
+  const unsigned bm = __ballot_sync(all, mn <= E);
+  *lane_band = mn <= E;
+  *band = ((bm >> (threadIdx.x & 24)) & 0xffu) != 0u;
   in += __shfl_xor_sync(all, in, 4);
   in += __shfl_xor_sync(all, in, 2);
   in += __shfl_xor_sync(all, in, 1);
@@ -973,17 +941,79 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   }
 }
 
+// the samples of plane a of a cell that lie in the band (|D| <= E, the same
+// FP32 D as group_count8), decided by the FP64 definition; the cell's FP64
+// offset from its box index t (box coordinates unwrapped around the centre,
+// ((double)k + 1/2) - x_p, as the fill pass forms it).  Returns the number
+// of those inside.
+__device__ int plane_band8(float dxf, float dyf, float dzf, float r2f, float E, int a, int t,
+                           const Box& b) {
+  const int nxy = b.n[0] * b.n[1];
+  const int kz = (int)b.div_nxy.div((unsigned)t);
+  const int rem = t - kz * nxy;
+  const int ky = (int)b.div_n0.div((unsigned)rem);
+  const int kx = rem - ky * b.n[0];
+  const double dx = ((double)(b.lo[0] + kx) + 0.5) - b.xp[0];
+  const double dy = ((double)(b.lo[1] + ky) + 0.5) - b.xp[1];
+  const double dz = ((double)(b.lo[2] + kz) + 0.5) - b.xp[2];
+  const double r2 = b.r * b.r;
+  const float px = dxf + (((float)a + 0.5f) * 0.125f - 0.5f);
+  const float Xr = px * px - r2f;
+  int in = 0;
+  for (int bb = 0; bb < 8; ++bb) {
+    const float py = dyf + (((float)bb + 0.5f) * 0.125f - 0.5f);
+    const float XY = Xr + py * py;
+    for (int c = 0; c < 8; ++c) {
+      const float pz = dzf + (((float)c + 0.5f) * 0.125f - 0.5f);
+      const float D = XY + pz * pz;
+      if (fabsf(D) <= E && sample_inside_fp64(dx, dy, dz, sample_offset(a, 8),
+                                                sample_offset(bb, 8), sample_offset(c, 8), r2))
+        ++in;
+    }
+  }
+  return in;
+}
+
+// B of a count from the table into slot sl of entry e
+template <int REC>
+__device__ __forceinline__ void write_count_weight(const MapParams& P, unsigned e, unsigned sl,
+                                                   int c) {
+  const long long rec = (long long)sl * P.s.cap + e;
+  if (REC == REC_FP32) {
+    reinterpret_cast<float*>(P.s.V)[4 * rec + 3] =
+        __ldg(reinterpret_cast<const float*>(P.wtab + WTAB) + c);
+  } else if (REC == REC_DF) {
+    const df w = reinterpret_cast<const df*>(P.wtab + WTAB_DF)[c];
+    float* R = reinterpret_cast<float*>(P.s.V) + 8 * rec;
+    R[6] = w.hi;
+    R[7] = w.lo;
+  } else {
+    reinterpret_cast<double*>(P.s.V)[4 * rec + 3] = __ldg(P.wtab + c);
+  }
+}
+
 // 8^3 counts of the cells the fill pass listed (one block per particle, four
 // cells per warp and round, eight lanes per cell): B of each count from the
-// table into the slot record's weight.
+// table into the slot record's weight.  A cell with samples in the certified
+// band (about one in eighty) is queued with its certain count, and after the
+// rounds each queued plane is finished by one thread (plane_band8), so that
+// the rounds never wait on the FP64 definition; cells beyond the queue keep
+// the fill pass's B = -1 and the finish pass samples them.
+constexpr int CQ_ITEMS = 128, CQ_PLANES = 256;
 constexpr int COUNT_THREADS = 128;
 template <int REC>
 __global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
   __shared__ Box sbox;
+  __shared__ int q_items, q_planes;
+  __shared__ int q_item[CQ_ITEMS], q_cnt[CQ_ITEMS], q_plane[CQ_PLANES];
   const int p = blockIdx.x;
   const int n = P.wl_cnt[p];
   if (n == 0) return;  // the whole block
-  load_box(P, p, &sbox);
+  if (threadIdx.x == 0) {
+    q_items = 0;
+    q_planes = 0;
+  }
+  load_box(P, p, &sbox);  // ends with __syncthreads
   const long long base = P.list_off[p];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 3;
   const float r2f = sbox.r2f, E = sbox.E;
@@ -1008,21 +1038,42 @@ __global__ void __launch_bounds__(COUNT_THREADS, 6) count8_kernel(MapParams P) {
       wkn = (unsigned)P.wl_work[it];
     }
     const unsigned e = wk >> 1, sl = wk & 1u;
-    const int c = group_count8(X.x, X.y, X.z, r2f, E, &sbox, __float_as_int(X.w));
-    if (valid && (lane & 7) == 0) {
-      const long long rec = (long long)sl * P.s.cap + e;
-      if (REC == REC_FP32) {
-        reinterpret_cast<float*>(P.s.V)[4 * rec + 3] =
-            __ldg(reinterpret_cast<const float*>(P.wtab + WTAB) + c);
-      } else if (REC == REC_DF) {
-        const df w = reinterpret_cast<const df*>(P.wtab + WTAB_DF)[c];
-        float* R = reinterpret_cast<float*>(P.s.V) + 8 * rec;
-        R[6] = w.hi;
-        R[7] = w.lo;
-      } else {
-        reinterpret_cast<double*>(P.s.V)[4 * rec + 3] = __ldg(P.wtab + c);
+    bool lane_band, band;
+    const int c = group_count8(X.x, X.y, X.z, r2f, E, &lane_band, &band);
+    if (valid && (lane & 7) == 0 && !band) write_count_weight<REC>(P, e, sl, c);
+    if (__any_sync(0xffffffffu, valid && band)) {
+      // queue the cell with its certain count, then its planes with band samples
+      int j = -1;
+      if (valid && band && (lane & 7) == 0) {
+        j = atomicAdd(&q_items, 1);
+        if (j < CQ_ITEMS) {
+          q_item[j] = i;
+          q_cnt[j] = c;
+        }
+      }
+      j = __shfl_sync(0xffffffffu, j, lane & 24);
+      __syncwarp();  // the leaders' entries before the planes' updates
+      if (valid && band && lane_band && j >= 0 && j < CQ_ITEMS) {
+        const int k = atomicAdd(&q_planes, 1);
+        if (k < CQ_PLANES) q_plane[k] = (j << 3) | (lane & 7);
+        else atomicOr(&q_cnt[j], (int)0x80000000);  // left to the finish pass
       }
     }
+  }
+  __syncthreads();
+  const int np = min(q_planes, CQ_PLANES), ni = min(q_items, CQ_ITEMS);
+  for (int k = threadIdx.x; k < np; k += COUNT_THREADS) {
+    const int j = q_plane[k] >> 3, a = q_plane[k] & 7;
+    const float4 X = P.wl_X[base + q_item[j]];
+    const int add = plane_band8(X.x, X.y, X.z, r2f, E, a, __float_as_int(X.w), sbox);
+    if (add) atomicAdd(&q_cnt[j], add);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < ni; j += COUNT_THREADS) {
+    const int cnt = q_cnt[j];
+    if (cnt < 0) continue;  // a plane did not fit the queue: B stays -1
+    const unsigned wk = (unsigned)P.wl_work[base + q_item[j]];
+    write_count_weight<REC>(P, wk >> 1, wk & 1u, cnt);
   }
 }
 
