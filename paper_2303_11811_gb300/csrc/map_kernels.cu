@@ -4,11 +4,13 @@
 // Mapping replaces the paper's CPU-built sub-block particle lists with a
 // device-side, particle-centric scan:
 //   1. mark   every cell within reach (centre closer than r + sqrt(3)/2) of a
-//             particle sets its bit in the coverage mask;
+//             particle sets its bit in the coverage mask (and, when the bit
+//             was set already, in the mask of shared cells);
 //   2. scan   exclusive prefix count of the mask words gives each covered
 //             cell its slot-table index, in cell order;
-//   3. fill   each (particle, covered cell) pair claims one of the cell's two
-//             slots, stores B_i = W(eps_i) and appends the entry to the
+//   3. fill   each (particle, covered cell) pair takes one of the cell's two
+//             slots (slot 0 when the cell is not shared, else a claim on a
+//             counter), stores B_i = W(eps_i) and appends the entry to the
 //             particle's list (box order, deterministic); with 8^3 sampling
 //             the cells that need samples go to a per-particle worklist,
 //             3b. count8 counts them, four cells per warp;
@@ -26,7 +28,7 @@ namespace psm {
 namespace {
 
 constexpr double HALF_SQRT3 = kHalfSqrt3;
-constexpr int MAP_THREADS = 256;
+constexpr int MAP_THREADS = 128;
 // threads of a fill block (one block per particle) and blocks per SM: a
 // block's phases wait on dependent global loads, so many small blocks keep
 // more of them in flight (settle512: 64 threads map 6-7% faster than 256)
@@ -222,38 +224,110 @@ __device__ __forceinline__ bool in_reach(const Box& b, int kx, int ky, int kz) {
   return reach_test(b, h);
 }
 
-// the row-wise mark pass serves boxes of rows long enough to pay for its run
-// search (radius about 7 and more) and of at most MARK_MAX_ROWS rows
+// inside by the margin (FP64 squared distance <= (r - sqrt(3)/2)^2, the
+// decision of the fill pass's class test), in FP32 outside the certified band
+__device__ __forceinline__ bool inside_margin(const Box& b, int kx, int ky, int kz) {
+  const float dxf = (float)(kx - b.ip[0]) + (0.5f - b.fpf[0]);
+  const float dyf = (float)(ky - b.ip[1]) + (0.5f - b.fpf[1]);
+  const float dzf = (float)(kz - b.ip[2]) + (0.5f - b.fpf[2]);
+  const float d2f = dxf * dxf + dyf * dyf + dzf * dzf;
+  if (d2f < b.rin2f - b.E) return true;
+  if (d2f > b.rin2f + b.E) return false;
+  const double dx = ((double)kx + 0.5) - b.xp[0];
+  const double dy = ((double)ky + 0.5) - b.xp[1];
+  const double dz = ((double)kz + 0.5) - b.xp[2];
+  return dx * dx + dy * dy + dz * dz <= b.rin2;
+}
+
+__device__ __forceinline__ bool wall_cell(const Grid& g, int ix, int iy, int iz) {
+  return (g.wall[0] && (ix == 0 || ix == g.nx - 1)) || (g.wall[1] && (iy == 0 || iy == g.ny - 1)) ||
+         (g.wall[2] && (iz == 0 || iz == g.nz - 1));
+}
+
+// surrogate mode: of the cells a..e of a box row (all in reach), those that
+// go to the network: not inside by the margin and not next to a wall face.
+// Like the cells in reach, the inside cells of a row form one run around
+// the centre's column kc (the FP64 squared distance is unimodal along x).
+__device__ int row_net(const Grid& g, const Box& b, int a, int e, int kc, int ky, int kz) {
+  const int iy = wrap1(ky, g.ny), iz = wrap1(kz, g.nz);
+  if ((g.wall[1] && (iy == 0 || iy == g.ny - 1)) || (g.wall[2] && (iz == 0 || iz == g.nz - 1)))
+    return 0;
+  int ai = 1, ei = 0;  // inside run (empty)
+  if (b.has_in && inside_margin(b, kc, ky, kz)) {
+    const float dyf = (float)(ky - b.ip[1]) + (0.5f - b.fpf[1]);
+    const float dzf = (float)(kz - b.ip[2]) + (0.5f - b.fpf[2]);
+    const float rem = b.rin2f - (dyf * dyf + dzf * dzf);
+    const int w = (int)sqrtf(rem > 0.f ? rem : 0.f) + 1;
+    ai = kc - w < a ? a : kc - w;
+    while (ai < kc && !inside_margin(b, ai, ky, kz)) ++ai;
+    while (ai > a && inside_margin(b, ai - 1, ky, kz)) --ai;
+    ei = kc + w > e ? e : kc + w;
+    while (ei > kc && !inside_margin(b, ei, ky, kz)) --ei;
+    while (ei < e && inside_margin(b, ei + 1, ky, kz)) ++ei;
+  }
+  int net = (e - a + 1) - (ei >= ai ? ei - ai + 1 : 0);
+  if (g.wall[0]) {  // along a wall axis box coordinates are not wrapped
+    if (a <= 0 && 0 <= e && !(ai <= 0 && 0 <= ei)) --net;
+    const int xl = g.nx - 1;
+    if (xl > 0 && a <= xl && xl <= e && !(ai <= xl && xl <= ei)) --net;
+  }
+  return net;
+}
+
+// coverage bits of the cells x0..x1 (0 <= x0 <= x1 < nx) of the grid row
+// whose first mask word is wb, one atomicOr per word; bits that were set
+// already (a second particle) go to the mask of shared cells
+__device__ __forceinline__ void cover_run(const Coverage& cov, long long wb, int x0, int x1) {
+  for (int w = x0 >> 5; w <= (x1 >> 5); ++w) {
+    const int b0 = x0 - 32 * w > 0 ? x0 - 32 * w : 0;
+    const int b1 = x1 - 32 * w < 31 ? x1 - 32 * w : 31;
+    const unsigned hi = b1 == 31 ? 0xffffffffu : (1u << (b1 + 1)) - 1u;
+    const unsigned bits = hi & ~((1u << b0) - 1u);
+    const unsigned old = atomicOr(cov.mask + wb + w, bits);
+    if (old & bits) atomicOr(cov.dup + wb + w, old & bits);
+  }
+}
+
+// the row pass serves boxes of at most MARK_MAX_ROWS rows (radius up to 14)
 constexpr int MARK_MAX_ROWS = 1024;
-constexpr int MARK_MIN_ROW = 16;
 
 // Cells in reach of one particle (one block per particle): the coverage bits
-// (one atomicOr per distinct word of a warp) and the particle's list of its
-// cells in box order, as box indices t; the fill pass replaces them by slot
-// indices.  Along an x-row of the box the FP64 squared distance is unimodal
-// (IEEE rounding is monotone), so the row's cells in reach form one run: its
-// ends are found with a few certified reach tests around the cell holding
-// the centre, the runs are scanned in row order and written by one warp per
-// row.  Small boxes (short rows) and very large ones test every cell.
+// (the mask of shared cells from the bits already set) and the particle's
+// list of its cells in box order, as box indices t; the fill pass replaces
+// them by slot indices.  Along an x-row of the box the FP64 squared distance
+// is unimodal (IEEE rounding is monotone), so the row's cells in reach form
+// one run: its ends are found with a few certified reach tests around the
+// cell holding the centre.  One thread per row finds the run, the run
+// lengths are scanned in row order, the same thread sets the run's bits with
+// one atomicOr per mask word, and the list entries are written in list order
+// (a thread per entry finds its row by bisection).  In surrogate mode the
+// row's cells for the network are counted as well.  Very large boxes test
+// every cell.
 __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
   __shared__ int warp_tot[MAP_THREADS / 32];
-  __shared__ int running;
+  __shared__ int running, net_sum;
   __shared__ Box sbox;
   __shared__ int row_lo[MARK_MAX_ROWS], row_n[MARK_MAX_ROWS], row_off[MARK_MAX_ROWS];
   const int p = blockIdx.x;
   const long long loff = P.list_off[p];
   const int lcap = (int)(P.list_off[p + 1] - loff);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) running = 0;
+  const bool count_net = P.list_net != nullptr;
+  if (threadIdx.x == 0) {
+    running = 0;
+    net_sum = 0;
+  }
   load_box(P, p, &sbox);  // ends with __syncthreads
   const Box b = sbox;
   const int rows = b.n[1] * b.n[2];
-  if (rows <= MARK_MAX_ROWS && b.n[0] >= MARK_MIN_ROW) {
+  int net = 0;
+  if (rows <= MARK_MAX_ROWS) {
     // ---- runs of the rows
     const int kc = b.ip[0];  // the x cell holding the centre: the row's closest
     for (int r = threadIdx.x; r < rows; r += MAP_THREADS) {
-      const int kz = b.lo[2] + r / b.n[1];
-      const int ky = b.lo[1] + (r - (r / b.n[1]) * b.n[1]);
+      const int rz = r / b.n[1];
+      const int kz = b.lo[2] + rz;
+      const int ky = b.lo[1] + (r - rz * b.n[1]);
       int lo = 0, cnt = 0;
       if (b.n[0] > 0 && in_reach(b, kc, ky, kz)) {
         const float dyf = (float)(ky - b.ip[1]) + (0.5f - b.fpf[1]);
@@ -269,6 +343,7 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
         while (e < x1 && in_reach(b, e + 1, ky, kz)) ++e;
         lo = a - x0;
         cnt = e - a + 1;
+        if (count_net) net += row_net(P.g, b, a, e, kc, ky, kz);
       }
       row_lo[r] = lo;
       row_n[r] = cnt;
@@ -298,41 +373,49 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
       off += row_n[r];
     }
     __syncthreads();
-    // ---- one warp per row: list entries and coverage bits
-    for (int r = wid; r < rows; r += MAP_THREADS / 32) {
+    // ---- coverage bits: one thread per row, one atomicOr per mask word
+    for (int r = threadIdx.x; r < rows; r += MAP_THREADS) {
       const int n = row_n[r];
       if (n == 0) continue;
-      const int kz = b.lo[2] + r / b.n[1];
-      const int ky = b.lo[1] + (r - (r / b.n[1]) * b.n[1]);
-      const int iy = wrap1(ky, P.g.ny), iz = wrap1(kz, P.g.nz);
-      for (int i0 = 0; i0 < n; i0 += 32) {
-        const int i = i0 + lane;
-        const bool in = i < n;
-        const int kxl = row_lo[r] + i;  // box-local x
-        const long long cell =
-            in ? padded_cell(P.g, wrap1(b.lo[0] + kxl, P.g.nx), iy, iz) : 0;
-        if (in) {
-          const int pos = row_off[r] + i;
-          if (pos < lcap) P.list[loff + pos] = kxl + b.n[0] * r;
-        }
-        unsigned pend = __ballot_sync(0xffffffffu, in);
-        while (pend) {
-          const int leader = __ffs(pend) - 1;
-          const long long w0 = __shfl_sync(0xffffffffu, cell >> 5, leader);
-          const bool mine_w = in && (cell >> 5) == w0;
-          const unsigned bits = __reduce_or_sync(0xffffffffu, mine_w ? 1u << (cell & 31) : 0u);
-          if (lane == leader) atomicOr(&P.cov.mask[w0], bits);
-          pend &= ~__ballot_sync(0xffffffffu, mine_w);
-        }
+      const int rz = r / b.n[1];
+      const int kz = b.lo[2] + rz;
+      const int ky = b.lo[1] + (r - rz * b.n[1]);
+      const long long wb = padded_cell(P.g, 0, wrap1(ky, P.g.ny), wrap1(kz, P.g.nz)) >> 5;
+      // the run in grid x: box x is unwrapped and the run is shorter than
+      // the period, so it wraps at most once
+      const int xs = wrap1(b.lo[0] + row_lo[r], P.g.nx), xe = xs + n - 1;
+      if (xe < P.g.nx) {
+        cover_run(P.cov, wb, xs, xe);
+      } else {
+        cover_run(P.cov, wb, xs, P.g.nx - 1);
+        cover_run(P.cov, wb, 0, xe - P.g.nx);
       }
     }
+    // ---- list entries in list order (coalesced stores): entry pos belongs
+    // to the last row whose offset is <= pos (that row is not empty)
+    const int m = total < lcap ? total : lcap;
+    for (int pos = threadIdx.x; pos < m; pos += MAP_THREADS) {
+      int lo = 0, hi = rows - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= pos) lo = mid;
+        else hi = mid - 1;
+      }
+      P.list[loff + pos] = row_lo[lo] + b.n[0] * lo + (pos - row_off[lo]);
+    }
+    if (count_net) {
+      net = __reduce_add_sync(0xffffffffu, net);
+      if (lane == 0 && net) atomicAdd(&net_sum, net);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       P.list_cnt[p] = total < lcap ? total : lcap;
       if (total > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
+      if (count_net) P.list_net[p] = net_sum;
     }
     return;
   }
-  // ---- large boxes: every cell of the box
+  // ---- very large boxes: every cell of the box
   for (int t0 = 0; t0 < b.count; t0 += MAP_THREADS) {
     const int t = t0 + threadIdx.x;
     CellHit h;
@@ -341,6 +424,9 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
       box_coords(P.g, b, t, h);
       in = reach_test(b, h);
     }
+    if (count_net && in && !wall_cell(P.g, h.ix, h.iy, h.iz) &&
+        !(b.has_in && inside_margin(b, h.kx, h.ky, h.kz)))
+      ++net;
     const unsigned bal = __ballot_sync(0xffffffffu, in);
     if (lane == 0) warp_tot[wid] = __popc(bal);
     const long long cell = in ? padded_cell(P.g, h.ix, h.iy, h.iz) : 0;
@@ -350,7 +436,10 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
       const long long w0 = __shfl_sync(0xffffffffu, cell >> 5, leader);
       const bool mine = in && (cell >> 5) == w0;
       const unsigned bits = __reduce_or_sync(0xffffffffu, mine ? 1u << (cell & 31) : 0u);
-      if (lane == leader) atomicOr(&P.cov.mask[w0], bits);
+      if (lane == leader) {
+        const unsigned old = atomicOr(&P.cov.mask[w0], bits);
+        if (old & bits) atomicOr(&P.cov.dup[w0], old & bits);
+      }
       pend &= ~__ballot_sync(0xffffffffu, mine);
     }
     __syncthreads();
@@ -365,9 +454,15 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
     if (threadIdx.x == 0) running += chunk;
     __syncthreads();
   }
+  if (count_net) {
+    net = __reduce_add_sync(0xffffffffu, net);
+    if (lane == 0 && net) atomicAdd(&net_sum, net);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
     P.list_cnt[p] = running < lcap ? running : lcap;
     if (running > lcap) atomicOr(P.status, ST_SLOT_OVERFLOW);
+    if (count_net) P.list_net[p] = net_sum;
   }
 }
 
@@ -646,10 +741,7 @@ __device__ __forceinline__ int net_class(const Grid& g, const Box& b, const Cell
     if (h.d2f < b.rin2f - b.E) return 1;
     if (h.d2f <= b.rin2f + b.E && h.dx * h.dx + h.dy * h.dy + h.dz * h.dz <= b.rin2) return 1;
   }
-  const bool wallcell = (g.wall[0] && (h.ix == 0 || h.ix == g.nx - 1)) ||
-                        (g.wall[1] && (h.iy == 0 || h.iy == g.ny - 1)) ||
-                        (g.wall[2] && (h.iz == 0 || h.iz == g.nz - 1));
-  return wallcell ? 2 : 0;
+  return wall_cell(g, h.ix, h.iy, h.iz) ? 2 : 0;
 }
 
 // Slots of one particle's cells (one block per particle, over the list the
@@ -683,8 +775,10 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   if (tables) {
     for (int t = threadIdx.x; t < 3 * FILL_AXIS; t += FILL_THREADS) {
       const int a = t / FILL_AXIS, k = t - a * FILL_AXIS;
-      if (k < b.n[a]) {
-        const double d = ((double)(b.lo[a] + k) + 0.5) - b.xp[a];
+      // the axis is a run-time index: read the shared copy (a local copy
+      // indexed at run time would live on the stack)
+      if (k < sbox.n[a]) {
+        const double d = ((double)(sbox.lo[a] + k) + 0.5) - sbox.xp[a];
         toff[a][k] = d;
         toff32[a][k] = (float)d;
         if (REC == REC_DF) toffd[a][k] = df(d);
@@ -715,20 +809,11 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     __syncthreads();
   }
   if constexpr (NS < 0) {
-    // count the block's network cells first and reserve their worklist
-    // range with one atomic (a counter shared by every block would serialise)
-    if (threadIdx.x == 0) net_cnt = 0;
-    __syncthreads();
-    int mine = 0;
-    for (int k = threadIdx.x; k < cnt; k += FILL_THREADS) {
-      CellHit h;
-      cell_hit(P.g, b, P.list[loff + k], tables, toff, toff32, h);
-      mine += net_class(P.g, b, h) == 0;
-    }
-    mine = __reduce_add_sync(0xffffffffu, mine);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&net_cnt, mine);
-    __syncthreads();
+    // the particle's network cells (counted by the mark pass) get one
+    // worklist range, reserved with one atomic (a counter shared by every
+    // block would serialise)
     if (threadIdx.x == 0) {
+      net_cnt = P.list_net[p];
       net_base = net_cnt ? atomicAdd(P.mlp_count, net_cnt) : 0;
       net_next = net_base;
     }
@@ -738,9 +823,35 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   // warp; lanes past the list idle); the other modes give each thread its
   // own cells
   const int lane = threadIdx.x & 31;
+  // software pipeline over a thread's rounds: the list entry two rounds
+  // ahead and the coverage words (base, mask, shared mask) of the next
+  // round's cell are loaded before this round's cell is filled
+  const int kfirst = NS == 8 ? (threadIdx.x & ~31) + lane : threadIdx.x;
+  auto words_of = [&](int t, int& wbase, uint32_t& wmask, uint32_t& wdup) {
+    CellHit q;
+    box_coords(P.g, b, t, q);
+    const long long w = padded_cell(P.g, q.ix, q.iy, q.iz) >> 5;
+    wbase = P.cov.base[w];
+    wmask = P.cov.mask[w];
+    wdup = P.cov.dup[w];
+  };
+  int tb_next = 0, tb_next2 = 0;  // list entries of the next two rounds
+  int nbase = 0;                  // coverage words of the next round's cell
+  uint32_t nmask = 0u, ndup = 0u;
+  if (kfirst < cnt) {
+    tb_next = P.list[loff + kfirst];
+    words_of(tb_next, nbase, nmask, ndup);
+  }
+  if (kfirst + FILL_THREADS < cnt) tb_next2 = P.list[loff + kfirst + FILL_THREADS];
   for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += FILL_THREADS) {
     const int k = NS == 8 ? k0 + lane : k0;
     bool ok = NS == 8 ? k < cnt : true;
+    const int tb = tb_next;  // box index of the cell (the list entry before the fill)
+    const int cbase = nbase;
+    const uint32_t cmask = nmask, cdup = ndup;
+    tb_next = tb_next2;
+    tb_next2 = k + 2 * FILL_THREADS < cnt ? P.list[loff + k + 2 * FILL_THREADS] : 0;
+    if (k + FILL_THREADS < cnt) words_of(tb_next, nbase, nmask, ndup);
     CellHit h;
     if constexpr (NS == 8) {  // lanes past the list still take part in the ballot
       h.dx = h.dy = h.dz = 0.0;
@@ -748,22 +859,27 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     }
     long long cell = 0, e = 0;
     int s = 0;
-    int tb = 0;  // box index of the cell (the list entry before the fill)
+    bool shared = false;  // a second particle in reach of the cell
     if (ok) {
-      tb = P.list[loff + k];
       cell_hit(P.g, b, tb, tables, toff, toff32, h);
       cell = padded_cell(P.g, h.ix, h.iy, h.iz);
-      e = slot_index(P.cov, cell);
+      const uint32_t bit = 1u << (cell & 31);
+      e = (long long)cbase + __popc(cmask & (bit - 1u));
+      shared = (cdup & bit) != 0u;
       if (e >= P.s.cap) {
         P.list[loff + k] = 0;  // the step reports the slot overflow
         ok = false;
       } else {
         P.list[loff + k] = (int)e;
-        // the cell's particle count: 2-bit fields, 16 per word, so that the
-        // counters of a whole mapping stay in L2 for these atomics
-        const int sh = 2 * (int)(e & 15);
-        s = (int)((atomicAdd(reinterpret_cast<unsigned*>(P.s.cnt) + (e >> 4), 1u << sh) >> sh) &
-                  3u);
+        // a cell of this particle alone takes slot 0; a shared cell claims
+        // its slot on a particle count (2-bit fields, 16 per word, so that
+        // the counters of a whole mapping stay in L2 for these atomics)
+        if (shared) {
+          const int sh = 2 * (int)(e & 15);
+          s = (int)((atomicAdd(reinterpret_cast<unsigned*>(P.s.cnt) + (e >> 4), 1u << sh) >>
+                     sh) &
+                    3u);
+        }
         if (s >= 2) {
           atomicOr(P.status, ST_SLOT_OVERFLOW);
           ok = false;
@@ -821,9 +937,11 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
         B = weight((double)c * (1.0 / 512.0), P.tau, P.weighting);
         Bf = (float)B;
       } else {
+        // a cell shared with another particle stays pending (8^3 sampling
+        // in the finish pass)
         B = -1.0;
         Bf = -1.f;
-        want = true;
+        want = !shared;
       }
     } else if (NS == 8 && pending) {
       B = -1.0;
@@ -901,7 +1019,8 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       // per group of converged lanes: the
       // network's inputs (|d/r| components in decreasing order, r), the
       // linear approximation of Eqs. 25-27, and 2 * entry + slot.  Items
-      // beyond the worklist's capacity keep B = -1 (8^3 sampling later).
+      // beyond the particle's range or the worklist's capacity keep B = -1
+      // (8^3 sampling later).
       const unsigned grp = __activemask();
       const unsigned wm = __ballot_sync(grp, want);
       if (want) {
@@ -911,7 +1030,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
         if (lane == leader) first = atomicAdd(&net_next, __popc(wm));
         first = __shfl_sync(wm, first, leader);
         const long long k = (long long)first + __popc(wm & ((1u << lane) - 1u));
-        if (k < P.mlp_cap) {
+        if (k < (long long)net_base + net_cnt && k < P.mlp_cap) {
           float a0 = fabsf(h.dxf) * rinvf, a1 = fabsf(h.dyf) * rinvf, a2 = fabsf(h.dzf) * rinvf;
           float t;
           if (a1 > a0) { t = a0; a0 = a1; a1 = t; }
@@ -1226,7 +1345,9 @@ __device__ double finish_entry(const MapParams& P, int e, int n, bool* full) {
     B = T(1);
   }
   r0[3] = two ? -r0[3] : r0[3];
-  rec_store(V + 4 * e, r0);
+  // a cell of one particle whose weight was not pending is unchanged (its B
+  // is at most 1 and keeps its sign): no store
+  if (two || ((pend >> (threadIdx.x & 31)) & 1u)) rec_store(V + 4 * e, r0);
   if (two) {
     P.s.pid[e] = pid;
     rec_store(V + 4 * e1, r1);
@@ -1256,6 +1377,9 @@ __device__ __forceinline__ void mark_full(const MapParams& P, int e, bool fl) {
   if (fl && (lane == 31 || wn != w)) atomicOr(P.cov.full + w, v);
 }
 
+// one instance per record format (REC_*), so that each carries only its own
+// path's registers
+template <int REC>
 __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   __shared__ double red[256];
   const int n = slot_count(P);
@@ -1265,10 +1389,10 @@ __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
     bool fl = false;
-    accB += P.fp32    ? finish_entry<float, float>(P, e, n, &fl)
-            : P.dfrec ? finish_entry<double, df>(P, e, n, &fl)
-                      : finish_entry<double, double>(P, e, n, &fl);
-    if (P.cov.full) mark_full(P, e, fl);
+    if constexpr (REC == REC_FP32) accB += finish_entry<float, float>(P, e, n, &fl);
+    else if constexpr (REC == REC_DF) accB += finish_entry<double, df>(P, e, n, &fl);
+    else accB += finish_entry<double, double>(P, e, n, &fl);
+    if (REC == REC_FP64 && P.cov.full) mark_full(P, e, fl);
   }
   red[threadIdx.x] = accB;
   __syncthreads();
@@ -1685,6 +1809,7 @@ void launch_fill(const MapParams& P, bool mlp, cudaStream_t s) {
 int map_common(MapParams P, cudaStream_t s, bool mlp) {
   int launches = 0;
   cudaMemsetAsync(P.cov.mask, 0, sizeof(uint32_t) * P.g.nwords, s);
+  cudaMemsetAsync(P.cov.dup, 0, sizeof(uint32_t) * P.g.nwords, s);
   if (P.cov.full) cudaMemsetAsync(P.cov.full, 0, sizeof(uint32_t) * P.g.nwords, s);
   if (mlp) cudaMemsetAsync(P.mlp_count, 0, sizeof(int), s);
   if (P.p.n > 0) {
@@ -1716,7 +1841,9 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
 
 int map_finish(MapParams P, cudaStream_t s) {
   const unsigned nfin = grid_cap(P.s.cap, 256);
-  finish_kernel<<<nfin, 256, 0, s>>>(P);
+  if (P.fp32) finish_kernel<REC_FP32><<<nfin, 256, 0, s>>>(P);
+  else if (P.dfrec) finish_kernel<REC_DF><<<nfin, 256, 0, s>>>(P);
+  else finish_kernel<REC_FP64><<<nfin, 256, 0, s>>>(P);
   vfluid_kernel<<<1, 256, 0, s>>>(P, (int)nfin);
   return 2;
 }
@@ -1736,7 +1863,6 @@ int launch_map_mlp(MapParams P, cudaStream_t s) {
   if (P.mlp && P.mlp_cap > 0) {
     InferSink out{};
     out.V = P.s.V;
-    out.cnt = P.s.cnt;
     out.lin = P.mlp_lin;
     out.work = P.mlp_work;
     out.cap = P.s.cap;

@@ -437,10 +437,6 @@ __global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long row = tile * INF_M + tid;
     const bool live = row < n;
-    // particles in reach of the item's cell (2-bit fields, 16 per word)
-    const int cnt = item >= 0 ? (int)((__ldg(&o.cnt[(item >> 1) >> 4]) >>
-                                        (2 * ((item >> 1) & 15))) & 3)
-                              : 0;
     float4 xn;
     int itemn;
     float linn;
@@ -497,7 +493,8 @@ __global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
     if (live) {
       if (o.eps) {
         o.eps[row] = y;
-      } else if (item >= 0 && cnt == 1) {  // item -1: an empty item
+      } else if (item >= 0) {  // item -1: an empty item (the fill pass lists
+                               // only cells in reach of one particle)
         float eps = lin + y;
         eps = eps < 0.f ? 0.f : (eps > 1.f ? 1.f : eps);
         apply_weight(o, (item & 1) * o.cap + (item >> 1), eps);

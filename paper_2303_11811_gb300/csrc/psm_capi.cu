@@ -83,6 +83,7 @@ struct psm_ctx {
   long long* list_off = nullptr;  // per-particle entry lists (force reduction)
   int* list = nullptr;
   int* list_cnt = nullptr;
+  int* list_net = nullptr;   // surrogate mode: the network's cells per particle
   void* boxes = nullptr;     // per-particle box of cells (mapping set-up)
   bool error_state = false;
   std::string err;
@@ -177,6 +178,7 @@ void free_particles(psm_ctx* c) {
   c->dem_nbr = nullptr;
   c->dem_xbuild = nullptr;
   c->list_cnt = nullptr;
+  c->list_net = nullptr;
   c->boxes = nullptr;
 }
 
@@ -215,6 +217,7 @@ MapParams map_params(psm_ctx* c) {
   P.list_off = c->list_off;
   P.list = c->list;
   P.list_cnt = c->list_cnt;
+  P.list_net = c->list_net;
   P.boxes = c->boxes;
   return P;
 }
@@ -553,6 +556,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   }
   c->cov.mask = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
   c->cov.base = alloc_n<int>(c, (size_t)g.nwords, c->allocs);
+  c->cov.dup = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
   if (c->prec == PREC_FP64) {
     c->cov.full = alloc_n<uint32_t>(c, (size_t)g.nwords, c->allocs);
     if (!c->cov.full) return bail(PSM_ERR_OOM, "allocator returned NULL");
@@ -568,7 +572,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   c->dem_bar = alloc_n<unsigned>(c, 4, c->allocs);
   // 513 doubles, 513 floats, 513 double-float pairs
   c->wtab = alloc_n<double>(c, 513 + 257 + 513, c->allocs);
-  if (!c->cov.mask || !c->cov.base || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
+  if (!c->cov.mask || !c->cov.base || !c->cov.dup || !c->cov.blocksum || !c->cov.ncov || !c->sc ||
       !c->status || !c->partials || !c->mlp || !c->mlp_count || !c->dem_bar || !c->wtab)
     return bail(PSM_ERR_OOM, "allocator returned NULL");
   cudaStream_t s = c->stream;
@@ -576,6 +580,7 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
   for (int b = 0; b < nbuf; ++b)
     ok = ok && cudaMemsetAsync(c->buf[b], 0, esz * Q * (size_t)ncell, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->cov.mask, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
+  ok = ok && cudaMemsetAsync(c->cov.dup, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
   if (c->cov.full)
     ok = ok && cudaMemsetAsync(c->cov.full, 0, sizeof(uint32_t) * g.nwords, s) == cudaSuccess;
   ok = ok && cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) == cudaSuccess;
@@ -750,6 +755,7 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
     c->mlp_X = alloc_n<float>(c, 4 * cp, c->palloc);
     c->mlp_lin = alloc_n<float>(c, cp, c->palloc);
     c->mlp_work = alloc_n<int>(c, cp, c->palloc);
+    c->list_net = alloc_n<int>(c, n1, c->palloc);
   }
   for (void* q : c->palloc)
     if (!q) {

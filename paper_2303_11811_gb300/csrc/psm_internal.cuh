@@ -168,6 +168,10 @@ struct Coverage {
   // FP64 records only (else nullptr): bit = covered cell with one particle
   // and B = 1 (every sample inside), written by the finish pass
   uint32_t* full;
+  // bit = cell in reach of two or more particles (the mark pass sets it when
+  // its coverage bit was already set): a cell without it takes slot 0 with no
+  // claim, and in surrogate mode it is the network's if partial
+  uint32_t* dup;
   int* blocksum;
   int* ncov;      // device scalar
   long long nblocks;
@@ -211,6 +215,10 @@ struct MapParams {
   const long long* list_off;   // n+1 offsets
   int* list;
   int* list_cnt;
+  // surrogate mode: per particle, its partial cells for the network (in
+  // reach, not inside by the margin, not next to a wall face), counted by the
+  // mark pass; the fill pass reserves that many worklist items
+  int* list_net;
 };
 constexpr int MAP_PARTIALS = 152 * 32;
 
@@ -326,7 +334,6 @@ int launch_adam(float* params, const float* grad, float* mstate, float* vstate, 
 struct InferSink {
   float* eps;          // raw outputs, or NULL
   void* V;             // Slots::V
-  const int* cnt;      // Slots::cnt
   const float* lin;    // linear approximation (Eqs. 25-27) per item
   const int* work;     // item -> 2 * slot entry + slot
   long long cap;       // slot entries allocated
