@@ -55,6 +55,7 @@ struct Box {
   // taken without sampling
   float in8f, out8f;
   FastDiv div_n0, div_nxy;  // box index t -> (kx, ky, kz)
+  FastDiv div_n1;           // box row r -> (ky, kz)
 };
 
 __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, double r) {
@@ -77,6 +78,7 @@ __device__ __forceinline__ Box particle_box(const Grid& g, const double* x, doub
   }
   b.count = b.n[0] * b.n[1] * b.n[2];
   b.div_n0 = make_fastdiv((unsigned)(b.n[0] > 0 ? b.n[0] : 1));
+  b.div_n1 = make_fastdiv((unsigned)(b.n[1] > 0 ? b.n[1] : 1));
   b.div_nxy = make_fastdiv((unsigned)(b.n[0] * b.n[1] > 0 ? b.n[0] * b.n[1] : 1));
   b.r = r;
   const double reach = r + HALF_SQRT3;
@@ -276,13 +278,28 @@ __device__ int row_net(const Grid& g, const Box& b, int a, int e, int kc, int ky
 
 // coverage bits of the cells x0..x1 (0 <= x0 <= x1 < nx) of the grid row
 // whose first mask word is wb, one atomicOr per word; bits that were set
-// already (a second particle) go to the mask of shared cells
+// already (a second particle) go to the mask of shared cells.  A run of at
+// most 33 cells spans at most two words, whose atomics are both issued
+// before either result is used.
+__device__ __forceinline__ unsigned run_bits(int x0, int x1, int w) {
+  const int b0 = x0 - 32 * w > 0 ? x0 - 32 * w : 0;
+  const int b1 = x1 - 32 * w < 31 ? x1 - 32 * w : 31;
+  const unsigned hi = b1 == 31 ? 0xffffffffu : (1u << (b1 + 1)) - 1u;
+  return hi & ~((1u << b0) - 1u);
+}
 __device__ __forceinline__ void cover_run(const Coverage& cov, long long wb, int x0, int x1) {
-  for (int w = x0 >> 5; w <= (x1 >> 5); ++w) {
-    const int b0 = x0 - 32 * w > 0 ? x0 - 32 * w : 0;
-    const int b1 = x1 - 32 * w < 31 ? x1 - 32 * w : 31;
-    const unsigned hi = b1 == 31 ? 0xffffffffu : (1u << (b1 + 1)) - 1u;
-    const unsigned bits = hi & ~((1u << b0) - 1u);
+  const int w0 = x0 >> 5, w1 = x1 >> 5;
+  if (w1 - w0 <= 1) {
+    const unsigned m0 = run_bits(x0, x1, w0);
+    const unsigned m1 = w1 > w0 ? run_bits(x0, x1, w1) : 0u;
+    const unsigned o0 = atomicOr(cov.mask + wb + w0, m0);
+    const unsigned o1 = w1 > w0 ? atomicOr(cov.mask + wb + w1, m1) : 0u;
+    if (o0 & m0) atomicOr(cov.dup + wb + w0, o0 & m0);
+    if (o1 & m1) atomicOr(cov.dup + wb + w1, o1 & m1);
+    return;
+  }
+  for (int w = w0; w <= w1; ++w) {
+    const unsigned bits = run_bits(x0, x1, w);
     const unsigned old = atomicOr(cov.mask + wb + w, bits);
     if (old & bits) atomicOr(cov.dup + wb + w, old & bits);
   }
@@ -303,7 +320,7 @@ constexpr int MARK_MAX_ROWS = 1024;
 // (a thread per entry finds its row by bisection).  In surrogate mode the
 // row's cells for the network are counted as well.  Very large boxes test
 // every cell.
-__global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
+__global__ void __launch_bounds__(MAP_THREADS, 12) mark_kernel(MapParams P) {
   __shared__ int warp_tot[MAP_THREADS / 32];
   __shared__ int running, net_sum;
   __shared__ Box sbox;
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
     // ---- runs of the rows
     const int kc = b.ip[0];  // the x cell holding the centre: the row's closest
     for (int r = threadIdx.x; r < rows; r += MAP_THREADS) {
-      const int rz = r / b.n[1];
+      const int rz = (int)b.div_n1.div((unsigned)r);
       const int kz = b.lo[2] + rz;
       const int ky = b.lo[1] + (r - rz * b.n[1]);
       int lo = 0, cnt = 0;
@@ -377,7 +394,7 @@ __global__ void __launch_bounds__(MAP_THREADS) mark_kernel(MapParams P) {
     for (int r = threadIdx.x; r < rows; r += MAP_THREADS) {
       const int n = row_n[r];
       if (n == 0) continue;
-      const int rz = r / b.n[1];
+      const int rz = (int)b.div_n1.div((unsigned)r);
       const int kz = b.lo[2] + rz;
       const int ky = b.lo[1] + (r - rz * b.n[1]);
       const long long wb = padded_cell(P.g, 0, wrap1(ky, P.g.ny), wrap1(kz, P.g.nz)) >> 5;
@@ -770,7 +787,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   const bool tab = P.eps_mode == 0 && P.wtab != nullptr;
   const double* wtab = P.wtab;
   load_offsets(P.eps_n, s64, s32);  // ends with __syncthreads
-  const Box b = sbox;
+  const Box& b = sbox;  // read from shared memory (a register copy spills)
   const bool tables = b.n[0] <= FILL_AXIS && b.n[1] <= FILL_AXIS && b.n[2] <= FILL_AXIS;
   if (tables) {
     for (int t = threadIdx.x; t < 3 * FILL_AXIS; t += FILL_THREADS) {
@@ -1304,18 +1321,18 @@ __device__ __noinline__ WeightPair<T> pending_weights(const MapParams& P, int e,
 // particles in surrogate mode, worklist overflow, no network) with 8^3 points,
 // normalise B > 1 (Sec. 2.3), flag a second particle in the sign of slot 0's
 // weight; returns min(B, 1) (0 for lanes without an entry)
+// pid and r0: the entry's particle pair and slot-0 record, loaded by the
+// caller a round ahead
 template <typename T, typename S>  // arithmetic in T, records stored as S
-__device__ double finish_entry(const MapParams& P, int e, int n, bool* full) {
+__device__ double finish_entry(const MapParams& P, int e, int n, int2 pid, const T* pre,
+                               bool* full) {
   const bool live = e < n;
-  int2 pid = make_int2(-1, -1);
-  T r0[4] = {T(0), T(0), T(0), T(0)}, r1[4] = {T(0), T(0), T(0), T(0)};
+  T r0[4] = {pre[0], pre[1], pre[2], pre[3]}, r1[4] = {T(0), T(0), T(0), T(0)};
   S* V = static_cast<S*>(P.s.V);
   const long long e1 = P.s.cap + e;
   bool two = false;
   if (live) {
-    pid = P.s.pid[e];
     two = pid.y >= 0;
-    rec_load(V + 4 * e, r0);
     if (two) rec_load(V + 4 * e1, r1);
     if (two && pid.y < pid.x) {
       const int t = pid.x;
@@ -1379,19 +1396,38 @@ __device__ __forceinline__ void mark_full(const MapParams& P, int e, bool fl) {
 
 // one instance per record format (REC_*), so that each carries only its own
 // path's registers
+template <int REC> struct RecTypes { using T = double; using S = double; };
+template <> struct RecTypes<REC_FP32> { using T = float; using S = float; };
+template <> struct RecTypes<REC_DF> { using T = double; using S = df; };
+
 template <int REC>
 __global__ void __launch_bounds__(256, 3) finish_kernel(MapParams P) {
+  using T = typename RecTypes<REC>::T;
+  using S = typename RecTypes<REC>::S;
   __shared__ double red[256];
   const int n = slot_count(P);
+  const S* V = static_cast<const S*>(P.s.V);
   double accB = 0.0;
-  // warp-uniform loop: every lane of a warp runs the same iterations
+  // warp-uniform loop: every lane of a warp runs the same iterations; the
+  // next round's particle pair and slot-0 record are loaded a round ahead
   const int stride = gridDim.x * blockDim.x;
+  const int efirst = blockIdx.x * blockDim.x + threadIdx.x;
+  int2 pid_n = make_int2(-1, -1);
+  T rec_n[4] = {T(0), T(0), T(0), T(0)};
+  if (efirst < n) {
+    pid_n = P.s.pid[efirst];
+    rec_load(V + 4 * (long long)efirst, rec_n);
+  }
   for (int e0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < n; e0 += stride) {
     const int e = e0 + (threadIdx.x & 31);
+    const int2 pid = pid_n;
+    const T r0[4] = {rec_n[0], rec_n[1], rec_n[2], rec_n[3]};
+    if (e + stride < n) {
+      pid_n = P.s.pid[e + stride];
+      rec_load(V + 4 * (long long)(e + stride), rec_n);
+    }
     bool fl = false;
-    if constexpr (REC == REC_FP32) accB += finish_entry<float, float>(P, e, n, &fl);
-    else if constexpr (REC == REC_DF) accB += finish_entry<double, df>(P, e, n, &fl);
-    else accB += finish_entry<double, double>(P, e, n, &fl);
+    accB += finish_entry<T, S>(P, e, n, pid, r0, &fl);
     if (REC == REC_FP64 && P.cov.full) mark_full(P, e, fl);
   }
   red[threadIdx.x] = accB;
