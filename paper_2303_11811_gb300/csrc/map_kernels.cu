@@ -31,9 +31,10 @@ constexpr double HALF_SQRT3 = kHalfSqrt3;
 constexpr int MAP_THREADS = 128;
 // threads of a fill block (one block per particle) and blocks per SM: a
 // block's phases wait on dependent global loads, so many small blocks keep
-// more of them in flight (settle512: 64 threads map 6-7% faster than 256)
+// more of them in flight (settle512: 64 threads map 6-7% faster than 256;
+// 10 blocks per SM, 102 registers, 3% faster than 12 blocks at 85)
 constexpr int FILL_THREADS = 64;
-constexpr int FILL_MIN_BLOCKS = 12;
+constexpr int FILL_MIN_BLOCKS = 10;
 constexpr int RED_THREADS = 128;
 constexpr int SCAN_THREADS = 1024;
 
@@ -721,18 +722,31 @@ __device__ __forceinline__ int group_count8(float dxf, float dyf, float dzf, flo
   return in;
 }
 
-// a cell of a particle's box (box index t): coordinates, FP64 offsets from
-// the centre and their FP32 roundings (from the per-block tables when the
-// box fits them), FP32 squared distance
-__device__ __forceinline__ void cell_hit(const Grid& g, const Box& b, int t, bool tables,
-                                         const double (*toff)[FILL_AXIS],
-                                         const float (*toff32)[FILL_AXIS], CellHit& h) {
-  box_coords(g, b, t, h);
+// offsets of a box cell whose coordinates are set: FP64 offsets from the
+// centre (cell_offsets64, or cell_offsets with fp64) and their FP32 roundings
+// (from the per-block tables when the box fits them), FP32 squared distance
+__device__ __forceinline__ void cell_offsets64(const Box& b, bool tables,
+                                               const double (*toff)[FILL_AXIS], CellHit& h) {
+  if (tables) {
+    h.dx = toff[0][h.kx - b.lo[0]];
+    h.dy = toff[1][h.ky - b.lo[1]];
+    h.dz = toff[2][h.kz - b.lo[2]];
+  } else {
+    h.dx = ((double)h.kx + 0.5) - b.xp[0];
+    h.dy = ((double)h.ky + 0.5) - b.xp[1];
+    h.dz = ((double)h.kz + 0.5) - b.xp[2];
+  }
+}
+__device__ __forceinline__ void cell_offsets(const Box& b, bool tables, bool fp64,
+                                             const double (*toff)[FILL_AXIS],
+                                             const float (*toff32)[FILL_AXIS], CellHit& h) {
   if (tables) {
     const int i0 = h.kx - b.lo[0], i1 = h.ky - b.lo[1], i2 = h.kz - b.lo[2];
-    h.dx = toff[0][i0];
-    h.dy = toff[1][i1];
-    h.dz = toff[2][i2];
+    if (fp64) {
+      h.dx = toff[0][i0];
+      h.dy = toff[1][i1];
+      h.dz = toff[2][i2];
+    }
     h.dxf = toff32[0][i0];
     h.dyf = toff32[1][i1];
     h.dzf = toff32[2][i2];
@@ -819,7 +833,8 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   const int cnt = P.list_cnt[p];
   // surrogate mode: the block's network cells, its worklist range and next free index
   __shared__ int net_cnt, net_base, net_next;
-  // 8^3 sampling: next free item of the particle's worklist
+  // 8^3 sampling (and, in surrogate mode, shared partial cells): next free
+  // item of the particle's 8^3 worklist
   __shared__ int wl_next;
   if constexpr (NS == 8) {
     if (threadIdx.x == 0) wl_next = 0;
@@ -830,6 +845,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     // worklist range, reserved with one atomic (a counter shared by every
     // block would serialise)
     if (threadIdx.x == 0) {
+      wl_next = 0;
       net_cnt = P.list_net[p];
       net_base = net_cnt ? atomicAdd(P.mlp_count, net_cnt) : 0;
       net_next = net_base;
@@ -844,42 +860,62 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
   // ahead and the coverage words (base, mask, shared mask) of the next
   // round's cell are loaded before this round's cell is filled
   const int kfirst = NS == 8 ? (threadIdx.x & ~31) + lane : threadIdx.x;
-  auto words_of = [&](int t, int& wbase, uint32_t& wmask, uint32_t& wdup) {
-    CellHit q;
-    box_coords(P.g, b, t, q);
-    const long long w = padded_cell(P.g, q.ix, q.iy, q.iz) >> 5;
+  // box index -> coordinates with the box's origin and divisors in registers
+  const int blo0 = b.lo[0], blo1 = b.lo[1], blo2 = b.lo[2];
+  const int bn0 = b.n[0], bn01 = b.n[0] * b.n[1];
+  const FastDiv bd0 = b.div_n0, bdxy = b.div_nxy;
+  // the FP32 records of the surrogate form need the FP64 offsets only for
+  // decisions inside the certified band and for wall cells
+  constexpr bool lazy64 = NS < 0 && REC == REC_FP32;
+  // the cell of box index t (coordinates in q) and its coverage words
+  auto words_of = [&](int t, CellHit& q, long long& c, int& wbase, uint32_t& wmask,
+                      uint32_t& wdup) {
+    const int kz = (int)bdxy.div((unsigned)t);
+    const int rem = t - kz * bn01;
+    const int ky = (int)bd0.div((unsigned)rem);
+    q.kx = blo0 + (rem - ky * bn0);
+    q.ky = blo1 + ky;
+    q.kz = blo2 + kz;
+    q.ix = wrap1(q.kx, P.g.nx);
+    q.iy = wrap1(q.ky, P.g.ny);
+    q.iz = wrap1(q.kz, P.g.nz);
+    c = padded_cell(P.g, q.ix, q.iy, q.iz);
+    const long long w = c >> 5;
     wbase = P.cov.base[w];
     wmask = P.cov.mask[w];
     wdup = P.cov.dup[w];
   };
   int tb_next = 0, tb_next2 = 0;  // list entries of the next two rounds
-  int nbase = 0;                  // coverage words of the next round's cell
+  CellHit hn;                      // the next round's cell: coordinates,
+  long long cell_next = 0;         // padded index
+  int nbase = 0;                   // and coverage words
   uint32_t nmask = 0u, ndup = 0u;
+  hn.kx = hn.ky = hn.kz = hn.ix = hn.iy = hn.iz = 0;
   if (kfirst < cnt) {
     tb_next = P.list[loff + kfirst];
-    words_of(tb_next, nbase, nmask, ndup);
+    words_of(tb_next, hn, cell_next, nbase, nmask, ndup);
   }
   if (kfirst + FILL_THREADS < cnt) tb_next2 = P.list[loff + kfirst + FILL_THREADS];
   for (int k0 = NS == 8 ? (threadIdx.x & ~31) : threadIdx.x; k0 < cnt; k0 += FILL_THREADS) {
     const int k = NS == 8 ? k0 + lane : k0;
     bool ok = NS == 8 ? k < cnt : true;
     const int tb = tb_next;  // box index of the cell (the list entry before the fill)
+    CellHit h = hn;
+    long long cell = cell_next;
     const int cbase = nbase;
     const uint32_t cmask = nmask, cdup = ndup;
     tb_next = tb_next2;
     tb_next2 = k + 2 * FILL_THREADS < cnt ? P.list[loff + k + 2 * FILL_THREADS] : 0;
-    if (k + FILL_THREADS < cnt) words_of(tb_next, nbase, nmask, ndup);
-    CellHit h;
+    if (k + FILL_THREADS < cnt) words_of(tb_next, hn, cell_next, nbase, nmask, ndup);
     if constexpr (NS == 8) {  // lanes past the list still take part in the ballot
       h.dx = h.dy = h.dz = 0.0;
       h.dxf = h.dyf = h.dzf = 0.f;
     }
-    long long cell = 0, e = 0;
+    long long e = 0;
     int s = 0;
     bool shared = false;  // a second particle in reach of the cell
     if (ok) {
-      cell_hit(P.g, b, tb, tables, toff, toff32, h);
-      cell = padded_cell(P.g, h.ix, h.iy, h.iz);
+      cell_offsets(b, tables, !lazy64, toff, toff32, h);
       const uint32_t bit = 1u << (cell & 31);
       e = (long long)cbase + __popc(cmask & (bit - 1u));
       shared = (cdup & bit) != 0u;
@@ -940,25 +976,30 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
     float Bf = 0.f;
     int cidx = -1;      // sampled count when B comes from the table
     bool want = false;  // surrogate mode: the cell goes to the network's worklist
+    bool pend8 = false;  // surrogate mode: a shared partial cell for the 8^3 count pass
     if constexpr (NS < 0) {
       // surrogate mode (reading I): inside by the margin -> 1; a partial
       // cell next to a wall face -> 8^3 sampling; any other partial cell ->
       // the network (B stays -1 until the inference writes it)
+      if (lazy64 && b.has_in && h.d2f >= b.rin2f - b.E && h.d2f <= b.rin2f + b.E)
+        cell_offsets64(b, tables, toff, h);  // the inside test's FP64 decision
       const int cls = net_class(P.g, b, h);
       if (cls == 1) {
         B = 1.0;
         Bf = 1.f;
       } else if (cls == 2) {
+        if (lazy64) cell_offsets64(b, tables, toff, h);
         const int c = supersample_count_n<8>(h.dx, h.dy, h.dz, b.r, h.dxf, h.dyf, h.dzf, b.r2f,
                                              b.E);
         B = weight((double)c * (1.0 / 512.0), P.tau, P.weighting);
         Bf = (float)B;
       } else {
-        // a cell shared with another particle stays pending (8^3 sampling
-        // in the finish pass)
+        // a cell shared with another particle stays pending: 8^3 sampling
+        // in the count pass (its worklist), else in the finish pass
         B = -1.0;
         Bf = -1.f;
         want = !shared;
+        pend8 = shared;
       }
     } else if (NS == 8 && pending) {
       B = -1.0;
@@ -1032,6 +1073,22 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       R[1] = make_double2(v2, B);
     }
     if constexpr (NS < 0) {
+      // shared partial cells: the particle's 8^3 worklist (FP32 offset and
+      // box index; 2 * entry + slot), counted by the count pass
+      if (P.wl_X) {
+        const unsigned grp8 = __activemask();
+        const unsigned pm = __ballot_sync(grp8, pend8);
+        if (pend8) {
+          const int lane = threadIdx.x & 31;
+          const int leader = __ffs(pm) - 1;
+          int first = 0;
+          if (lane == leader) first = atomicAdd(&wl_next, __popc(pm));
+          first = __shfl_sync(pm, first, leader);
+          const long long k2 = loff + first + __popc(pm & ((1u << lane) - 1u));
+          P.wl_X[k2] = make_float4(h.dxf, h.dyf, h.dzf, __int_as_float(tb));
+          P.wl_work[k2] = (int)(unsigned)(2 * e + s);
+        }
+      }
       // worklist append within the block's range, one shared-memory atomic
       // per group of converged lanes: the
       // network's inputs (|d/r| components in decreasing order, r), the
@@ -1061,7 +1118,7 @@ __global__ void __launch_bounds__(FILL_THREADS, FILL_MIN_BLOCKS) fill_kernel(Map
       }
     }
   }
-  if constexpr (NS == 8) {
+  if constexpr (NS == 8 || NS < 0) {
     __syncthreads();
     if (threadIdx.x == 0 && P.wl_cnt) P.wl_cnt[p] = wl_next;
   }
@@ -1500,6 +1557,41 @@ __device__ __forceinline__ double warp_sum6(const double (&v)[6], int lane, int&
   return u[0];
 }
 
+// A thread's walk over a particle's list entries k = threadIdx.x,
+// + RED_THREADS, ... with the list entries loaded two rounds ahead and the
+// next round's particle pair and cell one round ahead (the same entries in
+// the same order as a plain loop, so the sums are unchanged).
+struct ListWalk {
+  const MapParams& P;
+  long long loff;
+  int cnt;
+  int e1, e2;  // list entries of the next two rounds
+  int2 pid1;   // the next round's particle pair and padded cell
+  int cell1;
+  __device__ __forceinline__ ListWalk(const MapParams& P_, long long loff_, int cnt_)
+      : P(P_), loff(loff_), cnt(cnt_), e1(0), e2(0), pid1(make_int2(-1, -1)), cell1(0) {
+    const int k = threadIdx.x;
+    if (k < cnt) {
+      e1 = P.list[loff + k];
+      pid1 = P.s.pid[e1];
+      cell1 = P.s.cell[e1];
+    }
+    if (k + RED_THREADS < cnt) e2 = P.list[loff + k + RED_THREADS];
+  }
+  // entry k's slot entry, particle pair and cell; loads ahead for k + 1, k + 2 rounds
+  __device__ __forceinline__ void next(int k, int& e, int2& pid, int& cell) {
+    e = e1;
+    pid = pid1;
+    cell = cell1;
+    e1 = e2;
+    if (k + 2 * RED_THREADS < cnt) e2 = P.list[loff + k + 2 * RED_THREADS];
+    if (k + RED_THREADS < cnt) {
+      pid1 = P.s.pid[e1];
+      cell1 = P.s.cell[e1];
+    }
+  }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) {
   __shared__ double sh[6][RED_THREADS / 32];
@@ -1519,13 +1611,15 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_kernel(MapParams P) 
   const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
   // F, then sum over cells of (k - i_p) x F_c
   double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  ListWalk walk(P, loff, cnt);
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
-    const int e = P.list[loff + k];
-    const int2 pid = P.s.pid[e];
+    int e, cell;
+    int2 pid;
+    walk.next(k, e, pid, cell);
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
     int c3[3];
-    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    cell_xyz(P.g, cell, c3[0], c3[1], c3[2]);
     double kd[3];
     for (int a = 0; a < 3; ++a) {  // nearest image of the integer offset
       int k0 = c3[a] - sip[a];
@@ -1616,12 +1710,15 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams
   const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
   FloatPair acc[6];
   for (int i = 0; i < 6; ++i) acc[i] = FloatPair{0.f, 0.f};
+  ListWalk walk(P, loff, cnt);
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
-    const int e = P.list[loff + k];
+    int e, cell;
+    int2 pid;
+    walk.next(k, e, pid, cell);
     // torque arm: the cell centre's nearest-image offset, in FP32 from the
     // integer and fractional parts of the centre
     int c3[3];
-    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    cell_xyz(P.g, cell, c3[0], c3[1], c3[2]);
     float d3[3];
     for (int a = 0; a < 3; ++a) {
       int k0 = c3[a] - sip[a];
@@ -1632,7 +1729,6 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_f32_kernel(MapParams
       d3[a] = (float)k0 + (0.5f - sfp[a]);
     }
     const float4 d = make_float4(d3[0], d3[1], d3[2], 0.f);
-    const int2 pid = P.s.pid[e];
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
     const long long fo = 3 * (s * P.s.cap + e);
@@ -1699,13 +1795,15 @@ __global__ void __launch_bounds__(RED_THREADS) force_reduce_df_kernel(MapParams 
   const int dims[3] = {P.g.nx, P.g.ny, P.g.nz};
   df acc[6];
   for (int i = 0; i < 6; ++i) acc[i] = df(0.f, 0.f);
+  ListWalk walk(P, loff, cnt);
   for (int k = threadIdx.x; k < cnt; k += RED_THREADS) {
-    const int e = P.list[loff + k];
-    const int2 pid = P.s.pid[e];
+    int e, cell;
+    int2 pid;
+    walk.next(k, e, pid, cell);
     const int s = pid.x == p ? 0 : (pid.y == p ? 1 : -1);
     if (s < 0) continue;
     int c3[3];
-    cell_xyz(P.g, P.s.cell[e], c3[0], c3[1], c3[2]);
+    cell_xyz(P.g, cell, c3[0], c3[1], c3[2]);
     df d3[3];
     for (int a = 0; a < 3; ++a) {
       int k0 = c3[a] - sip[a];
@@ -1865,7 +1963,8 @@ int map_common(MapParams P, cudaStream_t s, bool mlp) {
     else if (rec == REC_DF) launch_fill<REC_DF>(P, mlp, s);
     else launch_fill<REC_FP64>(P, mlp, s);
     ++launches;
-    if (!mlp && P.eps_mode == 0 && P.eps_n == 8 && P.wtab && P.wl_X) {
+    // the count pass: 8^3 sampling's worklist, or the surrogate's shared cells
+    if ((mlp || P.eps_mode == 0) && P.eps_n == 8 && P.wtab && P.wl_X) {
       if (rec == REC_FP32) count8_kernel<REC_FP32><<<P.p.n, COUNT_THREADS, 0, s>>>(P);
       else if (rec == REC_DF) count8_kernel<REC_DF><<<P.p.n, COUNT_THREADS, 0, s>>>(P);
       else count8_kernel<REC_FP64><<<P.p.n, COUNT_THREADS, 0, s>>>(P);

@@ -236,6 +236,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 
 constexpr int INF_M = 128;         // rows per tile: the MMA's M
 constexpr int INF_THREADS = 128;   // thread t owns row t; warp w reads TMEM lanes 32w..32w+31
+constexpr int INF_PER_SM = 8;      // resident CTAs per SM: the grid is one wave of them
 constexpr unsigned INF_TMEM_COLS = 32;  // FP32 accumulator, N = 32 columns
 constexpr unsigned long long kInferWaitNs = 1000000000ull;
 // instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
@@ -372,7 +373,7 @@ __device__ __forceinline__ void apply_weight(const InferSink& o, long long rec, 
 // when the cell is within reach of this particle only (cells shared by two
 // particles keep B = -1 and are sampled by the finish pass).  count: number
 // of inputs, read from *count_dev when count < 0, at most cap.
-__global__ void __launch_bounds__(INF_THREADS) infer_tc_kernel(
+__global__ void __launch_bounds__(INF_THREADS, INF_PER_SM) infer_tc_kernel(
     const float* __restrict__ P, long long count, const int* __restrict__ count_dev,
     long long cap, const float4* __restrict__ X, InferSink o, unsigned* status) {
   __shared__ InferSmem S;
@@ -560,13 +561,33 @@ int launch_wait_selftest_mlp(unsigned* status, unsigned long long limit_ns, cuda
 
 // network outputs for m inputs (m_dev: count on the device, m < 0), at most
 // cap; results to the sink
+// resident inference CTAs on the device (all SMs), set by mlp_configure
+static int g_infer_ctas = 0;
+
+int mlp_configure() {
+  // INF_PER_SM CTAs per SM (the launch bounds keep their registers within
+  // the SM's file; 8 x 32 of the 512 tensor-memory columns) times the SMs
+  // shared memory for all of them (8 x 11 KB): the carveout's maximum
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0 ||
+      cudaFuncSetAttribute(infer_tc_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+    return 1;
+  g_infer_ctas = sms * INF_PER_SM;
+  return 0;
+}
+
 int launch_mlp_infer(const float* params, long long m, const int* m_dev, long long cap,
                      const float* X, const InferSink& out, unsigned* status, cudaStream_t s) {
   const long long rows = m >= 0 ? (m < cap ? m : cap) : cap;
   if (rows <= 0) return 0;
-  // up to 12 resident CTAs per SM (12 x 32 of the 512 tensor-memory columns)
+  // one wave of CTAs, each looping over tiles (a second, partial wave would
+  // leave SMs idle)
   long long blocks = (rows + INF_M - 1) / INF_M;
-  if (blocks > 152 * 12) blocks = 152 * 12;
+  const long long wave = g_infer_ctas > 0 ? g_infer_ctas : 152 * INF_PER_SM;
+  if (blocks > wave) blocks = wave;
   infer_tc_kernel<<<(unsigned)blocks, INF_THREADS, 0, s>>>(
       params, m, m_dev, cap, reinterpret_cast<const float4*>(X), out, status);
   return 1;

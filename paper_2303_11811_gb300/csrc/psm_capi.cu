@@ -599,6 +599,10 @@ psm_status psm_create(const psm_grid* grid, double tau, psm_relax relax, const p
     cudaGetLastError();
     return bail(PSM_ERR_CUDA, "could not set the shared-memory size of the collision kernel");
   }
+  if (mlp_configure() != 0) {
+    cudaGetLastError();
+    return bail(PSM_ERR_CUDA, "occupancy query of the inference kernel failed");
+  }
   c->dem_blocks = dem_max_blocks();
   if (c->dem_blocks <= 0) {
     cudaGetLastError();
@@ -745,7 +749,10 @@ psm_status psm_set_particles(psm_ctx* c, int n, const double* x, const double* r
   c->dem_items = alloc_n<int>(c, 3 * n1, c->palloc);
   c->dem_nbr = alloc_n<int>(c, n1 * kDemListCap, c->palloc);
   c->dem_xbuild = alloc_n<float4>(c, n1, c->palloc);
-  if (c->opt.eps_mode == PSM_EPS_SUPERSAMPLE && c->opt.eps_n == 8) {
+  // the 8^3 count pass's worklist: 8^3 sampling, and the surrogate's shared
+  // cells (its fallback samples 8^3 points)
+  if ((c->opt.eps_mode == PSM_EPS_SUPERSAMPLE || c->opt.eps_mode == PSM_EPS_MLP) &&
+      c->opt.eps_n == 8) {
     c->wl_X = alloc_n<float4>(c, (size_t)list_total, c->palloc);
     c->wl_work = alloc_n<int>(c, (size_t)list_total, c->palloc);
     c->wl_cnt = alloc_n<int>(c, n1, c->palloc);

@@ -343,5 +343,6 @@ struct InferSink {
 int launch_mlp_infer(const float* params, long long m, const int* m_dev, long long cap,
                      const float* X, const InferSink& out, unsigned* status, cudaStream_t s);
 int mlp_grad_blocks(long long m);
+int mlp_configure();  // inference grid from the device's occupancy; call once (returns != 0 on error)
 
 }  // namespace psm

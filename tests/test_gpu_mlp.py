@@ -123,12 +123,15 @@ def _bf16_forward_bound(ref, X):
     return bf16 + (2.0 ** -18) * path + 1e-6
 
 
-def test_mlp_mode_mapping_matches_oracle(eng):
+@pytest.mark.parametrize("eps_n", [4, 8])
+def test_mlp_mode_mapping_matches_oracle(eng, eps_n):
     """Mapping in surrogate mode: the same cells are partial, single-particle
     and wall-free on both sides; every network cell agrees within the BF16
     bound derived for its own inputs, every other cell (8^3 fallback, inside
     cells) exactly.  The network's output varies by O(0.1-1) over the cells,
-    so a swapped input, a wrong radius scaling or a dropped bias shows."""
+    so a swapped input, a wrong radius scaling or a dropped bias shows.  With
+    eps_n = 8 the cells shared by two particles go to the 8^3 count pass,
+    otherwise the finish pass samples them."""
     _, capi = eng
     net = inputs.mlp_init(4)
     net[4] = net[4] * 60.0   # W3 at 0.6 of its He bound: outputs of order 0.1-1
@@ -137,7 +140,7 @@ def test_mlp_mode_mapping_matches_oracle(eng):
     ref = capi.unpack_mlp(params)
     shape = (40, 32, 36)
     kw = dict(tau=0.6, relax="trt", walls=(1, 1, 0, 0, 0, 0), weighting="eps",
-              eps_mode="mlp")
+              eps_mode="mlp", eps_n=eps_n)
     g = capi.Engine(*shape, **kw)
     o = Oracle(*shape, **kw)
     x = np.array([[6.5, 10.2, 12.3], [14.0, 10.6, 12.0], [30.3, 20.2, 30.9]])
