@@ -176,6 +176,32 @@ def test_mapping_slots_large_spheres(capi, eps_mode, eps_n):
     e.close()
 
 
+@pytest.mark.parametrize("eps_mode,eps_n", [("supersample", 4), ("linear", 4)])
+def test_mapping_slots_very_large_sphere(capi, eps_mode, eps_n):
+    """A sphere whose box has more than 1,024 rows (radius 16.5: the mark
+    pass tests every cell of the box), wrapping around two periodic faces and
+    sharing cells with a small sphere: the same slots and weights as the
+    oracle."""
+    shape = (80, 76, 80)
+    e, o = pair(capi, shape, tau=0.6, relax="srt", weighting="nt", eps_mode=eps_mode,
+                eps_n=eps_n)
+    x = np.array([[3.4, 70.2, 36.3], [3.4 + 22.0, 70.5, 36.0]])
+    r = np.array([16.5, 5.1])
+    for s_ in (e, o):
+        s_.set_particles(x, r)
+    assert o.map() == 0
+    pg0, bg0, pg1, bg1 = e.slots()
+    po0, bo0, po1, bo1 = o.slots()
+    Bsum = bo0 + bo1
+    over = Bsum > 1.0
+    bo0 = np.where(over, bo0 / np.where(over, Bsum, 1.0), bo0)
+    bo1 = np.where(over, bo1 / np.where(over, Bsum, 1.0), bo1)
+    assert np.array_equal(pg0, po0) and np.array_equal(pg1, po1)
+    assert np.max(np.abs(bg0 - bo0)) < 1e-15 and np.max(np.abs(bg1 - bo1)) < 1e-15
+    assert (pg1 >= 0).sum() > 0
+    e.close()
+
+
 def test_aa_equals_pull_bitwise_fp64(capi):
     """The AA pattern changes where PDFs live, not what is computed: FP64 AA
     and pull give identical bits after an odd and an even number of steps."""
