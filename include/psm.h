@@ -109,7 +109,10 @@ typedef struct {
   int precision;         /* PSM_FP64 | PSM_FP32_DEV | PSM_FP64_DF */
   int streaming;         /* PSM_PULL | PSM_AA */
   int eps_mode;          /* PSM_EPS_* */
-  int eps_n;             /* samples per axis for PSM_EPS_SUPERSAMPLE (1..16) */
+  int eps_n;             /* samples per axis for PSM_EPS_SUPERSAMPLE (1..16); with
+                            PSM_EPS_MLP the fallback always samples 8^3 points,
+                            and eps_n = 8 lets the batched 8^3 count pass take
+                            the shared cells (same results, faster) */
   int weighting;         /* PSM_W_EPS | PSM_W_NT */
   double body_force[3];  /* fluid body-force density f_ext */
   double gravity[3];     /* acceleration of free particles; a free particle
